@@ -1,0 +1,166 @@
+/*
+ * digs.h -- C-ABI of the GB300 (sm_103a) DIGS hot path.
+ *
+ * DIGS (arXiv 2506.22280) reconstructs dynamic cone-beam CT as a cloud of 3D Gaussians warped by a
+ * low-rank cubic B-spline free-form deformation (FFD).  For every projection the hot path evaluates the
+ * FFD and its Jacobian at each Gaussian mean (Sec. 3.3, Eq. 9-11), moves the mean and transforms the
+ * covariance Sigma' = K Sigma K^T (Sec. 3.2, Eq. 7-8), integrates every deformed Gaussian along every
+ * detector ray in closed form (the X-ray transform of Sec. 3.1, Eq. 1-4), and runs the backward pass of
+ * a projection-domain L2 loss (Sec. 4.2).
+ *
+ * Conventions shared by every entry point:
+ *  - All array pointers are DEVICE pointers to contiguous FP32 (or int32) memory owned by the caller,
+ *    unless a comment says "host".  The library allocates no memory: scratch space is a caller-owned
+ *    workspace of digs_workspace_size() bytes.
+ *  - Calls are enqueued on `stream` (a cudaStream_t; NULL = legacy default stream) and return without
+ *    synchronising, except digs_count_pairs() and digs_sync_status(), which say so.
+ *  - Host-detected errors (bad arguments, launch failures) are returned at once.  Device-detected errors
+ *    (workspace too small for the number of (ray-tile, Gaussian) pairs) are recorded in a status word
+ *    inside the workspace; digs_sync_status() reports and clears it.
+ *  - Gradient outputs are overwritten, never accumulated into.
+ *
+ * Layouts (N Gaussians, P projections, R <= DIGS_MAX_R ranks):
+ *  mu0[N][3] mm, scale[N][3] mm (> 0), quat[N][4] as (w, x, y, z) (normalised inside), rho[N] mm^-1:
+ *      the reference Gaussians, Sigma = R(q) diag(scale)^2 R(q)^T (Sec. 3.1, after Eq. 2).
+ *  phi[R][nz][ny][nx][3] mm: control-point displacements d^r_ijk (Sec. 3.3, Eq. 10); node (i, j, k)
+ *      sits at origin + (i, j, k) * spacing, i (x) fastest.  Nodes outside the lattice read as zero.
+ *  w[P][R]: temporal weights omega_r(t) at each projection's time point (Eq. 9).
+ *  proj[P][nv][nu]: line integrals, pixel (i, j) at proj[p][j][i].
+ */
+#ifndef DIGS_H
+#define DIGS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DIGS_MAX_R 4        /* ranks N_r of the low-rank motion model (the paper uses 2)            */
+#define DIGS_MAX_VIEWS 128  /* projections per call                                                 */
+
+typedef enum {
+  DIGS_OK = 0,
+  DIGS_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, non-finite geometry, ...)    */
+  DIGS_ERR_CUDA = 2,       /* a CUDA launch or runtime call failed                                   */
+  DIGS_ERR_CAPACITY = 3,   /* more (tile, Gaussian) pairs than the workspace holds: grow and retry   */
+  DIGS_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up                                     */
+  DIGS_ERR_NONFINITE = 5   /* a non-finite value was found where finite input was required           */
+} digs_status;
+
+/* Reference Gaussians {rho_n, mu_n, R_n, S_n} (Sec. 3.1, Eq. 2).  n may be 0. */
+typedef struct {
+  int n;
+  const float* mu0;    /* [n][3] */
+  const float* scale;  /* [n][3] */
+  const float* quat;   /* [n][4] (w, x, y, z) */
+  const float* rho;    /* [n]    */
+} DigsGaussians;
+
+/* Uniform control lattice of the FFD spatial basis (Sec. 3.3, text before Eq. 10). */
+typedef struct {
+  int nx, ny, nz, R;
+  float origin[3];   /* world position of node (0, 0, 0), mm */
+  float spacing[3];  /* node spacing per axis, mm (> 0)      */
+} DigsLattice;
+
+/* One projection's scan geometry (host memory, double precision).  The detector axes e_u, e_v must be
+ * orthonormal.  Pixel (i, j) has centre det_c + (i - (nu-1)/2 + off_u) du e_u + (j - (nv-1)/2 + off_v) dv e_v.
+ * Cone beam (parallel = 0): rays run from src through each pixel centre.  Parallel beam: rays run
+ * through each pixel centre along the unit vector from src to det_c. */
+typedef struct {
+  double src[3], det_c[3], e_u[3], e_v[3];
+  double du, dv, off_u, off_v;
+  int nu, nv, parallel;
+} DigsView;
+
+/* Options.  cutoff: a (ray, Gaussian) pair contributes iff the squared Mahalanobis distance E from the
+ * ray to the deformed mean is <= cutoff^2 (default 3.5).  tile: square raster tile edge in pixels (8, 16
+ * or 32; 0 = 16).  flags: DIGS_FLAG_* bits. */
+typedef struct {
+  float cutoff;
+  int tile;
+  int flags;
+} DigsOpts;
+
+#define DIGS_FLAG_REUSE_BINNING 1  /* project_bwd: reuse records and tile lists left in `ws` by the
+                                      immediately preceding project_fwd with identical inputs          */
+
+/* Bytes of workspace for n Gaussians, P projections of nu x nv pixels, R ranks and room for
+ * `max_pairs` (tile, Gaussian) pairs.  Use digs_count_pairs() to learn the pair count of an input. */
+size_t digs_workspace_size(int n, int P, int nu, int nv, int R, long long max_pairs, const DigsOpts* opts);
+
+/* u_r(x) and its world-space gradient at each point (Sec. 3.3, Eq. 10 and the gradient inside Eq. 11).
+ * x[n][3] in; U[n][R][3] and dU[n][R][3][3] out, dU[.][r][i][j] = d u_{r,i} / d x_j.
+ * One thread per point; needs no workspace. */
+digs_status digs_ffd_eval(const DigsLattice* lat, const float* phi, const float* x, int n,
+                          float* U, float* dU, void* stream);
+
+/* Number of (tile, Gaussian) pairs the binning of these inputs produces, written to *count_host.
+ * SYNCHRONISES the stream.  `ws` may be sized with max_pairs = 0. */
+digs_status digs_count_pairs(const DigsGaussians* g, const DigsLattice* lat, const float* phi, const float* w,
+                             const DigsView* views, int P, const DigsOpts* opts, void* ws, size_t ws_bytes,
+                             long long* count_host, void* stream);
+
+/* Forward projection: deform the Gaussians at each projection's weights (Eq. 7-11) and integrate them
+ * along every detector ray (Eq. 1, 3, 4), writing proj[P][nv][nu].  All views in one call must share
+ * nu and nv.  views: host array [P]. */
+digs_status digs_project_fwd(const DigsGaussians* g, const DigsLattice* lat, const float* phi, const float* w,
+                             const DigsView* views, int P, const DigsOpts* opts, float* proj,
+                             void* ws, size_t ws_bytes, void* stream);
+
+/* Backward projection: given grad_proj = dL/dproj [P][nv][nu], write dL/d of every input:
+ * g_mu0[n][3], g_scale[n][3], g_quat[n][4], g_rho[n], g_phi[R][nz][ny][nx][3], g_w[P][R].
+ * The truncated sum is differentiated almost everywhere (the cutoff's boundary term is ignored). */
+digs_status digs_project_bwd(const DigsGaussians* g, const DigsLattice* lat, const float* phi, const float* w,
+                             const DigsView* views, int P, const DigsOpts* opts, const float* grad_proj,
+                             float* g_mu0, float* g_scale, float* g_quat, float* g_rho, float* g_phi, float* g_w,
+                             void* ws, size_t ws_bytes, void* stream);
+
+/* Adam hyper-parameters of one reconstruction (Sec. 4.2: Adam, learning rates decaying linearly from
+ * lr0 to lr1 over total_iters).  Groups: means (mm), log-scales, quaternions, density pre-activation
+ * (rho = softplus(theta)), the spatial B-spline grid phi and the temporal weights w. */
+typedef struct {
+  float lr0[6], lr1[6];   /* per group: mu0, log-scale, quat, density, phi, w */
+  float beta1, beta2, eps;
+  int total_iters;
+} DigsAdamConfig;
+
+/* Reconstruction state in caller-owned device memory.  Parameters are updated in place.  m and v are
+ * Adam moments laid out like the parameters, concatenated in group order
+ * (mu0 3n, log-scale 3n, quat 4n, density n, phi R*nz*ny*nx*3, w n_w*R), zero before the first step. */
+typedef struct {
+  int n;
+  float *mu0, *scale, *quat, *rho;  /* physical parameters (scale > 0, rho > 0)     */
+  float *phi;                        /* [R][nz][ny][nx][3]                           */
+  float *w;                          /* [n_w][R]: weights of every time point of the scan */
+  int n_w;
+  float *m, *v;                      /* Adam moments                                 */
+  float *grad;                       /* gradient scratch, laid out like m            */
+  int iter;                          /* completed steps; digs_step increments it     */
+  DigsLattice lat;
+  DigsAdamConfig adam;
+} DigsState;
+
+/* Number of floats in DigsState.m (and v, grad). */
+size_t digs_state_moments(int n, const DigsLattice* lat, int n_w);
+
+/* One optimisation step over a batch of B projections (Eq. 1 with the L2 loss of Sec. 4.2):
+ * render the projections `proj_ids` (host int array [B], rows of st->w) with geometry views[B] (host),
+ * loss = mean over the batch's pixels of (I - meas)^2 written to loss_out (device float), gradients of
+ * every parameter, then one fused Adam update of all groups with the learning rates of iteration st->iter.
+ * meas: [B][nv][nu].  The workspace must be sized for n Gaussians and B projections. */
+digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, const DigsView* views, int B,
+                      const DigsOpts* opts, float* loss_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Synchronise `stream`, return the device-detected status recorded in `ws` since the last call, and
+ * clear it. */
+digs_status digs_sync_status(void* ws, void* stream);
+
+/* Static description of a status code. */
+const char* digs_status_string(digs_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIGS_H */

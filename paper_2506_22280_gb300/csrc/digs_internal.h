@@ -1,0 +1,89 @@
+// Host-side launchers shared between the translation units of libdigs (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "digs_common.cuh"
+
+namespace digs {
+
+// Workspace carve-up for one call.  Every pointer is 256-byte aligned inside the caller's buffer.
+struct Workspace {
+  int* status;            // [4]  device-detected status
+  uint32_t* n_pairs;      // [2]  number of (tile, Gaussian) pairs produced, pairs kept (<= cap)
+  float4* rec;            // [P * n * 3]
+  uint32_t* counts;       // [P * n + 1] tiles touched per (projection, Gaussian)
+  uint32_t* offsets;      // [P * n + 1] exclusive scan of counts (offsets[P*n] = total)
+  uint32_t* scan_tmp;     // block sums of the scans
+  uint32_t* keys;         // [cap] (projection, tile) key per pair
+  uint32_t* vals;         // [cap] slot of the pair (its position before sorting)
+  uint32_t* keys_alt;     // [cap]
+  uint32_t* vals_alt;     // [cap]
+  uint32_t* rid;          // [cap] (projection, Gaussian) record of each slot
+  uint32_t* hist;         // radix histograms [256][sort blocks]
+  uint2* ranges;          // [P * T] sorted-range of each (projection, tile)
+  float4* partials;       // [cap * 3] backward partial sums per slot
+  float* gw_part;         // [gauss blocks][P * R]
+  float* loss_part;       // [P * T]
+  float* proj;            // [P * nv * nu] (digs_step)
+  float* dldi;            // [P * nv * nu] (digs_step)
+  float* grads;           // all parameter gradients (digs_step)
+  size_t bytes;
+  long long cap;
+  int n, P, nu, nv, R, tile, tiles_x, tiles_y, T;
+  int n_sort_blocks, n_gauss_blocks;
+};
+
+size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, long long cap, int tile, size_t grad_floats);
+
+// scan.cu
+cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int n, uint32_t* tmp, cudaStream_t st);
+size_t scan_tmp_words(int n);
+
+// sort.cu: LSD radix sort of (key, value) pairs on the low `bits` bits; count read from the device.
+// Returns via *out_keys / *out_vals which of the two buffers holds the result.
+cudaError_t radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, const uint32_t* n_dev,
+                       long long cap, int bits, uint32_t* hist, uint32_t* scan_tmp, int n_sort_blocks,
+                       uint32_t** out_keys, uint32_t** out_vals, cudaStream_t st);
+cudaError_t tile_ranges(const uint32_t* sorted_keys, const uint32_t* n_dev, long long cap, uint2* ranges, int n_ranges,
+                        cudaStream_t st);
+int sort_blocks(long long cap);
+
+// prep.cu
+cudaError_t launch_ffd_eval(const LatticeC& L, const float* phi, const float* x, int n, float* U, float* dU,
+                            cudaStream_t st);
+cudaError_t launch_prep_fwd(const GaussPtrs& g, const LatticeC& L, const float* phi, const float* w,
+                            const ViewsParam& views, int P, float c2, const Workspace& ws, cudaStream_t st);
+cudaError_t launch_emit(const Workspace& ws, cudaStream_t st);
+
+// raster.cu
+cudaError_t launch_raster_fwd(const Workspace& ws, const uint32_t* sorted_vals, const ViewsParam& views, float c2,
+                              float* proj, const float* meas, float* dldi, float inv_count, cudaStream_t st);
+cudaError_t launch_raster_bwd(const Workspace& ws, const uint32_t* sorted_vals, const ViewsParam& views, float c2,
+                              const float* grad_proj, cudaStream_t st);
+cudaError_t launch_loss_reduce(const float* part, int n, float* out, float scale, cudaStream_t st);
+
+// chain.cu
+cudaError_t launch_chain_bwd(const GaussPtrs& g, const LatticeC& L, const float* phi, const float* w,
+                             const ViewsParam& views, int P, float c2, const Workspace& ws, float* g_mu0,
+                             float* g_scale, float* g_quat, float* g_rho, float* g_phi, cudaStream_t st);
+cudaError_t launch_gw_reduce(const Workspace& ws, const ViewsParam& views, int P, int R, float* g_w, int w_rows,
+                             cudaStream_t st);
+int chain_blocks(int n);
+
+// adam.cu
+struct AdamGroup {
+  float* p;
+  const float* g;
+  float* m;
+  float* v;
+  long long n;
+  long long off;   // offset of this group inside m / v
+  int kind;        // 0 plain, 1 log-parameterised (scale), 2 softplus-parameterised (density)
+  float lr;
+};
+cudaError_t launch_adam(const AdamGroup* groups, int ngroups, float beta1, float beta2, float eps, int step,
+                        cudaStream_t st);
+
+}  // namespace digs

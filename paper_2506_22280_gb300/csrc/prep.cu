@@ -1,0 +1,171 @@
+// Per-Gaussian forward preparation: FFD evaluation (Sec. 3.3, Eq. 10-11), deformation-informed warp of
+// mean and covariance for every projection of the call (Sec. 3.2, Eq. 7-8), projection records with
+// their pixel boxes, and emission of one (projection, tile) key per tile a box touches.
+#include "digs_internal.h"
+#include "ffd.cuh"
+#include "setup.cuh"
+
+namespace digs {
+
+template <int R>
+__global__ void __launch_bounds__(128) k_ffd_eval(LatticeC L, const float* __restrict__ phi,
+                                                  const float* __restrict__ x, int n, float* __restrict__ U,
+                                                  float* __restrict__ dU) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float p[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  float u[R][3], du[R][9];
+  ffd_eval_point<R>(phi, L, p, u, du);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) U[((size_t)i * R + r) * 3 + c] = u[r][c];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) dU[((size_t)i * R + r) * 9 + c] = du[r][c];
+  }
+}
+
+cudaError_t launch_ffd_eval(const LatticeC& L, const float* phi, const float* x, int n, float* U, float* dU,
+                            cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid((n + 127) / 128);
+  switch (L.R) {
+    case 1: k_ffd_eval<1><<<grid, 128, 0, st>>>(L, phi, x, n, U, dU); break;
+    case 2: k_ffd_eval<2><<<grid, 128, 0, st>>>(L, phi, x, n, U, dU); break;
+    case 3: k_ffd_eval<3><<<grid, 128, 0, st>>>(L, phi, x, n, U, dU); break;
+    case 4: k_ffd_eval<4><<<grid, 128, 0, st>>>(L, phi, x, n, U, dU); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Reference Gaussian in registers: normalised quaternion, rotation, inverse scales.
+struct GaussLocal {
+  float mu0[3], s[3], inv_s[3], qh[4], qnorm, R[9], rho;
+};
+
+__device__ __forceinline__ void load_gauss(const GaussPtrs& g, int n, GaussLocal& o) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    o.mu0[c] = g.mu0[3 * n + c];
+    o.s[c] = g.scale[3 * n + c];
+    o.inv_s[c] = 1.f / o.s[c];
+  }
+  float q[4] = {g.quat[4 * n], g.quat[4 * n + 1], g.quat[4 * n + 2], g.quat[4 * n + 3]};
+  o.qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  float iq = 1.f / o.qnorm;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) o.qh[c] = q[c] * iq;
+  quat_to_R(o.qh, o.R);
+  o.rho = g.rho[n];
+}
+
+// One thread per Gaussian; loops over the call's projections so the FFD is evaluated once.
+template <int R>
+__global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, LatticeC L, const float* __restrict__ phi,
+                                                  const float* __restrict__ w, const __grid_constant__ ViewsParam views,
+                                                  int P, float c2, int tile, int tiles_x, float4* __restrict__ rec,
+                                                  uint32_t* __restrict__ counts, int* status) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.n) return;
+  GaussLocal G;
+  load_gauss(g, n, G);
+  float U[R][3], dU[R][9];
+  ffd_eval_point<R>(phi, L, G.mu0, U, dU);
+  bool finite_in = isfinite(G.mu0[0] + G.mu0[1] + G.mu0[2] + G.s[0] + G.s[1] + G.s[2] + G.qnorm + G.rho);
+  if (!finite_in) set_status(status, DIGS_ERR_NONFINITE);
+  for (int b = 0; b < P; ++b) {
+    const ViewC& v = views.v[b];
+    const float* wb = w + (size_t)v.w_row * R;
+    float mu[3], K[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) mu[c] = G.mu0[c];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) K[c] = (c % 4 == 0) ? 1.f : 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float wr = __ldg(wb + r);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) mu[c] = fmaf(wr, U[r][c], mu[c]);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) K[c] = fmaf(wr, dU[r][c], K[c]);
+    }
+    float Ki[9], A[9];
+    float detK = inv3(K, Ki);
+    Rec r;
+    uint32_t cnt = 0;
+    bool alive = finite_in && detK > DIGS_FOLD_EPS;
+    if (alive) {
+      make_A(G.inv_s, G.R, Ki, A);
+      alive = setup_record(v, mu, A, G.rho, c2, r);
+    }
+    if (alive) {
+      int x0 = r.bx & 0xffff, x1 = r.bx >> 16, y0 = r.by & 0xffff, y1 = r.by >> 16;
+      cnt = (uint32_t)((x1 / tile - x0 / tile + 1) * (y1 / tile - y0 / tile + 1));
+    } else {
+      r = Rec{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0};
+    }
+    size_t idx = (size_t)b * g.n + n;
+    store_rec(rec + idx * DIGS_REC_F4, r);
+    counts[idx] = cnt;
+  }
+}
+
+cudaError_t launch_prep_fwd(const GaussPtrs& g, const LatticeC& L, const float* phi, const float* w,
+                            const ViewsParam& views, int P, float c2, const Workspace& ws, cudaStream_t st) {
+  if (g.n <= 0 || P <= 0) return cudaSuccess;
+  dim3 grid((g.n + 127) / 128);
+#define DIGS_PREP(RR)                                                                                      \
+  k_prep_fwd<RR><<<grid, 128, 0, st>>>(g, L, phi, w, views, P, c2, ws.tile, ws.tiles_x, ws.rec, ws.counts, \
+                                       ws.status)
+  switch (L.R) {
+    case 1: DIGS_PREP(1); break;
+    case 2: DIGS_PREP(2); break;
+    case 3: DIGS_PREP(3); break;
+    case 4: DIGS_PREP(4); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef DIGS_PREP
+  return cudaGetLastError();
+}
+
+// One thread per (projection, Gaussian): write key = b * T + tile and slot index for each tile of its
+// box, at the slots [offsets[i], offsets[i + 1]) reserved by the scan.  Pairs beyond the capacity are
+// dropped and flagged.
+__global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ rec, const uint32_t* __restrict__ offsets,
+                                              int PN, int n, int tile, int tiles_x, int T, uint32_t* __restrict__ keys,
+                                              uint32_t* __restrict__ vals, uint32_t* __restrict__ rid, long long cap,
+                                              uint32_t* n_pairs, int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    uint32_t total = offsets[PN];
+    n_pairs[0] = total;
+    n_pairs[1] = (long long)total > cap ? (uint32_t)cap : total;
+    if ((long long)total > cap) set_status(status, DIGS_ERR_CAPACITY);
+  }
+  if (i >= PN) return;
+  uint32_t off = offsets[i], end = offsets[i + 1];
+  if (off == end) return;
+  float4 c = rec[(size_t)i * DIGS_REC_F4 + 2];
+  int bx = __float_as_int(c.y), by = __float_as_int(c.z);
+  int tx0 = (bx & 0xffff) / tile, tx1 = (bx >> 16) / tile, ty0 = (by & 0xffff) / tile, ty1 = (by >> 16) / tile;
+  uint32_t base = (uint32_t)(i / n) * (uint32_t)T;
+  uint32_t k = off;
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx, ++k) {
+      if ((long long)k >= cap) return;
+      keys[k] = base + (uint32_t)(ty * tiles_x + tx);
+      vals[k] = k;
+      rid[k] = (uint32_t)i;
+    }
+}
+
+cudaError_t launch_emit(const Workspace& ws, cudaStream_t st) {
+  int PN = ws.P * ws.n;
+  dim3 grid((PN + 255) / 256 > 0 ? (PN + 255) / 256 : 1);
+  k_emit<<<grid, 256, 0, st>>>(ws.rec, ws.offsets, PN, ws.n, ws.tile, ws.tiles_x, ws.T, ws.keys, ws.vals, ws.rid,
+                               ws.cap, ws.n_pairs, ws.status);
+  return cudaGetLastError();
+}
+
+}  // namespace digs

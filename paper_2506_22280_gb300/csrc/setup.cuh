@@ -1,0 +1,243 @@
+// Per-(projection, Gaussian) set-up: rotation, deformation-informed warp (Sec. 3.2, Eq. 7-8) and the
+// closed-form description of the Gaussian's ray integrals on the detector (Sec. 3.1, Eq. 4), plus the
+// hand-written adjoint of all of it.
+//
+// Formulation.  Write the deformed precision as P' = A^T A with A = S^-1 R^T K^-1 (so P' = (K R S^2 R^T
+// K^T)^-1 = Sigma'^-1 exactly, without inverting Sigma').  For a cone-beam ray from the source s through
+// the detector point X_c + [e_u du, e_v dv] Delta (X_c: the detector image of the mean mu', Delta in
+// pixels), with d0 = mu' - s, lambda = |X_c - s| / |d0|, alpha = A d0, Lm = |alpha|, Y = A [e_u du, e_v dv]
+// / lambda, y_a = Y^T alpha / Lm and Z = (I - alpha alpha^T / Lm^2) Y, the squared Mahalanobis distance
+// from the ray to mu' is E = |Z Delta|^2 / D with D = (1 - w . Delta)^2 + |Z Delta|^2 / Lm^2, w = -y_a / Lm,
+// and the whole-line integral is rho sqrt(2 pi) / (lambda Lm) * |X - s| * D^-1/2 * exp(-E / 2).
+// Neither expression subtracts two quantities of the source-distance scale, which keeps FP32 accurate;
+// for parallel rays along u the same holds with alpha = A u, lambda = 1, D = 1 and no |X - s| factor.
+#pragma once
+
+#include "digs_common.cuh"
+
+// Rotation matrix (row-major) of the unit quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_to_R(const float q[4], float R[9]) {
+  float w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// dL/dq for dL/dR = gR, through R(q_hat) and q_hat = q / |q|.
+__device__ __forceinline__ void quat_bwd(const float qh[4], float qnorm, const float g[9], float gq[4]) {
+  float w = qh[0], x = qh[1], y = qh[2], z = qh[3];
+  float gw = 2.f * (-z * g[1] + y * g[2] + z * g[3] - x * g[5] - y * g[6] + x * g[7]);
+  float gx = 2.f * (y * g[1] + z * g[2] + y * g[3] - 2.f * x * g[4] - w * g[5] + z * g[6] + w * g[7] - 2.f * x * g[8]);
+  float gy = 2.f * (-2.f * y * g[0] + x * g[1] + w * g[2] + x * g[3] + z * g[5] - w * g[6] + z * g[7] - 2.f * y * g[8]);
+  float gz = 2.f * (-2.f * z * g[0] - w * g[1] + x * g[2] + w * g[3] - 2.f * z * g[4] + y * g[5] + x * g[6] + y * g[7]);
+  float dot = w * gw + x * gx + y * gy + z * gz;
+  float inv = 1.f / qnorm;
+  gq[0] = (gw - w * dot) * inv;
+  gq[1] = (gx - x * dot) * inv;
+  gq[2] = (gy - y * dot) * inv;
+  gq[3] = (gz - z * dot) * inv;
+}
+
+// Inverse (row-major) by the adjugate; returns det K.
+__device__ __forceinline__ float inv3(const float K[9], float Ki[9]) {
+  float c0 = K[4] * K[8] - K[5] * K[7];
+  float c1 = K[5] * K[6] - K[3] * K[8];
+  float c2 = K[3] * K[7] - K[4] * K[6];
+  float det = K[0] * c0 + K[1] * c1 + K[2] * c2;
+  float id = 1.f / det;
+  Ki[0] = c0 * id; Ki[1] = (K[2] * K[7] - K[1] * K[8]) * id; Ki[2] = (K[1] * K[5] - K[2] * K[4]) * id;
+  Ki[3] = c1 * id; Ki[4] = (K[0] * K[8] - K[2] * K[6]) * id; Ki[5] = (K[2] * K[3] - K[0] * K[5]) * id;
+  Ki[6] = c2 * id; Ki[7] = (K[1] * K[6] - K[0] * K[7]) * id; Ki[8] = (K[0] * K[4] - K[1] * K[3]) * id;
+  return det;
+}
+
+// A = S^-1 R^T K^-1.
+__device__ __forceinline__ void make_A(const float inv_s[3], const float R[9], const float Ki[9], float A[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      A[3 * i + j] = inv_s[i] * (R[i] * Ki[j] + R[3 + i] * Ki[3 + j] + R[6 + i] * Ki[6 + j]);
+}
+
+// Forward intermediates shared by the set-up and its adjoint.
+struct SetupState {
+  float mu_d[3], d0[3];
+  float Ad[9];           // A expressed in the detector frame: Ad[i][c] = A[i] . frame_c
+  float lam, inv_lam;
+  float al[3], Lm, inv_Lm, ah[3];
+  float Y0[3], Y1[3], ya0, ya1, Z0[3], Z1[3];
+  float n00, n01, n11, w0, w1, kappa, amp, xc, yc;
+};
+
+__device__ __forceinline__ bool setup_core(const ViewC& v, const float mu[3], const float A[9], float rho,
+                                           SetupState& s) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) s.mu_d[c] = v.F[3 * c] * mu[0] + v.F[3 * c + 1] * mu[1] + v.F[3 * c + 2] * mu[2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      s.Ad[3 * i + c] = A[3 * i] * v.F[3 * c] + A[3 * i + 1] * v.F[3 * c + 1] + A[3 * i + 2] * v.F[3 * c + 2];
+  const float* ray;
+  if (!v.parallel) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s.d0[c] = s.mu_d[c] - v.src_d[c];
+    if (!(s.d0[2] > 0.f)) return false;  // mean not in front of the source
+    s.lam = v.sdd_n / s.d0[2];
+    s.inv_lam = s.d0[2] / v.sdd_n;
+    s.xc = v.cx0 + (v.su + s.lam * s.d0[0]) * v.inv_du;
+    s.yc = v.cy0 + (v.sv + s.lam * s.d0[1]) * v.inv_dv;
+    ray = s.d0;
+  } else {
+    s.lam = 1.f;
+    s.inv_lam = 1.f;
+    float t = (v.det_d[2] - s.mu_d[2]) / v.dir_d[2];
+    s.xc = v.cx0 + (s.mu_d[0] - v.det_d[0] + t * v.dir_d[0]) * v.inv_du;
+    s.yc = v.cy0 + (s.mu_d[1] - v.det_d[1] + t * v.dir_d[1]) * v.inv_dv;
+    ray = v.dir_d;
+  }
+  float Lm2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    s.al[i] = s.Ad[3 * i] * ray[0] + s.Ad[3 * i + 1] * ray[1] + s.Ad[3 * i + 2] * ray[2];
+    Lm2 += s.al[i] * s.al[i];
+    s.Y0[i] = s.Ad[3 * i] * v.du * s.inv_lam;
+    s.Y1[i] = s.Ad[3 * i + 1] * v.dv * s.inv_lam;
+  }
+  s.Lm = sqrtf(Lm2);
+  s.inv_Lm = 1.f / s.Lm;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) s.ah[i] = s.al[i] * s.inv_Lm;
+  s.ya0 = s.Y0[0] * s.ah[0] + s.Y0[1] * s.ah[1] + s.Y0[2] * s.ah[2];
+  s.ya1 = s.Y1[0] * s.ah[0] + s.Y1[1] * s.ah[1] + s.Y1[2] * s.ah[2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    s.Z0[i] = s.Y0[i] - s.ah[i] * s.ya0;
+    s.Z1[i] = s.Y1[i] - s.ah[i] * s.ya1;
+  }
+  s.n00 = s.Z0[0] * s.Z0[0] + s.Z0[1] * s.Z0[1] + s.Z0[2] * s.Z0[2];
+  s.n01 = s.Z0[0] * s.Z1[0] + s.Z0[1] * s.Z1[1] + s.Z0[2] * s.Z1[2];
+  s.n11 = s.Z1[0] * s.Z1[0] + s.Z1[1] * s.Z1[1] + s.Z1[2] * s.Z1[2];
+  if (!v.parallel) {
+    s.w0 = -s.ya0 * s.inv_Lm;
+    s.w1 = -s.ya1 * s.inv_Lm;
+    s.kappa = s.inv_Lm * s.inv_Lm;
+  } else {
+    s.w0 = s.w1 = s.kappa = 0.f;
+  }
+  s.amp = rho * DIGS_SQRT_2PI * s.inv_lam * s.inv_Lm;
+  return isfinite(s.xc) && isfinite(s.yc) && isfinite(s.n00) && isfinite(s.n11) && isfinite(s.amp);
+}
+
+// Record plus conservative pixel box of { Delta : E(Delta) <= c2 }.  Returns false when the pair cannot
+// contribute (mean behind the source, source inside the cutoff ellipsoid, box off the detector).
+__device__ __forceinline__ bool setup_record(const ViewC& v, const float mu[3], const float A[9], float rho,
+                                             float c2, Rec& r) {
+  SetupState s;
+  if (!setup_core(v, mu, A, rho, s)) return false;
+  // E <= c2  <=>  Delta^T M Delta + 2 c2 w . Delta - c2 <= 0 with M = (1 - c2 kappa) N - c2 w w^T, an
+  // ellipse when M is positive definite (the source lies outside the cutoff ellipsoid).
+  float sc = 1.f - c2 * s.kappa;
+  float m00 = sc * s.n00 - c2 * s.w0 * s.w0;
+  float m01 = sc * s.n01 - c2 * s.w0 * s.w1;
+  float m11 = sc * s.n11 - c2 * s.w1 * s.w1;
+  float det = m00 * m11 - m01 * m01;
+  if (!(m00 > 0.f) || !(det > 0.f)) return false;
+  float i00 = m11 / det, i01 = -m01 / det, i11 = m00 / det;
+  float mw0 = i00 * s.w0 + i01 * s.w1, mw1 = i01 * s.w0 + i11 * s.w1;
+  float ox = -c2 * mw0, oy = -c2 * mw1;
+  float cp = c2 + c2 * c2 * (s.w0 * mw0 + s.w1 * mw1);
+  float hx = sqrtf(cp * i00) * 1.0001f + 1e-3f, hy = sqrtf(cp * i11) * 1.0001f + 1e-3f;
+  float fx0 = ceilf(s.xc + ox - hx), fx1 = floorf(s.xc + ox + hx);
+  float fy0 = ceilf(s.yc + oy - hy), fy1 = floorf(s.yc + oy + hy);
+  fx0 = fmaxf(fx0, 0.f); fy0 = fmaxf(fy0, 0.f);
+  fx1 = fminf(fx1, (float)(v.nu - 1)); fy1 = fminf(fy1, (float)(v.nv - 1));
+  if (!(fx0 <= fx1) || !(fy0 <= fy1)) return false;
+  int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
+  r.xc = s.xc; r.yc = s.yc;
+  r.n00 = s.n00; r.n01x2 = 2.f * s.n01; r.n11 = s.n11;
+  r.wn0 = -s.w0; r.wn1 = -s.w1; r.kappa = s.kappa; r.amp = s.amp;
+  r.bx = x0 | (x1 << 16);
+  r.by = y0 | (y1 << 16);
+  return true;
+}
+
+// Adjoint of setup_core.  g = dL/d(xc, yc, n00, n01, n11, w0, w1, kappa) and g_amp_base = dL/damp * amp / rho
+// is folded as gA_amp = dL/damp (see below).  Outputs dL/dmu (world), dL/dA and dL/drho.
+// gamp: dL/damp.  (amp itself is rho sqrt(2 pi) / (lambda Lm).)
+__device__ __forceinline__ void setup_adjoint(const ViewC& v, const SetupState& s, float rho, float g_xc, float g_yc,
+                                              float g_n00, float g_n01, float g_n11, float g_w0, float g_w1,
+                                              float g_kappa, float gamp, float gmu[3], float gA[9], float& grho) {
+  float gZ0[3], gZ1[3], gY0[3], gY1[3], gah[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    gZ0[i] = 2.f * g_n00 * s.Z0[i] + g_n01 * s.Z1[i];
+    gZ1[i] = 2.f * g_n11 * s.Z1[i] + g_n01 * s.Z0[i];
+    gY0[i] = gZ0[i];
+    gY1[i] = gZ1[i];
+    gah[i] = -(s.ya0 * gZ0[i] + s.ya1 * gZ1[i]);
+  }
+  float gya0 = -(s.ah[0] * gZ0[0] + s.ah[1] * gZ0[1] + s.ah[2] * gZ0[2]);
+  float gya1 = -(s.ah[0] * gZ1[0] + s.ah[1] * gZ1[1] + s.ah[2] * gZ1[2]);
+  float gLm = 0.f, glam = 0.f;
+  if (!v.parallel) {
+    gya0 -= g_w0 * s.inv_Lm;
+    gya1 -= g_w1 * s.inv_Lm;
+    gLm += (g_w0 * s.ya0 + g_w1 * s.ya1) * s.inv_Lm * s.inv_Lm;
+    gLm -= 2.f * g_kappa * s.inv_Lm * s.inv_Lm * s.inv_Lm;
+  }
+  // amp = rho sqrt(2 pi) inv_lam inv_Lm
+  float ga = gamp * s.amp;  // dL/damp * amp
+  grho = gamp * DIGS_SQRT_2PI * s.inv_lam * s.inv_Lm;
+  gLm -= ga * s.inv_Lm;
+  if (!v.parallel) glam -= ga * s.inv_lam;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    gY0[i] += gya0 * s.ah[i];
+    gY1[i] += gya1 * s.ah[i];
+    gah[i] += gya0 * s.Y0[i] + gya1 * s.Y1[i];
+  }
+  float ahg = s.ah[0] * gah[0] + s.ah[1] * gah[1] + s.ah[2] * gah[2];
+  float gal[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) gal[i] = (gah[i] - s.ah[i] * ahg) * s.inv_Lm + gLm * s.ah[i];
+  // Y = C inv_lam, C0 = Ad[:,0] du, C1 = Ad[:,1] dv
+  if (!v.parallel) {
+    glam -= (gY0[0] * s.Y0[0] + gY0[1] * s.Y0[1] + gY0[2] * s.Y0[2] + gY1[0] * s.Y1[0] + gY1[1] * s.Y1[1] +
+             gY1[2] * s.Y1[2]) * s.inv_lam;
+  }
+  float gAd[9];
+  const float* ray = v.parallel ? v.dir_d : s.d0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    gAd[3 * i + 0] = gal[i] * ray[0] + gY0[i] * s.inv_lam * v.du;
+    gAd[3 * i + 1] = gal[i] * ray[1] + gY1[i] * s.inv_lam * v.dv;
+    gAd[3 * i + 2] = gal[i] * ray[2];
+  }
+  float gmu_d[3];
+  if (!v.parallel) {
+    float gd0[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gd0[c] = s.Ad[c] * gal[0] + s.Ad[3 + c] * gal[1] + s.Ad[6 + c] * gal[2];
+    glam += g_xc * s.d0[0] * v.inv_du + g_yc * s.d0[1] * v.inv_dv;
+    gd0[0] += g_xc * s.lam * v.inv_du;
+    gd0[1] += g_yc * s.lam * v.inv_dv;
+    gd0[2] -= glam * s.lam / s.d0[2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gmu_d[c] = gd0[c];
+  } else {
+    gmu_d[0] = g_xc * v.inv_du;
+    gmu_d[1] = g_yc * v.inv_dv;
+    float gt = g_xc * v.dir_d[0] * v.inv_du + g_yc * v.dir_d[1] * v.inv_dv;
+    gmu_d[2] = -gt / v.dir_d[2];
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) gmu[k] = v.F[k] * gmu_d[0] + v.F[3 + k] * gmu_d[1] + v.F[6 + k] * gmu_d[2];
+  // Ad[i][c] = sum_k A[i][k] F[c][k]
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      gA[3 * i + k] = gAd[3 * i] * v.F[k] + gAd[3 * i + 1] * v.F[3 + k] + gAd[3 * i + 2] * v.F[6 + k];
+}

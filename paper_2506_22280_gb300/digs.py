@@ -1,0 +1,365 @@
+"""Thin Python binding of libdigs (include/digs.h): argument marshalling only.
+
+Every step of the hot path runs in the CUDA kernels of ``libdigs.so``; this module turns torch CUDA
+tensors into device pointers, scan geometry dicts into ``DigsView`` structs and forwards the call on
+torch's current stream.  There is no CPU fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Dict, List, Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdigs.so")
+
+DIGS_MAX_R = 4
+DIGS_MAX_VIEWS = 128
+DIGS_FLAG_REUSE_BINNING = 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "workspace too small for the pairs",
+          4: "device-side wait timed out", 5: "non-finite input"}
+
+
+class DigsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)} (status {code})")
+        self.code = code
+
+
+class DigsGaussians(C.Structure):
+    _fields_ = [("n", C.c_int), ("mu0", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("rho", C.c_void_p)]
+
+
+class DigsLattice(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("R", C.c_int),
+                ("origin", C.c_float * 3), ("spacing", C.c_float * 3)]
+
+
+class DigsView(C.Structure):
+    _fields_ = [("src", C.c_double * 3), ("det_c", C.c_double * 3), ("e_u", C.c_double * 3), ("e_v", C.c_double * 3),
+                ("du", C.c_double), ("dv", C.c_double), ("off_u", C.c_double), ("off_v", C.c_double),
+                ("nu", C.c_int), ("nv", C.c_int), ("parallel", C.c_int)]
+
+
+class DigsOpts(C.Structure):
+    _fields_ = [("cutoff", C.c_float), ("tile", C.c_int), ("flags", C.c_int)]
+
+
+class DigsAdamConfig(C.Structure):
+    _fields_ = [("lr0", C.c_float * 6), ("lr1", C.c_float * 6), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("total_iters", C.c_int)]
+
+
+class DigsState(C.Structure):
+    _fields_ = [("n", C.c_int), ("mu0", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("rho", C.c_void_p),
+                ("phi", C.c_void_p), ("w", C.c_void_p), ("n_w", C.c_int), ("m", C.c_void_p), ("v", C.c_void_p),
+                ("grad", C.c_void_p), ("iter", C.c_int), ("lat", DigsLattice), ("adam", DigsAdamConfig)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libdigs.so (built in-tree by ``paper_2506_22280_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(LIB_PATH)
+    P, I, S, LL = C.c_void_p, C.c_int, C.c_size_t, C.c_longlong
+    sig = {
+        "digs_workspace_size": (S, [I, I, I, I, I, LL, P]),
+        "digs_ffd_eval": (I, [P, P, P, I, P, P, P]),
+        "digs_count_pairs": (I, [P, P, P, P, P, I, P, P, S, C.POINTER(LL), P]),
+        "digs_project_fwd": (I, [P, P, P, P, P, I, P, P, P, S, P]),
+        "digs_project_bwd": (I, [P, P, P, P, P, I, P, P, P, P, P, P, P, P, P, S, P]),
+        "digs_state_moments": (S, [I, P, I]),
+        "digs_step": (I, [P, P, P, P, I, P, P, P, S, P]),
+        "digs_sync_status": (I, [P, P]),
+        "digs_status_string": (C.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols() -> List[str]:
+    return ["digs_workspace_size", "digs_ffd_eval", "digs_count_pairs", "digs_project_fwd", "digs_project_bwd",
+            "digs_state_moments", "digs_step", "digs_sync_status", "digs_status_string"]
+
+
+# ----------------------------------------------------------------------------- marshalling helpers
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libdigs takes CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("libdigs takes contiguous tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _f32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32, got {t.dtype}")
+    return t
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise DigsError(code, where)
+
+
+def lattice_struct(lat: Dict) -> DigsLattice:
+    s = DigsLattice()
+    s.nx, s.ny, s.nz, s.R = int(lat["nx"]), int(lat["ny"]), int(lat["nz"]), int(lat["R"])
+    for a in range(3):
+        s.origin[a] = float(lat["origin"][a])
+        s.spacing[a] = float(lat["spacing"][a])
+    return s
+
+
+def views_array(views: Sequence[Dict]):
+    arr = (DigsView * max(len(views), 1))()
+    for i, v in enumerate(views):
+        d = arr[i]
+        for key in ("src", "det_c", "e_u", "e_v"):
+            vec = getattr(d, key)
+            for a in range(3):
+                vec[a] = float(v[key][a])
+        d.du, d.dv = float(v["du"]), float(v["dv"])
+        d.off_u, d.off_v = float(v.get("off_u", 0.0)), float(v.get("off_v", 0.0))
+        d.nu, d.nv = int(v["nu"]), int(v["nv"])
+        d.parallel = 1 if v.get("parallel", False) else 0
+    return arr
+
+
+def opts_struct(cutoff: float = 3.5, tile: int = 16, flags: int = 0) -> DigsOpts:
+    return DigsOpts(float(cutoff), int(tile), int(flags))
+
+
+def gauss_struct(mu0, scale, quat, rho) -> DigsGaussians:
+    return DigsGaussians(int(mu0.shape[0]), _ptr(_f32(mu0, "mu0")), _ptr(_f32(scale, "scale")),
+                         _ptr(_f32(quat, "quat")), _ptr(_f32(rho, "rho")))
+
+
+# ----------------------------------------------------------------------------- entry points
+def workspace_size(n: int, P: int, nu: int, nv: int, R: int, max_pairs: int, cutoff=3.5, tile=16) -> int:
+    o = opts_struct(cutoff, tile)
+    return int(lib().digs_workspace_size(n, P, nu, nv, R, int(max_pairs), C.byref(o)))
+
+
+def ffd_eval(phi: torch.Tensor, lattice: Dict, x: torch.Tensor):
+    """u_r(x) [n][R][3] and grad u_r(x) [n][R][3][3] (Eq. 10-11), one CUDA thread per point."""
+    R = int(lattice["R"])
+    n = int(x.shape[0])
+    U = torch.empty(n, R, 3, device=x.device, dtype=torch.float32)
+    dU = torch.empty(n, R, 3, 3, device=x.device, dtype=torch.float32)
+    lat = lattice_struct(lattice)
+    _check(lib().digs_ffd_eval(C.byref(lat), _ptr(_f32(phi, "phi")), _ptr(_f32(x, "x")), n, _ptr(U), _ptr(dU),
+                               _stream()), "digs_ffd_eval")
+    return U, dU
+
+
+class Workspace:
+    """Caller-owned scratch memory for libdigs calls (a zero-initialised torch uint8 buffer)."""
+
+    def __init__(self, device="cuda"):
+        self.device = torch.device(device)
+        self.buf: Optional[torch.Tensor] = None
+
+    def ensure(self, nbytes: int) -> "Workspace":
+        nbytes = int(nbytes)
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.zeros(nbytes + 256, dtype=torch.uint8, device=self.device)
+        return self
+
+    @property
+    def ptr(self):
+        base = self.buf.data_ptr()
+        return C.c_void_p((base + 255) & ~255)
+
+    @property
+    def nbytes(self) -> int:
+        base = self.buf.data_ptr()
+        return int(self.buf.numel() - (((base + 255) & ~255) - base))
+
+
+def sync_status(ws: Workspace) -> int:
+    return int(lib().digs_sync_status(ws.ptr, _stream()))
+
+
+class Projector:
+    """Forward / backward projection of one Gaussian set through the C-ABI, keeping a workspace sized
+    by the pair count of the inputs it last saw (recounted when a call reports overflow)."""
+
+    def __init__(self, lattice: Dict, views: Sequence[Dict], cutoff: float = 3.5, tile: int = 16,
+                 headroom: float = 1.25, device="cuda"):
+        if len(views) > DIGS_MAX_VIEWS:
+            raise ValueError(f"at most {DIGS_MAX_VIEWS} views per call")
+        self.lattice = dict(lattice)
+        self.lat = lattice_struct(lattice)
+        self.views = list(views)
+        self.varr = views_array(self.views)
+        self.P = len(self.views)
+        self.nu = int(self.views[0]["nu"]) if self.views else 1
+        self.nv = int(self.views[0]["nv"]) if self.views else 1
+        self.opts = opts_struct(cutoff, tile)
+        self.cutoff, self.tile, self.headroom = cutoff, tile, headroom
+        self.ws = Workspace(device)
+        self.cap = -1
+
+    def _size(self, n, cap):
+        return workspace_size(n, self.P, self.nu, self.nv, int(self.lattice["R"]), cap, self.cutoff, self.tile)
+
+    def count_pairs(self, mu0, scale, quat, rho, phi, w) -> int:
+        n = int(mu0.shape[0])
+        self.ws.ensure(self._size(n, 0))
+        g = gauss_struct(mu0, scale, quat, rho)
+        out = C.c_longlong(0)
+        _check(lib().digs_count_pairs(C.byref(g), C.byref(self.lat), _ptr(_f32(phi, "phi")), _ptr(_f32(w, "w")),
+                                      self.varr, self.P, C.byref(self.opts), self.ws.ptr, self.ws.nbytes,
+                                      C.byref(out), _stream()), "digs_count_pairs")
+        return int(out.value)
+
+    def reserve(self, mu0, scale, quat, rho, phi, w, force: bool = False) -> int:
+        n = int(mu0.shape[0])
+        if force or self.cap < 0:
+            cnt = self.count_pairs(mu0, scale, quat, rho, phi, w)
+            self.cap = int(math.ceil(cnt * self.headroom)) + 1024
+            self.ws.ensure(self._size(n, self.cap))
+        return self.cap
+
+    def forward(self, mu0, scale, quat, rho, phi, w, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        self.reserve(mu0, scale, quat, rho, phi, w)
+        if out is None:
+            out = torch.empty(self.P, self.nv, self.nu, device=mu0.device, dtype=torch.float32)
+        g = gauss_struct(mu0, scale, quat, rho)
+        _check(lib().digs_project_fwd(C.byref(g), C.byref(self.lat), _ptr(_f32(phi, "phi")), _ptr(_f32(w, "w")),
+                                      self.varr, self.P, C.byref(self.opts), _ptr(out), self.ws.ptr, self.ws.nbytes,
+                                      _stream()), "digs_project_fwd")
+        return out
+
+    def backward(self, mu0, scale, quat, rho, phi, w, grad_proj, reuse: bool = False):
+        self.reserve(mu0, scale, quat, rho, phi, w)
+        n = int(mu0.shape[0])
+        dev = mu0.device
+        g_mu0 = torch.empty(n, 3, device=dev)
+        g_scale = torch.empty(n, 3, device=dev)
+        g_quat = torch.empty(n, 4, device=dev)
+        g_rho = torch.empty(n, device=dev)
+        g_phi = torch.empty_like(phi)
+        g_w = torch.empty(self.P, int(self.lattice["R"]), device=dev)
+        g = gauss_struct(mu0, scale, quat, rho)
+        o = opts_struct(self.cutoff, self.tile, DIGS_FLAG_REUSE_BINNING if reuse else 0)
+        _check(lib().digs_project_bwd(C.byref(g), C.byref(self.lat), _ptr(_f32(phi, "phi")), _ptr(_f32(w, "w")),
+                                      self.varr, self.P, C.byref(o), _ptr(_f32(grad_proj.contiguous(), "grad_proj")),
+                                      _ptr(g_mu0), _ptr(g_scale), _ptr(g_quat), _ptr(g_rho), _ptr(g_phi), _ptr(g_w),
+                                      self.ws.ptr, self.ws.nbytes, _stream()), "digs_project_bwd")
+        return dict(mu0=g_mu0, scale=g_scale, quat=g_quat, rho=g_rho, phi=g_phi, w=g_w)
+
+    def status(self) -> int:
+        return sync_status(self.ws)
+
+
+class DigsRender(torch.autograd.Function):
+    """Differentiable projection: ``DigsRender.apply(projector, mu0, scale, quat, rho, phi, w)`` returns
+    the projections [P][nv][nu]; its backward runs the hand-written CUDA backward (tile lists are rebuilt
+    in the backward rather than stored)."""
+
+    @staticmethod
+    def forward(ctx, projector: Projector, mu0, scale, quat, rho, phi, w):
+        ctx.projector = projector
+        ctx.save_for_backward(mu0, scale, quat, rho, phi, w)
+        return projector.forward(mu0, scale, quat, rho, phi, w)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        mu0, scale, quat, rho, phi, w = ctx.saved_tensors
+        g = ctx.projector.backward(mu0, scale, quat, rho, phi, w, grad_out.contiguous())
+        return None, g["mu0"], g["scale"], g["quat"], g["rho"], g["phi"], g["w"]
+
+
+def adam_config(lr0: Sequence[float], lr1: Sequence[float], total_iters: int, beta1=0.9, beta2=0.999,
+                eps=1e-15) -> DigsAdamConfig:
+    c = DigsAdamConfig()
+    for k in range(6):
+        c.lr0[k] = float(lr0[k])
+        c.lr1[k] = float(lr1[k])
+    c.beta1, c.beta2, c.eps, c.total_iters = float(beta1), float(beta2), float(eps), int(total_iters)
+    return c
+
+
+class Reconstruction:
+    """Parameters, Adam moments and gradient scratch of one reconstruction in device memory, stepped by
+    ``digs_step`` (render a batch, L2 loss, backward, fused Adam)."""
+
+    def __init__(self, mu0, scale, quat, rho, phi, w, lattice: Dict, adam: DigsAdamConfig, cutoff=3.5, tile=16,
+                 headroom=1.3, device="cuda"):
+        dev = torch.device(device)
+        f = lambda a: torch.as_tensor(a, dtype=torch.float32, device=dev).contiguous().clone()
+        self.mu0, self.scale, self.quat, self.rho = f(mu0), f(scale), f(quat), f(rho)
+        self.phi, self.w = f(phi), f(w)
+        self.lattice = dict(lattice)
+        self.lat = lattice_struct(lattice)
+        n = int(self.mu0.shape[0])
+        self.n_w = int(self.w.shape[0])
+        nm = int(lib().digs_state_moments(n, C.byref(self.lat), self.n_w))
+        self.m = torch.zeros(nm, device=dev)
+        self.v = torch.zeros(nm, device=dev)
+        self.grad = torch.zeros(nm, device=dev)
+        self.state = DigsState()
+        self.state.n = n
+        self.state.mu0, self.state.scale = self.mu0.data_ptr(), self.scale.data_ptr()
+        self.state.quat, self.state.rho = self.quat.data_ptr(), self.rho.data_ptr()
+        self.state.phi, self.state.w, self.state.n_w = self.phi.data_ptr(), self.w.data_ptr(), self.n_w
+        self.state.m, self.state.v, self.state.grad = self.m.data_ptr(), self.v.data_ptr(), self.grad.data_ptr()
+        self.state.iter = 0
+        self.state.lat = self.lat
+        self.state.adam = adam
+        self.cutoff, self.tile, self.headroom = cutoff, tile, headroom
+        self.ws = Workspace(dev)
+        self.cap = {}
+        self.loss = torch.zeros(1, device=dev)
+
+    def _reserve(self, views, B, proj_ids):
+        key = B
+        if key in self.cap:
+            return
+        pj = Projector(self.lattice, views, self.cutoff, self.tile, self.headroom, self.mu0.device)
+        w_rows = self.w[torch.as_tensor(proj_ids, device=self.w.device)].contiguous()
+        cnt = pj.count_pairs(self.mu0, self.scale, self.quat, self.rho, self.phi, w_rows)
+        cap = int(math.ceil(cnt * self.headroom)) + 4096
+        nu, nv = int(views[0]["nu"]), int(views[0]["nv"])
+        self.ws.ensure(workspace_size(self.mu0.shape[0], B, nu, nv, int(self.lattice["R"]), cap, self.cutoff,
+                                      self.tile))
+        self.cap[key] = cap
+
+    def step(self, meas: torch.Tensor, proj_ids: Sequence[int], views: Sequence[Dict]) -> torch.Tensor:
+        """One iteration over the batch; returns the (device) loss tensor of this step."""
+        B = len(proj_ids)
+        self._reserve(views, B, proj_ids)
+        ids = (C.c_int * B)(*[int(i) for i in proj_ids])
+        varr = views_array(views)
+        o = opts_struct(self.cutoff, self.tile)
+        _check(lib().digs_step(C.byref(self.state), _ptr(_f32(meas, "meas")), ids, varr, B, C.byref(o),
+                               _ptr(self.loss), self.ws.ptr, self.ws.nbytes, _stream()), "digs_step")
+        return self.loss
+
+    @property
+    def iter(self) -> int:
+        return int(self.state.iter)
+
+    def status(self) -> int:
+        return sync_status(self.ws)

@@ -51,7 +51,7 @@ class Workload:
 
     def subset(self, idx) -> "Workload":
         """Same workload restricted to Gaussians ``idx`` (lattice, weights, views unchanged)."""
-        idx = np.asarray(idx)
+        idx = np.asarray(idx, dtype=np.int64)
         return dataclasses.replace(self, mu0=self.mu0[idx], scale=self.scale[idx], quat=self.quat[idx],
                                    rho=self.rho[idx], extra=dict(self.extra))
 
