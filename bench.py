@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Throughput of the DIGS hot path on GB300: fwd+bwd projections/s on the synthetic 100k-Gaussian thorax
+(256 x 256 detector, R = 3, 680 projections).
+
+One step = one reconstruction iteration through the public C-ABI (``digs_step``): deform and project a
+batch of B projections (B = --batch), L2 loss against the measured projections, the full backward to
+Gaussians, control points and temporal weights, and the fused Adam update of every parameter group.
+
+Prints ONE JSON line (rank 0).  ``value`` = projections processed by all ranks / max over ranks of the
+summed device time of the timed steps (CUDA events around each step; L2 is flushed between steps by a
+512 MB write outside the events).  ``e2e`` times the same steps end to end: host-to-device copy of the
+batch's measured projections from pinned memory, the step, and a device-to-host read of the loss.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload instead.
+Multi-GPU (torchrun): every rank reconstructs its own independent scan (no data-path collective).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd projections/s (100k Gauss, 256²); % roofline; warm-start speedup"
+UNIT = "projections/s"
+# FP32 operations and MUFU (SFU) operations per (pixel, Gaussian) pair inside the cutoff, counted from
+# the kernels' pair loops (an FMA counts as 2 FP32 operations).
+PAIR_WORK = {"raster_fwd": (24, 2), "raster_bwd": (58, 2)}
+FP32_LANES_PER_SM = 128
+MUFU_PER_SM_CLK = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=16, help="projections per step")
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--n", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(pw) if pw else None}
+
+
+def visible_gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip() != ""]
+    if ids and all(v.strip().isdigit() for v in ids) and local_rank < len(ids):
+        return int(ids[local_rank])
+    return local_rank
+
+
+def adam_defaults(total):
+    # per group: mu0 (mm), log-scale, quaternion, density pre-activation, phi (mm), w
+    lr0 = [0.02, 0.005, 0.002, 0.01, 0.02, 0.01]
+    lr1 = [x / 10 for x in lr0]
+    return lr0, lr1, total
+
+
+def batch_ids(step, B, n_proj):
+    stride = max(n_proj // B, 1)
+    return [int((step * 7 + j * stride) % n_proj) for j in range(B)]
+
+
+def render_measured(pkg, wl, device):
+    """Measured projections of all views, rendered from the ground truth by the forward model."""
+    import torch
+    gt = wl.extra["gt"]
+    f = lambda a: torch.as_tensor(a, dtype=torch.float32, device=device).contiguous()
+    ins = [f(gt["mu0"]), f(gt["scale"]), f(gt["quat"]), f(gt["rho"]), f(gt["phi"])]
+    out = torch.empty(len(wl.views), wl.views[0]["nv"], wl.views[0]["nu"], device=device)
+    for s in range(0, len(wl.views), 128):
+        ids = list(range(s, min(s + 128, len(wl.views))))
+        pj = pkg.Projector(wl.lattice, [wl.views[i] for i in ids])
+        pj.forward(*ins, f(gt["w"][ids]), out=out[s:s + len(ids)])
+    torch.cuda.synchronize()
+    return out
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the current
+    source of that kernel (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(kernel)
+        src = open(os.path.join(ROOT, "paper_2506_22280_gb300", "csrc", rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec["sha256"]:
+            return None
+        return float(rec["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def cpu_baseline(wl):
+    """The FP64 oracle, as it stands, on one projection of the full workload (fwd + bwd)."""
+    import torch
+    from oracle import digs_oracle as O
+    import synth
+    sub = wl.select_views([0])
+    g = dict(mu0=sub.mu0, scale=sub.scale, quat=sub.quat, rho=sub.rho)
+    gp = synth.random_grad_proj(1, sub.views[0]["nv"], sub.views[0]["nu"], seed=2)
+    t0 = time.perf_counter()
+    O.project_vjp(g, sub.lattice, sub.phi, sub.w, sub.views, gp)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"1 projection of the {wl.n}-Gaussian thorax, FP64 oracle forward + backward (box mode), "
+                      f"{dt:.1f} s"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2506_22280_gb300 as pkg
+    from paper_2506_22280_gb300 import digs as D
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+    pkg.lib()
+    wl = synth.thorax(seed=1 + 101 * rank, n=args.n)
+    n_proj = len(wl.views)
+    meas = render_measured(pkg, wl, device)
+    B = args.batch
+    lr0, lr1, total = adam_defaults(10_000)
+    rec = pkg.Reconstruction(wl.mu0, wl.scale, wl.quat, wl.rho, wl.phi, wl.w, wl.lattice,
+                             D.adam_config(lr0, lr1, total), tile=args.tile, device=device)
+    K, W = args.steps, args.warmup
+    plan = [batch_ids(s, B, n_proj) for s in range(W + K)]
+    views = [[wl.views[i] for i in ids] for ids in plan]
+    varrs = [D.views_array(v) for v in views]
+    mb = [meas[torch.as_tensor(ids, device=device)].contiguous() for ids in plan]
+    for s in range(W):
+        rec.step(mb[s], plan[s], views[s], varr=varrs[s])
+    torch.cuda.synchronize()
+    if rec.status() != 0:
+        raise RuntimeError("device status after warm-up: %d" % rec.status())
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    stages = {k: 0.0 for k in D.STAGES}
+    clocks = ClockSampler(visible_gpu_index(local))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = D.kernel_launches()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for s in range(K):
+        flush.fill_(float(s))
+        e0, e1 = ev[s]
+        e0.record()
+        rec.step(mb[W + s], plan[W + s], views[W + s], time_stages=True, varr=varrs[W + s])
+        e1.record()
+        st = D.stage_times()
+        for k in stages:
+            stages[k] += st[k]
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = D.kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    dev_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    status = rec.status()
+    # pair statistics of one forward of the last batch (for the roofline's algorithmic work)
+    pj = pkg.Projector(wl.lattice, views[-1], tile=args.tile, device=device)
+    ins = [rec.mu0, rec.scale, rec.quat, rec.rho, rec.phi, rec.w[torch.as_tensor(plan[-1], device=device)].contiguous()]
+    pj.forward(*ins)
+    pairs = D.pair_stats(pj.ws)
+    # end to end: pinned host measured projections -> device, step, loss -> host
+    e2e = None
+    if not args.no_e2e:
+        host = [m.cpu().pin_memory() for m in mb[W:]]
+        dev_buf = torch.empty_like(mb[0])
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for s in range(K):
+            dev_buf.copy_(host[s], non_blocking=True)
+            loss = rec.step(dev_buf, plan[W + s], views[W + s], varr=varrs[W + s])
+            float(loss.item())
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+    red = torch.tensor([dev_ms, t_wall, e2e_s if not args.no_e2e else 0.0], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(red, op=dist.ReduceOp.MAX)
+    dev_ms, t_wall, e2e_s = [float(x) for x in red.tolist()]
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    total_proj = world * B * K
+    value = total_proj / (dev_ms / 1e3)
+    if not args.no_e2e:
+        e2e = {"value": total_proj / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(mb[0].numel() * 4),
+               "d2h_bytes_per_step": 4}
+    # roofline of the dominant kernel
+    props = torch.cuda.get_device_properties(device)
+    n_sm = props.multi_processor_count
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    dom = max(("raster_fwd", "raster_bwd"), key=lambda k: stages[k])
+    flops, mufu = PAIR_WORK[dom]
+    pair_rate_peak = n_sm * f_max * min(2 * FP32_LANES_PER_SM / flops, MUFU_PER_SM_CLK / mufu)
+    per_launch_ms = stages[dom] / K
+    achieved = pairs["cutoff_pairs"] * flops / (per_launch_ms / 1e3) / 1e12
+    peak = pair_rate_peak * flops / 1e12
+    roofline = {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_for("k_" + dom),
+                "peak_basis": (f"{n_sm} SMs x {f_max / 1e6:.0f} MHz; per in-cutoff pair {flops} FP32 ops "
+                               f"(128 lanes/SM, FMA = 2) and {mufu} MUFU ops (16/clk/SM): the slower pipe bounds"),
+                "pairs_per_launch": pairs["cutoff_pairs"], "box_pairs_per_launch": pairs["box_pairs"],
+                "tile_pairs_per_launch": pairs["tile_pairs"], "launch_ms": per_launch_ms}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": dev_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": (f"synthetic thorax, {args.n} Gaussians, 256x256 detector (1.6 mm), R=3, "
+                                    f"lattice 19^3 at 16 mm, 680-projection scan; {B} projections per step "
+                                    "(fwd + bwd + Adam)"),
+                       "batch_projections": B, "tile": args.tile, "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"{world} independent scans (replicas)", "wall_s_timed": t_wall},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "stages_ms_per_step": {k: v / K for k, v in stages.items()}, "device_status": status}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, timed on the machine's host cores; each step is one projection of a
+    20,000-Gaussian sample of the workload, scaled to the full Gaussian count (the cost is linear in it)."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+    import synth
+    from oracle import digs_oracle as O
+    wl = synth.thorax(seed=1, n=args.n)
+    n_s = min(20_000, args.n)
+    rng = np.random.default_rng(0)
+    steps = []
+    for s in range(args.warmup + args.steps):
+        idx = rng.choice(args.n, n_s, replace=False)
+        sub = wl.subset(idx).select_views([batch_ids(s, 1, len(wl.views))[0]])
+        g = dict(mu0=sub.mu0, scale=sub.scale, quat=sub.quat, rho=sub.rho)
+        gp = synth.random_grad_proj(1, 256, 256, seed=s)
+        t0 = time.perf_counter()
+        O.project_vjp(g, sub.lattice, sub.phi, sub.w, sub.views, gp)
+        if s >= args.warmup:
+            steps.append(time.perf_counter() - t0)
+    t = sum(steps) * (args.n / n_s)
+    value = len(steps) / t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / len(steps), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"synthetic thorax, {args.n} Gaussians, 256x256 detector, R=3; one projection "
+                                   f"fwd + bwd per step, sampled on {n_s} Gaussians and scaled to {args.n}"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": f"{len(steps)} steps x 1 projection x {n_s} of {args.n} Gaussians"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

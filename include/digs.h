@@ -157,6 +157,26 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
  * clear it. */
 digs_status digs_sync_status(void* ws, void* stream);
 
+/* ---- Diagnostics (not part of the method; used to measure it) ---------------------------------- */
+
+/* Stage timing: a call whose opts->flags has DIGS_FLAG_TIME_STAGES records CUDA events around each of
+ * its stages on its stream.  digs_stage_times() waits for the last of them and writes the milliseconds
+ * of each stage of the most recent timed call to ms[DIGS_NUM_STAGES] (0 for stages it did not run):
+ * 0 FFD + deformation + projection set-up, 1 prefix sum + key emission, 2 radix sort + tile ranges,
+ * 3 forward raster, 4 loss reduction, 5 backward raster, 6 per-Gaussian chain + FFD backward + dL/dw,
+ * 7 fused Adam.  Process-wide state: time one call at a time. */
+#define DIGS_FLAG_TIME_STAGES 2
+#define DIGS_NUM_STAGES 8
+digs_status digs_stage_times(float* ms);
+
+/* Number of CUDA kernels this library has launched since it was loaded (memsets not counted). */
+long long digs_kernel_launches(void);
+
+/* Pair statistics of the most recent forward pass that used `ws` (synchronises `stream`):
+ * out[0] = (tile, Gaussian) pairs binned, out[1] = (pixel, Gaussian) pairs inside the pixel boxes that
+ * the forward raster evaluated, out[2] = pairs within the cutoff (E <= cutoff^2) that it accumulated. */
+digs_status digs_pair_stats(void* ws, long long* out, void* stream);
+
 /* Static description of a status code. */
 const char* digs_status_string(digs_status s);
 

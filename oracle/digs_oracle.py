@@ -426,3 +426,25 @@ def adam_update(param, grad, m, v, step: int, lr: float, beta1: float, beta2: fl
     mhat = m / (1 - beta1 ** step)
     vhat = v / (1 - beta2 ** step)
     return param - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def adam_update_reparam(param, grad, m, v, step: int, lr: float, beta1: float, beta2: float, eps: float,
+                        kind: str = "plain"):
+    """Adam on a re-parameterisation of a positive physical parameter: kind 'log' optimises
+    theta = log(param), kind 'softplus' optimises theta with param = log(1 + exp(theta)); 'plain' is
+    :func:`adam_update`.  ``grad`` is dL/dparam; the chain rule gives dL/dtheta.  Returns the new physical
+    parameter and the moments (which live in theta space)."""
+    param = np.asarray(param, dtype=np.float64)
+    grad = np.asarray(grad, dtype=np.float64)
+    if kind == "plain":
+        return adam_update(param, grad, m, v, step, lr, beta1, beta2, eps)
+    if kind == "log":
+        theta, dtheta = np.log(param), param                       # d param / d theta = exp(theta)
+    elif kind == "softplus":
+        theta = np.log(np.expm1(param))
+        dtheta = 1.0 / (1.0 + np.exp(-theta))                     # sigmoid(theta)
+    else:
+        raise ValueError(kind)
+    theta, m, v = adam_update(theta, grad * dtheta, m, v, step, lr, beta1, beta2, eps)
+    new = np.exp(theta) if kind == "log" else np.log1p(np.exp(theta))
+    return new, m, v

@@ -61,6 +61,7 @@ cudaError_t launch_adam(const AdamGroup* groups, int ngroups, float beta1, float
   long long blocks = (off + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_adam<<<(unsigned)blocks, 256, 0, st>>>(P);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -7,7 +7,12 @@
 
 #include "digs_internal.h"
 
+#include <atomic>
+
 namespace digs {
+
+static std::atomic<long long> g_launches{0};
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -31,6 +36,7 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   };
   w.status = (int*)take(256);
   w.n_pairs = (uint32_t*)(w.status ? (char*)w.status + 64 : nullptr);
+  w.counters = (unsigned long long*)(w.status ? (char*)w.status + 128 : nullptr);
   w.rec = (float4*)take(PN * DIGS_REC_F4 * sizeof(float4));
   w.counts = (uint32_t*)take((PN + 1) * 4);
   w.offsets = (uint32_t*)take((PN + 1) * 4);
@@ -154,8 +160,26 @@ struct Call {
   Workspace ws;
   float c2;
   int P;
+  int flags;
   cudaStream_t st;
 };
+
+// Stage events of the most recent call made with DIGS_FLAG_TIME_STAGES (process-wide, diagnostic).
+cudaEvent_t g_ev[DIGS_NUM_STAGES + 1];
+bool g_ev_ready = false;
+unsigned g_ev_marked = 0;
+
+// Record the boundary `i` (stage i - 1 ends, stage i starts) when the call is timed.
+void mark(const Call& c, int i) {
+  if (!(c.flags & DIGS_FLAG_TIME_STAGES)) return;
+  if (!g_ev_ready) {
+    for (auto& e : g_ev) cudaEventCreate(&e);
+    g_ev_ready = true;
+  }
+  if (i == 0) g_ev_marked = 0;
+  cudaEventRecord(g_ev[i], c.st);
+  g_ev_marked |= 1u << i;
+}
 
 digs_status prepare(const DigsGaussians* g, const DigsLattice* lat, const float* phi, const float* w,
                     const DigsView* views, int P, const DigsOpts* opts, const int* rows, void* wsp, size_t ws_bytes,
@@ -175,6 +199,7 @@ digs_status prepare(const DigsGaussians* g, const DigsLattice* lat, const float*
   c.g = GaussPtrs{g->mu0, g->scale, g->quat, g->rho, g->n};
   c.c2 = opt_c2(opts);
   c.P = P;
+  c.flags = opts ? opts->flags : 0;
   c.st = (cudaStream_t)stream;
   int tile = opt_tile(opts);
   long long cap = capacity_for(ws_bytes, g->n, P, nu, nv, c.L.R, tile);
@@ -186,13 +211,18 @@ digs_status prepare(const DigsGaussians* g, const DigsLattice* lat, const float*
 // Steps up to the sorted tile lists.  Returns the buffer holding the sorted slot values.
 digs_status bin(Call& c, const float* phi, const float* w, uint32_t** sorted_vals) {
   Workspace& ws = c.ws;
+  mark(c, 0);
+  DIGS_TRY(cudaMemsetAsync(ws.counters, 0, 2 * sizeof(unsigned long long), c.st));
   DIGS_TRY(launch_prep_fwd(c.g, c.L, phi, w, c.views, c.P, c.c2, ws, c.st));
+  mark(c, 1);
   DIGS_TRY(exclusive_scan(ws.counts, ws.offsets, c.P * c.g.n, ws.scan_tmp, c.st));
   DIGS_TRY(launch_emit(ws, c.st));
+  mark(c, 2);
   uint32_t *sk = nullptr, *sv = nullptr;
   DIGS_TRY(radix_sort(ws.keys, ws.vals, ws.keys_alt, ws.vals_alt, ws.n_pairs, ws.cap, key_bits((long long)c.P * ws.T),
                       ws.hist, ws.scan_tmp, ws.n_sort_blocks, &sk, &sv, c.st));
   DIGS_TRY(tile_ranges(sk, ws.n_pairs, ws.cap, ws.ranges, c.P * ws.T, c.st));
+  mark(c, 3);
   *sorted_vals = sv;
   return DIGS_OK;
 }
@@ -206,12 +236,14 @@ uint32_t* sorted_vals_of(const Call& c) {
 digs_status backward(Call& c, const float* phi, const float* w, const float* grad_proj, uint32_t* sv, float* g_mu0,
                      float* g_scale, float* g_quat, float* g_rho, float* g_phi, float* g_w, int w_rows) {
   size_t nphi = (size_t)c.L.nx * c.L.ny * c.L.nz * 3 * c.L.R;
+  mark(c, 5);
   DIGS_TRY(cudaMemsetAsync(g_phi, 0, nphi * sizeof(float), c.st));
-  if (c.g.n > 0) {
-    DIGS_TRY(launch_raster_bwd(c.ws, sv, c.views, c.c2, grad_proj, c.st));
+  if (c.g.n > 0) DIGS_TRY(launch_raster_bwd(c.ws, sv, c.views, c.c2, grad_proj, c.st));
+  mark(c, 6);
+  if (c.g.n > 0)
     DIGS_TRY(launch_chain_bwd(c.g, c.L, phi, w, c.views, c.P, c.c2, c.ws, g_mu0, g_scale, g_quat, g_rho, g_phi, c.st));
-  }
   DIGS_TRY(launch_gw_reduce(c.ws, c.views, c.P, c.L.R, g_w, w_rows, c.st));
+  mark(c, 7);
   return DIGS_OK;
 }
 
@@ -262,6 +294,7 @@ digs_status digs_project_fwd(const DigsGaussians* g, const DigsLattice* lat, con
   s = bin(c, phi, w, &sv);
   if (s != DIGS_OK) return s;
   DIGS_TRY(launch_raster_fwd(c.ws, sv, c.views, c.c2, proj, nullptr, nullptr, 0.f, c.st));
+  mark(c, 4);
   return DIGS_OK;
 }
 
@@ -319,6 +352,7 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
   if (s != DIGS_OK) return s;
   float inv_count = 1.f / ((float)B * c.ws.nu * c.ws.nv);
   DIGS_TRY(launch_raster_fwd(c.ws, sv, c.views, c.c2, c.ws.proj, meas, c.ws.dldi, inv_count, c.st));
+  mark(c, 4);
   DIGS_TRY(launch_loss_reduce(c.ws.loss_part, B * c.ws.T, loss_out, inv_count, c.st));
   s = backward(c, st->phi, st->w, c.ws.dldi, sv, g_mu0, g_ls, g_q, g_rho, g_phi, g_w, st->n_w);
   if (s != DIGS_OK) return s;
@@ -339,6 +373,7 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
     off += sizes[k];
   }
   DIGS_TRY(launch_adam(groups, 6, a.beta1, a.beta2, a.eps, st->iter + 1, c.st));
+  mark(c, 8);
   st->iter += 1;
   return DIGS_OK;
 }
@@ -351,6 +386,43 @@ digs_status digs_sync_status(void* ws, void* stream) {
   DIGS_TRY(cudaMemcpy(&h, ws, sizeof(int), cudaMemcpyDeviceToHost));
   DIGS_TRY(cudaMemset(ws, 0, sizeof(int)));
   return (digs_status)h;
+}
+
+digs_status digs_stage_times(float* ms) {
+  if (!ms) return DIGS_ERR_ARG;
+  for (int i = 0; i < DIGS_NUM_STAGES; ++i) ms[i] = 0.f;
+  if (!g_ev_ready || !(g_ev_marked & 1u)) return DIGS_OK;
+  int last = 0;
+  for (int i = 0; i <= DIGS_NUM_STAGES; ++i)
+    if (g_ev_marked & (1u << i)) last = i;
+  DIGS_TRY(cudaEventSynchronize(g_ev[last]));
+  // stage i spans from boundary i to the next recorded boundary; stage 4 (loss) ends at boundary 5
+  int prev = 0;
+  for (int i = 1; i <= DIGS_NUM_STAGES; ++i) {
+    if (!(g_ev_marked & (1u << i))) continue;
+    float t = 0.f;
+    DIGS_TRY(cudaEventElapsedTime(&t, g_ev[prev], g_ev[i]));
+    ms[i - 1] = t;
+    prev = i;
+  }
+  return DIGS_OK;
+}
+
+long long digs_kernel_launches(void) { return g_launches.load(); }
+
+digs_status digs_pair_stats(void* ws, long long* out, void* stream) {
+  if (!ws || !out) return DIGS_ERR_ARG;
+  Workspace w;
+  layout(&w, ws, 0, 0, 1, 1, 1, 0, 16, 0);
+  uint32_t np[2] = {0, 0};
+  unsigned long long cnt[2] = {0, 0};
+  DIGS_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  DIGS_TRY(cudaMemcpy(np, w.n_pairs, sizeof(np), cudaMemcpyDeviceToHost));
+  DIGS_TRY(cudaMemcpy(cnt, w.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+  out[0] = np[0];
+  out[1] = (long long)cnt[0];
+  out[2] = (long long)cnt[1];
+  return DIGS_OK;
 }
 
 const char* digs_status_string(digs_status s) {

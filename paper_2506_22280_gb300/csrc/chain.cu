@@ -193,6 +193,7 @@ cudaError_t launch_chain_bwd(const GaussPtrs& g, const LatticeC& L, const float*
     default: return cudaErrorInvalidValue;
   }
 #undef DIGS_CH
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -215,6 +216,7 @@ cudaError_t launch_gw_reduce(const Workspace& ws, const ViewsParam& views, int P
   int nblk = ws.n > 0 ? (ws.n + kChainThreads - 1) / kChainThreads : 0;
   if (nblk == 0) return cudaSuccess;
   k_gw_reduce<<<(P * R + 127) / 128, 128, 0, st>>>(ws.gw_part, nblk, P, R, g_w, views);
+  note_launches(1);
   return cudaGetLastError();
 }
 

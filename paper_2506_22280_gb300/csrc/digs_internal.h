@@ -8,10 +8,14 @@
 
 namespace digs {
 
+// Kernel-launch bookkeeping (diagnostic): every launcher reports how many kernels it enqueued.
+void note_launches(int k);
+
 // Workspace carve-up for one call.  Every pointer is 256-byte aligned inside the caller's buffer.
 struct Workspace {
   int* status;            // [4]  device-detected status
   uint32_t* n_pairs;      // [2]  number of (tile, Gaussian) pairs produced, pairs kept (<= cap)
+  unsigned long long* counters;  // [2] forward raster: box pairs evaluated, pairs within the cutoff
   float4* rec;            // [P * n * 3]
   uint32_t* counts;       // [P * n + 1] tiles touched per (projection, Gaussian)
   uint32_t* offsets;      // [P * n + 1] exclusive scan of counts (offsets[P*n] = total)

@@ -36,6 +36,7 @@ cudaError_t launch_ffd_eval(const LatticeC& L, const float* phi, const float* x,
     case 4: k_ffd_eval<4><<<grid, 128, 0, st>>>(L, phi, x, n, U, dU); break;
     default: return cudaErrorInvalidValue;
   }
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -126,6 +127,7 @@ cudaError_t launch_prep_fwd(const GaussPtrs& g, const LatticeC& L, const float* 
     default: return cudaErrorInvalidValue;
   }
 #undef DIGS_PREP
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -165,6 +167,7 @@ cudaError_t launch_emit(const Workspace& ws, cudaStream_t st) {
   dim3 grid((PN + 255) / 256 > 0 ? (PN + 255) / 256 : 1);
   k_emit<<<grid, 256, 0, st>>>(ws.rec, ws.offsets, PN, ws.n, ws.tile, ws.tiles_x, ws.T, ws.keys, ws.vals, ws.rid,
                                ws.cap, ws.n_pairs, ws.status);
+  note_launches(1);
   return cudaGetLastError();
 }
 

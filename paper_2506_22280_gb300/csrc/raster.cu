@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
     const float4* __restrict__ rec, const uint32_t* __restrict__ svals, const uint32_t* __restrict__ rid,
     const uint2* __restrict__ ranges, const __grid_constant__ ViewsParam views, int tiles_x, int T, int nu, int nv,
     float c2, float* __restrict__ proj, const float* __restrict__ meas, float* __restrict__ dldi,
-    float* __restrict__ loss_part, float inv_count) {
+    float* __restrict__ loss_part, float inv_count, unsigned long long* __restrict__ counters) {
   constexpr int NPX = TS * TS;
   __shared__ float acc[kRasterWarps][NPX];
   __shared__ float4 srec[kRasterThreads * DIGS_REC_F4];
@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
   for (int p = threadIdx.x; p < kRasterWarps * NPX; p += kRasterThreads) (&acc[0][0])[p] = 0.f;
   const uint2 rg = ranges[(size_t)b * T + tile];
   const ViewC& v = views.v[b];
+  unsigned n_box = 0, n_cut = 0;  // per warp (lane 0) / per thread
   for (uint32_t base = rg.x; base < rg.y; base += kRasterThreads) {
     __syncthreads();
     uint32_t k = base + threadIdx.x;
@@ -61,6 +62,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
       if (wdt <= 0 || hgt <= 0) continue;  // cannot happen for keys emitted from the box; kept as a guard
       int npx = wdt * hgt;
       float inv_w = 1.f / (float)wdt;
+      n_box += npx;
       for (int kk = lane; kk < npx; kk += 32) {
         int rr = (int)(((float)kk + 0.5f) * inv_w);
         int px = x0 + (kk - rr * wdt), py = y0 + rr;
@@ -69,6 +71,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
           float rs = rsqrtf(pe.D);
           float E = pe.num * rs * rs;
           acc[warp][(py - oy) * TS + (px - ox)] += r.amp * rs * exp2f(-0.5f * DIGS_LOG2E * E);
+          ++n_cut;
         }
       }
       __syncwarp();
@@ -90,6 +93,15 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
         lsum = fmaf(res, res, lsum);
         if (dldi) dldi[idx] = 2.f * res * inv_count;
       }
+    }
+  }
+  if (counters) {
+    unsigned c = n_cut;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0 && (n_box | c)) {
+      atomicAdd(counters, (unsigned long long)n_box);
+      atomicAdd(counters + 1, (unsigned long long)c);
     }
   }
   if (loss_part) {
@@ -196,7 +208,7 @@ cudaError_t launch_raster_fwd(const Workspace& ws, const uint32_t* sorted_vals, 
 #define DIGS_RF(TS)                                                                                            \
   k_raster_fwd<TS><<<grid, kRasterThreads, 0, st>>>(ws.rec, sorted_vals, ws.rid, ws.ranges, views, ws.tiles_x,  \
                                                     ws.T, ws.nu, ws.nv, c2, proj, meas, dldi,                  \
-                                                    meas ? ws.loss_part : nullptr, inv_count)
+                                                    meas ? ws.loss_part : nullptr, inv_count, ws.counters)
   switch (ws.tile) {
     case 8: DIGS_RF(8); break;
     case 16: DIGS_RF(16); break;
@@ -204,6 +216,7 @@ cudaError_t launch_raster_fwd(const Workspace& ws, const uint32_t* sorted_vals, 
     default: return cudaErrorInvalidValue;
   }
 #undef DIGS_RF
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -221,6 +234,7 @@ cudaError_t launch_raster_bwd(const Workspace& ws, const uint32_t* sorted_vals, 
     default: return cudaErrorInvalidValue;
   }
 #undef DIGS_RB
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -242,6 +256,7 @@ __global__ void __launch_bounds__(1024) k_loss_reduce(const float* __restrict__ 
 cudaError_t launch_loss_reduce(const float* part, int n, float* out, float scale, cudaStream_t st) {
   // part holds per-tile sums of squared residuals; out[0] = scale * their sum
   k_loss_reduce<<<1, 1024, 0, st>>>(part, n, out, scale);
+  note_launches(1);
   return cudaGetLastError();
 }
 

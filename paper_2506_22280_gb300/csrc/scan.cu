@@ -93,12 +93,14 @@ __global__ void k_scan_empty(uint32_t* out) { out[0] = 0u; }
 cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int n, uint32_t* tmp, cudaStream_t st) {
   if (n <= 0) {
     k_scan_empty<<<1, 1, 0, st>>>(out);
+    note_launches(1);
     return cudaGetLastError();
   }
   int nb = (n + kScanTile - 1) / kScanTile;
   k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, n, tmp);
   k_scan_top<<<1, kScanThreads, 0, st>>>(tmp, nb);
   k_scan_apply<<<nb, kScanThreads, 0, st>>>(in, out, n, tmp, nb);
+  note_launches(3);
   return cudaGetLastError();
 }
 

@@ -97,6 +97,7 @@ cudaError_t radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint3
       cudaError_t e = exclusive_scan(hist, hist, 256 * nblk, scan_tmp, st);
       if (e != cudaSuccess) return e;
       k_radix_scatter<<<nblk, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_dev, shift, hist, nblk);
+      note_launches(2);
       uint32_t* t = ki; ki = ko; ko = t;
       t = vi; vi = vo; vo = t;
     }
@@ -123,6 +124,7 @@ cudaError_t tile_ranges(const uint32_t* sorted_keys, const uint32_t* n_dev, long
   if (cap <= 0) return cudaSuccess;
   long long blocks = (cap + 255) / 256;
   k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(sorted_keys, n_dev, ranges);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -81,6 +81,9 @@ def lib() -> C.CDLL:
         "digs_step": (I, [P, P, P, P, I, P, P, P, S, P]),
         "digs_sync_status": (I, [P, P]),
         "digs_status_string": (C.c_char_p, [I]),
+        "digs_stage_times": (I, [P]),
+        "digs_kernel_launches": (LL, []),
+        "digs_pair_stats": (I, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -92,7 +95,30 @@ def lib() -> C.CDLL:
 
 def exported_symbols() -> List[str]:
     return ["digs_workspace_size", "digs_ffd_eval", "digs_count_pairs", "digs_project_fwd", "digs_project_bwd",
-            "digs_state_moments", "digs_step", "digs_sync_status", "digs_status_string"]
+            "digs_state_moments", "digs_step", "digs_sync_status", "digs_status_string", "digs_stage_times",
+            "digs_kernel_launches", "digs_pair_stats"]
+
+
+DIGS_FLAG_TIME_STAGES = 2
+STAGES = ["setup", "bin", "sort", "raster_fwd", "loss", "raster_bwd", "chain_bwd", "adam"]
+
+
+def stage_times() -> Dict[str, float]:
+    """Milliseconds per stage of the most recent call made with time_stages=True (synchronises)."""
+    arr = (C.c_float * len(STAGES))()
+    _check(lib().digs_stage_times(arr), "digs_stage_times")
+    return {k: float(arr[i]) for i, k in enumerate(STAGES)}
+
+
+def kernel_launches() -> int:
+    return int(lib().digs_kernel_launches())
+
+
+def pair_stats(ws: "Workspace") -> Dict[str, int]:
+    """Pairs binned into tiles, pixel-box pairs evaluated and pairs within the cutoff in the last forward."""
+    out = (C.c_longlong * 3)()
+    _check(lib().digs_pair_stats(ws.ptr, out, _stream()), "digs_pair_stats")
+    return dict(tile_pairs=int(out[0]), box_pairs=int(out[1]), cutoff_pairs=int(out[2]))
 
 
 # ----------------------------------------------------------------------------- marshalling helpers
@@ -346,13 +372,16 @@ class Reconstruction:
                                       self.tile))
         self.cap[key] = cap
 
-    def step(self, meas: torch.Tensor, proj_ids: Sequence[int], views: Sequence[Dict]) -> torch.Tensor:
-        """One iteration over the batch; returns the (device) loss tensor of this step."""
+    def step(self, meas: torch.Tensor, proj_ids: Sequence[int], views: Sequence[Dict], time_stages: bool = False,
+             varr=None) -> torch.Tensor:
+        """One iteration over the batch; returns the (device) loss tensor of this step.  ``varr`` may hold
+        the pre-marshalled views of the batch."""
         B = len(proj_ids)
         self._reserve(views, B, proj_ids)
         ids = (C.c_int * B)(*[int(i) for i in proj_ids])
-        varr = views_array(views)
-        o = opts_struct(self.cutoff, self.tile)
+        if varr is None:
+            varr = views_array(views)
+        o = opts_struct(self.cutoff, self.tile, DIGS_FLAG_TIME_STAGES if time_stages else 0)
         _check(lib().digs_step(C.byref(self.state), _ptr(_f32(meas, "meas")), ids, varr, B, C.byref(o),
                                _ptr(self.loss), self.ws.ptr, self.ws.nbytes, _stream()), "digs_step")
         return self.loss

@@ -98,3 +98,20 @@ def test_adam_first_step_and_scalar_trajectory():
     v3 = 0.01 * 0.99 ** 2 * 1.0 + 0.01 * 0.99 * 4.0 + 0.01 * 0.25
     assert abs(float(m) - m3) < 1e-15 and abs(float(v) - v3) < 1e-15
     assert O.lr_at(1e-2, 1e-3, 0, 100) == 1e-2 and abs(O.lr_at(1e-2, 1e-3, 99, 100) - 1e-3) < 1e-18
+
+
+def test_reparameterised_adam():
+    """Log and softplus re-parameterisations: the first step moves theta by -lr sign(g) exactly, so the
+    physical parameter moves by the closed forms exp(-+lr) and the softplus of theta -+ lr; the chain-rule
+    factor never changes a sign, so the move follows -sign(dL/dparam)."""
+    rng = np.random.default_rng(4)
+    s = rng.uniform(0.5, 3.0, 30)
+    g = rng.normal(size=30)
+    lr = 0.05
+    s1, _, _ = O.adam_update_reparam(s, g, np.zeros(30), np.zeros(30), 1, lr, 0.9, 0.999, 1e-15, "log")
+    assert np.allclose(s1, s * np.exp(-lr * np.sign(g)), rtol=1e-12)
+    rho = rng.uniform(0.001, 0.05, 30)
+    r1, _, _ = O.adam_update_reparam(rho, g, np.zeros(30), np.zeros(30), 1, lr, 0.9, 0.999, 1e-15, "softplus")
+    theta = np.log(np.exp(rho) - 1)
+    assert np.allclose(r1, np.log(1 + np.exp(theta - lr * np.sign(g))), rtol=1e-10)
+    assert np.all(np.sign(r1 - rho) == -np.sign(g))
