@@ -109,6 +109,27 @@ digs_status digs_project_fwd(const DigsGaussians* g, const DigsLattice* lat, con
                              const DigsView* views, int P, const DigsOpts* opts, float* proj,
                              void* ws, size_t ws_bytes, void* stream);
 
+/* Forward projection without a workspace (the paper has no counterpart to this entry point; it exists
+ * for callers).  Same inputs, output and result as digs_project_fwd, but its scratch memory is a
+ * file-scope device array of DIGS_STATIC_SCRATCH_BYTES (32 MiB) inside this library, so the caller
+ * allocates nothing.  It serves callers that cannot call cudaMalloc: plug-ins whose host application
+ * owns all device memory through its own allocator, code that runs under a fixed device-memory budget
+ * set before it is loaded, and small C programs that should not have to size and manage a workspace.
+ *  - Every GPU on which the library's device code is loaded holds the 32 MiB until the process exits.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ *    device current; make that first call before any stream capture.
+ *  - All calls share the array and each overwrites what the last one left: calls whose work overlaps
+ *    on the GPU (other streams, other host threads) race and must not be issued.
+ *  - Returns DIGS_ERR_ARG, before launching anything, if the problem's pair-independent scratch
+ *    (records, counts, ranges, per-pixel buffers: roughly 56 B per (projection, Gaussian) plus 8 B per
+ *    pixel) exceeds the array.  The call then waits for its stream and returns DIGS_ERR_CAPACITY if the
+ *    (tile, Gaussian) pairs did not fit in the rest of the array (the output is then incomplete).
+ *  - Calls no cudaMalloc, cudaFree or other allocating routine. */
+#define DIGS_STATIC_SCRATCH_BYTES (32u << 20)
+digs_status digs_project_fwd_static(const DigsGaussians* g, const DigsLattice* lat, const float* phi,
+                                    const float* w, const DigsView* views, int P, const DigsOpts* opts,
+                                    float* proj, void* stream);
+
 /* Backward projection: given grad_proj = dL/dproj [P][nv][nu], write dL/d of every input:
  * g_mu0[n][3], g_scale[n][3], g_quat[n][4], g_rho[n], g_phi[R][nz][ny][nx][3], g_w[P][R].
  * The truncated sum is differentiated almost everywhere (the cutoff's boundary term is ignored). */
