@@ -47,11 +47,16 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.keys_alt = (uint32_t*)take((size_t)cap * 4);
   w.vals_alt = (uint32_t*)take((size_t)cap * 4);
   w.rid = (uint32_t*)take((size_t)cap * 4);
+  w.srid = (uint32_t*)take((size_t)cap * 4);
+  w.inv = (uint32_t*)take((size_t)cap * 4);
   w.hist = (uint32_t*)take(((size_t)256 * w.n_sort_blocks + 1) * 4);
   w.ranges = (uint2*)take((size_t)P * w.T * sizeof(uint2));
   w.partials = (float4*)take((size_t)cap * DIGS_PARTIAL_F4 * sizeof(float4));
-  w.gw_part = (float*)take((size_t)w.n_gauss_blocks * P * R * 4 + 4);
+  w.gw_part = (float*)take((size_t)std::max(w.n_gauss_blocks, 32) * P * R * 4 + 4);  // >= kGwSplit partials per (b, r)
   w.loss_part = (float*)take((size_t)P * w.T * 4 + 4);
+  w.ffd = (float*)take((size_t)12 * R * n * 4 + 4);
+  w.ffd2 = (float*)take((size_t)18 * R * n * 4 + 4);
+  w.padj = (float*)take((size_t)(kPairAdj + R) * P * n * 4 + 4);
   w.proj = (float*)take((size_t)P * nu * nv * 4);
   w.dldi = (float*)take((size_t)P * nu * nv * 4);
   w.bytes = off;
@@ -221,9 +226,10 @@ digs_status bin(Call& c, const float* phi, const float* w, uint32_t** sorted_val
   uint32_t *sk = nullptr, *sv = nullptr;
   DIGS_TRY(radix_sort(ws.keys, ws.vals, ws.keys_alt, ws.vals_alt, ws.n_pairs, ws.cap, key_bits((long long)c.P * ws.T),
                       ws.hist, ws.scan_tmp, ws.n_sort_blocks, &sk, &sv, c.st));
-  DIGS_TRY(tile_ranges(sk, ws.n_pairs, ws.cap, ws.ranges, c.P * ws.T, c.st));
+  DIGS_TRY(tile_ranges(sk, sv, ws.rid, ws.n_pairs, ws.cap, ws.ranges, c.P * ws.T, ws.srid, nullptr, c.st));
   mark(c, 3);
   *sorted_vals = sv;
+  ws.svals = sv;
   return DIGS_OK;
 }
 
@@ -238,7 +244,8 @@ digs_status backward(Call& c, const float* phi, const float* w, const float* gra
   size_t nphi = (size_t)c.L.nx * c.L.ny * c.L.nz * 3 * c.L.R;
   mark(c, 5);
   DIGS_TRY(cudaMemsetAsync(g_phi, 0, nphi * sizeof(float), c.st));
-  if (c.g.n > 0) DIGS_TRY(launch_raster_bwd(c.ws, sv, c.views, c.c2, grad_proj, c.st));
+  (void)sv;
+  if (c.g.n > 0) DIGS_TRY(launch_raster_bwd(c.ws, c.views, c.c2, grad_proj, c.st));
   mark(c, 6);
   if (c.g.n > 0)
     DIGS_TRY(launch_chain_bwd(c.g, c.L, phi, w, c.views, c.P, c.c2, c.ws, g_mu0, g_scale, g_quat, g_rho, g_phi, c.st));
@@ -293,7 +300,7 @@ digs_status digs_project_fwd(const DigsGaussians* g, const DigsLattice* lat, con
   uint32_t* sv = nullptr;
   s = bin(c, phi, w, &sv);
   if (s != DIGS_OK) return s;
-  DIGS_TRY(launch_raster_fwd(c.ws, sv, c.views, c.c2, proj, nullptr, nullptr, 0.f, c.st));
+  DIGS_TRY(launch_raster_fwd(c.ws, c.views, c.c2, proj, nullptr, nullptr, 0.f, c.st));
   mark(c, 4);
   return DIGS_OK;
 }
@@ -321,6 +328,7 @@ digs_status digs_project_bwd(const DigsGaussians* g, const DigsLattice* lat, con
   uint32_t* sv = nullptr;
   if (opts && (opts->flags & DIGS_FLAG_REUSE_BINNING)) {
     sv = sorted_vals_of(c);
+    c.ws.svals = sv;
   } else {
     s = bin(c, phi, w, &sv);
     if (s != DIGS_OK) return s;
@@ -351,7 +359,7 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
   s = bin(c, st->phi, st->w, &sv);
   if (s != DIGS_OK) return s;
   float inv_count = 1.f / ((float)B * c.ws.nu * c.ws.nv);
-  DIGS_TRY(launch_raster_fwd(c.ws, sv, c.views, c.c2, c.ws.proj, meas, c.ws.dldi, inv_count, c.st));
+  DIGS_TRY(launch_raster_fwd(c.ws, c.views, c.c2, c.ws.proj, meas, c.ws.dldi, inv_count, c.st));
   mark(c, 4);
   DIGS_TRY(launch_loss_reduce(c.ws.loss_part, B * c.ws.T, loss_out, inv_count, c.st));
   s = backward(c, st->phi, st->w, c.ws.dldi, sv, g_mu0, g_ls, g_q, g_rho, g_phi, g_w, st->n_w);

@@ -1,6 +1,15 @@
 // Per-Gaussian backward chain: record gradients (summed over the Gaussian's tile slots) -> deformed mean
 // and precision factor A -> K, S, R -> reference Gaussian; then through the DI warp (Eq. 7-8) and the
 // FFD (Eq. 9-11) to the control points phi and the temporal weights w.
+//
+// Three kernels.  (1) One thread per (projection, Gaussian) pair sums the pair's backward partials over
+// its tiles (contiguous slots), runs the adjoint of the projection set-up and of A = S^-1 R^T K^-1, and
+// writes 25 + R numbers (dL/dmu', dL/dK, dL/ds, dL/dR, dL/drho, dL/dw_r) component-major.  (2) One thread
+// per Gaussian sums them over the projections, forms dL/du_r and dL/d(grad u_r), and scatters the FFD
+// backward to the control points: when all 32 Gaussians of a warp sit in the same lattice cell (the
+// usual case for spatially ordered clouds) the warp first sums its 64 x 3R values with a transposed
+// shuffle reduction and issues one atomic per control-point component; otherwise each lane adds its own.
+// (3) dL/dw is a tree reduction over the Gaussians of each (projection, rank), in a fixed order.
 #include "digs_internal.h"
 #include "ffd.cuh"
 #include "setup.cuh"
@@ -9,117 +18,211 @@ namespace digs {
 
 constexpr int kChainThreads = 128;
 
+int chain_blocks(int n) { return (n + kChainThreads - 1) / kChainThreads; }
+
+// Sum 48 per-lane values over the warp; lane l ends with 3 complete sums, values
+// base(l) + j (j < 3) with base = 24 b4 + 12 b3 + 6 b2 + 3 b1 (b_i = bit i of l); lanes l and l^1 agree.
+__device__ __forceinline__ void warp_reduce_scatter48(float v[48], int lane) {
+#pragma unroll
+  for (int half = 24, bit = 16; half >= 3; half >>= 1, bit >>= 1) {
+    const bool hi = (lane & bit) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      float send = hi ? v[i] : v[i + half];
+      float keep = hi ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 1);
+}
+
+// Scatter of the control-point gradient for a whole warp: dL/dphi_r[node]_c += beta GU_c + sum_j GdU_cj
+// d_j beta for the 64 nodes around x (Eq. 10 differentiated); lanes in the same lattice cell are summed
+// over the warp first.  GU / GdU: this thread's dL/du_r and
+// dL/d(grad u_r), read from shared memory at stride `st`.  Lanes with valid == false contribute nothing
+// but take part in the warp collectives.
 template <int R>
-__global__ void __launch_bounds__(kChainThreads) k_chain_bwd(
-    GaussPtrs g, LatticeC L, const float* __restrict__ phi, const float* __restrict__ w,
-    const __grid_constant__ ViewsParam views, int P, float c2, const uint32_t* __restrict__ offsets,
-    long long cap, const float4* __restrict__ partials, float* __restrict__ g_mu0, float* __restrict__ g_scale,
-    float* __restrict__ g_quat, float* __restrict__ g_rho, float* __restrict__ g_phi, float* __restrict__ gw_part) {
-  __shared__ float red[kChainThreads / 32][R];
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = n < g.n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float mu0[3] = {0.f, 0.f, 0.f}, s[3] = {1.f, 1.f, 1.f}, inv_s[3] = {1.f, 1.f, 1.f}, qh[4] = {1.f, 0.f, 0.f, 0.f};
-  float qnorm = 1.f, Rm[9], rho = 0.f;
-  if (valid) {
+__device__ __forceinline__ void ffd_scatter_warp(float* __restrict__ g_phi, const LatticeC& L, const float x[3],
+                                                 bool valid, const float* GU, const float* GdU, int st) {
+  const int lane = threadIdx.x & 31;
+  int f[3];
+  float u[3];
+  lattice_cell(L, x, f, u);
+  float B[3][4], dB[3][4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    bspline4(u[a], B[a]);
+    bspline4_d1(u[a], dB[a]);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) dB[a][l] *= L.inv_h[a];
+  }
+  const unsigned key = valid ? ((unsigned)(f[0] + 1024) | ((unsigned)(f[1] + 1024) << 11) |
+                                ((unsigned)(f[2] + 512) << 22))
+                             : 0xffffffffu - (unsigned)lane;
+  // Lanes sharing a lattice cell share the 64 nodes: group them (up to kMaxGroups groups per warp) and
+  // let each group sum its values over the warp before one atomic per node component.
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const unsigned leaders = __ballot_sync(0xffffffffu, (peers & ((1u << lane) - 1u)) == 0u);
+  const bool grouped = __popc(leaders) <= 4;
+  const size_t rank_stride = (size_t)L.nx * L.ny * L.nz * 3;
+#pragma unroll 1
+  for (int r = 0; r < R; ++r) {
+    float gu[3], gdu[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gu[c] = valid ? GU[(r * 3 + c) * st] : 0.f;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) gdu[c] = valid ? GdU[(r * 9 + c) * st] : 0.f;
+#pragma unroll 1
+    for (int n3 = 0; n3 < 4; ++n3) {
+      const float bz = n3 == 0 ? B[2][0] : n3 == 1 ? B[2][1] : n3 == 2 ? B[2][2] : B[2][3];
+      const float dbz = n3 == 0 ? dB[2][0] : n3 == 1 ? dB[2][1] : n3 == 2 ? dB[2][2] : dB[2][3];
+      // v[(m * 4 + l) * 3 + c] = beta gu_c + sum_j gdu_cj d_j beta for node (l, m, n3); zero unless `on`
+      auto slab = [&](float v[48], bool on) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            const float bx = B[0][l], by = B[1][m];
+            const float beta = on ? bx * by * bz : 0.f;
+            const float gb0 = on ? dB[0][l] * by * bz : 0.f, gb1 = on ? bx * dB[1][m] * bz : 0.f;
+            const float gb2 = on ? bx * by * dbz : 0.f;
+            const int q = (m * 4 + l) * 3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              v[q + c] = beta * gu[c] + gdu[3 * c] * gb0 + gdu[3 * c + 1] * gb1 + gdu[3 * c + 2] * gb2;
+          }
+        }
+      };
+      if (grouped) {
+        unsigned rem = leaders;
+        while (rem) {  // warp-uniform
+          const int ld = __ffs(rem) - 1;
+          rem &= rem - 1u;
+          const unsigned gmask = __shfl_sync(0xffffffffu, peers, ld);
+          const int gi = __shfl_sync(0xffffffffu, f[0], ld), gj = __shfl_sync(0xffffffffu, f[1], ld);
+          const int gk = __shfl_sync(0xffffffffu, f[2], ld) + n3;
+          const bool gvalid = __shfl_sync(0xffffffffu, valid ? 1 : 0, ld) != 0;
+          float v[48];
+          slab(v, ((gmask >> lane) & 1u) != 0u);
+          warp_reduce_scatter48(v, lane);
+          if ((lane & 1) == 0 && gvalid && gk >= 0 && gk < L.nz) {
+            const int base = ((lane >> 4) & 1) * 24 + ((lane >> 3) & 1) * 12 + ((lane >> 2) & 1) * 6 + ((lane >> 1) & 1) * 3;
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) {
+              const int idx = base + jj, node = idx / 3, c = idx % 3;
+              const int i = gi + (node & 3), j = gj + (node >> 2);
+              if (i >= 0 && i < L.nx && j >= 0 && j < L.ny)
+                atomicAdd(g_phi + r * rank_stride + (((size_t)gk * L.ny + j) * L.nx + i) * 3 + c, v[jj]);
+            }
+          }
+        }
+      } else {
+        const int k = f[2] + n3;
+        if (valid && k >= 0 && k < L.nz) {
+          float v[48];
+          slab(v, true);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int j = f[1] + m;
+            if (j < 0 || j >= L.ny) continue;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+              const int i = f[0] + l;
+              if (i < 0 || i >= L.nx) continue;
+              float* gp = g_phi + r * rank_stride + (((size_t)k * L.ny + j) * L.nx + i) * 3;
+              const int q = (m * 4 + l) * 3;
+              atomicAdd(gp, v[q]);
+              atomicAdd(gp + 1, v[q + 1]);
+              atomicAdd(gp + 2, v[q + 2]);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// (1) Adjoint of one (projection, Gaussian) pair.
+template <int R>
+__global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, const float* __restrict__ ffd,
+                                                      const float* __restrict__ w,
+                                                      const __grid_constant__ ViewsParam views, int P,
+                                                      const uint32_t* __restrict__ offsets, long long cap,
+                                                      const float4* __restrict__ partials, float* __restrict__ padj) {
+  const int N = g.n;
+  const size_t PN = (size_t)P * N;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= PN) return;
+  const int b = (int)(i / N), n = (int)(i - (size_t)b * N);
+  float out[kPairAdj + R];
+#pragma unroll
+  for (int q = 0; q < kPairAdj + R; ++q) out[q] = 0.f;
+  uint32_t off = offsets[i], end = offsets[i + 1];
+  if ((long long)end > cap) end = (uint32_t)cap;  // pairs past the capacity were never binned
+  if (off > end) off = end;
+  if (off != end) {
+    const ViewC& v = views.v[b];
+    float mu0[3], inv_s[3], qh[4], Rm[9];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       mu0[c] = g.mu0[3 * n + c];
-      s[c] = g.scale[3 * n + c];
-      inv_s[c] = 1.f / s[c];
+      inv_s[c] = 1.f / g.scale[3 * n + c];
     }
-    float q[4] = {g.quat[4 * n], g.quat[4 * n + 1], g.quat[4 * n + 2], g.quat[4 * n + 3]};
-    qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const float q0 = g.quat[4 * n], q1 = g.quat[4 * n + 1], q2 = g.quat[4 * n + 2], q3 = g.quat[4 * n + 3];
+    const float iq = 1.f / sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    qh[0] = q0 * iq; qh[1] = q1 * iq; qh[2] = q2 * iq; qh[3] = q3 * iq;
+    quat_to_R(qh, Rm);
+    const float rho = g.rho[n];
+    const float* wb = w + (size_t)v.w_row * R;
+    float wr[R], mu[3], K[9];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) qh[c] = q[c] / qnorm;
-    rho = g.rho[n];
-  }
-  quat_to_R(qh, Rm);
-  float U[R][3], dU[R][9];
-  if (valid) {
-    ffd_eval_point<R>(phi, L, mu0, U, dU);
-  } else {
+    for (int c = 0; c < 3; ++c) mu[c] = mu0[c];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) K[c] = (c % 4 == 0) ? 1.f : 0.f;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+      wr[r] = __ldg(wb + r);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) U[r][c] = 0.f;
+      for (int c = 0; c < 3; ++c) mu[c] = fmaf(wr[r], __ldg(ffd + (size_t)(r * 3 + c) * N + n), mu[c]);
 #pragma unroll
-      for (int c = 0; c < 9; ++c) dU[r][c] = 0.f;
+      for (int c = 0; c < 9; ++c) K[c] = fmaf(wr[r], __ldg(ffd + (size_t)(3 * R + r * 9 + c) * N + n), K[c]);
     }
-  }
-  float GU[R][3], GdU[R][9];
+    float Ki[9], A[9];
+    inv3(K, Ki);
+    make_A(inv_s, Rm, Ki, A);
+    SetupState st;
+    setup_core(v, mu, A, rho, st);
+    float S[10];
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
+    for (int q = 0; q < 10; ++q) S[q] = 0.f;
+    for (uint32_t k = off; k < end; ++k) {  // the pair's tiles, in slot order
+      const float4* p = partials + (size_t)k * DIGS_PARTIAL_F4;
+      const float4 a = p[0], c = p[1], d = p[2];
+      S[0] += a.x; S[1] += a.y; S[2] += a.z; S[3] += a.w;
+      S[4] += c.x; S[5] += c.y; S[6] += c.z; S[7] += c.w;
+      S[8] += d.x; S[9] += d.y;
+    }
+    // record-parameter gradients (see the raster's pair formulas)
+    const float g_xc = -(2.f * (st.n00 * S[4] + st.n01 * S[5]) - st.w0 * S[6]);
+    const float g_yc = -(2.f * (st.n01 * S[4] + st.n11 * S[5]) - st.w1 * S[6]);
+    float gmu[3], gA[9], grho;
+    setup_adjoint(v, st, rho, g_xc, g_yc, S[1], 2.f * S[2], S[3], -S[7], -S[8], S[9], S[0], gmu, gA, grho);
+    // A = S^-1 R^T K^-1: dL/ds, dL/dR, dL/dK = -A^T gA K^-T
+    float gK[9];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) GU[r][c] = 0.f;
+    for (int c = 0; c < 3; ++c) out[c] = gmu[c];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) GdU[r][c] = 0.f;
-  }
-  float gmu0[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gR[9], grho = 0.f;
+    for (int ii = 0; ii < 3; ++ii)
+      out[12 + ii] = -inv_s[ii] * (gA[3 * ii] * A[3 * ii] + gA[3 * ii + 1] * A[3 * ii + 1] + gA[3 * ii + 2] * A[3 * ii + 2]);
 #pragma unroll
-  for (int c = 0; c < 9; ++c) gR[c] = 0.f;
-
-  for (int b = 0; b < P; ++b) {
-    const ViewC& v = views.v[b];
-    float gw[R];
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int r = 0; r < R; ++r) gw[r] = 0.f;
-    size_t idx = (size_t)b * g.n + n;
-    uint32_t off = valid ? offsets[idx] : 0u, end = valid ? offsets[idx + 1] : 0u;
-    if ((long long)end > cap) end = (uint32_t)cap;  // pairs past the capacity were never binned
-    if (off > end) off = end;
-    if (off != end) {
-      const float* wb = w + (size_t)v.w_row * R;
-      float wr[R], mu[3], K[9];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) mu[c] = mu0[c];
-#pragma unroll
-      for (int c = 0; c < 9; ++c) K[c] = (c % 4 == 0) ? 1.f : 0.f;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        wr[r] = __ldg(wb + r);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mu[c] = fmaf(wr[r], U[r][c], mu[c]);
-#pragma unroll
-        for (int c = 0; c < 9; ++c) K[c] = fmaf(wr[r], dU[r][c], K[c]);
-      }
-      float Ki[9], A[9];
-      inv3(K, Ki);
-      make_A(inv_s, Rm, Ki, A);
-      SetupState st;
-      setup_core(v, mu, A, rho, st);
-      // sum the backward partials of this (projection, Gaussian) over its tiles, in slot order
-      float S[10];
-#pragma unroll
-      for (int q = 0; q < 10; ++q) S[q] = 0.f;
-      for (uint32_t k = off; k < end; ++k) {
-        const float4* p = partials + (size_t)k * DIGS_PARTIAL_F4;
-        float4 a = p[0], c = p[1], d = p[2];
-        S[0] += a.x; S[1] += a.y; S[2] += a.z; S[3] += a.w;
-        S[4] += c.x; S[5] += c.y; S[6] += c.z; S[7] += c.w;
-        S[8] += d.x; S[9] += d.y;
-      }
-      // record-parameter gradients (see the raster's pair formulas)
-      float g_amp = S[0];
-      float g_n00 = S[1], g_n01 = 2.f * S[2], g_n11 = S[3];
-      float g_w0 = -S[7], g_w1 = -S[8];
-      float g_kappa = S[9];
-      float g_xc = -(2.f * (st.n00 * S[4] + st.n01 * S[5]) - st.w0 * S[6]);
-      float g_yc = -(2.f * (st.n01 * S[4] + st.n11 * S[5]) - st.w1 * S[6]);
-      float gmu[3], gA[9], grho_b;
-      setup_adjoint(v, st, rho, g_xc, g_yc, g_n00, g_n01, g_n11, g_w0, g_w1, g_kappa, g_amp, gmu, gA, grho_b);
-      grho += grho_b;
-      // A = S^-1 R^T K^-1
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-        gs[i] -= inv_s[i] * (gA[3 * i] * A[3 * i] + gA[3 * i + 1] * A[3 * i + 1] + gA[3 * i + 2] * A[3 * i + 2]);
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int bb = 0; bb < 3; ++bb)
-          gR[3 * a + bb] += inv_s[bb] * (gA[3 * bb] * Ki[3 * a] + gA[3 * bb + 1] * Ki[3 * a + 1] + gA[3 * bb + 2] * Ki[3 * a + 2]);
-      // g_K = -A^T gA K^-T
-      float Tm[9], gK[9];
+      for (int bb = 0; bb < 3; ++bb)
+        out[15 + 3 * a + bb] =
+            inv_s[bb] * (gA[3 * bb] * Ki[3 * a] + gA[3 * bb + 1] * Ki[3 * a + 1] + gA[3 * bb + 2] * Ki[3 * a + 2]);
+    {
+      float Tm[9];
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -129,44 +232,124 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_bwd(
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb)
           gK[3 * a + bb] = -(Tm[3 * a] * Ki[3 * bb] + Tm[3 * a + 1] * Ki[3 * bb + 1] + Tm[3 * a + 2] * Ki[3 * bb + 2]);
-      // mu' = mu0 + sum_r w_r U_r, K = I + sum_r w_r dU_r
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) out[3 + c] = gK[c];
+    out[24] = grho;
+    // dL/dw_r = dL/dmu' . u_r + dL/dK : grad u_r
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float acc = 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc = fmaf(gmu[c], __ldg(ffd + (size_t)(r * 3 + c) * N + n), acc);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) acc = fmaf(gK[c], __ldg(ffd + (size_t)(3 * R + r * 9 + c) * N + n), acc);
+      out[kPairAdj + r] = acc;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kPairAdj + R; ++q) padj[(size_t)q * PN + i] = out[q];
+}
+
+// Second derivatives of u_r at each mean ([18 R][n], see ffd_hessian_point), for the mean's gradient.
+template <int R>
+__global__ void __launch_bounds__(128) k_ffd_hessian(GaussPtrs g, LatticeC L, const float* __restrict__ phi,
+                                                    float* __restrict__ out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.n) return;
+  const float x[3] = {g.mu0[3 * n], g.mu0[3 * n + 1], g.mu0[3 * n + 2]};
+  float H[R][18];
+  ffd_hessian_point<R>(phi, L, x, H);
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < 18; ++c) out[(size_t)(r * 18 + c) * g.n + n] = H[r][c];
+}
+
+// (2) Per Gaussian: sum the pair adjoints over the projections, then the FFD backward.
+template <int R>
+__global__ void __launch_bounds__(kChainThreads) k_gauss_bwd(
+    GaussPtrs g, LatticeC L, const float* __restrict__ ffd, const float* __restrict__ ffd2,
+    const float* __restrict__ w, const __grid_constant__ ViewsParam views, int P, const float* __restrict__ padj,
+    float* __restrict__ g_mu0,
+    float* __restrict__ g_scale, float* __restrict__ g_quat, float* __restrict__ g_rho, float* __restrict__ g_phi) {
+  __shared__ float Gs[12 * R * kChainThreads];  // dL/du_r (3R) then dL/d(grad u_r) (9R), thread-fastest
+  constexpr int ST = kChainThreads;
+  const int N = g.n;
+  const size_t PN = (size_t)P * N;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = n < N;
+  float GU[R][3], GdU[R][9], gmu0[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gR[9], grho = 0.f;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) GU[r][c] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) GdU[r][c] = 0.f;
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) gR[c] = 0.f;
+  if (valid) {
+    for (int b = 0; b < P; ++b) {
+      const size_t i = (size_t)b * N + n;
+      const float* wb = w + (size_t)views.v[b].w_row * R;
+      float gmu[3], gK[9];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gmu[c] = padj[(size_t)c * PN + i];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) gK[c] = padj[(size_t)(3 + c) * PN + i];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gs[c] += padj[(size_t)(12 + c) * PN + i];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) gR[c] += padj[(size_t)(15 + c) * PN + i];
+      grho += padj[(size_t)24 * PN + i];
 #pragma unroll
       for (int c = 0; c < 3; ++c) gmu0[c] += gmu[c];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        float acc = 0.f;
+        const float wr = __ldg(wb + r);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          GU[r][c] = fmaf(wr[r], gmu[c], GU[r][c]);
-          acc = fmaf(gmu[c], U[r][c], acc);
-        }
+        for (int c = 0; c < 3; ++c) GU[r][c] = fmaf(wr, gmu[c], GU[r][c]);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) {
-          GdU[r][c] = fmaf(wr[r], gK[c], GdU[r][c]);
-          acc = fmaf(gK[c], dU[r][c], acc);
-        }
-        gw[r] = acc;
+        for (int c = 0; c < 9; ++c) GdU[r][c] = fmaf(wr, gK[c], GdU[r][c]);
       }
     }
-    // deterministic block reduction of dL/dw[b][r]
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Gs[(r * 3 + c) * ST + threadIdx.x] = GU[r][c];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) Gs[(3 * R + r * 9 + c) * ST + threadIdx.x] = GdU[r][c];
+  }
+  float mu0[3] = {0.f, 0.f, 0.f};
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) mu0[c] = g.mu0[3 * n + c];
+    // u_r and grad u_r are evaluated at mu0: dL/dmu0 += sum_r (grad u_r)^T dL/du_r + H_r : dL/d(grad u_r)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      float t = warp_sum(gw[r]);
-      if (lane == 0) red[warp][r] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < R) {
-      float t = 0.f;
 #pragma unroll
-      for (int ww = 0; ww < kChainThreads / 32; ++ww) t += red[ww][threadIdx.x];
-      gw_part[((size_t)blockIdx.x * P + b) * R + threadIdx.x] = t;
+      for (int c = 0; c < 3; ++c) {
+        const float* du = ffd + (size_t)(3 * R + r * 9 + c * 3) * N + n;   // d u_rc / dx_m, m = 0..2
+        const float* h = ffd2 + (size_t)(r * 18 + c * 6) * N + n;          // xx, yy, zz, xy, xz, yz
+        const float hxx = h[0], hyy = h[(size_t)N], hzz = h[(size_t)2 * N];
+        const float hxy = h[(size_t)3 * N], hxz = h[(size_t)4 * N], hyz = h[(size_t)5 * N];
+        const float g0 = GdU[r][3 * c], g1 = GdU[r][3 * c + 1], g2 = GdU[r][3 * c + 2];
+        gmu0[0] += du[0] * GU[r][c] + hxx * g0 + hxy * g1 + hxz * g2;
+        gmu0[1] += du[(size_t)N] * GU[r][c] + hxy * g0 + hyy * g1 + hyz * g2;
+        gmu0[2] += du[(size_t)2 * N] * GU[r][c] + hxz * g0 + hyz * g1 + hzz * g2;
+      }
     }
-    __syncthreads();
   }
+  // each thread reads back only its own column of Gs, so no barrier is needed
+  ffd_scatter_warp<R>(g_phi, L, mu0, valid, Gs + threadIdx.x, Gs + 3 * R * ST + threadIdx.x, ST);
   if (!valid) return;
-  ffd_bwd_point<R>(phi, g_phi, L, mu0, GU, GdU, gmu0);
-  float gq[4];
-  quat_bwd(qh, qnorm, gR, gq);
+  float qh[4], gq[4];
+  const float q0 = g.quat[4 * n], q1 = g.quat[4 * n + 1], q2 = g.quat[4 * n + 2], q3 = g.quat[4 * n + 3];
+  const float qn = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+  qh[0] = q0 / qn; qh[1] = q1 / qn; qh[2] = q2 / qn; qh[3] = q3 / qn;
+  quat_bwd(qh, qn, gR, gq);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     g_mu0[3 * n + c] = gmu0[c];
@@ -180,11 +363,17 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_bwd(
 cudaError_t launch_chain_bwd(const GaussPtrs& g, const LatticeC& L, const float* phi, const float* w,
                              const ViewsParam& views, int P, float c2, const Workspace& ws, float* g_mu0,
                              float* g_scale, float* g_quat, float* g_rho, float* g_phi, cudaStream_t st) {
+  (void)c2;
   if (g.n <= 0) return cudaSuccess;
-  dim3 grid((g.n + kChainThreads - 1) / kChainThreads);
-#define DIGS_CH(RR)                                                                                            \
-  k_chain_bwd<RR><<<grid, kChainThreads, 0, st>>>(g, L, phi, w, views, P, c2, ws.offsets, ws.cap, ws.partials, g_mu0, \
-                                                  g_scale, g_quat, g_rho, g_phi, ws.gw_part)
+  const size_t PN = (size_t)P * g.n;
+  const unsigned ga = (unsigned)((PN + 255) / 256);
+  dim3 gb(chain_blocks(g.n));
+#define DIGS_CH(RR)                                                                                             \
+  k_ffd_hessian<RR><<<gb, 128, 0, st>>>(g, L, phi, ws.ffd2);                                                    \
+  if (PN > 0)                                                                                                   \
+    k_pair_adjoint<RR><<<ga, 256, 0, st>>>(g, ws.ffd, w, views, P, ws.offsets, ws.cap, ws.partials, ws.padj);   \
+  k_gauss_bwd<RR><<<gb, kChainThreads, 0, st>>>(g, L, ws.ffd, ws.ffd2, w, views, P, ws.padj, g_mu0, g_scale,     \
+                                               g_quat, g_rho, g_phi)
   switch (L.R) {
     case 1: DIGS_CH(1); break;
     case 2: DIGS_CH(2); break;
@@ -193,33 +382,54 @@ cudaError_t launch_chain_bwd(const GaussPtrs& g, const LatticeC& L, const float*
     default: return cudaErrorInvalidValue;
   }
 #undef DIGS_CH
-  note_launches(1);
+  note_launches(PN > 0 ? 3 : 2);
   return cudaGetLastError();
 }
 
-// dL/dw[row][r] = sum over the Gaussian blocks of their partials, in block order.  Rows of w that no
-// projection of the call uses get zero (the caller's buffer is cleared first).
-__global__ void k_gw_reduce(const float* __restrict__ gw_part, int nblk, int P, int R, float* __restrict__ g_w,
-                            const __grid_constant__ ViewsParam views) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P * R) return;
-  int b = i / R, r = i % R;
+// (3) dL/dw[row(b)][r] = sum over the Gaussians of the pair adjoints: kGwSplit blocks per (projection,
+// rank) sum contiguous ranges (strided, then a fixed-order tree), and a second kernel adds the kGwSplit
+// partials in order.  Rows of w that no projection of the call uses get zero.
+constexpr int kGwSplit = 32;
+
+__global__ void __launch_bounds__(256) k_gw_partial(const float* __restrict__ padj, int N, int P, int R,
+                                                    float* __restrict__ part) {
+  __shared__ float red[8];
+  const int pr = blockIdx.x / kGwSplit, j = blockIdx.x % kGwSplit;
+  const int b = pr / R, r = pr % R;
+  const size_t PN = (size_t)P * N;
+  const int chunk = (N + kGwSplit - 1) / kGwSplit;
+  const int n0 = j * chunk, n1 = min(N, n0 + chunk);
+  const float* src = padj + (size_t)(kPairAdj + r) * PN + (size_t)b * N;
   float s = 0.f;
-  for (int k = 0; k < nblk; ++k) s += gw_part[((size_t)k * P + b) * R + r];
-  atomicAdd(&g_w[(size_t)views.v[b].w_row * R + r], s);  // rows repeat only if a time point repeats
+  for (int n = n0 + threadIdx.x; n < n1; n += blockDim.x) s += src[n];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int k = 0; k < 8; ++k) t += red[k];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_gw_final(const float* __restrict__ part, int P, int R, float* __restrict__ g_w,
+                           const __grid_constant__ ViewsParam views) {
+  const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pr >= P * R) return;
+  const int b = pr / R, r = pr % R;
+  float t = 0.f;
+  for (int j = 0; j < kGwSplit; ++j) t += part[(size_t)pr * kGwSplit + j];
+  atomicAdd(&g_w[(size_t)views.v[b].w_row * R + r], t);  // rows repeat only if a time point repeats
 }
 
 cudaError_t launch_gw_reduce(const Workspace& ws, const ViewsParam& views, int P, int R, float* g_w, int w_rows,
                              cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(g_w, 0, sizeof(float) * (size_t)w_rows * R, st);
-  if (e != cudaSuccess || P * R == 0) return e;
-  int nblk = ws.n > 0 ? (ws.n + kChainThreads - 1) / kChainThreads : 0;
-  if (nblk == 0) return cudaSuccess;
-  k_gw_reduce<<<(P * R + 127) / 128, 128, 0, st>>>(ws.gw_part, nblk, P, R, g_w, views);
-  note_launches(1);
+  if (e != cudaSuccess || P * R == 0 || ws.n == 0) return e;
+  k_gw_partial<<<P * R * kGwSplit, 256, 0, st>>>(ws.padj, ws.n, P, R, ws.gw_part);
+  k_gw_final<<<(P * R + 127) / 128, 128, 0, st>>>(ws.gw_part, P, R, g_w, views);
+  note_launches(2);
   return cudaGetLastError();
 }
-
-int chain_blocks(int n) { return (n + kChainThreads - 1) / kChainThreads; }
 
 }  // namespace digs

@@ -53,10 +53,11 @@ struct GaussPtrs {
 //   num = n00 dx^2 + n01x2 dx dy + n11 dy^2,   t = 1 + wn0 dx + wn1 dy,   D = t^2 + kappa num,
 //   E = num / D (squared Mahalanobis distance from the ray to the mean),
 //   V = amp * L_pix * D^-1/2 * exp(-E / 2) (the whole-line integral; L_pix = |pixel - source| per pixel).
-// Words 9 and 10 hold the inclusive pixel box (x0 | x1 << 16, y0 | y1 << 16) outside which E > cutoff^2.
+// Words 9 and 10 hold the inclusive pixel box (x0 | x1 << 16, y0 | y1 << 16) outside which E > cutoff^2;
+// word 11 is 1 when |D - 1| <= 0.02 over the box (D^-1/2 may then be taken from its binomial series).
 struct Rec {
   float xc, yc, n00, n01x2, n11, wn0, wn1, kappa, amp;
-  int bx, by;
+  int bx, by, poly;
 };
 
 __device__ __forceinline__ Rec load_rec(const float4* r3) {
@@ -64,14 +65,14 @@ __device__ __forceinline__ Rec load_rec(const float4* r3) {
   Rec r;
   r.xc = a.x; r.yc = a.y; r.n00 = a.z; r.n01x2 = a.w;
   r.n11 = b.x; r.wn0 = b.y; r.wn1 = b.z; r.kappa = b.w;
-  r.amp = c.x; r.bx = __float_as_int(c.y); r.by = __float_as_int(c.z);
+  r.amp = c.x; r.bx = __float_as_int(c.y); r.by = __float_as_int(c.z); r.poly = __float_as_int(c.w);
   return r;
 }
 
 __device__ __forceinline__ void store_rec(float4* r3, const Rec& r) {
   r3[0] = make_float4(r.xc, r.yc, r.n00, r.n01x2);
   r3[1] = make_float4(r.n11, r.wn0, r.wn1, r.kappa);
-  r3[2] = make_float4(r.amp, __int_as_float(r.bx), __int_as_float(r.by), 0.f);
+  r3[2] = make_float4(r.amp, __int_as_float(r.bx), __int_as_float(r.by), __int_as_float(r.poly));
 }
 
 // |pixel centre - source| for pixel (px, py) (cone beam); 1 for parallel beams.

@@ -92,6 +92,61 @@ __device__ __forceinline__ void ffd_eval_point(const float* __restrict__ phi, co
   }
 }
 
+// Second derivatives d2 u_{r,c} / dx_m dx_j at x: H[r][6 c + s] for s = xx, yy, zz, xy, xz, yz.
+template <int R>
+__device__ __forceinline__ void ffd_hessian_point(const float* __restrict__ phi, const LatticeC& L, const float x[3],
+                                                  float H[R][18]) {
+  int f[3];
+  float u[3];
+  lattice_cell(L, x, f, u);
+  float B[3][4], dB[3][4], d2B[3][4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    bspline4(u[a], B[a]);
+    bspline4_d1(u[a], dB[a]);
+    bspline4_d2(u[a], d2B[a]);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      dB[a][l] *= L.inv_h[a];
+      d2B[a][l] *= L.inv_h[a] * L.inv_h[a];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < 18; ++c) H[r][c] = 0.f;
+  const size_t rank_stride = (size_t)L.nx * L.ny * L.nz * 3;
+#pragma unroll
+  for (int n3 = 0; n3 < 4; ++n3) {
+    int k = f[2] + n3;
+    if (k < 0 || k >= L.nz) continue;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      int j = f[1] + m;
+      if (j < 0 || j >= L.ny) continue;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        int i = f[0] + l;
+        if (i < 0 || i >= L.nx) continue;
+        const float bx = B[0][l], by = B[1][m], bz = B[2][n3];
+        const float dbx = dB[0][l], dby = dB[1][m], dbz = dB[2][n3];
+        const float h[6] = {d2B[0][l] * by * bz, bx * d2B[1][m] * bz, bx * by * d2B[2][n3],
+                            dbx * dby * bz,      dbx * by * dbz,      bx * dby * dbz};
+        const float* d = phi + (((size_t)k * L.ny + j) * L.nx + i) * 3;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float v = __ldg(d + r * rank_stride + c);
+#pragma unroll
+            for (int s = 0; s < 6; ++s) H[r][6 * c + s] = fmaf(h[s], v, H[r][6 * c + s]);
+          }
+        }
+      }
+    }
+  }
+}
+
 // Backward of ffd_eval_point for upstream gradients GU = dL/dU and GdU = dL/d(dU):
 //   dL/dphi_r[node]_c += beta GU_c + sum_j GdU_cj d_j beta          (atomically, into g_phi)
 //   dL/dx_m           += sum_{r,node,c} phi_c (GU_c d_m beta + sum_j GdU_cj d_m d_j beta)

@@ -66,13 +66,23 @@ template <int R>
 __global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, LatticeC L, const float* __restrict__ phi,
                                                   const float* __restrict__ w, const __grid_constant__ ViewsParam views,
                                                   int P, float c2, int tile, int tiles_x, float4* __restrict__ rec,
-                                                  uint32_t* __restrict__ counts, int* status) {
+                                                  uint32_t* __restrict__ counts, float* __restrict__ ffd_out,
+                                                  int* status) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.n) return;
   GaussLocal G;
   load_gauss(g, n, G);
   float U[R][3], dU[R][9];
   ffd_eval_point<R>(phi, L, G.mu0, U, dU);
+  // keep u_r and grad u_r for the backward, component-major ([12 R][n]: coalesced for both passes)
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ffd_out[(size_t)(r * 3 + c) * g.n + n] = U[r][c];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) ffd_out[(size_t)(3 * R + r * 9 + c) * g.n + n] = dU[r][c];
+  }
+
   bool finite_in = isfinite(G.mu0[0] + G.mu0[1] + G.mu0[2] + G.s[0] + G.s[1] + G.s[2] + G.qnorm + G.rho);
   if (!finite_in) set_status(status, DIGS_ERR_NONFINITE);
   for (int b = 0; b < P; ++b) {
@@ -104,7 +114,7 @@ __global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, LatticeC L, const
       int x0 = r.bx & 0xffff, x1 = r.bx >> 16, y0 = r.by & 0xffff, y1 = r.by >> 16;
       cnt = (uint32_t)((x1 / tile - x0 / tile + 1) * (y1 / tile - y0 / tile + 1));
     } else {
-      r = Rec{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0};
+      r = Rec{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0, 0};
     }
     size_t idx = (size_t)b * g.n + n;
     store_rec(rec + idx * DIGS_REC_F4, r);
@@ -118,7 +128,7 @@ cudaError_t launch_prep_fwd(const GaussPtrs& g, const LatticeC& L, const float* 
   dim3 grid((g.n + 127) / 128);
 #define DIGS_PREP(RR)                                                                                      \
   k_prep_fwd<RR><<<grid, 128, 0, st>>>(g, L, phi, w, views, P, c2, ws.tile, ws.tiles_x, ws.rec, ws.counts, \
-                                       ws.status)
+                                       ws.ffd, ws.status)
   switch (L.R) {
     case 1: DIGS_PREP(1); break;
     case 2: DIGS_PREP(2); break;

@@ -1,90 +1,293 @@
 // Tile rasteriser of the X-ray transform (Sec. 3.1, Eq. 1, 3-4) and its backward pass.
 //
-// One CTA per (projection, tile).  The tile's (sorted) Gaussian list is staged into shared memory in
-// chunks of 256 records with 16-byte vector loads; each warp then takes one Gaussian at a time and its
-// lanes sweep the pixels of that Gaussian's box inside the tile.  The forward adds each pair's line
-// integral into a per-warp tile accumulator (no atomics; warps merge in a fixed order at the end), so the
-// result is deterministic.  The backward recomputes every pair, accumulates the ten sums that carry the
-// record gradients in registers, reduces them across the warp with shuffles and writes them to the pair's
-// slot; the per-Gaussian chain kernel then adds the slots of each Gaussian in order (again no atomics).
+// One CTA per (projection, tile).  The tile's sorted Gaussian list is staged into shared memory in
+// chunks of 256 records (48 B each) by 16-byte cp.async copies, double-buffered so the next chunk lands
+// while the current one is processed.  The thread that staged a record also derives, once, the part of
+// the Gaussian's pixel box inside the tile (its offset from the projected mean, size and smem offset).
+//
+// A warp then takes one Gaussian at a time and its lanes sweep that w x h box two pixels per lane per
+// step in packed FP32x2 arithmetic (fma/mul/add.rn.f32x2).  Narrow boxes (w <= 16): lane l owns column
+// (l mod w), starts at row (l div w) and takes the row pair (r, r + s), s = 32 div w, stepping 2s rows.
+// Wide boxes (w > 16, 32-pixel tiles): lane l owns the column pair (c, c + ceil(w/2)) of row (l div
+// ceil(w/2)), stepping s = 32 div ceil(w/2) rows.  Per pixel, with (dx, dy) its offset from the
+// projected mean:
+//   num = dy (n11 dy + n01x2 dx) + n00 dx^2,  t = 1 + wn0 dx + wn1 dy,  D = t^2 + kappa num,  E = num / D.
+// D stays within 2 % of 1 for these geometries; D^-1/2 then comes from its binomial series through the
+// cubic term (FMA pipe) and the only SFU operation per pixel is the exp2.
+//
+// Forward: each warp adds into its own tile accumulator (no atomics); warps merge in a fixed order, so
+// the result is deterministic.  Backward: each lane accumulates seven sums per pixel of its pair, turns
+// them into the ten sufficient statistics of the record gradient, the warp reduces them with a
+// transposed 16-shuffle butterfly and ten lanes write them to the pair's sorted position; the
+// per-Gaussian chain kernel adds a Gaussian's positions in slot order (again no atomics).
 #include "digs_internal.h"
 
 namespace digs {
 
 constexpr int kRasterThreads = 256;
 constexpr int kRasterWarps = kRasterThreads / 32;
+constexpr int kChunk = kRasterThreads;
+constexpr float kNegHalfLog2e = -0.5f * DIGS_LOG2E;
 
-struct PairEval {
-  float dx, dy, num, t, D;
-};
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-__device__ __forceinline__ bool eval_pair(const Rec& r, int px, int py, float c2, PairEval& p) {
-  p.dx = (float)px - r.xc;
-  p.dy = (float)py - r.yc;
-  p.num = p.dx * fmaf(r.n00, p.dx, r.n01x2 * p.dy) + r.n11 * p.dy * p.dy;
-  p.t = fmaf(r.wn0, p.dx, fmaf(r.wn1, p.dy, 1.f));
-  p.D = fmaf(p.t, p.t, r.kappa * p.num);
-  return p.num <= c2 * p.D;  // E = num / D <= c2, D > 0
+// ---- packed FP32x2: the two pixels of a lane's pair in one register pair ------------------------
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ f2 f2_dup(float x) { return f2_pack(x, x); }
+__device__ __forceinline__ void f2_unpack(f2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// The SFU's 2^x and 1/sqrt(x) (PTX ex2.approx / rsqrt.approx, flushing subnormals: the arguments here
+// are in [-9, 0] and near 1).
+__device__ __forceinline__ float sfu_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sfu_rsqrt(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ f2 f2_exp2(f2 x) {
+  float a, b;
+  f2_unpack(x, a, b);
+  return f2_pack(sfu_exp2(a), sfu_exp2(b));
+}
+// D^-1/2: binomial series (1 + e)^-1/2 ~ 1 - e/2 + 3e^2/8 - 5e^3/16 when |e| <= 0.02, else the SFU.
+template <bool POLY>
+__device__ __forceinline__ f2 f2_inv_sqrt(f2 D) {
+  if (POLY) {
+    f2 e = f2_add(D, f2_dup(-1.f));
+    return f2_fma(e, f2_fma(e, f2_fma(e, f2_dup(-0.3125f), f2_dup(0.375f)), f2_dup(-0.5f)), f2_dup(1.f));
+  }
+  float a, b;
+  f2_unpack(D, a, b);
+  return f2_pack(sfu_rsqrt(a), sfu_rsqrt(b));
 }
 
 template <int TS>
+struct RasterSmem {
+  static constexpr size_t rec_bytes = 2 * kChunk * DIGS_REC_F4 * sizeof(float4);
+  static constexpr size_t info_bytes = 2 * kChunk * sizeof(int4);
+  static constexpr size_t map_bytes = (TS + 1) * 32 * sizeof(int2);
+  static constexpr size_t head = rec_bytes + info_bytes + map_bytes;
+  static constexpr size_t fwd = head + kRasterWarps * TS * TS * sizeof(float);
+  static constexpr size_t bwd = head + TS * TS * sizeof(float);
+};
+
+// Lane layout for a box w pixels wide (see the file comment), packed in an int2:
+//  x = smem offset of the lane's first pixel | c << 10 | r0 << 15 | active << 20
+//  y = partner column offset | partner row offset << 6 | row step << 12 | partner smem delta << 19
+// (row step <= 64 needs 7 bits; the step is never 0).
+template <int TS>
+__device__ __forceinline__ int2 lane_layout(int w, int l) {
+  int cw, s, pdx, pdy, ystep;
+  if (w <= 0) return make_int2(0, 1 << 12);
+  if (w <= 16) {
+    cw = w; s = min(32 / w, TS); pdx = 0; pdy = s; ystep = 2 * s;
+  } else {
+    cw = (w + 1) / 2; s = min(32 / cw, TS); pdx = cw; pdy = 0; ystep = s;
+  }
+  int c = l % cw, r0 = l / cw;
+  int active = r0 < s ? 1 : 0;
+  if (!active) { c = 0; r0 = 0; }
+  return make_int2((r0 * TS + c) | (c << 10) | (r0 << 15) | (active << 20),
+                   pdx | (pdy << 6) | (ystep << 12) | ((pdy * TS + pdx) << 19));
+}
+
+// Per-CTA staging state.
+template <int TS>
+struct Stage {
+  float4* rec;    // [2][kChunk * 3] records
+  int4* info;     // [2][kChunk]: (smem offset | w << 10 | h << 16 | poly << 28, dx0, dy0, slot)
+  int2* lanemap;  // [TS + 1][32] lane layouts
+  __device__ void init(unsigned char* sm) {
+    rec = (float4*)sm;
+    info = (int4*)(sm + RasterSmem<TS>::rec_bytes);
+    lanemap = (int2*)(sm + RasterSmem<TS>::rec_bytes + RasterSmem<TS>::info_bytes);
+    for (int i = threadIdx.x; i < (TS + 1) * 32; i += kRasterThreads) lanemap[i] = lane_layout<TS>(i >> 5, i & 31);
+    slot0 = slot1 = 0u;
+  }
+  // Enqueue the copies of chunk [base, end) into buffer `buf` (commits a group even when empty).
+  uint32_t slot0, slot1;  // pre-sort slot of this thread's entry in each buffer (backward only)
+  __device__ void issue(const float4* __restrict__ grec, const uint32_t* __restrict__ srid,
+                        const uint32_t* __restrict__ svals, uint32_t base, uint32_t end, int buf) {
+    uint32_t k = base + threadIdx.x;
+    if (k < end) {
+      if (svals) {
+        if (buf) slot1 = svals[k]; else slot0 = svals[k];
+      }
+      const float4* src = grec + (size_t)srid[k] * DIGS_REC_F4;
+      float4* dst = rec + ((size_t)buf * kChunk + threadIdx.x) * DIGS_REC_F4;
+#pragma unroll
+      for (int q = 0; q < DIGS_REC_F4; ++q) cp_async16(dst + q, src + q);
+    }
+    cp_async_commit();
+  }
+  // After the chunk landed: this thread's record -> its box inside the tile.
+  __device__ void derive(uint32_t base, uint32_t end, int buf, int ox, int oy) {
+    uint32_t k = base + threadIdx.x;
+    if (k >= end) return;
+    const float4* r3 = rec + ((size_t)buf * kChunk + threadIdx.x) * DIGS_REC_F4;
+    float4 a = r3[0], c = r3[2];
+    int bx = __float_as_int(c.y), by = __float_as_int(c.z);
+    int x0 = max(bx & 0xffff, ox) - ox, x1 = min(bx >> 16, ox + TS - 1) - ox;
+    int y0 = max(by & 0xffff, oy) - oy, y1 = min(by >> 16, oy + TS - 1) - oy;
+    int w = x1 - x0 + 1, h = y1 - y0 + 1;
+    if (w <= 0 || h <= 0) { w = 1; h = 0; x0 = 0; y0 = 0; }  // keys come from the box: kept as a guard
+    int packed = (y0 * TS + x0) | (w << 10) | (h << 16) | ((__float_as_int(c.w) & 1) << 28);
+    info[buf * kChunk + threadIdx.x] = make_int4(packed, __float_as_int((float)(ox + x0) - a.x),
+                                                 __float_as_int((float)(oy + y0) - a.y), (int)(buf ? slot1 : slot0));
+  }
+};
+
+// Per-lane view of one staged entry.
+struct EntryLane {
+  float n00, n01x2, n11, wn0, wn1, kappa, amp;
+  float dx1, dx2, dy1, dy2;  // offsets of the lane's two first pixels from the projected mean
+  int off, d2;               // smem offset of the first pixel, delta to the partner pixel
+  int r0, pdy, ystep, h;     // first row, partner row offset, rows per step, box height
+  bool active, col2, poly;   // lane has pixels; partner column inside the box; series for D^-1/2
+};
+
+template <int TS>
+__device__ __forceinline__ EntryLane load_entry(const Stage<TS>& S, int buf, int e, int lane) {
+  const float4* r3 = S.rec + ((size_t)buf * kChunk + e) * DIGS_REC_F4;
+  float4 a = r3[0], b = r3[1], c = r3[2];
+  int4 inf = S.info[buf * kChunk + e];
+  EntryLane L;
+  L.n00 = a.z; L.n01x2 = a.w;
+  L.n11 = b.x; L.wn0 = b.y; L.wn1 = b.z; L.kappa = b.w; L.amp = c.x;
+  const int w = (inf.x >> 10) & 63;
+  L.h = (inf.x >> 16) & 63;
+  L.poly = (inf.x >> 28) & 1;
+  const int2 lm = S.lanemap[w * 32 + lane];
+  const int col = (lm.x >> 10) & 31, pdx = lm.y & 63;
+  L.r0 = (lm.x >> 15) & 31;
+  L.active = ((lm.x >> 20) & 1) && L.r0 < L.h;
+  L.pdy = (lm.y >> 6) & 63;
+  L.ystep = (lm.y >> 12) & 127;
+  L.d2 = lm.y >> 19;
+  L.col2 = TS <= 16 || col + pdx < w;  // boxes wider than 16 px only occur in 32-px tiles
+  L.off = (inf.x & 1023) + (lm.x & 1023);
+  L.dx1 = __int_as_float(inf.y) + (float)col;
+  L.dx2 = L.dx1 + (float)pdx;
+  L.dy1 = __int_as_float(inf.z) + (float)L.r0;
+  L.dy2 = L.dy1 + (float)L.pdy;
+  return L;
+}
+
+// Forward over the lane's pixel pairs; p points at the lane's first pixel in the warp's accumulator.
+template <int TS, bool POLY, bool COUNT>
+__device__ __forceinline__ void fwd_pixels(const EntryLane& L, float* p, float c2, unsigned& n_cut) {
+  const f2 DX = f2_pack(L.dx1, L.dx2);
+  const f2 A = f2_mul(f2_mul(f2_dup(L.n00), DX), DX), BQ = f2_mul(f2_dup(L.n01x2), DX);
+  const f2 T0 = f2_fma(f2_dup(L.wn0), DX, f2_dup(1.f));
+  const f2 N11 = f2_dup(L.n11), WN1 = f2_dup(L.wn1), KAP = f2_dup(L.kappa), AMP = f2_dup(L.amp);
+  const f2 C2 = f2_dup(c2), KNEG = f2_dup(kNegHalfLog2e), STEP = f2_dup((float)L.ystep);
+  const int pstep = L.ystep * TS;
+  f2 DY = f2_pack(L.dy1, L.dy2);
+  for (int r = L.r0; r < L.h; r += L.ystep, DY = f2_add(DY, STEP), p += pstep) {
+    f2 NUM = f2_fma(DY, f2_fma(N11, DY, BQ), A);
+    f2 T = f2_fma(WN1, DY, T0);
+    f2 D = f2_fma(T, T, f2_mul(KAP, NUM));
+    f2 RS = f2_inv_sqrt<POLY>(D);
+    f2 EX = f2_exp2(f2_mul(f2_mul(NUM, f2_mul(RS, RS)), KNEG));
+    f2 VAL = f2_mul(f2_mul(AMP, RS), EX);
+    f2 LIM = f2_mul(C2, D);
+    float na, nb, la, lb, va, vb;
+    f2_unpack(NUM, na, nb);
+    f2_unpack(LIM, la, lb);
+    f2_unpack(VAL, va, vb);
+    if (na <= la) {                                  // E = num / D <= cutoff^2
+      p[0] += va;
+      if (COUNT) ++n_cut;
+    }
+    // the partner may lie past the box part inside this tile (last row pair, or the column past w)
+    if ((TS <= 16 || L.col2) && r + L.pdy < L.h && nb <= lb) {
+      p[L.d2] += vb;
+      if (COUNT) ++n_cut;
+    }
+  }
+}
+
+template <int TS, bool COUNT>
 __global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
-    const float4* __restrict__ rec, const uint32_t* __restrict__ svals, const uint32_t* __restrict__ rid,
-    const uint2* __restrict__ ranges, const __grid_constant__ ViewsParam views, int tiles_x, int T, int nu, int nv,
-    float c2, float* __restrict__ proj, const float* __restrict__ meas, float* __restrict__ dldi,
-    float* __restrict__ loss_part, float inv_count, unsigned long long* __restrict__ counters) {
-  constexpr int NPX = TS * TS;
-  __shared__ float acc[kRasterWarps][NPX];
-  __shared__ float4 srec[kRasterThreads * DIGS_REC_F4];
+    const float4* __restrict__ grec, const uint32_t* __restrict__ srid, const uint2* __restrict__ ranges,
+    const __grid_constant__ ViewsParam views, int tiles_x, int T, int nu, int nv, float c2, float* __restrict__ proj,
+    const float* __restrict__ meas, float* __restrict__ dldi, float* __restrict__ loss_part, float inv_count,
+    unsigned long long* __restrict__ counters) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Stage<TS> S;
+  S.init(smem);
+  float* acc = (float*)(smem + RasterSmem<TS>::head);  // [warps][TS * TS]
   __shared__ float red[kRasterWarps];
   const int b = blockIdx.y, tile = blockIdx.x;
   const int ox = (tile % tiles_x) * TS, oy = (tile / tiles_x) * TS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int p = threadIdx.x; p < kRasterWarps * NPX; p += kRasterThreads) (&acc[0][0])[p] = 0.f;
+  for (int p = threadIdx.x; p < kRasterWarps * TS * TS; p += kRasterThreads) acc[p] = 0.f;
   const uint2 rg = ranges[(size_t)b * T + tile];
   const ViewC& v = views.v[b];
-  unsigned n_box = 0, n_cut = 0;  // per warp (lane 0) / per thread
-  for (uint32_t base = rg.x; base < rg.y; base += kRasterThreads) {
+  float* accw = acc + warp * TS * TS;
+  unsigned n_box = 0, n_cut = 0;
+  if (rg.x < rg.y) S.issue(grec, srid, nullptr, rg.x, rg.y, 0);
+  for (uint32_t base = rg.x, it = 0; base < rg.y; base += kChunk, ++it) {
+    const int buf = it & 1;
+    S.issue(grec, srid, nullptr, base + kChunk, rg.y, buf ^ 1);
+    cp_async_wait_prev();
+    S.derive(base, rg.y, buf, ox, oy);
     __syncthreads();
-    uint32_t k = base + threadIdx.x;
-    if (k < rg.y) {
-      const float4* src = rec + (size_t)rid[svals[k]] * DIGS_REC_F4;
-#pragma unroll
-      for (int q = 0; q < DIGS_REC_F4; ++q) srec[threadIdx.x * DIGS_REC_F4 + q] = src[q];
-    }
-    __syncthreads();
-    int cnt = min((int)(rg.y - base), kRasterThreads);
+    const int cnt = min((int)(rg.y - base), kChunk);
     for (int e = warp; e < cnt; e += kRasterWarps) {
-      Rec r = load_rec(&srec[e * DIGS_REC_F4]);
-      int x0 = max(r.bx & 0xffff, ox), x1 = min(r.bx >> 16, ox + TS - 1);
-      int y0 = max(r.by & 0xffff, oy), y1 = min(r.by >> 16, oy + TS - 1);
-      int wdt = x1 - x0 + 1, hgt = y1 - y0 + 1;
-      if (wdt <= 0 || hgt <= 0) continue;  // cannot happen for keys emitted from the box; kept as a guard
-      int npx = wdt * hgt;
-      float inv_w = 1.f / (float)wdt;
-      n_box += npx;
-      for (int kk = lane; kk < npx; kk += 32) {
-        int rr = (int)(((float)kk + 0.5f) * inv_w);
-        int px = x0 + (kk - rr * wdt), py = y0 + rr;
-        PairEval pe;
-        if (eval_pair(r, px, py, c2, pe)) {
-          float rs = rsqrtf(pe.D);
-          float E = pe.num * rs * rs;
-          acc[warp][(py - oy) * TS + (px - ox)] += r.amp * rs * exp2f(-0.5f * DIGS_LOG2E * E);
-          ++n_cut;
-        }
+      const EntryLane L = load_entry<TS>(S, buf, e, lane);
+      if (COUNT && lane == 0) {
+        int x = S.info[buf * kChunk + e].x;
+        n_box += ((x >> 10) & 63) * ((x >> 16) & 63);
+      }
+      if (L.active) {
+        if (L.poly)
+          fwd_pixels<TS, true, COUNT>(L, accw + L.off, c2, n_cut);
+        else
+          fwd_pixels<TS, false, COUNT>(L, accw + L.off, c2, n_cut);
       }
       __syncwarp();
     }
+    __syncthreads();
   }
-  __syncthreads();
   float lsum = 0.f;
-  for (int p = threadIdx.x; p < NPX; p += kRasterThreads) {
+  for (int p = threadIdx.x; p < TS * TS; p += kRasterThreads) {
     int px = ox + p % TS, py = oy + p / TS;
     if (px < nu && py < nv) {
       float s = 0.f;
 #pragma unroll
-      for (int w = 0; w < kRasterWarps; ++w) s += acc[w][p];
+      for (int w = 0; w < kRasterWarps; ++w) s += acc[w * TS * TS + p];
       float I = s * pixel_ray_length(v, (float)px, (float)py);
       size_t idx = ((size_t)b * nv + py) * nu + px;
       if (proj) proj[idx] = I;
@@ -95,7 +298,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
       }
     }
   }
-  if (counters) {
+  if (COUNT) {
     unsigned c = n_cut;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -116,126 +319,199 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
   }
 }
 
+// Sum ten per-lane values over the warp; value i ends in the even lane whose bits 4..1 spell i.
+// Recursive halving: each exchange sends the half of the values the partner keeps (8 + 4 + 2 + 1 + 1
+// shuffles instead of 10 x 5).
+__device__ __forceinline__ void warp_reduce_store10(const float v[10], float* out, int lane) {
+  float x[16];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) x[i] = v[i];
+#pragma unroll
+  for (int i = 10; i < 16; ++i) x[i] = 0.f;
+#pragma unroll
+  for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
+    const bool hi = (lane & bit) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      float send = hi ? x[i] : x[i + half];
+      float keep = hi ? x[i + half] : x[i];
+      x[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
+  }
+  x[0] += __shfl_xor_sync(0xffffffffu, x[0], 1);
+  const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+  if ((lane & 1) == 0 && idx < 10) out[idx] = x[0];
+}
+
+// Backward over the lane's pixel pairs; gp points at dL/dI * |X - s| of the lane's first pixel.
+// Sv receives the lane's share of the ten record-gradient sums: sum g V/amp; sum dL/dnum (dx^2, dx dy,
+// dy^2); sum dL/dnum (dx, dy); sum dL/dt (1, dx, dy); sum dL/dkappa.
+template <int TS, bool POLY>
+__device__ __forceinline__ void bwd_pixels(const EntryLane& L, const float* gp, float c2, float Sv[10]) {
+  const f2 DX = f2_pack(L.dx1, L.dx2);
+  const f2 AQ = f2_mul(f2_mul(f2_dup(L.n00), DX), DX), BQ = f2_mul(f2_dup(L.n01x2), DX);
+  const f2 T0 = f2_fma(f2_dup(L.wn0), DX, f2_dup(1.f));
+  const f2 N11 = f2_dup(L.n11), WN1 = f2_dup(L.wn1), KAP = f2_dup(L.kappa), AMPH = f2_dup(0.5f * L.amp);
+  const f2 KNEG = f2_dup(kNegHalfLog2e), MONE = f2_dup(-1.f), STEP = f2_dup((float)L.ystep);
+  const int pstep = L.ystep * TS;
+  f2 DY = f2_pack(L.dy1, L.dy2);
+  f2 S0 = f2_dup(0.f), S1 = S0, S2 = S0, S3 = S0, S4 = S0, S5 = S0, S6 = S0;
+  for (int r = L.r0; r < L.h; r += L.ystep, DY = f2_add(DY, STEP), gp += pstep) {
+    f2 NUM = f2_fma(DY, f2_fma(N11, DY, BQ), AQ);
+    f2 T = f2_fma(WN1, DY, T0);
+    f2 D = f2_fma(T, T, f2_mul(KAP, NUM));
+    f2 RS = f2_inv_sqrt<POLY>(D);
+    f2 INVD = f2_mul(RS, RS);
+    f2 E = f2_mul(NUM, INVD);
+    f2 BV = f2_mul(RS, f2_exp2(f2_mul(E, KNEG)));      // V / amp
+    float na, nb, da, db;
+    f2_unpack(NUM, na, nb);
+    f2_unpack(D, da, db);
+    float ga = (na <= c2 * da) ? gp[0] : 0.f;               // dL/dI * |X - s| inside the cutoff
+    float gb = ((TS <= 16 || L.col2) && r + L.pdy < L.h && nb <= c2 * db) ? gp[L.d2] : 0.f;
+    f2 G = f2_pack(ga, gb);
+    S0 = f2_fma(G, BV, S0);
+    f2 AL = f2_mul(f2_mul(G, AMPH), f2_mul(BV, INVD));     // dL/dV * V / (2 D)
+    f2 EM1 = f2_add(E, MONE);
+    f2 GNUM = f2_mul(AL, f2_fma(KAP, EM1, MONE));          // dL/dnum
+    f2 AEM = f2_mul(AL, EM1);
+    f2 GTH = f2_mul(AEM, T);                                 // (dL/dt) / 2
+    f2 GND = f2_mul(GNUM, DY);
+    S1 = f2_add(S1, GNUM);
+    S2 = f2_add(S2, GND);
+    S3 = f2_fma(GND, DY, S3);
+    S4 = f2_add(S4, GTH);
+    S5 = f2_fma(GTH, DY, S5);
+    S6 = f2_fma(AEM, NUM, S6);                               // dL/dkappa
+  }
+  // each pixel of the pair keeps its column, so its dx-moments follow from its dy-moments
+  float a[7][2];
+  f2 Sp[7] = {S0, S1, S2, S3, S4, S5, S6};
+#pragma unroll
+  for (int i = 0; i < 7; ++i) f2_unpack(Sp[i], a[i][0], a[i][1]);
+  const float dxs[2] = {L.dx1, L.dx2};
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float dx = dxs[j];
+    Sv[0] += a[0][j];
+    Sv[1] += dx * dx * a[1][j];
+    Sv[2] += dx * a[2][j];
+    Sv[3] += a[3][j];
+    Sv[4] += dx * a[1][j];
+    Sv[5] += a[2][j];
+    Sv[6] += 2.f * a[4][j];
+    Sv[7] += 2.f * dx * a[4][j];
+    Sv[8] += 2.f * a[5][j];
+    Sv[9] += a[6][j];
+  }
+}
+
 template <int TS>
 __global__ void __launch_bounds__(kRasterThreads) k_raster_bwd(
-    const float4* __restrict__ rec, const uint32_t* __restrict__ svals, const uint32_t* __restrict__ rid,
-    const uint2* __restrict__ ranges, const __grid_constant__ ViewsParam views, int tiles_x, int T, int nu, int nv,
-    float c2, const float* __restrict__ grad_proj, float4* __restrict__ partials) {
-  constexpr int NPX = TS * TS;
-  __shared__ float gpix[NPX];
-  __shared__ float4 srec[kRasterThreads * DIGS_REC_F4];
-  __shared__ uint32_t sslot[kRasterThreads];
+    const float4* __restrict__ grec, const uint32_t* __restrict__ srid, const uint2* __restrict__ ranges,
+    const __grid_constant__ ViewsParam views, int tiles_x, int T, int nu, int nv, float c2,
+    const float* __restrict__ grad_proj, const uint32_t* __restrict__ svals, float* __restrict__ partials) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint2 rg = ranges[(size_t)blockIdx.y * T + blockIdx.x];
+  if (rg.x == rg.y) return;
+  Stage<TS> S;
+  S.init(smem);
+  float* gpix = (float*)(smem + RasterSmem<TS>::head);  // [TS * TS] dL/dI * |pixel - source|
   const int b = blockIdx.y, tile = blockIdx.x;
   const int ox = (tile % tiles_x) * TS, oy = (tile / tiles_x) * TS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint2 rg = ranges[(size_t)b * T + tile];
-  if (rg.x == rg.y) return;
   const ViewC& v = views.v[b];
-  for (int p = threadIdx.x; p < NPX; p += kRasterThreads) {
+  for (int p = threadIdx.x; p < TS * TS; p += kRasterThreads) {
     int px = ox + p % TS, py = oy + p / TS;
     float g = 0.f;
     if (px < nu && py < nv)
       g = grad_proj[((size_t)b * nv + py) * nu + px] * pixel_ray_length(v, (float)px, (float)py);
     gpix[p] = g;
   }
-  for (uint32_t base = rg.x; base < rg.y; base += kRasterThreads) {
+  S.issue(grec, srid, svals, rg.x, rg.y, 0);
+  for (uint32_t base = rg.x, it = 0; base < rg.y; base += kChunk, ++it) {
+    const int buf = it & 1;
+    S.issue(grec, srid, svals, base + kChunk, rg.y, buf ^ 1);
+    cp_async_wait_prev();
+    S.derive(base, rg.y, buf, ox, oy);
     __syncthreads();
-    uint32_t k = base + threadIdx.x;
-    if (k < rg.y) {
-      uint32_t slot = svals[k];
-      sslot[threadIdx.x] = slot;
-      const float4* src = rec + (size_t)rid[slot] * DIGS_REC_F4;
-#pragma unroll
-      for (int q = 0; q < DIGS_REC_F4; ++q) srec[threadIdx.x * DIGS_REC_F4 + q] = src[q];
-    }
-    __syncthreads();
-    int cnt = min((int)(rg.y - base), kRasterThreads);
+    const int cnt = min((int)(rg.y - base), kChunk);
     for (int e = warp; e < cnt; e += kRasterWarps) {
-      Rec r = load_rec(&srec[e * DIGS_REC_F4]);
-      int x0 = max(r.bx & 0xffff, ox), x1 = min(r.bx >> 16, ox + TS - 1);
-      int y0 = max(r.by & 0xffff, oy), y1 = min(r.by >> 16, oy + TS - 1);
-      int wdt = x1 - x0 + 1, hgt = y1 - y0 + 1;
-      if (wdt <= 0 || hgt <= 0) continue;  // cannot happen for keys emitted from the box; kept as a guard
-      int npx = wdt * hgt;
-      float inv_w = 1.f / (float)wdt;
-      float S[10];
-#pragma unroll
-      for (int q = 0; q < 10; ++q) S[q] = 0.f;
-      for (int kk = lane; kk < npx; kk += 32) {
-        int rr = (int)(((float)kk + 0.5f) * inv_w);
-        int px = x0 + (kk - rr * wdt), py = y0 + rr;
-        PairEval pe;
-        if (eval_pair(r, px, py, c2, pe)) {
-          float g = gpix[(py - oy) * TS + (px - ox)];
-          float rs = rsqrtf(pe.D);
-          float inv_D = rs * rs;
-          float E = pe.num * inv_D;
-          float base_v = rs * exp2f(-0.5f * DIGS_LOG2E * E);  // V / amp
-          float G = g * r.amp * base_v;                        // dL/dV * V
-          float al = 0.5f * G * inv_D;
-          float em1 = E - 1.f;
-          float gnum = al * fmaf(r.kappa, em1, -1.f);
-          float gt = 2.f * al * em1 * pe.t;
-          float gnx = gnum * pe.dx, gny = gnum * pe.dy;
-          S[0] = fmaf(g, base_v, S[0]);
-          S[1] = fmaf(gnx, pe.dx, S[1]);
-          S[2] = fmaf(gnx, pe.dy, S[2]);
-          S[3] = fmaf(gny, pe.dy, S[3]);
-          S[4] += gnx;
-          S[5] += gny;
-          S[6] += gt;
-          S[7] = fmaf(gt, pe.dx, S[7]);
-          S[8] = fmaf(gt, pe.dy, S[8]);
-          S[9] = fmaf(al * em1, pe.num, S[9]);
-        }
+      const EntryLane L = load_entry<TS>(S, buf, e, lane);
+      float Sv[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (L.active) {
+        if (L.poly)
+          bwd_pixels<TS, true>(L, gpix + L.off, c2, Sv);
+        else
+          bwd_pixels<TS, false>(L, gpix + L.off, c2, Sv);
       }
-#pragma unroll
-      for (int q = 0; q < 10; ++q) S[q] = warp_sum(S[q]);
-      if (lane == 0) {
-        float4* dst = partials + (size_t)sslot[e] * DIGS_PARTIAL_F4;
-        dst[0] = make_float4(S[0], S[1], S[2], S[3]);
-        dst[1] = make_float4(S[4], S[5], S[6], S[7]);
-        dst[2] = make_float4(S[8], S[9], 0.f, 0.f);
-      }
+      warp_reduce_store10(Sv, partials + (size_t)S.info[buf * kChunk + e].w * (DIGS_PARTIAL_F4 * 4), lane);  // pre-sort slot
     }
+    __syncthreads();
   }
 }
 
-cudaError_t launch_raster_fwd(const Workspace& ws, const uint32_t* sorted_vals, const ViewsParam& views, float c2,
-                              float* proj, const float* meas, float* dldi, float inv_count, cudaStream_t st) {
-  if (ws.P <= 0) return cudaSuccess;
-  dim3 grid(ws.T, ws.P);
-#define DIGS_RF(TS)                                                                                            \
-  k_raster_fwd<TS><<<grid, kRasterThreads, 0, st>>>(ws.rec, sorted_vals, ws.rid, ws.ranges, views, ws.tiles_x,  \
-                                                    ws.T, ws.nu, ws.nv, c2, proj, meas, dldi,                  \
-                                                    meas ? ws.loss_part : nullptr, inv_count, ws.counters)
-  switch (ws.tile) {
-    case 8: DIGS_RF(8); break;
-    case 16: DIGS_RF(16); break;
-    case 32: DIGS_RF(32); break;
-    default: return cudaErrorInvalidValue;
+template <int TS>
+static cudaError_t fwd_launch(const Workspace& ws, const ViewsParam& views, float c2, float* proj, const float* meas,
+                              float* dldi, float inv_count, bool count, cudaStream_t st) {
+  const size_t smem = RasterSmem<TS>::fwd;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_raster_fwd<TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_raster_fwd<TS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
   }
-#undef DIGS_RF
+  dim3 grid(ws.T, ws.P);
+  float* lp = meas ? ws.loss_part : nullptr;
+  if (count)
+    k_raster_fwd<TS, true><<<grid, kRasterThreads, smem, st>>>(ws.rec, ws.srid, ws.ranges, views, ws.tiles_x, ws.T,
+                                                                ws.nu, ws.nv, c2, proj, meas, dldi, lp, inv_count,
+                                                                ws.counters);
+  else
+    k_raster_fwd<TS, false><<<grid, kRasterThreads, smem, st>>>(ws.rec, ws.srid, ws.ranges, views, ws.tiles_x, ws.T,
+                                                                 ws.nu, ws.nv, c2, proj, meas, dldi, lp, inv_count,
+                                                                 ws.counters);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_raster_bwd(const Workspace& ws, const uint32_t* sorted_vals, const ViewsParam& views, float c2,
-                              const float* grad_proj, cudaStream_t st) {
-  if (ws.P <= 0) return cudaSuccess;
-  dim3 grid(ws.T, ws.P);
-#define DIGS_RB(TS)                                                                                           \
-  k_raster_bwd<TS><<<grid, kRasterThreads, 0, st>>>(ws.rec, sorted_vals, ws.rid, ws.ranges, views, ws.tiles_x, \
-                                                    ws.T, ws.nu, ws.nv, c2, grad_proj, ws.partials)
-  switch (ws.tile) {
-    case 8: DIGS_RB(8); break;
-    case 16: DIGS_RB(16); break;
-    case 32: DIGS_RB(32); break;
-    default: return cudaErrorInvalidValue;
+template <int TS>
+static cudaError_t bwd_launch(const Workspace& ws, const ViewsParam& views, float c2, const float* grad_proj,
+                              cudaStream_t st) {
+  const size_t smem = RasterSmem<TS>::bwd;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_raster_bwd<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
   }
-#undef DIGS_RB
+  dim3 grid(ws.T, ws.P);
+  k_raster_bwd<TS><<<grid, kRasterThreads, smem, st>>>(ws.rec, ws.srid, ws.ranges, views, ws.tiles_x, ws.T, ws.nu,
+                                                        ws.nv, c2, grad_proj, ws.svals, (float*)ws.partials);
   note_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_raster_fwd(const Workspace& ws, const ViewsParam& views, float c2, float* proj, const float* meas,
+                              float* dldi, float inv_count, cudaStream_t st) {
+  if (ws.P <= 0) return cudaSuccess;
+  const bool count = meas == nullptr;  // pair statistics are gathered by plain projections only
+  switch (ws.tile) {
+    case 8: return fwd_launch<8>(ws, views, c2, proj, meas, dldi, inv_count, count, st);
+    case 16: return fwd_launch<16>(ws, views, c2, proj, meas, dldi, inv_count, count, st);
+    case 32: return fwd_launch<32>(ws, views, c2, proj, meas, dldi, inv_count, count, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_raster_bwd(const Workspace& ws, const ViewsParam& views, float c2, const float* grad_proj,
+                              cudaStream_t st) {
+  if (ws.P <= 0) return cudaSuccess;
+  switch (ws.tile) {
+    case 8: return bwd_launch<8>(ws, views, c2, grad_proj, st);
+    case 16: return bwd_launch<16>(ws, views, c2, grad_proj, st);
+    case 32: return bwd_launch<32>(ws, views, c2, grad_proj, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 __global__ void __launch_bounds__(1024) k_loss_reduce(const float* __restrict__ part, int n, float* out,

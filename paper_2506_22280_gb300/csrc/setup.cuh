@@ -160,12 +160,19 @@ __device__ __forceinline__ bool setup_record(const ViewC& v, const float mu[3], 
   r.wn0 = -s.w0; r.wn1 = -s.w1; r.kappa = s.kappa; r.amp = s.amp;
   r.bx = x0 | (x1 << 16);
   r.by = y0 | (y1 << 16);
+  // Bound on |D - 1| over the box for pairs inside the cutoff: |t - 1| <= tau, kappa num <= kappa c2 D.
+  // When it is small, D^-1/2 = (1 + e)^-1/2 is evaluated by its binomial series through e^3 (truncation
+  // below 35/128 e^4 < 5e-8 for |e| <= 0.02) instead of the SFU's rsqrt.
+  float mdx = fmaxf(fabsf((float)x0 - s.xc), fabsf((float)x1 - s.xc));
+  float mdy = fmaxf(fabsf((float)y0 - s.yc), fabsf((float)y1 - s.yc));
+  float tau = fabsf(s.w0) * mdx + fabsf(s.w1) * mdy;
+  float emax = 2.f * tau + tau * tau + 2.f * c2 * s.kappa;
+  r.poly = emax <= 0.02f ? 1 : 0;
   return true;
 }
 
-// Adjoint of setup_core.  g = dL/d(xc, yc, n00, n01, n11, w0, w1, kappa) and g_amp_base = dL/damp * amp / rho
-// is folded as gA_amp = dL/damp (see below).  Outputs dL/dmu (world), dL/dA and dL/drho.
-// gamp: dL/damp.  (amp itself is rho sqrt(2 pi) / (lambda Lm).)
+// Adjoint of setup_core: from dL/d(xc, yc, n00, n01, n11, w0, w1, kappa, amp) to dL/dmu (world
+// coordinates), dL/dA and dL/drho (amp = rho sqrt(2 pi) / (lambda Lm)).
 __device__ __forceinline__ void setup_adjoint(const ViewC& v, const SetupState& s, float rho, float g_xc, float g_yc,
                                               float g_n00, float g_n01, float g_n11, float g_w0, float g_w1,
                                               float g_kappa, float gamp, float gmu[3], float gA[9], float& grho) {

@@ -215,6 +215,12 @@ def thorax(seed: int = 1, n: int = 100_000, n_proj: int = 680, nu: int = 256, nv
     rho0 = rho_gt * irng.uniform(0.5, 1.5, size=n)
     phi0 = irng.normal(0.0, 0.1, size=phi_gt.shape)
     w0 = irng.normal(0.0, 0.1, size=w_gt.shape)
+    # Store the cloud in lattice-cell order (z, y, x) of the starting means: the order of the Gaussians is
+    # free for the method, and spatial order keeps the FFD neighbourhoods of neighbouring Gaussians together.
+    cell = np.floor((mu0 - lat["origin"]) / lat["spacing"]).astype(np.int64)
+    order = np.lexsort((cell[:, 0], cell[:, 1], cell[:, 2]))
+    mu0, scale0, rho0 = mu0[order], scale0[order], rho0[order]
+    mu_gt, scale_gt, quat_gt, rho_gt = mu_gt[order], scale_gt[order], quat_gt[order], rho_gt[order]
     gt = dict(mu0=mu_gt, scale=scale_gt, quat=quat_gt.copy(), rho=rho_gt, phi=phi_gt, w=w_gt)
     return Workload("thorax", mu0, scale0, quat_gt.copy(), rho0, lat, phi0, w0, views, times, angles,
                     dict(seed=seed, gt=gt))
