@@ -83,8 +83,8 @@ typedef struct {
   int flags;
 } DigsOpts;
 
-#define DIGS_FLAG_REUSE_BINNING 1  /* project_bwd: reuse records and tile lists left in `ws` by the
-                                      immediately preceding project_fwd with identical inputs          */
+#define DIGS_FLAG_REUSE_BINNING 1  /* project_bwd: reuse the per-pair records left in `ws` (same size)
+                                      by the immediately preceding project_fwd with identical inputs   */
 
 /* Bytes of workspace for n Gaussians, P projections of nu x nv pixels, R ranks and room for
  * `max_pairs` (tile, Gaussian) pairs.  Use digs_count_pairs() to learn the pair count of an input. */
@@ -121,8 +121,8 @@ digs_status digs_project_fwd(const DigsGaussians* g, const DigsLattice* lat, con
  *  - All calls share the array and each overwrites what the last one left: calls whose work overlaps
  *    on the GPU (other streams, other host threads) race and must not be issued.
  *  - Returns DIGS_ERR_ARG, before launching anything, if the problem's pair-independent scratch
- *    (records, counts, ranges, per-pixel buffers: roughly 56 B per (projection, Gaussian) plus 8 B per
- *    pixel) exceeds the array.  The call then waits for its stream and returns DIGS_ERR_CAPACITY if the
+ *    (records, counts, backward sums, ranges, per-pixel buffers: roughly 104 B per (projection,
+ *    Gaussian) plus 8 B per pixel) exceeds the array.  The call then waits for its stream and returns DIGS_ERR_CAPACITY if the
  *    (tile, Gaussian) pairs did not fit in the rest of the array (the output is then incomplete).
  *  - Calls no cudaMalloc, cudaFree or other allocating routine. */
 #define DIGS_STATIC_SCRATCH_BYTES (32u << 20)
@@ -132,7 +132,8 @@ digs_status digs_project_fwd_static(const DigsGaussians* g, const DigsLattice* l
 
 /* Backward projection: given grad_proj = dL/dproj [P][nv][nu], write dL/d of every input:
  * g_mu0[n][3], g_scale[n][3], g_quat[n][4], g_rho[n], g_phi[R][nz][ny][nx][3], g_w[P][R].
- * The truncated sum is differentiated almost everywhere (the cutoff's boundary term is ignored). */
+ * The truncated sum is differentiated almost everywhere (the cutoff's boundary term is ignored).
+ * Needs no tile lists: `ws` may be sized with max_pairs = 0. */
 digs_status digs_project_bwd(const DigsGaussians* g, const DigsLattice* lat, const float* phi, const float* w,
                              const DigsView* views, int P, const DigsOpts* opts, const float* grad_proj,
                              float* g_mu0, float* g_scale, float* g_quat, float* g_rho, float* g_phi, float* g_w,

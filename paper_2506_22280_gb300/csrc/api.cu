@@ -48,10 +48,9 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.vals_alt = (uint32_t*)take((size_t)cap * 4);
   w.rid = (uint32_t*)take((size_t)cap * 4);
   w.srid = (uint32_t*)take((size_t)cap * 4);
-  w.inv = (uint32_t*)take((size_t)cap * 4);
   w.hist = (uint32_t*)take(((size_t)256 * w.n_sort_blocks + 1) * 4);
   w.ranges = (uint2*)take((size_t)P * w.T * sizeof(uint2));
-  w.partials = (float4*)take((size_t)cap * DIGS_PARTIAL_F4 * sizeof(float4));
+  w.grec = (float4*)take(PN * DIGS_PARTIAL_F4 * sizeof(float4));
   w.gw_part = (float*)take((size_t)std::max(w.n_gauss_blocks, 32) * P * R * 4 + 4);  // >= kGwSplit partials per (b, r)
   w.loss_part = (float*)take((size_t)P * w.T * 4 + 4);
   w.ffd = (float*)take((size_t)12 * R * n * 4 + 4);
@@ -213,38 +212,38 @@ digs_status prepare(const DigsGaussians* g, const DigsLattice* lat, const float*
   return DIGS_OK;
 }
 
-// Steps up to the sorted tile lists.  Returns the buffer holding the sorted slot values.
-digs_status bin(Call& c, const float* phi, const float* w, uint32_t** sorted_vals) {
+// Warp, projection set-up and the per-pair records (all the backward needs).
+digs_status prep(Call& c, const float* phi, const float* w) {
   Workspace& ws = c.ws;
   mark(c, 0);
   DIGS_TRY(cudaMemsetAsync(ws.counters, 0, 2 * sizeof(unsigned long long), c.st));
   DIGS_TRY(launch_prep_fwd(c.g, c.L, phi, w, c.views, c.P, c.c2, ws, c.st));
   mark(c, 1);
+  return DIGS_OK;
+}
+
+// Steps up to the sorted tile lists (what the forward raster needs).
+digs_status bin(Call& c, const float* phi, const float* w) {
+  Workspace& ws = c.ws;
+  digs_status s = prep(c, phi, w);
+  if (s != DIGS_OK) return s;
   DIGS_TRY(exclusive_scan(ws.counts, ws.offsets, c.P * c.g.n, ws.scan_tmp, c.st));
   DIGS_TRY(launch_emit(ws, c.st));
   mark(c, 2);
   uint32_t *sk = nullptr, *sv = nullptr;
   DIGS_TRY(radix_sort(ws.keys, ws.vals, ws.keys_alt, ws.vals_alt, ws.n_pairs, ws.cap, key_bits((long long)c.P * ws.T),
                       ws.hist, ws.scan_tmp, ws.n_sort_blocks, &sk, &sv, c.st));
-  DIGS_TRY(tile_ranges(sk, sv, ws.rid, ws.n_pairs, ws.cap, ws.ranges, c.P * ws.T, ws.srid, nullptr, c.st));
+  DIGS_TRY(tile_ranges(sk, sv, ws.rid, ws.n_pairs, ws.cap, ws.ranges, c.P * ws.T, ws.srid, c.st));
   mark(c, 3);
-  *sorted_vals = sv;
-  ws.svals = sv;
   return DIGS_OK;
 }
 
-uint32_t* sorted_vals_of(const Call& c) {
-  int passes = (key_bits((long long)c.P * c.ws.T) + 7) / 8;
-  if (c.ws.cap <= 0) return c.ws.vals;
-  return (passes % 2) ? c.ws.vals_alt : c.ws.vals;
-}
-
-digs_status backward(Call& c, const float* phi, const float* w, const float* grad_proj, uint32_t* sv, float* g_mu0,
+// grad_proj = dL/dI, or nullptr when ws.dldi already holds dL/dI * |X - s|.
+digs_status backward(Call& c, const float* phi, const float* w, const float* grad_proj, float* g_mu0,
                      float* g_scale, float* g_quat, float* g_rho, float* g_phi, float* g_w, int w_rows) {
   size_t nphi = (size_t)c.L.nx * c.L.ny * c.L.nz * 3 * c.L.R;
   mark(c, 5);
   DIGS_TRY(cudaMemsetAsync(g_phi, 0, nphi * sizeof(float), c.st));
-  (void)sv;
   if (c.g.n > 0) DIGS_TRY(launch_raster_bwd(c.ws, c.views, c.c2, grad_proj, c.st));
   mark(c, 6);
   if (c.g.n > 0)
@@ -297,8 +296,7 @@ digs_status digs_project_fwd(const DigsGaussians* g, const DigsLattice* lat, con
   if (s != DIGS_OK) return s;
   if (P == 0) return DIGS_OK;
   if (!proj) return DIGS_ERR_ARG;
-  uint32_t* sv = nullptr;
-  s = bin(c, phi, w, &sv);
+  s = bin(c, phi, w);
   if (s != DIGS_OK) return s;
   DIGS_TRY(launch_raster_fwd(c.ws, c.views, c.c2, proj, nullptr, nullptr, 0.f, c.st));
   mark(c, 4);
@@ -325,15 +323,11 @@ digs_status digs_project_bwd(const DigsGaussians* g, const DigsLattice* lat, con
     }
     return DIGS_OK;
   }
-  uint32_t* sv = nullptr;
-  if (opts && (opts->flags & DIGS_FLAG_REUSE_BINNING)) {
-    sv = sorted_vals_of(c);
-    c.ws.svals = sv;
-  } else {
-    s = bin(c, phi, w, &sv);
+  if (!(opts && (opts->flags & DIGS_FLAG_REUSE_BINNING))) {  // else the records of the forward call stand
+    s = prep(c, phi, w);
     if (s != DIGS_OK) return s;
   }
-  return backward(c, phi, w, grad_proj, sv, g_mu0, g_scale, g_quat, g_rho, g_phi, g_w, P);
+  return backward(c, phi, w, grad_proj, g_mu0, g_scale, g_quat, g_rho, g_phi, g_w, P);
 }
 
 size_t digs_state_moments(int n, const DigsLattice* lat, int n_w) {
@@ -355,14 +349,13 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
   float* gr = st->grad;
   float *g_mu0 = gr, *g_ls = gr + 3 * (size_t)n, *g_q = gr + 6 * (size_t)n, *g_rho = gr + 10 * (size_t)n;
   float *g_phi = gr + 11 * (size_t)n, *g_w = g_phi + nphi;
-  uint32_t* sv = nullptr;
-  s = bin(c, st->phi, st->w, &sv);
+  s = bin(c, st->phi, st->w);
   if (s != DIGS_OK) return s;
   float inv_count = 1.f / ((float)B * c.ws.nu * c.ws.nv);
   DIGS_TRY(launch_raster_fwd(c.ws, c.views, c.c2, c.ws.proj, meas, c.ws.dldi, inv_count, c.st));
   mark(c, 4);
   DIGS_TRY(launch_loss_reduce(c.ws.loss_part, B * c.ws.T, loss_out, inv_count, c.st));
-  s = backward(c, st->phi, st->w, c.ws.dldi, sv, g_mu0, g_ls, g_q, g_rho, g_phi, g_w, st->n_w);
+  s = backward(c, st->phi, st->w, nullptr, g_mu0, g_ls, g_q, g_rho, g_phi, g_w, st->n_w);
   if (s != DIGS_OK) return s;
   const DigsAdamConfig& a = st->adam;
   float lr[6];

@@ -1,9 +1,9 @@
-// Per-Gaussian backward chain: record gradients (summed over the Gaussian's tile slots) -> deformed mean
+// Per-Gaussian backward chain: record gradients (the raster backward's ten sums per pair) -> deformed mean
 // and precision factor A -> K, S, R -> reference Gaussian; then through the DI warp (Eq. 7-8) and the
 // FFD (Eq. 9-11) to the control points phi and the temporal weights w.
 //
-// Three kernels.  (1) One thread per (projection, Gaussian) pair sums the pair's backward partials over
-// its tiles (contiguous slots), runs the adjoint of the projection set-up and of A = S^-1 R^T K^-1, and
+// Three kernels.  (1) One thread per (projection, Gaussian) pair takes the pair's ten pixel sums, runs the
+// adjoint of the projection set-up and of A = S^-1 R^T K^-1, and
 // writes 25 + R numbers (dL/dmu', dL/dK, dL/ds, dL/dR, dL/drho, dL/dw_r) component-major.  (2) One thread
 // per Gaussian sums them over the projections, forms dL/du_r and dL/d(grad u_r), and scatters the FFD
 // backward to the control points: when all 32 Gaussians of a warp sit in the same lattice cell (the
@@ -148,8 +148,8 @@ template <int R>
 __global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, const float* __restrict__ ffd,
                                                       const float* __restrict__ w,
                                                       const __grid_constant__ ViewsParam views, int P,
-                                                      const uint32_t* __restrict__ offsets, long long cap,
-                                                      const float4* __restrict__ partials, float* __restrict__ padj) {
+                                                      const uint32_t* __restrict__ counts,
+                                                      const float4* __restrict__ sums, float* __restrict__ padj) {
   const int N = g.n;
   const size_t PN = (size_t)P * N;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -158,10 +158,7 @@ __global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, const float* 
   float out[kPairAdj + R];
 #pragma unroll
   for (int q = 0; q < kPairAdj + R; ++q) out[q] = 0.f;
-  uint32_t off = offsets[i], end = offsets[i + 1];
-  if ((long long)end > cap) end = (uint32_t)cap;  // pairs past the capacity were never binned
-  if (off > end) off = end;
-  if (off != end) {
+  if (counts[i] != 0u) {  // else the pair was culled by the projection set-up
     const ViewC& v = views.v[b];
     float mu0[3], inv_s[3], qh[4], Rm[9];
 #pragma unroll
@@ -194,14 +191,12 @@ __global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, const float* 
     SetupState st;
     setup_core(v, mu, A, rho, st);
     float S[10];
-#pragma unroll
-    for (int q = 0; q < 10; ++q) S[q] = 0.f;
-    for (uint32_t k = off; k < end; ++k) {  // the pair's tiles, in slot order
-      const float4* p = partials + (size_t)k * DIGS_PARTIAL_F4;
+    {
+      const float4* p = sums + i * DIGS_PARTIAL_F4;
       const float4 a = p[0], c = p[1], d = p[2];
-      S[0] += a.x; S[1] += a.y; S[2] += a.z; S[3] += a.w;
-      S[4] += c.x; S[5] += c.y; S[6] += c.z; S[7] += c.w;
-      S[8] += d.x; S[9] += d.y;
+      S[0] = a.x; S[1] = a.y; S[2] = a.z; S[3] = a.w;
+      S[4] = c.x; S[5] = c.y; S[6] = c.z; S[7] = c.w;
+      S[8] = d.x; S[9] = d.y;
     }
     // record-parameter gradients (see the raster's pair formulas)
     const float g_xc = -(2.f * (st.n00 * S[4] + st.n01 * S[5]) - st.w0 * S[6]);
@@ -371,7 +366,7 @@ cudaError_t launch_chain_bwd(const GaussPtrs& g, const LatticeC& L, const float*
 #define DIGS_CH(RR)                                                                                             \
   k_ffd_hessian<RR><<<gb, 128, 0, st>>>(g, L, phi, ws.ffd2);                                                    \
   if (PN > 0)                                                                                                   \
-    k_pair_adjoint<RR><<<ga, 256, 0, st>>>(g, ws.ffd, w, views, P, ws.offsets, ws.cap, ws.partials, ws.padj);   \
+    k_pair_adjoint<RR><<<ga, 256, 0, st>>>(g, ws.ffd, w, views, P, ws.counts, ws.grec, ws.padj);                 \
   k_gauss_bwd<RR><<<gb, kChainThreads, 0, st>>>(g, L, ws.ffd, ws.ffd2, w, views, P, ws.padj, g_mu0, g_scale,     \
                                                g_quat, g_rho, g_phi)
   switch (L.R) {

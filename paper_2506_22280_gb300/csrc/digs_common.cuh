@@ -7,7 +7,7 @@
 #include "digs.h"
 
 #define DIGS_REC_F4 3              // a (projection, Gaussian) record is 3 float4 = 48 bytes
-#define DIGS_PARTIAL_F4 3          // a (tile, Gaussian) backward partial is 3 float4 = 48 bytes
+#define DIGS_PARTIAL_F4 3          // the backward's ten sums of a record, padded to 3 float4 = 48 bytes
 #define DIGS_FOLD_EPS 1e-6f        // det K at or below this: the deformation folds, drop the Gaussian
 #define DIGS_SQRT_2PI 2.5066282746310002f
 #define DIGS_LOG2E 1.4426950408889634f

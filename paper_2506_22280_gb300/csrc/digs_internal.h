@@ -30,11 +30,9 @@ struct Workspace {
   uint32_t* vals_alt;     // [cap]
   uint32_t* rid;          // [cap] (projection, Gaussian) record of each slot
   uint32_t* srid;         // [cap] record of each sorted position
-  uint32_t* inv;          // [cap] sorted position of each slot (optional)
-  uint32_t* svals;        // the sorted slot values of the current binning (one of vals / vals_alt)
   uint32_t* hist;         // radix histograms [256][sort blocks]
   uint2* ranges;          // [P * T] sorted-range of each (projection, tile)
-  float4* partials;       // [cap * 3] backward partial sums per slot
+  float4* grec;           // [P * n * 3] backward: the ten pixel sums of each (projection, Gaussian) record
   float* gw_part;         // [gauss blocks][P * R]
   float* ffd;             // [12 R][n]: u_r (3R components) then grad u_r (9R) at each mean
   float* ffd2;            // [18 R][n]: second derivatives of u_r (6 per component)
@@ -60,10 +58,10 @@ size_t scan_tmp_words(int n);
 cudaError_t radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, const uint32_t* n_dev,
                        long long cap, int bits, uint32_t* hist, uint32_t* scan_tmp, int n_sort_blocks,
                        uint32_t** out_keys, uint32_t** out_vals, cudaStream_t st);
-// Per-(projection, tile) ranges of the sorted keys, plus srid[k] = rid[slot(k)] and inv[slot(k)] = k.
+// Per-(projection, tile) ranges of the sorted keys, plus srid[k] = rid[slot(k)].
 cudaError_t tile_ranges(const uint32_t* sorted_keys, const uint32_t* sorted_vals, const uint32_t* rid,
                         const uint32_t* n_dev, long long cap, uint2* ranges, int n_ranges, uint32_t* srid,
-                        uint32_t* inv, cudaStream_t st);
+                        cudaStream_t st);
 int sort_blocks(long long cap);
 
 // prep.cu
@@ -76,6 +74,7 @@ cudaError_t launch_emit(const Workspace& ws, cudaStream_t st);
 // raster.cu
 cudaError_t launch_raster_fwd(const Workspace& ws, const ViewsParam& views, float c2, float* proj, const float* meas,
                               float* dldi, float inv_count, cudaStream_t st);
+// grad_proj = dL/dI, or nullptr when ws.dldi already holds dL/dI * |X - s| (from the step's forward).
 cudaError_t launch_raster_bwd(const Workspace& ws, const ViewsParam& views, float c2, const float* grad_proj,
                               cudaStream_t st);
 cudaError_t launch_loss_reduce(const float* part, int n, float* out, float scale, cudaStream_t st);

@@ -16,10 +16,13 @@
 // cubic term (FMA pipe) and the only SFU operation per pixel is the exp2.
 //
 // Forward: each warp adds into its own tile accumulator (no atomics); warps merge in a fixed order, so
-// the result is deterministic.  Backward: each lane accumulates seven sums per pixel of its pair, turns
-// them into the ten sufficient statistics of the record gradient, the warp reduces them with a
-// transposed 16-shuffle butterfly and ten lanes write them to the pair's sorted position; the
-// per-Gaussian chain kernel adds a Gaussian's positions in slot order (again no atomics).
+// the result is deterministic.
+//
+// Backward: needs no tile lists.  One warp per (projection, Gaussian) record sweeps the record's whole
+// pixel box (in 32-column slices), with the same lane layouts, reading g = dL/dI * |X - s| straight from
+// the projection-sized image (L1/L2 resident).  Each lane accumulates seven sums per pixel of its pair
+// and turns them into the ten sufficient statistics of the record gradient; the warp reduces them with
+// a transposed 16-shuffle butterfly and ten lanes write them to the record's slot (no atomics).
 #include "digs_internal.h"
 
 namespace digs {
@@ -99,7 +102,6 @@ struct RasterSmem {
   static constexpr size_t map_bytes = (TS + 1) * 32 * sizeof(int2);
   static constexpr size_t head = rec_bytes + info_bytes + map_bytes;
   static constexpr size_t fwd = head + kRasterWarps * TS * TS * sizeof(float);
-  static constexpr size_t bwd = head + TS * TS * sizeof(float);
 };
 
 // Lane layout for a box w pixels wide (see the file comment), packed in an int2:
@@ -126,24 +128,19 @@ __device__ __forceinline__ int2 lane_layout(int w, int l) {
 template <int TS>
 struct Stage {
   float4* rec;    // [2][kChunk * 3] records
-  int4* info;     // [2][kChunk]: (smem offset | w << 10 | h << 16 | poly << 28, dx0, dy0, slot)
+  int4* info;     // [2][kChunk]: (smem offset | w << 10 | h << 16 | poly << 28, dx0, dy0, unused)
   int2* lanemap;  // [TS + 1][32] lane layouts
   __device__ void init(unsigned char* sm) {
     rec = (float4*)sm;
     info = (int4*)(sm + RasterSmem<TS>::rec_bytes);
     lanemap = (int2*)(sm + RasterSmem<TS>::rec_bytes + RasterSmem<TS>::info_bytes);
     for (int i = threadIdx.x; i < (TS + 1) * 32; i += kRasterThreads) lanemap[i] = lane_layout<TS>(i >> 5, i & 31);
-    slot0 = slot1 = 0u;
   }
   // Enqueue the copies of chunk [base, end) into buffer `buf` (commits a group even when empty).
-  uint32_t slot0, slot1;  // pre-sort slot of this thread's entry in each buffer (backward only)
-  __device__ void issue(const float4* __restrict__ grec, const uint32_t* __restrict__ srid,
-                        const uint32_t* __restrict__ svals, uint32_t base, uint32_t end, int buf) {
+  __device__ void issue(const float4* __restrict__ grec, const uint32_t* __restrict__ srid, uint32_t base,
+                        uint32_t end, int buf) {
     uint32_t k = base + threadIdx.x;
     if (k < end) {
-      if (svals) {
-        if (buf) slot1 = svals[k]; else slot0 = svals[k];
-      }
       const float4* src = grec + (size_t)srid[k] * DIGS_REC_F4;
       float4* dst = rec + ((size_t)buf * kChunk + threadIdx.x) * DIGS_REC_F4;
 #pragma unroll
@@ -164,7 +161,7 @@ struct Stage {
     if (w <= 0 || h <= 0) { w = 1; h = 0; x0 = 0; y0 = 0; }  // keys come from the box: kept as a guard
     int packed = (y0 * TS + x0) | (w << 10) | (h << 16) | ((__float_as_int(c.w) & 1) << 28);
     info[buf * kChunk + threadIdx.x] = make_int4(packed, __float_as_int((float)(ox + x0) - a.x),
-                                                 __float_as_int((float)(oy + y0) - a.y), (int)(buf ? slot1 : slot0));
+                                                 __float_as_int((float)(oy + y0) - a.y), 0);
   }
 };
 
@@ -257,10 +254,10 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
   const ViewC& v = views.v[b];
   float* accw = acc + warp * TS * TS;
   unsigned n_box = 0, n_cut = 0;
-  if (rg.x < rg.y) S.issue(grec, srid, nullptr, rg.x, rg.y, 0);
+  if (rg.x < rg.y) S.issue(grec, srid, rg.x, rg.y, 0);
   for (uint32_t base = rg.x, it = 0; base < rg.y; base += kChunk, ++it) {
     const int buf = it & 1;
-    S.issue(grec, srid, nullptr, base + kChunk, rg.y, buf ^ 1);
+    S.issue(grec, srid, base + kChunk, rg.y, buf ^ 1);
     cp_async_wait_prev();
     S.derive(base, rg.y, buf, ox, oy);
     __syncthreads();
@@ -288,13 +285,14 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
       float s = 0.f;
 #pragma unroll
       for (int w = 0; w < kRasterWarps; ++w) s += acc[w * TS * TS + p];
-      float I = s * pixel_ray_length(v, (float)px, (float)py);
+      const float lp = pixel_ray_length(v, (float)px, (float)py);
+      float I = s * lp;
       size_t idx = ((size_t)b * nv + py) * nu + px;
       if (proj) proj[idx] = I;
       if (meas) {
         float res = I - meas[idx];
         lsum = fmaf(res, res, lsum);
-        if (dldi) dldi[idx] = 2.f * res * inv_count;
+        if (dldi) dldi[idx] = 2.f * res * inv_count * lp;  // dL/dI * |X - s|, what the backward consumes
       }
     }
   }
@@ -343,20 +341,44 @@ __device__ __forceinline__ void warp_reduce_store10(const float v[10], float* ou
   if ((lane & 1) == 0 && idx < 10) out[idx] = x[0];
 }
 
-// Backward over the lane's pixel pairs; gp points at dL/dI * |X - s| of the lane's first pixel.
-// Sv receives the lane's share of the ten record-gradient sums: sum g V/amp; sum dL/dnum (dx^2, dx dy,
-// dy^2); sum dL/dnum (dx, dy); sum dL/dt (1, dx, dy); sum dL/dkappa.
-template <int TS, bool POLY>
-__device__ __forceinline__ void bwd_pixels(const EntryLane& L, const float* gp, float c2, float Sv[10]) {
-  const f2 DX = f2_pack(L.dx1, L.dx2);
-  const f2 AQ = f2_mul(f2_mul(f2_dup(L.n00), DX), DX), BQ = f2_mul(f2_dup(L.n01x2), DX);
-  const f2 T0 = f2_fma(f2_dup(L.wn0), DX, f2_dup(1.f));
-  const f2 N11 = f2_dup(L.n11), WN1 = f2_dup(L.wn1), KAP = f2_dup(L.kappa), AMPH = f2_dup(0.5f * L.amp);
-  const f2 KNEG = f2_dup(kNegHalfLog2e), MONE = f2_dup(-1.f), STEP = f2_dup((float)L.ystep);
-  const int pstep = L.ystep * TS;
-  f2 DY = f2_pack(L.dy1, L.dy2);
+// ---- backward: one warp per (projection, Gaussian) record, over the record's whole pixel box -------
+
+// Lane layout for a box (or a 32-column slice of one) w pixels wide and h high; see the file comment.
+struct BoxLanes {
+  int c, r0, pdx, pdy, ystep;
+  bool active, col2;
+};
+__device__ __forceinline__ BoxLanes box_lanes(int w, int h, int lane) {
+  BoxLanes L;
+  int cw, s;
+  if (w <= 16) {
+    cw = w; s = 32 / w; L.pdx = 0; L.pdy = s; L.ystep = 2 * s;
+  } else {
+    cw = (w + 1) >> 1; s = 32 / cw; L.pdx = cw; L.pdy = 0; L.ystep = s;
+  }
+  L.c = lane % cw;
+  L.r0 = lane / cw;
+  L.active = L.r0 < s && L.r0 < h;
+  L.col2 = L.c + L.pdx < w;
+  return L;
+}
+
+// Adds the lane's share of the ten record-gradient sums: sum g V/amp; sum dL/dnum (dx^2, dx dy, dy^2);
+// sum dL/dnum (dx, dy); sum dL/dt (1, dx, dy); sum dL/dkappa.  gp points at g = dL/dI * |X - s| of the
+// lane's first pixel in the projection image (row pitch nu); (dx1, dy1) is that pixel's offset.
+template <bool POLY>
+__device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const BoxLanes& B, int h, float dx1, float dy1,
+                                               const float* __restrict__ gp, int nu, float c2, float Sv[10]) {
+  const float dx2 = dx1 + (float)B.pdx;
+  const f2 DX = f2_pack(dx1, dx2);
+  const f2 AQ = f2_mul(f2_mul(f2_dup(R0.n00), DX), DX), BQ = f2_mul(f2_dup(R0.n01x2), DX);
+  const f2 T0 = f2_fma(f2_dup(R0.wn0), DX, f2_dup(1.f));
+  const f2 N11 = f2_dup(R0.n11), WN1 = f2_dup(R0.wn1), KAP = f2_dup(R0.kappa), AMPH = f2_dup(0.5f * R0.amp);
+  const f2 KNEG = f2_dup(kNegHalfLog2e), MONE = f2_dup(-1.f), STEP = f2_dup((float)B.ystep);
+  const int pstep = B.ystep * nu, d2 = B.pdy * nu + B.pdx;
+  f2 DY = f2_pack(dy1, dy1 + (float)B.pdy);
   f2 S0 = f2_dup(0.f), S1 = S0, S2 = S0, S3 = S0, S4 = S0, S5 = S0, S6 = S0;
-  for (int r = L.r0; r < L.h; r += L.ystep, DY = f2_add(DY, STEP), gp += pstep) {
+  for (int r = B.r0; r < h; r += B.ystep, DY = f2_add(DY, STEP), gp += pstep) {
     f2 NUM = f2_fma(DY, f2_fma(N11, DY, BQ), AQ);
     f2 T = f2_fma(WN1, DY, T0);
     f2 D = f2_fma(T, T, f2_mul(KAP, NUM));
@@ -367,8 +389,8 @@ __device__ __forceinline__ void bwd_pixels(const EntryLane& L, const float* gp, 
     float na, nb, da, db;
     f2_unpack(NUM, na, nb);
     f2_unpack(D, da, db);
-    float ga = (na <= c2 * da) ? gp[0] : 0.f;               // dL/dI * |X - s| inside the cutoff
-    float gb = ((TS <= 16 || L.col2) && r + L.pdy < L.h && nb <= c2 * db) ? gp[L.d2] : 0.f;
+    const float ga = (na <= c2 * da) ? __ldg(gp) : 0.f;                                     // E <= cutoff^2
+    const float gb = (B.col2 && r + B.pdy < h && nb <= c2 * db) ? __ldg(gp + d2) : 0.f;  // partner in the box
     f2 G = f2_pack(ga, gb);
     S0 = f2_fma(G, BV, S0);
     f2 AL = f2_mul(f2_mul(G, AMPH), f2_mul(BV, INVD));     // dL/dV * V / (2 D)
@@ -386,10 +408,10 @@ __device__ __forceinline__ void bwd_pixels(const EntryLane& L, const float* gp, 
   }
   // each pixel of the pair keeps its column, so its dx-moments follow from its dy-moments
   float a[7][2];
-  f2 Sp[7] = {S0, S1, S2, S3, S4, S5, S6};
+  const f2 Sp[7] = {S0, S1, S2, S3, S4, S5, S6};
 #pragma unroll
   for (int i = 0; i < 7; ++i) f2_unpack(Sp[i], a[i][0], a[i][1]);
-  const float dxs[2] = {L.dx1, L.dx2};
+  const float dxs[2] = {dx1, dx2};
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const float dx = dxs[j];
@@ -406,49 +428,45 @@ __device__ __forceinline__ void bwd_pixels(const EntryLane& L, const float* gp, 
   }
 }
 
-template <int TS>
-__global__ void __launch_bounds__(kRasterThreads) k_raster_bwd(
-    const float4* __restrict__ grec, const uint32_t* __restrict__ srid, const uint2* __restrict__ ranges,
-    const __grid_constant__ ViewsParam views, int tiles_x, int T, int nu, int nv, float c2,
-    const float* __restrict__ grad_proj, const uint32_t* __restrict__ svals, float* __restrict__ partials) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const uint2 rg = ranges[(size_t)blockIdx.y * T + blockIdx.x];
-  if (rg.x == rg.y) return;
-  Stage<TS> S;
-  S.init(smem);
-  float* gpix = (float*)(smem + RasterSmem<TS>::head);  // [TS * TS] dL/dI * |pixel - source|
-  const int b = blockIdx.y, tile = blockIdx.x;
-  const int ox = (tile % tiles_x) * TS, oy = (tile / tiles_x) * TS;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const ViewC& v = views.v[b];
-  for (int p = threadIdx.x; p < TS * TS; p += kRasterThreads) {
-    int px = ox + p % TS, py = oy + p / TS;
-    float g = 0.f;
-    if (px < nu && py < nv)
-      g = grad_proj[((size_t)b * nv + py) * nu + px] * pixel_ray_length(v, (float)px, (float)py);
-    gpix[p] = g;
-  }
-  S.issue(grec, srid, svals, rg.x, rg.y, 0);
-  for (uint32_t base = rg.x, it = 0; base < rg.y; base += kChunk, ++it) {
-    const int buf = it & 1;
-    S.issue(grec, srid, svals, base + kChunk, rg.y, buf ^ 1);
-    cp_async_wait_prev();
-    S.derive(base, rg.y, buf, ox, oy);
-    __syncthreads();
-    const int cnt = min((int)(rg.y - base), kChunk);
-    for (int e = warp; e < cnt; e += kRasterWarps) {
-      const EntryLane L = load_entry<TS>(S, buf, e, lane);
-      float Sv[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (L.active) {
-        if (L.poly)
-          bwd_pixels<TS, true>(L, gpix + L.off, c2, Sv);
+// One warp per (projection, Gaussian) record: the ten sums over every pixel of the record's box, reduced
+// over the warp and written to grec[record] (12 floats).  Records whose Gaussian was culled get zeros.
+__global__ void __launch_bounds__(256) k_raster_bwd(const float4* __restrict__ rec, const uint32_t* __restrict__ counts,
+                                                    long long PN, int N, int nu, int nv, const float* __restrict__ gpix,
+                                                    float c2, float* __restrict__ grec) {
+  const int lane = threadIdx.x & 31;
+  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= PN) return;  // whole warps
+  float Sv[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (counts[i] != 0u) {
+    const Rec R0 = load_rec(rec + (size_t)i * DIGS_REC_F4);
+    const int b = (int)(i / N);
+    const int x0 = R0.bx & 0xffff, x1 = R0.bx >> 16, y0 = R0.by & 0xffff, y1 = R0.by >> 16;
+    const int w = x1 - x0 + 1, h = y1 - y0 + 1;
+    const float* gimg = gpix + (size_t)b * nv * nu;
+    for (int cx = 0; cx < w; cx += 32) {  // boxes wider than 32 pixels: 32-column slices
+      const BoxLanes B = box_lanes(min(32, w - cx), h, lane);
+      if (B.active) {
+        const int px = x0 + cx + B.c, py = y0 + B.r0;
+        const float dx1 = (float)px - R0.xc, dy1 = (float)py - R0.yc;
+        const float* gp = gimg + (size_t)py * nu + px;
+        if (R0.poly)
+          bwd_box_pixels<true>(R0, B, h, dx1, dy1, gp, nu, c2, Sv);
         else
-          bwd_pixels<TS, false>(L, gpix + L.off, c2, Sv);
+          bwd_box_pixels<false>(R0, B, h, dx1, dy1, gp, nu, c2, Sv);
       }
-      warp_reduce_store10(Sv, partials + (size_t)S.info[buf * kChunk + e].w * (DIGS_PARTIAL_F4 * 4), lane);  // pre-sort slot
     }
-    __syncthreads();
   }
+  warp_reduce_store10(Sv, grec + (size_t)i * (DIGS_PARTIAL_F4 * 4), lane);
+}
+
+// g = dL/dI * |X - s| for every pixel (the per-pixel factor of the line integral, applied once).
+__global__ void __launch_bounds__(256) k_gpix(const float* __restrict__ grad_proj, const __grid_constant__ ViewsParam views,
+                                              int nu, int nv, float* __restrict__ gpix) {
+  const int b = blockIdx.y;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nu * nv) return;
+  const size_t idx = (size_t)b * nu * nv + p;
+  gpix[idx] = grad_proj[idx] * pixel_ray_length(views.v[b], (float)(p % nu), (float)(p / nu));
 }
 
 template <int TS>
@@ -475,22 +493,6 @@ static cudaError_t fwd_launch(const Workspace& ws, const ViewsParam& views, floa
   return cudaGetLastError();
 }
 
-template <int TS>
-static cudaError_t bwd_launch(const Workspace& ws, const ViewsParam& views, float c2, const float* grad_proj,
-                              cudaStream_t st) {
-  const size_t smem = RasterSmem<TS>::bwd;
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_raster_bwd<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = true;
-  }
-  dim3 grid(ws.T, ws.P);
-  k_raster_bwd<TS><<<grid, kRasterThreads, smem, st>>>(ws.rec, ws.srid, ws.ranges, views, ws.tiles_x, ws.T, ws.nu,
-                                                        ws.nv, c2, grad_proj, ws.svals, (float*)ws.partials);
-  note_launches(1);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_raster_fwd(const Workspace& ws, const ViewsParam& views, float c2, float* proj, const float* meas,
                               float* dldi, float inv_count, cudaStream_t st) {
   if (ws.P <= 0) return cudaSuccess;
@@ -505,13 +507,18 @@ cudaError_t launch_raster_fwd(const Workspace& ws, const ViewsParam& views, floa
 
 cudaError_t launch_raster_bwd(const Workspace& ws, const ViewsParam& views, float c2, const float* grad_proj,
                               cudaStream_t st) {
-  if (ws.P <= 0) return cudaSuccess;
-  switch (ws.tile) {
-    case 8: return bwd_launch<8>(ws, views, c2, grad_proj, st);
-    case 16: return bwd_launch<16>(ws, views, c2, grad_proj, st);
-    case 32: return bwd_launch<32>(ws, views, c2, grad_proj, st);
+  if (ws.P <= 0 || ws.n <= 0) return cudaSuccess;
+  if (grad_proj) {  // else ws.dldi already holds dL/dI * |X - s| (written by the step's forward)
+    dim3 g((ws.nu * ws.nv + 255) / 256, ws.P);
+    k_gpix<<<g, 256, 0, st>>>(grad_proj, views, ws.nu, ws.nv, ws.dldi);
+    note_launches(1);
   }
-  return cudaErrorInvalidValue;
+  const long long PN = (long long)ws.P * ws.n;
+  const long long blocks = (PN * 32 + 255) / 256;
+  k_raster_bwd<<<(unsigned)blocks, 256, 0, st>>>(ws.rec, ws.counts, PN, ws.n, ws.nu, ws.nv, ws.dldi, c2,
+                                                 (float*)ws.grec);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(1024) k_loss_reduce(const float* __restrict__ part, int n, float* out,
