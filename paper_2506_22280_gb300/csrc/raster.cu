@@ -317,63 +317,58 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
   }
 }
 
-// Sum ten per-lane values over the warp; value i ends in the even lane whose bits 4..1 spell i.
-// Recursive halving: each exchange sends the half of the values the partner keeps (8 + 4 + 2 + 1 + 1
-// shuffles instead of 10 x 5).
-__device__ __forceinline__ void warp_reduce_store10(const float v[10], float* out, int lane) {
-  float x[16];
-#pragma unroll
-  for (int i = 0; i < 10; ++i) x[i] = v[i];
-#pragma unroll
-  for (int i = 10; i < 16; ++i) x[i] = 0.f;
-#pragma unroll
-  for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
-    const bool hi = (lane & bit) != 0;
-#pragma unroll
-    for (int i = 0; i < half; ++i) {
-      float send = hi ? x[i] : x[i + half];
-      float keep = hi ? x[i + half] : x[i];
-      x[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+// ---- backward: one half-warp per (projection, Gaussian) record, over the record's whole pixel box ----
+
+constexpr int kBwdThreads = 256;
+constexpr int kBwdRecords = kBwdThreads / 16;  // records per CTA
+
+// Half-warp lane layout of a box slice w <= 16 pixels wide, per w: cw | s << 5 | m << 10, where cw is
+// the number of lane columns, s the rows covered per pass and m = ceil(256 / cw), so that
+// (l * m) >> 8 = l / cw exactly for l < 16.  w <= 8: lane l takes column l mod w and the row pair
+// (r, r + s), s = 16 div w, stepping 2s rows.  8 < w <= 16: the column pair (c, c + ceil(w/2)),
+// stepping s = 16 div ceil(w/2) rows.
+struct HalfLaneTable {
+  int v[17];
+  constexpr HalfLaneTable() : v() {
+    for (int w = 1; w <= 16; ++w) {
+      const int cw = w <= 8 ? w : (w + 1) / 2;
+      v[w] = cw | ((16 / cw) << 5) | (((256 + cw - 1) / cw) << 10);
     }
   }
-  x[0] += __shfl_xor_sync(0xffffffffu, x[0], 1);
-  const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-  if ((lane & 1) == 0 && idx < 10) out[idx] = x[0];
-}
+};
+__constant__ HalfLaneTable kHalfLanes = HalfLaneTable();
 
-// ---- backward: one warp per (projection, Gaussian) record, over the record's whole pixel box -------
-
-// Lane layout for a box (or a 32-column slice of one) w pixels wide and h high; see the file comment.
-struct BoxLanes {
+struct HalfLanes {
   int c, r0, pdx, pdy, ystep;
   bool active, col2;
 };
-__device__ __forceinline__ BoxLanes box_lanes(int w, int h, int lane) {
-  BoxLanes L;
-  int cw, s;
-  if (w <= 16) {
-    cw = w; s = 32 / w; L.pdx = 0; L.pdy = s; L.ystep = 2 * s;
-  } else {
-    cw = (w + 1) >> 1; s = 32 / cw; L.pdx = cw; L.pdy = 0; L.ystep = s;
-  }
-  L.c = lane % cw;
-  L.r0 = lane / cw;
-  L.active = L.r0 < s && L.r0 < h;
+__device__ __forceinline__ HalfLanes half_lanes(int w, int h, int hl) {
+  const int t = kHalfLanes.v[w];
+  const int cw = t & 31, s = (t >> 5) & 31, m = t >> 10;
+  const int q = (hl * m) >> 8;
+  const bool rows = w <= 8;
+  HalfLanes L;
+  L.c = hl - q * cw;
+  L.r0 = q;
+  L.pdx = rows ? 0 : cw;
+  L.pdy = rows ? s : 0;
+  L.ystep = rows ? 2 * s : s;
+  L.active = q < s && q < h;
   L.col2 = L.c + L.pdx < w;
   return L;
 }
 
-// Adds the lane's share of the ten record-gradient sums: sum g V/amp; sum dL/dnum (dx^2, dx dy, dy^2);
-// sum dL/dnum (dx, dy); sum dL/dt (1, dx, dy); sum dL/dkappa.  gp points at g = dL/dI * |X - s| of the
-// lane's first pixel in the projection image (row pitch nu); (dx1, dy1) is that pixel's offset.
-template <bool POLY>
-__device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const BoxLanes& B, int h, float dx1, float dy1,
+// Adds the lane's share of the ten record-gradient sums, all but the first divided by amp / 2:
+// sum g V/amp; sum dL/dnum (dx^2, dx dy, dy^2); sum dL/dnum (dx, dy); sum dL/dt (1, dx, dy);
+// sum dL/dkappa.  gp points at g = dL/dI * |X - s| of the lane's first pixel in the projection image
+// (row pitch nu); (dx1, dy1) is that pixel's offset from the projected mean.
+__device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const HalfLanes& B, int h, float dx1, float dy1,
                                                const float* __restrict__ gp, int nu, float c2, float Sv[10]) {
   const float dx2 = dx1 + (float)B.pdx;
   const f2 DX = f2_pack(dx1, dx2);
   const f2 AQ = f2_mul(f2_mul(f2_dup(R0.n00), DX), DX), BQ = f2_mul(f2_dup(R0.n01x2), DX);
   const f2 T0 = f2_fma(f2_dup(R0.wn0), DX, f2_dup(1.f));
-  const f2 N11 = f2_dup(R0.n11), WN1 = f2_dup(R0.wn1), KAP = f2_dup(R0.kappa), AMPH = f2_dup(0.5f * R0.amp);
+  const f2 N11 = f2_dup(R0.n11), WN1 = f2_dup(R0.wn1), KAP = f2_dup(R0.kappa);
   const f2 KNEG = f2_dup(kNegHalfLog2e), MONE = f2_dup(-1.f), STEP = f2_dup((float)B.ystep);
   const int pstep = B.ystep * nu, d2 = B.pdy * nu + B.pdx;
   f2 DY = f2_pack(dy1, dy1 + (float)B.pdy);
@@ -382,7 +377,7 @@ __device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const BoxLanes& B,
     f2 NUM = f2_fma(DY, f2_fma(N11, DY, BQ), AQ);
     f2 T = f2_fma(WN1, DY, T0);
     f2 D = f2_fma(T, T, f2_mul(KAP, NUM));
-    f2 RS = f2_inv_sqrt<POLY>(D);
+    f2 RS = f2_inv_sqrt<false>(D);
     f2 INVD = f2_mul(RS, RS);
     f2 E = f2_mul(NUM, INVD);
     f2 BV = f2_mul(RS, f2_exp2(f2_mul(E, KNEG)));      // V / amp
@@ -393,7 +388,7 @@ __device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const BoxLanes& B,
     const float gb = (B.col2 && r + B.pdy < h && nb <= c2 * db) ? __ldg(gp + d2) : 0.f;  // partner in the box
     f2 G = f2_pack(ga, gb);
     S0 = f2_fma(G, BV, S0);
-    f2 AL = f2_mul(f2_mul(G, AMPH), f2_mul(BV, INVD));     // dL/dV * V / (2 D)
+    f2 AL = f2_mul(G, f2_mul(BV, INVD));                     // (dL/dV * V / (2 D)) / (amp / 2)
     f2 EM1 = f2_add(E, MONE);
     f2 GNUM = f2_mul(AL, f2_fma(KAP, EM1, MONE));          // dL/dnum
     f2 AEM = f2_mul(AL, EM1);
@@ -428,35 +423,77 @@ __device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const BoxLanes& B,
   }
 }
 
-// One warp per (projection, Gaussian) record: the ten sums over every pixel of the record's box, reduced
-// over the warp and written to grec[record] (12 floats).  Records whose Gaussian was culled get zeros.
-__global__ void __launch_bounds__(256) k_raster_bwd(const float4* __restrict__ rec, const uint32_t* __restrict__ counts,
-                                                    long long PN, int N, int nu, int nv, const float* __restrict__ gpix,
-                                                    float c2, float* __restrict__ grec) {
-  const int lane = threadIdx.x & 31;
-  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (i >= PN) return;  // whole warps
+// Sum ten per-lane values over each half-warp (lanes hl = 0..15) and store them to out[0..9].
+// Recursive halving over an uneven split, 5 + 3 + 2 + 1 shuffles: after the xor-8 exchange a lane
+// holds five values (0-4 or 5-9), after xor-4 three of those five (local 0-2, or 3-4 plus a pad),
+// after xor-2 two, after xor-1 one, the value 5 b3 + 3 b2 + 2 b1 + b0 (b_k = bit k of hl) when that
+// lies inside its group of five.
+__device__ __forceinline__ void half_reduce_store10(const float v[10], float* out, int hl, bool store) {
+  const unsigned full = 0xffffffffu;
+  float a[5];
+  {
+    const bool hi = (hl & 8) != 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const float keep = hi ? v[5 + j] : v[j], send = hi ? v[j] : v[5 + j];
+      a[j] = keep + __shfl_xor_sync(full, send, 8);
+    }
+  }
+  float b0, b1, b2;
+  {
+    const bool hi = (hl & 4) != 0;
+    const float k0 = hi ? a[3] : a[0], k1 = hi ? a[4] : a[1], k2 = hi ? 0.f : a[2];
+    const float s0 = hi ? a[0] : a[3], s1 = hi ? a[1] : a[4], s2 = hi ? a[2] : 0.f;
+    b0 = k0 + __shfl_xor_sync(full, s0, 4);
+    b1 = k1 + __shfl_xor_sync(full, s1, 4);
+    b2 = k2 + __shfl_xor_sync(full, s2, 4);
+  }
+  float c0, c1;
+  {
+    const bool hi = (hl & 2) != 0;
+    const float k0 = hi ? b2 : b0, k1 = hi ? 0.f : b1;
+    const float s0 = hi ? b0 : b2, s1 = hi ? b1 : 0.f;
+    c0 = k0 + __shfl_xor_sync(full, s0, 2);
+    c1 = k1 + __shfl_xor_sync(full, s1, 2);
+  }
+  const bool hi = (hl & 1) != 0;
+  const float d = (hi ? c1 : c0) + __shfl_xor_sync(full, hi ? c0 : c1, 1);
+  const int bit2 = (hl >> 2) & 1;
+  const int local = 3 * bit2 + 2 * ((hl >> 1) & 1) + (hl & 1);
+  if (store && local < (bit2 ? 5 : 3)) out[((hl & 8) ? 5 : 0) + local] = d;
+}
+
+// One half-warp per (projection, Gaussian) record: the ten sums over every pixel of the record's box,
+// reduced over the half-warp and written to grec[record] (12 floats, the last two unused).  Records
+// whose Gaussian was culled get zeros.  Grid: (ceil(N / 16), P).
+__global__ void __launch_bounds__(kBwdThreads, 4) k_raster_bwd(const float4* __restrict__ rec,
+                                                                const uint32_t* __restrict__ counts, int N, int nu,
+                                                                int nv, const float* __restrict__ gpix, float c2,
+                                                                float* __restrict__ grec) {
+  const int hl = threadIdx.x & 15;
+  const int b = blockIdx.y;
+  const int n = blockIdx.x * kBwdRecords + (threadIdx.x >> 4);
+  const bool valid = n < N;
+  const size_t i = (size_t)b * N + (valid ? n : 0);
   float Sv[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (counts[i] != 0u) {
-    const Rec R0 = load_rec(rec + (size_t)i * DIGS_REC_F4);
-    const int b = (int)(i / N);
+  if (valid && counts[i] != 0u) {
+    const Rec R0 = load_rec(rec + i * DIGS_REC_F4);
     const int x0 = R0.bx & 0xffff, x1 = R0.bx >> 16, y0 = R0.by & 0xffff, y1 = R0.by >> 16;
     const int w = x1 - x0 + 1, h = y1 - y0 + 1;
     const float* gimg = gpix + (size_t)b * nv * nu;
-    for (int cx = 0; cx < w; cx += 32) {  // boxes wider than 32 pixels: 32-column slices
-      const BoxLanes B = box_lanes(min(32, w - cx), h, lane);
+    for (int cx = 0; cx < w; cx += 16) {  // boxes wider than 16 pixels: 16-column slices
+      const HalfLanes B = half_lanes(min(16, w - cx), h, hl);
       if (B.active) {
         const int px = x0 + cx + B.c, py = y0 + B.r0;
-        const float dx1 = (float)px - R0.xc, dy1 = (float)py - R0.yc;
         const float* gp = gimg + (size_t)py * nu + px;
-        if (R0.poly)
-          bwd_box_pixels<true>(R0, B, h, dx1, dy1, gp, nu, c2, Sv);
-        else
-          bwd_box_pixels<false>(R0, B, h, dx1, dy1, gp, nu, c2, Sv);
+        bwd_box_pixels(R0, B, h, (float)px - R0.xc, (float)py - R0.yc, gp, nu, c2, Sv);
       }
     }
+    const float amph = 0.5f * R0.amp;
+#pragma unroll
+    for (int q = 1; q < 10; ++q) Sv[q] *= amph;
   }
-  warp_reduce_store10(Sv, grec + (size_t)i * (DIGS_PARTIAL_F4 * 4), lane);
+  half_reduce_store10(Sv, grec + i * (DIGS_PARTIAL_F4 * 4), hl, valid);
 }
 
 // g = dL/dI * |X - s| for every pixel (the per-pixel factor of the line integral, applied once).
@@ -513,10 +550,8 @@ cudaError_t launch_raster_bwd(const Workspace& ws, const ViewsParam& views, floa
     k_gpix<<<g, 256, 0, st>>>(grad_proj, views, ws.nu, ws.nv, ws.dldi);
     note_launches(1);
   }
-  const long long PN = (long long)ws.P * ws.n;
-  const long long blocks = (PN * 32 + 255) / 256;
-  k_raster_bwd<<<(unsigned)blocks, 256, 0, st>>>(ws.rec, ws.counts, PN, ws.n, ws.nu, ws.nv, ws.dldi, c2,
-                                                 (float*)ws.grec);
+  dim3 grid((ws.n + kBwdRecords - 1) / kBwdRecords, ws.P);
+  k_raster_bwd<<<grid, kBwdThreads, 0, st>>>(ws.rec, ws.counts, ws.n, ws.nu, ws.nv, ws.dldi, c2, (float*)ws.grec);
   note_launches(1);
   return cudaGetLastError();
 }
