@@ -1,28 +1,26 @@
 // Tile rasteriser of the X-ray transform (Sec. 3.1, Eq. 1, 3-4) and its backward pass.
 //
-// One CTA per (projection, tile).  The tile's sorted Gaussian list is staged into shared memory in
-// chunks of 256 records (48 B each) by 16-byte cp.async copies, double-buffered so the next chunk lands
-// while the current one is processed.  The thread that staged a record also derives, once, the part of
-// the Gaussian's pixel box inside the tile (its offset from the projected mean, size and smem offset).
-//
-// A warp then takes one Gaussian at a time and its lanes sweep that w x h box two pixels per lane per
-// step in packed FP32x2 arithmetic (fma/mul/add.rn.f32x2).  Narrow boxes (w <= 16): lane l owns column
-// (l mod w), starts at row (l div w) and takes the row pair (r, r + s), s = 32 div w, stepping 2s rows.
-// Wide boxes (w > 16, 32-pixel tiles): lane l owns the column pair (c, c + ceil(w/2)) of row (l div
-// ceil(w/2)), stepping s = 32 div ceil(w/2) rows.  Per pixel, with (dx, dy) its offset from the
-// projected mean:
+// Work is done by half-warps (16 lanes), each sweeping one Gaussian's pixel box (or a 16-column slice
+// of it) two pixels per lane per step in packed FP32x2 arithmetic (fma/mul/add.rn.f32x2).  Narrow
+// slices (w <= 8): lane l owns column (l mod w), starts at row (l div w) and takes the row pair
+// (r, r + s), s = 16 div w, stepping 2s rows.  Wider slices (8 < w <= 16): lane l owns the column pair
+// (c, c + ceil(w/2)) of row (l div ceil(w/2)), stepping s = 16 div ceil(w/2) rows.  Per pixel, with
+// (dx, dy) its offset from the projected mean:
 //   num = dy (n11 dy + n01x2 dx) + n00 dx^2,  t = 1 + wn0 dx + wn1 dy,  D = t^2 + kappa num,  E = num / D.
-// D stays within 2 % of 1 for these geometries; D^-1/2 then comes from its binomial series through the
-// cubic term (FMA pipe) and the only SFU operation per pixel is the exp2.
+// The only SFU operations per pixel are the exp2 and, unless D stays within 2 % of 1 over the box
+// (then its binomial series through the cubic term is used in the forward), the reciprocal square root.
 //
-// Forward: each warp adds into its own tile accumulator (no atomics); warps merge in a fixed order, so
-// the result is deterministic.
+// Forward: one CTA per (projection, tile).  The tile's sorted Gaussian list is staged into shared
+// memory in chunks of 256 records (48 B each) by 16-byte cp.async copies, double-buffered so the next
+// chunk lands while the current one is processed; the thread that staged a record also derives, once,
+// the part of the Gaussian's box inside the tile.  Each half-warp adds its Gaussians into its own tile
+// canvas (no atomics); the 16 canvases merge in a fixed order, so the result is deterministic.
 //
-// Backward: needs no tile lists.  One warp per (projection, Gaussian) record sweeps the record's whole
-// pixel box (in 32-column slices), with the same lane layouts, reading g = dL/dI * |X - s| straight from
-// the projection-sized image (L1/L2 resident).  Each lane accumulates seven sums per pixel of its pair
-// and turns them into the ten sufficient statistics of the record gradient; the warp reduces them with
-// a transposed 16-shuffle butterfly and ten lanes write them to the record's slot (no atomics).
+// Backward: needs no tile lists.  One half-warp per (projection, Gaussian) record sweeps the record's
+// whole pixel box, reading g = dL/dI * |X - s| straight from the projection-sized image (L1/L2
+// resident).  Each lane accumulates seven sums per pixel of its pair and turns them into the ten
+// sufficient statistics of the record gradient; the half-warp reduces them with an 11-shuffle
+// recursive halving and ten lanes write them to the record's slot (no atomics).
 #include "digs_internal.h"
 
 namespace digs {
@@ -95,232 +93,7 @@ __device__ __forceinline__ f2 f2_inv_sqrt(f2 D) {
   return f2_pack(sfu_rsqrt(a), sfu_rsqrt(b));
 }
 
-template <int TS>
-struct RasterSmem {
-  static constexpr size_t rec_bytes = 2 * kChunk * DIGS_REC_F4 * sizeof(float4);
-  static constexpr size_t info_bytes = 2 * kChunk * sizeof(int4);
-  static constexpr size_t map_bytes = (TS + 1) * 32 * sizeof(int2);
-  static constexpr size_t head = rec_bytes + info_bytes + map_bytes;
-  static constexpr size_t fwd = head + kRasterWarps * TS * TS * sizeof(float);
-};
-
-// Lane layout for a box w pixels wide (see the file comment), packed in an int2:
-//  x = smem offset of the lane's first pixel | c << 10 | r0 << 15 | active << 20
-//  y = partner column offset | partner row offset << 6 | row step << 12 | partner smem delta << 19
-// (row step <= 64 needs 7 bits; the step is never 0).
-template <int TS>
-__device__ __forceinline__ int2 lane_layout(int w, int l) {
-  int cw, s, pdx, pdy, ystep;
-  if (w <= 0) return make_int2(0, 1 << 12);
-  if (w <= 16) {
-    cw = w; s = min(32 / w, TS); pdx = 0; pdy = s; ystep = 2 * s;
-  } else {
-    cw = (w + 1) / 2; s = min(32 / cw, TS); pdx = cw; pdy = 0; ystep = s;
-  }
-  int c = l % cw, r0 = l / cw;
-  int active = r0 < s ? 1 : 0;
-  if (!active) { c = 0; r0 = 0; }
-  return make_int2((r0 * TS + c) | (c << 10) | (r0 << 15) | (active << 20),
-                   pdx | (pdy << 6) | (ystep << 12) | ((pdy * TS + pdx) << 19));
-}
-
-// Per-CTA staging state.
-template <int TS>
-struct Stage {
-  float4* rec;    // [2][kChunk * 3] records
-  int4* info;     // [2][kChunk]: (smem offset | w << 10 | h << 16 | poly << 28, dx0, dy0, unused)
-  int2* lanemap;  // [TS + 1][32] lane layouts
-  __device__ void init(unsigned char* sm) {
-    rec = (float4*)sm;
-    info = (int4*)(sm + RasterSmem<TS>::rec_bytes);
-    lanemap = (int2*)(sm + RasterSmem<TS>::rec_bytes + RasterSmem<TS>::info_bytes);
-    for (int i = threadIdx.x; i < (TS + 1) * 32; i += kRasterThreads) lanemap[i] = lane_layout<TS>(i >> 5, i & 31);
-  }
-  // Enqueue the copies of chunk [base, end) into buffer `buf` (commits a group even when empty).
-  __device__ void issue(const float4* __restrict__ grec, const uint32_t* __restrict__ srid, uint32_t base,
-                        uint32_t end, int buf) {
-    uint32_t k = base + threadIdx.x;
-    if (k < end) {
-      const float4* src = grec + (size_t)srid[k] * DIGS_REC_F4;
-      float4* dst = rec + ((size_t)buf * kChunk + threadIdx.x) * DIGS_REC_F4;
-#pragma unroll
-      for (int q = 0; q < DIGS_REC_F4; ++q) cp_async16(dst + q, src + q);
-    }
-    cp_async_commit();
-  }
-  // After the chunk landed: this thread's record -> its box inside the tile.
-  __device__ void derive(uint32_t base, uint32_t end, int buf, int ox, int oy) {
-    uint32_t k = base + threadIdx.x;
-    if (k >= end) return;
-    const float4* r3 = rec + ((size_t)buf * kChunk + threadIdx.x) * DIGS_REC_F4;
-    float4 a = r3[0], c = r3[2];
-    int bx = __float_as_int(c.y), by = __float_as_int(c.z);
-    int x0 = max(bx & 0xffff, ox) - ox, x1 = min(bx >> 16, ox + TS - 1) - ox;
-    int y0 = max(by & 0xffff, oy) - oy, y1 = min(by >> 16, oy + TS - 1) - oy;
-    int w = x1 - x0 + 1, h = y1 - y0 + 1;
-    if (w <= 0 || h <= 0) { w = 1; h = 0; x0 = 0; y0 = 0; }  // keys come from the box: kept as a guard
-    int packed = (y0 * TS + x0) | (w << 10) | (h << 16) | ((__float_as_int(c.w) & 1) << 28);
-    info[buf * kChunk + threadIdx.x] = make_int4(packed, __float_as_int((float)(ox + x0) - a.x),
-                                                 __float_as_int((float)(oy + y0) - a.y), 0);
-  }
-};
-
-// Per-lane view of one staged entry.
-struct EntryLane {
-  float n00, n01x2, n11, wn0, wn1, kappa, amp;
-  float dx1, dx2, dy1, dy2;  // offsets of the lane's two first pixels from the projected mean
-  int off, d2;               // smem offset of the first pixel, delta to the partner pixel
-  int r0, pdy, ystep, h;     // first row, partner row offset, rows per step, box height
-  bool active, col2, poly;   // lane has pixels; partner column inside the box; series for D^-1/2
-};
-
-template <int TS>
-__device__ __forceinline__ EntryLane load_entry(const Stage<TS>& S, int buf, int e, int lane) {
-  const float4* r3 = S.rec + ((size_t)buf * kChunk + e) * DIGS_REC_F4;
-  float4 a = r3[0], b = r3[1], c = r3[2];
-  int4 inf = S.info[buf * kChunk + e];
-  EntryLane L;
-  L.n00 = a.z; L.n01x2 = a.w;
-  L.n11 = b.x; L.wn0 = b.y; L.wn1 = b.z; L.kappa = b.w; L.amp = c.x;
-  const int w = (inf.x >> 10) & 63;
-  L.h = (inf.x >> 16) & 63;
-  L.poly = (inf.x >> 28) & 1;
-  const int2 lm = S.lanemap[w * 32 + lane];
-  const int col = (lm.x >> 10) & 31, pdx = lm.y & 63;
-  L.r0 = (lm.x >> 15) & 31;
-  L.active = ((lm.x >> 20) & 1) && L.r0 < L.h;
-  L.pdy = (lm.y >> 6) & 63;
-  L.ystep = (lm.y >> 12) & 127;
-  L.d2 = lm.y >> 19;
-  L.col2 = TS <= 16 || col + pdx < w;  // boxes wider than 16 px only occur in 32-px tiles
-  L.off = (inf.x & 1023) + (lm.x & 1023);
-  L.dx1 = __int_as_float(inf.y) + (float)col;
-  L.dx2 = L.dx1 + (float)pdx;
-  L.dy1 = __int_as_float(inf.z) + (float)L.r0;
-  L.dy2 = L.dy1 + (float)L.pdy;
-  return L;
-}
-
-// Forward over the lane's pixel pairs; p points at the lane's first pixel in the warp's accumulator.
-template <int TS, bool POLY, bool COUNT>
-__device__ __forceinline__ void fwd_pixels(const EntryLane& L, float* p, float c2, unsigned& n_cut) {
-  const f2 DX = f2_pack(L.dx1, L.dx2);
-  const f2 A = f2_mul(f2_mul(f2_dup(L.n00), DX), DX), BQ = f2_mul(f2_dup(L.n01x2), DX);
-  const f2 T0 = f2_fma(f2_dup(L.wn0), DX, f2_dup(1.f));
-  const f2 N11 = f2_dup(L.n11), WN1 = f2_dup(L.wn1), KAP = f2_dup(L.kappa), AMP = f2_dup(L.amp);
-  const f2 C2 = f2_dup(c2), KNEG = f2_dup(kNegHalfLog2e), STEP = f2_dup((float)L.ystep);
-  const int pstep = L.ystep * TS;
-  f2 DY = f2_pack(L.dy1, L.dy2);
-  for (int r = L.r0; r < L.h; r += L.ystep, DY = f2_add(DY, STEP), p += pstep) {
-    f2 NUM = f2_fma(DY, f2_fma(N11, DY, BQ), A);
-    f2 T = f2_fma(WN1, DY, T0);
-    f2 D = f2_fma(T, T, f2_mul(KAP, NUM));
-    f2 RS = f2_inv_sqrt<POLY>(D);
-    f2 EX = f2_exp2(f2_mul(f2_mul(NUM, f2_mul(RS, RS)), KNEG));
-    f2 VAL = f2_mul(f2_mul(AMP, RS), EX);
-    f2 LIM = f2_mul(C2, D);
-    float na, nb, la, lb, va, vb;
-    f2_unpack(NUM, na, nb);
-    f2_unpack(LIM, la, lb);
-    f2_unpack(VAL, va, vb);
-    if (na <= la) {                                  // E = num / D <= cutoff^2
-      p[0] += va;
-      if (COUNT) ++n_cut;
-    }
-    // the partner may lie past the box part inside this tile (last row pair, or the column past w)
-    if ((TS <= 16 || L.col2) && r + L.pdy < L.h && nb <= lb) {
-      p[L.d2] += vb;
-      if (COUNT) ++n_cut;
-    }
-  }
-}
-
-template <int TS, bool COUNT>
-__global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
-    const float4* __restrict__ grec, const uint32_t* __restrict__ srid, const uint2* __restrict__ ranges,
-    const __grid_constant__ ViewsParam views, int tiles_x, int T, int nu, int nv, float c2, float* __restrict__ proj,
-    const float* __restrict__ meas, float* __restrict__ dldi, float* __restrict__ loss_part, float inv_count,
-    unsigned long long* __restrict__ counters) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Stage<TS> S;
-  S.init(smem);
-  float* acc = (float*)(smem + RasterSmem<TS>::head);  // [warps][TS * TS]
-  __shared__ float red[kRasterWarps];
-  const int b = blockIdx.y, tile = blockIdx.x;
-  const int ox = (tile % tiles_x) * TS, oy = (tile / tiles_x) * TS;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int p = threadIdx.x; p < kRasterWarps * TS * TS; p += kRasterThreads) acc[p] = 0.f;
-  const uint2 rg = ranges[(size_t)b * T + tile];
-  const ViewC& v = views.v[b];
-  float* accw = acc + warp * TS * TS;
-  unsigned n_box = 0, n_cut = 0;
-  if (rg.x < rg.y) S.issue(grec, srid, rg.x, rg.y, 0);
-  for (uint32_t base = rg.x, it = 0; base < rg.y; base += kChunk, ++it) {
-    const int buf = it & 1;
-    S.issue(grec, srid, base + kChunk, rg.y, buf ^ 1);
-    cp_async_wait_prev();
-    S.derive(base, rg.y, buf, ox, oy);
-    __syncthreads();
-    const int cnt = min((int)(rg.y - base), kChunk);
-    for (int e = warp; e < cnt; e += kRasterWarps) {
-      const EntryLane L = load_entry<TS>(S, buf, e, lane);
-      if (COUNT && lane == 0) {
-        int x = S.info[buf * kChunk + e].x;
-        n_box += ((x >> 10) & 63) * ((x >> 16) & 63);
-      }
-      if (L.active) {
-        if (L.poly)
-          fwd_pixels<TS, true, COUNT>(L, accw + L.off, c2, n_cut);
-        else
-          fwd_pixels<TS, false, COUNT>(L, accw + L.off, c2, n_cut);
-      }
-      __syncwarp();
-    }
-    __syncthreads();
-  }
-  float lsum = 0.f;
-  for (int p = threadIdx.x; p < TS * TS; p += kRasterThreads) {
-    int px = ox + p % TS, py = oy + p / TS;
-    if (px < nu && py < nv) {
-      float s = 0.f;
-#pragma unroll
-      for (int w = 0; w < kRasterWarps; ++w) s += acc[w * TS * TS + p];
-      const float lp = pixel_ray_length(v, (float)px, (float)py);
-      float I = s * lp;
-      size_t idx = ((size_t)b * nv + py) * nu + px;
-      if (proj) proj[idx] = I;
-      if (meas) {
-        float res = I - meas[idx];
-        lsum = fmaf(res, res, lsum);
-        if (dldi) dldi[idx] = 2.f * res * inv_count * lp;  // dL/dI * |X - s|, what the backward consumes
-      }
-    }
-  }
-  if (COUNT) {
-    unsigned c = n_cut;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0 && (n_box | c)) {
-      atomicAdd(counters, (unsigned long long)n_box);
-      atomicAdd(counters + 1, (unsigned long long)c);
-    }
-  }
-  if (loss_part) {
-    lsum = warp_sum(lsum);
-    if (lane == 0) red[warp] = lsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float s = 0.f;
-      for (int w = 0; w < kRasterWarps; ++w) s += red[w];
-      loss_part[(size_t)b * T + tile] = s;
-    }
-  }
-}
-
-// ---- backward: one half-warp per (projection, Gaussian) record, over the record's whole pixel box ----
-
-constexpr int kBwdThreads = 256;
-constexpr int kBwdRecords = kBwdThreads / 16;  // records per CTA
+// ---- lane layouts (forward and backward) ---------------------------------------------------------
 
 // Half-warp lane layout of a box slice w <= 16 pixels wide, per w: cw | s << 5 | m << 10, where cw is
 // the number of lane columns, s the rows covered per pass and m = ceil(256 / cw), so that
@@ -357,6 +130,197 @@ __device__ __forceinline__ HalfLanes half_lanes(int w, int h, int hl) {
   L.col2 = L.c + L.pdx < w;
   return L;
 }
+
+// ---- forward ------------------------------------------------------------------------------------
+
+constexpr int kHalves = kRasterThreads / 16;  // half-warps per CTA, one canvas each
+
+template <int TS>
+struct RasterSmem {
+  static constexpr size_t rec_bytes = 2 * kChunk * DIGS_REC_F4 * sizeof(float4);
+  static constexpr size_t info_bytes = 2 * kChunk * sizeof(int4);
+  static constexpr size_t head = rec_bytes + info_bytes;
+  // Canvas rows are TS + 1 floats apart and consecutive canvases 16 banks apart, so the rows of one
+  // half-warp's pixels and the two half-warps of a warp fall on different banks.
+  static constexpr int pitch = TS + 1;
+  static constexpr int canvas = TS * pitch + ((16 - (TS * pitch) % 32) + 32) % 32;
+  static constexpr size_t fwd = head + kHalves * canvas * sizeof(float);
+};
+
+// Per-CTA staging state.
+template <int TS>
+struct Stage {
+  float4* rec;    // [2][kChunk * 3] records
+  int4* info;     // [2][kChunk]: (canvas offset y0 pitch + x0 | w << 11 | h << 17 | poly << 28, dx0, dy0, 0)
+  __device__ void init(unsigned char* sm) {
+    rec = (float4*)sm;
+    info = (int4*)(sm + RasterSmem<TS>::rec_bytes);
+  }
+  // Enqueue the copies of chunk [base, end) into buffer `buf` (commits a group even when empty).
+  __device__ void issue(const float4* __restrict__ grec, const uint32_t* __restrict__ srid, uint32_t base,
+                        uint32_t end, int buf) {
+    uint32_t k = base + threadIdx.x;
+    if (k < end) {
+      const float4* src = grec + (size_t)srid[k] * DIGS_REC_F4;
+      float4* dst = rec + ((size_t)buf * kChunk + threadIdx.x) * DIGS_REC_F4;
+#pragma unroll
+      for (int q = 0; q < DIGS_REC_F4; ++q) cp_async16(dst + q, src + q);
+    }
+    cp_async_commit();
+  }
+  // After the chunk landed: this thread's record -> its box inside the tile.
+  __device__ void derive(uint32_t base, uint32_t end, int buf, int ox, int oy) {
+    uint32_t k = base + threadIdx.x;
+    if (k >= end) return;
+    const float4* r3 = rec + ((size_t)buf * kChunk + threadIdx.x) * DIGS_REC_F4;
+    float4 a = r3[0], c = r3[2];
+    int bx = __float_as_int(c.y), by = __float_as_int(c.z);
+    int x0 = max(bx & 0xffff, ox) - ox, x1 = min(bx >> 16, ox + TS - 1) - ox;
+    int y0 = max(by & 0xffff, oy) - oy, y1 = min(by >> 16, oy + TS - 1) - oy;
+    int w = x1 - x0 + 1, h = y1 - y0 + 1;
+    if (w <= 0 || h <= 0) { w = 1; h = 0; x0 = 0; y0 = 0; }  // keys come from the box: kept as a guard
+    int packed = (y0 * RasterSmem<TS>::pitch + x0) | (w << 11) | (h << 17) | ((__float_as_int(c.w) & 1) << 28);
+    info[buf * kChunk + threadIdx.x] = make_int4(packed, __float_as_int((float)(ox + x0) - a.x),
+                                                 __float_as_int((float)(oy + y0) - a.y), 0);
+  }
+};
+
+// Forward over the lane's pixel pairs of one box slice; p points at the lane's first pixel in the
+// half-warp's canvas.
+template <int TS, bool POLY, bool COUNT>
+__device__ __forceinline__ void fwd_pixels(const float4* r3, const HalfLanes& B, int h, float dx1, float dy1,
+                                           float* p, float c2, unsigned& n_cut) {
+  const float4 ra = r3[0], rb = r3[1];
+  const float amp = r3[2].x;
+  const float dx2 = dx1 + (float)B.pdx;
+  const f2 DX = f2_pack(dx1, dx2);
+  const f2 A = f2_mul(f2_mul(f2_dup(ra.z), DX), DX), BQ = f2_mul(f2_dup(ra.w), DX);
+  const f2 T0 = f2_fma(f2_dup(rb.y), DX, f2_dup(1.f));
+  const f2 N11 = f2_dup(rb.x), WN1 = f2_dup(rb.z), KAP = f2_dup(rb.w), AMP = f2_dup(amp);
+  const f2 C2 = f2_dup(c2), KNEG = f2_dup(kNegHalfLog2e), STEP = f2_dup((float)B.ystep);
+  constexpr int pitch = RasterSmem<TS>::pitch;
+  const int pstep = B.ystep * pitch, d2 = B.pdy * pitch + B.pdx, hb = B.col2 ? h - B.pdy : 0;
+  f2 DY = f2_pack(dy1, dy1 + (float)B.pdy);
+  for (int r = B.r0; r < h; r += B.ystep, DY = f2_add(DY, STEP), p += pstep) {
+    f2 NUM = f2_fma(DY, f2_fma(N11, DY, BQ), A);
+    f2 T = f2_fma(WN1, DY, T0);
+    f2 D = f2_fma(T, T, f2_mul(KAP, NUM));
+    f2 RS = f2_inv_sqrt<POLY>(D);
+    f2 EX = f2_exp2(f2_mul(f2_mul(NUM, f2_mul(RS, RS)), KNEG));
+    f2 VAL = f2_mul(f2_mul(AMP, RS), EX);
+    f2 LIM = f2_mul(C2, D);
+    float na, nb, la, lb, va, vb;
+    f2_unpack(NUM, na, nb);
+    f2_unpack(LIM, la, lb);
+    f2_unpack(VAL, va, vb);
+    if (na <= la) {  // E = num / D <= cutoff^2
+      p[0] += va;
+      if (COUNT) ++n_cut;
+    }
+    if (r < hb && nb <= lb) {  // the partner lies inside the box part in this tile
+      p[d2] += vb;
+      if (COUNT) ++n_cut;
+    }
+  }
+}
+
+// One CTA per (projection, tile); each half-warp takes one staged entry at a time and adds it into its
+// own canvas; the 16 canvases are merged in a fixed order.
+template <int TS, bool COUNT>
+__global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
+    const float4* __restrict__ grec, const uint32_t* __restrict__ srid, const uint2* __restrict__ ranges,
+    const __grid_constant__ ViewsParam views, int tiles_x, int T, int nu, int nv, float c2, float* __restrict__ proj,
+    const float* __restrict__ meas, float* __restrict__ dldi, float* __restrict__ loss_part, float inv_count,
+    unsigned long long* __restrict__ counters) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Stage<TS> S;
+  S.init(smem);
+  constexpr int pitch = RasterSmem<TS>::pitch, canvas = RasterSmem<TS>::canvas;
+  float* acc = (float*)(smem + RasterSmem<TS>::head);  // [kHalves][canvas]
+  __shared__ float red[kRasterWarps];
+  const int b = blockIdx.y, tile = blockIdx.x;
+  const int ox = (tile % tiles_x) * TS, oy = (tile / tiles_x) * TS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, hl = threadIdx.x & 15;
+  for (int p = threadIdx.x; p < kHalves * canvas; p += kRasterThreads) acc[p] = 0.f;
+  const uint2 rg = ranges[(size_t)b * T + tile];
+  const ViewC& v = views.v[b];
+  float* acch = acc + (threadIdx.x >> 4) * canvas;
+  unsigned n_box = 0, n_cut = 0;
+  if (rg.x < rg.y) S.issue(grec, srid, rg.x, rg.y, 0);
+  for (uint32_t base = rg.x, it = 0; base < rg.y; base += kChunk, ++it) {
+    const int buf = it & 1;
+    S.issue(grec, srid, base + kChunk, rg.y, buf ^ 1);
+    cp_async_wait_prev();
+    S.derive(base, rg.y, buf, ox, oy);
+    __syncthreads();
+    const int cnt = min((int)(rg.y - base), kChunk);
+    for (int e0 = 2 * warp; e0 < cnt; e0 += kHalves) {  // warp-uniform trip count
+      const int e = e0 + ((threadIdx.x >> 4) & 1);
+      const bool has = e < cnt;
+      const int4 inf = S.info[buf * kChunk + (has ? e : e0)];
+      const int w = has ? (inf.x >> 11) & 63 : 0, h = (inf.x >> 17) & 63;
+      const bool poly = __all_sync(0xffffffffu, !has || ((inf.x >> 28) & 1));
+      if (COUNT && hl == 0) n_box += w * h;
+      const float4* r3 = S.rec + ((size_t)buf * kChunk + e) * DIGS_REC_F4;
+      for (int cx = 0; cx < w; cx += 16) {  // 16-column slices (one unless TS = 32)
+        const HalfLanes B = half_lanes(min(16, w - cx), h, hl);
+        if (B.active) {
+          const float dx1 = __int_as_float(inf.y) + (float)(cx + B.c), dy1 = __int_as_float(inf.z) + (float)B.r0;
+          float* p = acch + (inf.x & 2047) + B.r0 * pitch + cx + B.c;
+          if (poly)
+            fwd_pixels<TS, true, COUNT>(r3, B, h, dx1, dy1, p, c2, n_cut);
+          else
+            fwd_pixels<TS, false, COUNT>(r3, B, h, dx1, dy1, p, c2, n_cut);
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  float lsum = 0.f;
+  for (int p = threadIdx.x; p < TS * TS; p += kRasterThreads) {
+    int px = ox + p % TS, py = oy + p / TS;
+    if (px < nu && py < nv) {
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < kHalves; ++q) s += acc[q * canvas + (p / TS) * pitch + p % TS];
+      const float lp = pixel_ray_length(v, (float)px, (float)py);
+      float I = s * lp;
+      size_t idx = ((size_t)b * nv + py) * nu + px;
+      if (proj) proj[idx] = I;
+      if (meas) {
+        float res = I - meas[idx];
+        lsum = fmaf(res, res, lsum);
+        if (dldi) dldi[idx] = 2.f * res * inv_count * lp;  // dL/dI * |X - s|, what the backward consumes
+      }
+    }
+  }
+  if (COUNT) {
+    unsigned c = n_cut;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    n_box += __shfl_xor_sync(0xffffffffu, n_box, 16);  // lanes 0 and 16 counted their half-warp's boxes
+    if (lane == 0 && (n_box | c)) {
+      atomicAdd(counters, (unsigned long long)n_box);
+      atomicAdd(counters + 1, (unsigned long long)c);
+    }
+  }
+  if (loss_part) {
+    lsum = warp_sum(lsum);
+    if (lane == 0) red[warp] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float s = 0.f;
+      for (int q = 0; q < kRasterWarps; ++q) s += red[q];
+      loss_part[(size_t)b * T + tile] = s;
+    }
+  }
+}
+
+// ---- backward: one half-warp per (projection, Gaussian) record, over the record's whole pixel box ----
+
+constexpr int kBwdThreads = 256;
+constexpr int kBwdRecords = kBwdThreads / 16;  // records per CTA
 
 // Adds the lane's share of the ten record-gradient sums, all but the first divided by amp / 2:
 // sum g V/amp; sum dL/dnum (dx^2, dx dy, dy^2); sum dL/dnum (dx, dy); sum dL/dt (1, dx, dy);
