@@ -50,9 +50,10 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.srid = (uint32_t*)take((size_t)cap * 4);
   w.hist = (uint32_t*)take(((size_t)256 * w.n_sort_blocks + 1) * 4);
   w.ranges = (uint2*)take((size_t)P * w.T * sizeof(uint2));
+  w.order = (uint32_t*)take((size_t)P * w.T * 4);
   w.grec = (float4*)take(PN * DIGS_PARTIAL_F4 * sizeof(float4));
   w.gw_part = (float*)take((size_t)std::max(w.n_gauss_blocks, 32) * P * R * 4 + 4);  // >= kGwSplit partials per (b, r)
-  w.loss_part = (float*)take((size_t)P * w.T * 4 + 4);
+  w.loss_part = (float*)take((size_t)P * w.T * fwd_warps(tile) * 4 + 4);
   w.ffd = (float*)take((size_t)12 * R * n * 4 + 4);
   w.ffd2 = (float*)take((size_t)18 * R * n * 4 + 4);
   w.padj = (float*)take((size_t)(kPairAdj + R) * P * n * 4 + 4);
@@ -234,6 +235,7 @@ digs_status bin(Call& c, const float* phi, const float* w) {
   DIGS_TRY(radix_sort(ws.keys, ws.vals, ws.keys_alt, ws.vals_alt, ws.n_pairs, ws.cap, key_bits((long long)c.P * ws.T),
                       ws.hist, ws.scan_tmp, ws.n_sort_blocks, &sk, &sv, c.st));
   DIGS_TRY(tile_ranges(sk, sv, ws.rid, ws.n_pairs, ws.cap, ws.ranges, c.P * ws.T, ws.srid, c.st));
+  DIGS_TRY(tile_order(ws.ranges, c.P * ws.T, ws.order, c.st));
   mark(c, 3);
   return DIGS_OK;
 }
@@ -242,8 +244,8 @@ digs_status bin(Call& c, const float* phi, const float* w) {
 digs_status backward(Call& c, const float* phi, const float* w, const float* grad_proj, float* g_mu0,
                      float* g_scale, float* g_quat, float* g_rho, float* g_phi, float* g_w, int w_rows) {
   size_t nphi = (size_t)c.L.nx * c.L.ny * c.L.nz * 3 * c.L.R;
-  mark(c, 5);
   DIGS_TRY(cudaMemsetAsync(g_phi, 0, nphi * sizeof(float), c.st));
+  mark(c, 5);
   if (c.g.n > 0) DIGS_TRY(launch_raster_bwd(c.ws, c.views, c.c2, grad_proj, c.st));
   mark(c, 6);
   if (c.g.n > 0)
@@ -354,7 +356,7 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
   float inv_count = 1.f / ((float)B * c.ws.nu * c.ws.nv);
   DIGS_TRY(launch_raster_fwd(c.ws, c.views, c.c2, c.ws.proj, meas, c.ws.dldi, inv_count, c.st));
   mark(c, 4);
-  DIGS_TRY(launch_loss_reduce(c.ws.loss_part, B * c.ws.T, loss_out, inv_count, c.st));
+  DIGS_TRY(launch_loss_reduce(c.ws.loss_part, B * c.ws.T * fwd_warps(c.ws.tile), loss_out, inv_count, c.st));
   s = backward(c, st->phi, st->w, nullptr, g_mu0, g_ls, g_q, g_rho, g_phi, g_w, st->n_w);
   if (s != DIGS_OK) return s;
   const DigsAdamConfig& a = st->adam;

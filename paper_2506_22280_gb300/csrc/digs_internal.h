@@ -32,12 +32,13 @@ struct Workspace {
   uint32_t* srid;         // [cap] record of each sorted position
   uint32_t* hist;         // radix histograms [256][sort blocks]
   uint2* ranges;          // [P * T] sorted-range of each (projection, tile)
+  uint32_t* order;        // [P * T] forward launch order (longest lists first)
   float4* grec;           // [P * n * 3] backward: the ten pixel sums of each (projection, Gaussian) record
   float* gw_part;         // [gauss blocks][P * R]
   float* ffd;             // [12 R][n]: u_r (3R components) then grad u_r (9R) at each mean
   float* ffd2;            // [18 R][n]: second derivatives of u_r (6 per component)
   float* padj;            // [kPairAdj + R][P * n]: per-(projection, Gaussian) adjoints
-  float* loss_part;       // [P * T]
+  float* loss_part;       // [P * T * fwd_warps(tile)] forward: squared residuals per warp
   float* proj;            // [P * nv * nu] (digs_step)
   float* dldi;            // [P * nv * nu] (digs_step)
   float* grads;           // all parameter gradients (digs_step)
@@ -46,6 +47,9 @@ struct Workspace {
   int n, P, nu, nv, R, tile, tiles_x, tiles_y, T;
   int n_sort_blocks, n_gauss_blocks;
 };
+
+// Warps per forward CTA (one per 8 x 8 block of a tile).
+inline int fwd_warps(int tile) { return (tile / 8) * (tile / 8); }
 
 size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, long long cap, int tile, size_t grad_floats);
 
@@ -63,6 +67,8 @@ cudaError_t tile_ranges(const uint32_t* sorted_keys, const uint32_t* sorted_vals
                         const uint32_t* n_dev, long long cap, uint2* ranges, int n_ranges, uint32_t* srid,
                         cudaStream_t st);
 int sort_blocks(long long cap);
+// order[P * T]: (projection, tile) indices by descending range length (power-of-two classes).
+cudaError_t tile_order(const uint2* ranges, int n, uint32_t* order, cudaStream_t st);
 
 // prep.cu
 cudaError_t launch_ffd_eval(const LatticeC& L, const float* phi, const float* x, int n, float* U, float* dU,

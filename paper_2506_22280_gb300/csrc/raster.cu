@@ -1,33 +1,30 @@
 // Tile rasteriser of the X-ray transform (Sec. 3.1, Eq. 1, 3-4) and its backward pass.
 //
-// Work is done by half-warps (16 lanes), each sweeping one Gaussian's pixel box (or a 16-column slice
-// of it) two pixels per lane per step in packed FP32x2 arithmetic (fma/mul/add.rn.f32x2).  Narrow
-// slices (w <= 8): lane l owns column (l mod w), starts at row (l div w) and takes the row pair
-// (r, r + s), s = 16 div w, stepping 2s rows.  Wider slices (8 < w <= 16): lane l owns the column pair
-// (c, c + ceil(w/2)) of row (l div ceil(w/2)), stepping s = 16 div ceil(w/2) rows.  Per pixel, with
-// (dx, dy) its offset from the projected mean:
-//   num = dy (n11 dy + n01x2 dx) + n00 dx^2,  t = 1 + wn0 dx + wn1 dy,  D = t^2 + kappa num,  E = num / D.
-// The only SFU operations per pixel are the exp2 and, unless D stays within 2 % of 1 over the box
-// (then its binomial series through the cubic term is used in the forward), the reciprocal square root.
+// Per pixel, with (dx, dy) its offset from the projected mean:
+//   num = n00 dx^2 + n01x2 dx dy + n11 dy^2,  t = 1 + wn0 dx + wn1 dy,  D = t^2 + kappa num,  E = num / D,
+// and the pixel takes V = amp |X - s| D^-1/2 exp(-E/2) when E <= cutoff^2.  The constant k = -log2(e)/2
+// is folded into num, so that k E is directly the argument of the SFU's exp2; D^-1/2 is the SFU's
+// reciprocal square root.  Pixels are taken two at a time in packed FP32x2 arithmetic
+// (fma/mul/add.rn.f32x2).
 //
-// Forward: one CTA per (projection, tile).  The tile's sorted Gaussian list is staged into shared
-// memory in chunks of 256 records (48 B each) by 16-byte cp.async copies, double-buffered so the next
-// chunk lands while the current one is processed; the thread that staged a record also derives, once,
-// the part of the Gaussian's box inside the tile.  Each half-warp adds its Gaussians into its own tile
-// canvas (no atomics); the 16 canvases merge in a fixed order, so the result is deterministic.
+// Forward: one CTA per (projection, tile) and one warp per 8 x 8 block of the tile; each lane owns two
+// pixels of the block and keeps their sums in registers.  Every warp walks the tile's sorted Gaussian
+// list in batches of 32 records staged by cp.async, keeps the Gaussians whose pixel box meets its block
+// and sweeps them in list order, two at a time: no canvas, no atomics, deterministic sums.  CTAs start
+// in order of decreasing list length.
 //
-// Backward: needs no tile lists.  One half-warp per (projection, Gaussian) record sweeps the record's
-// whole pixel box, reading g = dL/dI * |X - s| straight from the projection-sized image (L1/L2
-// resident).  Each lane accumulates seven sums per pixel of its pair and turns them into the ten
-// sufficient statistics of the record gradient; the half-warp reduces them with an 11-shuffle
-// recursive halving and ten lanes write them to the record's slot (no atomics).
+// Backward: needs no tile lists.  One half-warp (16 lanes) per (projection, Gaussian) record sweeps the
+// record's whole pixel box in 16-column slices, reading g = dL/dI * |X - s| straight from the
+// projection-sized image (L1/L2 resident).  Narrow slices (w <= 8): lane l owns column (l mod w),
+// starts at row (l div w) and takes the row pair (r, r + s), s = 16 div w, stepping 2s rows; wider
+// slices: the column pair (c, c + ceil(w/2)) of row (l div ceil(w/2)), stepping s = 16 div ceil(w/2)
+// rows.  Each lane accumulates seven sums per pixel of its pair and turns them into the ten sufficient
+// statistics of the record gradient; the half-warp reduces them with an 11-shuffle recursive halving
+// and ten lanes write them to the record's slot (no atomics).
 #include "digs_internal.h"
 
 namespace digs {
 
-constexpr int kRasterThreads = 256;
-constexpr int kRasterWarps = kRasterThreads / 32;
-constexpr int kChunk = kRasterThreads;
 constexpr float kNegHalfLog2e = -0.5f * DIGS_LOG2E;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -35,7 +32,7 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ---- packed FP32x2: the two pixels of a lane's pair in one register pair ------------------------
 typedef unsigned long long f2;
@@ -81,15 +78,9 @@ __device__ __forceinline__ f2 f2_exp2(f2 x) {
   f2_unpack(x, a, b);
   return f2_pack(sfu_exp2(a), sfu_exp2(b));
 }
-// D^-1/2: binomial series (1 + e)^-1/2 ~ 1 - e/2 + 3e^2/8 - 5e^3/16 when |e| <= 0.02, else the SFU.
-template <bool POLY>
-__device__ __forceinline__ f2 f2_inv_sqrt(f2 D) {
-  if (POLY) {
-    f2 e = f2_add(D, f2_dup(-1.f));
-    return f2_fma(e, f2_fma(e, f2_fma(e, f2_dup(-0.3125f), f2_dup(0.375f)), f2_dup(-0.5f)), f2_dup(1.f));
-  }
+__device__ __forceinline__ f2 f2_rsqrt(f2 x) {
   float a, b;
-  f2_unpack(D, a, b);
+  f2_unpack(x, a, b);
   return f2_pack(sfu_rsqrt(a), sfu_rsqrt(b));
 }
 
@@ -133,187 +124,161 @@ __device__ __forceinline__ HalfLanes half_lanes(int w, int h, int hl) {
 
 // ---- forward ------------------------------------------------------------------------------------
 
-constexpr int kHalves = kRasterThreads / 16;  // half-warps per CTA, one canvas each
-
+// One CTA per (projection, tile), launched in the order `order` gives; one warp per 8 x 8 block of the tile.  Lane l owns the pixels
+// (l mod 8, l div 8) and (l mod 8, l div 8 + 4) of its block and keeps their sums in a register pair.
 template <int TS>
-struct RasterSmem {
-  static constexpr size_t rec_bytes = 2 * kChunk * DIGS_REC_F4 * sizeof(float4);
-  static constexpr size_t info_bytes = 2 * kChunk * sizeof(int4);
-  static constexpr size_t head = rec_bytes + info_bytes;
-  // Canvas rows are TS + 1 floats apart and consecutive canvases 16 banks apart, so the rows of one
-  // half-warp's pixels and the two half-warps of a warp fall on different banks.
-  static constexpr int pitch = TS + 1;
-  static constexpr int canvas = TS * pitch + ((16 - (TS * pitch) % 32) + 32) % 32;
-  static constexpr size_t fwd = head + kHalves * canvas * sizeof(float);
+struct FwdCfg {
+  static constexpr int blocks_x = TS / 8;
+  static constexpr int warps = blocks_x * blocks_x;
+  static constexpr int threads = 32 * warps;
+  static constexpr int batch = 32;                              // records a warp stages at a time
+  static constexpr int raw_f4 = batch * DIGS_REC_F4;            // staged records
+  static constexpr int ent_f4 = batch * 5;                      // derived entries
+  static constexpr size_t smem = (size_t)warps * (raw_f4 + ent_f4) * sizeof(float4);
 };
 
-// Per-CTA staging state.
-template <int TS>
-struct Stage {
-  float4* rec;    // [2][kChunk * 3] records
-  int4* info;     // [2][kChunk]: (canvas offset y0 pitch + x0 | w << 11 | h << 17 | poly << 28, dx0, dy0, 0)
-  __device__ void init(unsigned char* sm) {
-    rec = (float4*)sm;
-    info = (int4*)(sm + RasterSmem<TS>::rec_bytes);
-  }
-  // Enqueue the copies of chunk [base, end) into buffer `buf` (commits a group even when empty).
-  __device__ void issue(const float4* __restrict__ grec, const uint32_t* __restrict__ srid, uint32_t base,
-                        uint32_t end, int buf) {
-    uint32_t k = base + threadIdx.x;
-    if (k < end) {
-      const float4* src = grec + (size_t)srid[k] * DIGS_REC_F4;
-      float4* dst = rec + ((size_t)buf * kChunk + threadIdx.x) * DIGS_REC_F4;
-#pragma unroll
-      for (int q = 0; q < DIGS_REC_F4; ++q) cp_async16(dst + q, src + q);
-    }
-    cp_async_commit();
-  }
-  // After the chunk landed: this thread's record -> its box inside the tile.
-  __device__ void derive(uint32_t base, uint32_t end, int buf, int ox, int oy) {
-    uint32_t k = base + threadIdx.x;
-    if (k >= end) return;
-    const float4* r3 = rec + ((size_t)buf * kChunk + threadIdx.x) * DIGS_REC_F4;
-    float4 a = r3[0], c = r3[2];
-    int bx = __float_as_int(c.y), by = __float_as_int(c.z);
-    int x0 = max(bx & 0xffff, ox) - ox, x1 = min(bx >> 16, ox + TS - 1) - ox;
-    int y0 = max(by & 0xffff, oy) - oy, y1 = min(by >> 16, oy + TS - 1) - oy;
-    int w = x1 - x0 + 1, h = y1 - y0 + 1;
-    if (w <= 0 || h <= 0) { w = 1; h = 0; x0 = 0; y0 = 0; }  // keys come from the box: kept as a guard
-    int packed = (y0 * RasterSmem<TS>::pitch + x0) | (w << 11) | (h << 17) | ((__float_as_int(c.w) & 1) << 28);
-    info[buf * kChunk + threadIdx.x] = make_int4(packed, __float_as_int((float)(ox + x0) - a.x),
-                                                 __float_as_int((float)(oy + y0) - a.y), 0);
-  }
-};
-
-// Forward over the lane's pixel pairs of one box slice; p points at the lane's first pixel in the
-// half-warp's canvas.
-template <int TS, bool POLY, bool COUNT>
-__device__ __forceinline__ void fwd_pixels(const float4* r3, const HalfLanes& B, int h, float dx1, float dy1,
-                                           float* p, float c2, unsigned& n_cut) {
-  const float4 ra = r3[0], rb = r3[1];
-  const float amp = r3[2].x;
-  const float dx2 = dx1 + (float)B.pdx;
-  const f2 DX = f2_pack(dx1, dx2);
-  const f2 A = f2_mul(f2_mul(f2_dup(ra.z), DX), DX), BQ = f2_mul(f2_dup(ra.w), DX);
-  const f2 T0 = f2_fma(f2_dup(rb.y), DX, f2_dup(1.f));
-  const f2 N11 = f2_dup(rb.x), WN1 = f2_dup(rb.z), KAP = f2_dup(rb.w), AMP = f2_dup(amp);
-  const f2 C2 = f2_dup(c2), KNEG = f2_dup(kNegHalfLog2e), STEP = f2_dup((float)B.ystep);
-  constexpr int pitch = RasterSmem<TS>::pitch;
-  const int pstep = B.ystep * pitch, d2 = B.pdy * pitch + B.pdx, hb = B.col2 ? h - B.pdy : 0;
-  f2 DY = f2_pack(dy1, dy1 + (float)B.pdy);
-  for (int r = B.r0; r < h; r += B.ystep, DY = f2_add(DY, STEP), p += pstep) {
-    f2 NUM = f2_fma(DY, f2_fma(N11, DY, BQ), A);
-    f2 T = f2_fma(WN1, DY, T0);
-    f2 D = f2_fma(T, T, f2_mul(KAP, NUM));
-    f2 RS = f2_inv_sqrt<POLY>(D);
-    f2 EX = f2_exp2(f2_mul(f2_mul(NUM, f2_mul(RS, RS)), KNEG));
-    f2 VAL = f2_mul(f2_mul(AMP, RS), EX);
-    f2 LIM = f2_mul(C2, D);
-    float na, nb, la, lb, va, vb;
-    f2_unpack(NUM, na, nb);
-    f2_unpack(LIM, la, lb);
-    f2_unpack(VAL, va, vb);
-    if (na <= la) {  // E = num / D <= cutoff^2
-      p[0] += va;
-      if (COUNT) ++n_cut;
-    }
-    if (r < hb && nb <= lb) {  // the partner lies inside the box part in this tile
-      p[d2] += vb;
-      if (COUNT) ++n_cut;
-    }
-  }
+// A staged record -> the entry the pixel loop reads, each constant stored twice so that one 16-byte
+// shared load yields two packed operands:
+//   (k n00, k n00, k n01x2, k n01x2), (k n11, k n11, wn0, wn0), (wn1, wn1, kappa / k, kappa / k),
+//   (amp, amp, -xc, -xc), (-yc, -yc, 0, 0)
+// with k = -log2(e) / 2, so that the loop forms the exp2 argument k E = k num / D directly.
+__device__ __forceinline__ void derive_entry(const float4* raw, float4* ent) {
+  const float4 a = raw[0], b = raw[1], c = raw[2];
+  const float n00 = kNegHalfLog2e * a.z, n01 = kNegHalfLog2e * a.w, n11 = kNegHalfLog2e * b.x;
+  const float kap = b.w * (1.f / kNegHalfLog2e);
+  ent[0] = make_float4(n00, n00, n01, n01);
+  ent[1] = make_float4(n11, n11, b.y, b.y);
+  ent[2] = make_float4(b.z, b.z, kap, kap);
+  ent[3] = make_float4(c.x, c.x, -a.x, -a.x);
+  ent[4] = make_float4(-a.y, -a.y, 0.f, 0.f);
 }
 
-// One CTA per (projection, tile); each half-warp takes one staged entry at a time and adds it into its
-// own canvas; the 16 canvases are merged in a fixed order.
+__device__ __forceinline__ f2 f2_lo(const float4& v) { return f2_pack(v.x, v.y); }
+__device__ __forceinline__ f2 f2_hi(const float4& v) { return f2_pack(v.z, v.w); }
+
+// V / |X - s| of one entry at the lane's two pixels (XX, YY), zero outside the cutoff (k E < c2k).
+template <bool COUNT>
+__device__ __forceinline__ f2 fwd_pair(const float4* en, f2 XX, f2 YY, float c2k, unsigned& n_cut) {
+  const float4 q0 = en[0], q1 = en[1], q2 = en[2], q3 = en[3], q4 = en[4];
+  const f2 DX = f2_add(XX, f2_hi(q3)), DY = f2_add(YY, f2_lo(q4));
+  const f2 AQ = f2_mul(f2_mul(f2_lo(q0), DX), DX), BQ = f2_mul(f2_hi(q0), DX);
+  const f2 NUM = f2_fma(DY, f2_fma(f2_lo(q1), DY, BQ), AQ);  // k num
+  const f2 T = f2_fma(f2_lo(q2), DY, f2_fma(f2_hi(q1), DX, f2_dup(1.f)));
+  const f2 D = f2_fma(T, T, f2_mul(f2_hi(q2), NUM));
+  const f2 RS = f2_rsqrt(D);
+  const f2 ARG = f2_mul(NUM, f2_mul(RS, RS));                  // k E
+  const f2 VAL = f2_mul(f2_mul(f2_lo(q3), RS), f2_exp2(ARG));
+  float aa, ab, va, vb;
+  f2_unpack(ARG, aa, ab);
+  f2_unpack(VAL, va, vb);
+  const bool ia = aa >= c2k, ib = ab >= c2k;
+  if (COUNT) n_cut += (unsigned)ia + (unsigned)ib;
+  return f2_pack(ia ? va : 0.f, ib ? vb : 0.f);
+}
+
+// Each warp walks the tile's whole sorted list in batches of 32: lane l copies record l of the batch
+// into shared memory (cp.async), tests its box against the warp's block and, if they meet, writes the
+// entry; the next batch's copies are then issued and the warp sweeps the meeting entries in list order
+// (so the sums are deterministic).  No canvas, no atomics, no CTA barrier.
 template <int TS, bool COUNT>
-__global__ void __launch_bounds__(kRasterThreads) k_raster_fwd(
+__global__ void __launch_bounds__(FwdCfg<TS>::threads) k_raster_fwd(
     const float4* __restrict__ grec, const uint32_t* __restrict__ srid, const uint2* __restrict__ ranges,
-    const __grid_constant__ ViewsParam views, int tiles_x, int T, int nu, int nv, float c2, float* __restrict__ proj,
-    const float* __restrict__ meas, float* __restrict__ dldi, float* __restrict__ loss_part, float inv_count,
-    unsigned long long* __restrict__ counters) {
+    const uint32_t* __restrict__ order, const __grid_constant__ ViewsParam views, int tiles_x, int T, int nu, int nv,
+    float c2, float* __restrict__ proj, const float* __restrict__ meas, float* __restrict__ dldi,
+    float* __restrict__ loss_part, float inv_count, unsigned long long* __restrict__ counters) {
+  using C = FwdCfg<TS>;
   extern __shared__ __align__(16) unsigned char smem[];
-  Stage<TS> S;
-  S.init(smem);
-  constexpr int pitch = RasterSmem<TS>::pitch, canvas = RasterSmem<TS>::canvas;
-  float* acc = (float*)(smem + RasterSmem<TS>::head);  // [kHalves][canvas]
-  __shared__ float red[kRasterWarps];
-  const int b = blockIdx.y, tile = blockIdx.x;
-  const int ox = (tile % tiles_x) * TS, oy = (tile / tiles_x) * TS;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, hl = threadIdx.x & 15;
-  for (int p = threadIdx.x; p < kHalves * canvas; p += kRasterThreads) acc[p] = 0.f;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4* raw = (float4*)smem + (size_t)warp * (C::raw_f4 + C::ent_f4);
+  float4* ent = raw + C::raw_f4;
+  const uint32_t bt = order[blockIdx.x];  // heaviest (projection, tile) lists first
+  const int b = (int)(bt / (uint32_t)T), tile = (int)(bt % (uint32_t)T);
+  const int qx = (tile % tiles_x) * TS + (warp % C::blocks_x) * 8, qy = (tile / tiles_x) * TS + (warp / C::blocks_x) * 8;
+  const int px = qx + (lane & 7), py = qy + (lane >> 3);  // the lane's pixels: (px, py) and (px, py + 4)
+  const f2 XX = f2_dup((float)px), YY = f2_pack((float)py, (float)(py + 4));
   const uint2 rg = ranges[(size_t)b * T + tile];
-  const ViewC& v = views.v[b];
-  float* acch = acc + (threadIdx.x >> 4) * canvas;
+  const float c2k = c2 * kNegHalfLog2e;
+  f2 ACC = f2_dup(0.f);
   unsigned n_box = 0, n_cut = 0;
-  if (rg.x < rg.y) S.issue(grec, srid, rg.x, rg.y, 0);
-  for (uint32_t base = rg.x, it = 0; base < rg.y; base += kChunk, ++it) {
-    const int buf = it & 1;
-    S.issue(grec, srid, base + kChunk, rg.y, buf ^ 1);
-    cp_async_wait_prev();
-    S.derive(base, rg.y, buf, ox, oy);
-    __syncthreads();
-    const int cnt = min((int)(rg.y - base), kChunk);
-    for (int e0 = 2 * warp; e0 < cnt; e0 += kHalves) {  // warp-uniform trip count
-      const int e = e0 + ((threadIdx.x >> 4) & 1);
-      const bool has = e < cnt;
-      const int4 inf = S.info[buf * kChunk + (has ? e : e0)];
-      const int w = has ? (inf.x >> 11) & 63 : 0, h = (inf.x >> 17) & 63;
-      const bool poly = __all_sync(0xffffffffu, !has || ((inf.x >> 28) & 1));
-      if (COUNT && hl == 0) n_box += w * h;
-      const float4* r3 = S.rec + ((size_t)buf * kChunk + e) * DIGS_REC_F4;
-      for (int cx = 0; cx < w; cx += 16) {  // 16-column slices (one unless TS = 32)
-        const HalfLanes B = half_lanes(min(16, w - cx), h, hl);
-        if (B.active) {
-          const float dx1 = __int_as_float(inf.y) + (float)(cx + B.c), dy1 = __int_as_float(inf.z) + (float)B.r0;
-          float* p = acch + (inf.x & 2047) + B.r0 * pitch + cx + B.c;
-          if (poly)
-            fwd_pixels<TS, true, COUNT>(r3, B, h, dx1, dy1, p, c2, n_cut);
-          else
-            fwd_pixels<TS, false, COUNT>(r3, B, h, dx1, dy1, p, c2, n_cut);
-        }
-      }
-      __syncwarp();
-    }
-    __syncthreads();
-  }
-  float lsum = 0.f;
-  for (int p = threadIdx.x; p < TS * TS; p += kRasterThreads) {
-    int px = ox + p % TS, py = oy + p / TS;
-    if (px < nu && py < nv) {
-      float s = 0.f;
+  auto issue = [&](uint32_t k0) {
+    const uint32_t k = k0 + lane;
+    if (k < rg.y) {
+      const float4* src = grec + (size_t)srid[k] * DIGS_REC_F4;
 #pragma unroll
-      for (int q = 0; q < kHalves; ++q) s += acc[q * canvas + (p / TS) * pitch + p % TS];
-      const float lp = pixel_ray_length(v, (float)px, (float)py);
-      float I = s * lp;
-      size_t idx = ((size_t)b * nv + py) * nu + px;
+      for (int q = 0; q < DIGS_REC_F4; ++q) cp_async16(raw + lane * DIGS_REC_F4 + q, src + q);
+    }
+    cp_async_commit();
+  };
+  if (rg.x < rg.y) issue(rg.x);
+  for (uint32_t k0 = rg.x; k0 < rg.y; k0 += C::batch) {
+    cp_async_wait_all();
+    bool meets = false;
+    if (k0 + lane < rg.y) {
+      const float4* r3 = raw + lane * DIGS_REC_F4;
+      const float4 c = r3[2];
+      const int bx = __float_as_int(c.y), by = __float_as_int(c.z);
+      const int x0 = max(bx & 0xffff, qx), x1 = min(bx >> 16, qx + 7);
+      const int y0 = max(by & 0xffff, qy), y1 = min(by >> 16, qy + 7);
+      meets = x0 <= x1 && y0 <= y1;
+      if (meets) {
+        derive_entry(r3, ent + lane * 5);
+        if (COUNT) n_box += (unsigned)((x1 - x0 + 1) * (y1 - y0 + 1));
+      }
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, meets);
+    __syncwarp();
+    issue(k0 + C::batch);  // lands while this batch is swept
+    while (mask) {  // two entries per step: two independent dependency chains
+      const int ea = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const float4* pa = ent + ea * 5;
+      if (mask) {
+        const int eb = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float4* pb = ent + eb * 5;
+        const f2 va = fwd_pair<COUNT>(pa, XX, YY, c2k, n_cut), vb = fwd_pair<COUNT>(pb, XX, YY, c2k, n_cut);
+        ACC = f2_add(f2_add(ACC, va), vb);  // list order
+      } else {
+        ACC = f2_add(ACC, fwd_pair<COUNT>(pa, XX, YY, c2k, n_cut));
+      }
+    }
+    __syncwarp();
+  }
+  cp_async_wait_all();  // the last (empty) group
+  const ViewC& v = views.v[b];
+  float s0, s1;
+  f2_unpack(ACC, s0, s1);
+  float lsum = 0.f;
+  auto emit = [&](int y, float sum) {
+    if (px < nu && y < nv) {
+      const float lp = pixel_ray_length(v, (float)px, (float)y);
+      const float I = sum * lp;
+      const size_t idx = ((size_t)b * nv + y) * nu + px;
       if (proj) proj[idx] = I;
       if (meas) {
-        float res = I - meas[idx];
+        const float res = I - meas[idx];
         lsum = fmaf(res, res, lsum);
         if (dldi) dldi[idx] = 2.f * res * inv_count * lp;  // dL/dI * |X - s|, what the backward consumes
       }
     }
-  }
+  };
+  emit(py, s0);
+  emit(py + 4, s1);
   if (COUNT) {
-    unsigned c = n_cut;
+    unsigned c = n_cut, nb = n_box;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    n_box += __shfl_xor_sync(0xffffffffu, n_box, 16);  // lanes 0 and 16 counted their half-warp's boxes
-    if (lane == 0 && (n_box | c)) {
-      atomicAdd(counters, (unsigned long long)n_box);
+    for (int o = 16; o > 0; o >>= 1) {
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+      nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    }
+    if (lane == 0 && (nb | c)) {
+      atomicAdd(counters, (unsigned long long)nb);
       atomicAdd(counters + 1, (unsigned long long)c);
     }
   }
-  if (loss_part) {
+  if (loss_part) {  // one partial per warp: no CTA barrier
     lsum = warp_sum(lsum);
-    if (lane == 0) red[warp] = lsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float s = 0.f;
-      for (int q = 0; q < kRasterWarps; ++q) s += red[q];
-      loss_part[(size_t)b * T + tile] = s;
-    }
+    if (lane == 0) loss_part[((size_t)b * T + tile) * C::warps + warp] = lsum;
   }
 }
 
@@ -328,33 +293,36 @@ constexpr int kBwdRecords = kBwdThreads / 16;  // records per CTA
 // (row pitch nu); (dx1, dy1) is that pixel's offset from the projected mean.
 __device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const HalfLanes& B, int h, float dx1, float dy1,
                                                const float* __restrict__ gp, int nu, float c2, float Sv[10]) {
+  // k = -log2(e) / 2 is folded into the quadratic form: NUM = k num, ARG = k E (the exp2 argument)
   const float dx2 = dx1 + (float)B.pdx;
   const f2 DX = f2_pack(dx1, dx2);
-  const f2 AQ = f2_mul(f2_mul(f2_dup(R0.n00), DX), DX), BQ = f2_mul(f2_dup(R0.n01x2), DX);
+  const f2 AQ = f2_mul(f2_mul(f2_dup(kNegHalfLog2e * R0.n00), DX), DX);
+  const f2 BQ = f2_mul(f2_dup(kNegHalfLog2e * R0.n01x2), DX);
   const f2 T0 = f2_fma(f2_dup(R0.wn0), DX, f2_dup(1.f));
-  const f2 N11 = f2_dup(R0.n11), WN1 = f2_dup(R0.wn1), KAP = f2_dup(R0.kappa);
-  const f2 KNEG = f2_dup(kNegHalfLog2e), MONE = f2_dup(-1.f), STEP = f2_dup((float)B.ystep);
-  const int pstep = B.ystep * nu, d2 = B.pdy * nu + B.pdx;
+  const f2 N11 = f2_dup(kNegHalfLog2e * R0.n11), WN1 = f2_dup(R0.wn1);
+  const f2 KAPK = f2_dup(R0.kappa * (1.f / kNegHalfLog2e)), MK1 = f2_dup(-1.f - R0.kappa);
+  const f2 IK = f2_dup(1.f / kNegHalfLog2e), MONE = f2_dup(-1.f), STEP = f2_dup((float)B.ystep);
+  const float c2k = c2 * kNegHalfLog2e;
+  const int pstep = B.ystep * nu, d2 = B.pdy * nu + B.pdx, hb = B.col2 ? h - B.pdy : 0;
   f2 DY = f2_pack(dy1, dy1 + (float)B.pdy);
   f2 S0 = f2_dup(0.f), S1 = S0, S2 = S0, S3 = S0, S4 = S0, S5 = S0, S6 = S0;
   for (int r = B.r0; r < h; r += B.ystep, DY = f2_add(DY, STEP), gp += pstep) {
     f2 NUM = f2_fma(DY, f2_fma(N11, DY, BQ), AQ);
     f2 T = f2_fma(WN1, DY, T0);
-    f2 D = f2_fma(T, T, f2_mul(KAP, NUM));
-    f2 RS = f2_inv_sqrt<false>(D);
+    f2 D = f2_fma(T, T, f2_mul(KAPK, NUM));
+    f2 RS = f2_rsqrt(D);
     f2 INVD = f2_mul(RS, RS);
-    f2 E = f2_mul(NUM, INVD);
-    f2 BV = f2_mul(RS, f2_exp2(f2_mul(E, KNEG)));      // V / amp
-    float na, nb, da, db;
-    f2_unpack(NUM, na, nb);
-    f2_unpack(D, da, db);
-    const float ga = (na <= c2 * da) ? __ldg(gp) : 0.f;                                     // E <= cutoff^2
-    const float gb = (B.col2 && r + B.pdy < h && nb <= c2 * db) ? __ldg(gp + d2) : 0.f;  // partner in the box
+    f2 ARG = f2_mul(NUM, INVD);
+    f2 BV = f2_mul(RS, f2_exp2(ARG));                      // V / amp
+    float aa, ab;
+    f2_unpack(ARG, aa, ab);
+    const float ga = (aa >= c2k) ? __ldg(gp) : 0.f;                      // E <= cutoff^2
+    const float gb = (r < hb && ab >= c2k) ? __ldg(gp + d2) : 0.f;      // partner in the box
     f2 G = f2_pack(ga, gb);
     S0 = f2_fma(G, BV, S0);
     f2 AL = f2_mul(G, f2_mul(BV, INVD));                     // (dL/dV * V / (2 D)) / (amp / 2)
-    f2 EM1 = f2_add(E, MONE);
-    f2 GNUM = f2_mul(AL, f2_fma(KAP, EM1, MONE));          // dL/dnum
+    f2 EM1 = f2_fma(ARG, IK, MONE);                         // E - 1
+    f2 GNUM = f2_mul(AL, f2_fma(KAPK, ARG, MK1));          // dL/dnum = AL (kappa (E - 1) - 1)
     f2 AEM = f2_mul(AL, EM1);
     f2 GTH = f2_mul(AEM, T);                                 // (dL/dt) / 2
     f2 GND = f2_mul(GNUM, DY);
@@ -363,7 +331,7 @@ __device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const HalfLanes& B
     S3 = f2_fma(GND, DY, S3);
     S4 = f2_add(S4, GTH);
     S5 = f2_fma(GTH, DY, S5);
-    S6 = f2_fma(AEM, NUM, S6);                               // dL/dkappa
+    S6 = f2_fma(AEM, NUM, S6);                               // k dL/dkappa
   }
   // each pixel of the pair keeps its column, so its dx-moments follow from its dy-moments
   float a[7][2];
@@ -383,7 +351,7 @@ __device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const HalfLanes& B
     Sv[6] += 2.f * a[4][j];
     Sv[7] += 2.f * dx * a[4][j];
     Sv[8] += 2.f * a[5][j];
-    Sv[9] += a[6][j];
+    Sv[9] += a[6][j] * (1.f / kNegHalfLog2e);
   }
 }
 
@@ -473,23 +441,23 @@ __global__ void __launch_bounds__(256) k_gpix(const float* __restrict__ grad_pro
 template <int TS>
 static cudaError_t fwd_launch(const Workspace& ws, const ViewsParam& views, float c2, float* proj, const float* meas,
                               float* dldi, float inv_count, bool count, cudaStream_t st) {
-  const size_t smem = RasterSmem<TS>::fwd;
+  using C = FwdCfg<TS>;
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(k_raster_fwd<TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_raster_fwd<TS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_raster_fwd<TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    cudaFuncSetAttribute(k_raster_fwd<TS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     configured = true;
   }
-  dim3 grid(ws.T, ws.P);
+  const unsigned grid = (unsigned)ws.T * (unsigned)ws.P;
   float* lp = meas ? ws.loss_part : nullptr;
   if (count)
-    k_raster_fwd<TS, true><<<grid, kRasterThreads, smem, st>>>(ws.rec, ws.srid, ws.ranges, views, ws.tiles_x, ws.T,
-                                                                ws.nu, ws.nv, c2, proj, meas, dldi, lp, inv_count,
-                                                                ws.counters);
+    k_raster_fwd<TS, true><<<grid, C::threads, C::smem, st>>>(ws.rec, ws.srid, ws.ranges, ws.order, views, ws.tiles_x,
+                                                              ws.T, ws.nu, ws.nv, c2, proj, meas, dldi, lp, inv_count,
+                                                              ws.counters);
   else
-    k_raster_fwd<TS, false><<<grid, kRasterThreads, smem, st>>>(ws.rec, ws.srid, ws.ranges, views, ws.tiles_x, ws.T,
-                                                                 ws.nu, ws.nv, c2, proj, meas, dldi, lp, inv_count,
-                                                                 ws.counters);
+    k_raster_fwd<TS, false><<<grid, C::threads, C::smem, st>>>(ws.rec, ws.srid, ws.ranges, ws.order, views,
+                                                               ws.tiles_x, ws.T, ws.nu, ws.nv, c2, proj, meas, dldi,
+                                                               lp, inv_count, ws.counters);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -132,4 +132,39 @@ cudaError_t tile_ranges(const uint32_t* sorted_keys, const uint32_t* sorted_vals
   return cudaGetLastError();
 }
 
+// Launch order of the forward raster's CTAs: (projection, tile) indices by descending list length, in
+// 33 power-of-two classes (longest first), so that the heaviest tiles start in the first wave and the
+// tail of the launch is made of light ones.  Only the launch order depends on it, not any result.
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ ranges, int n,
+                                                     uint32_t* __restrict__ order) {
+  __shared__ uint32_t cls[33];
+  if (threadIdx.x < 33) cls[threadIdx.x] = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint2 r = ranges[i];
+    atomicAdd(&cls[__clz(r.y - r.x)], 1u);  // 0 for the longest lists, 32 for empty ones
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int c = 0; c < 33; ++c) {
+      const uint32_t k = cls[c];
+      cls[c] = acc;
+      acc += k;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint2 r = ranges[i];
+    order[atomicAdd(&cls[__clz(r.y - r.x)], 1u)] = (uint32_t)i;
+  }
+}
+
+cudaError_t tile_order(const uint2* ranges, int n, uint32_t* order, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_tile_order<<<1, 1024, 0, st>>>(ranges, n, order);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace digs
