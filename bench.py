@@ -30,9 +30,11 @@ if ROOT not in sys.path:
 
 METRIC = "fwd+bwd projections/s (100k Gauss, 256²); % roofline; warm-start speedup"
 UNIT = "projections/s"
-# FP32 operations and MUFU (SFU) operations per (pixel, Gaussian) pair inside the cutoff, counted from
-# the kernels' pair loops (an FMA counts as 2 FP32 operations).
-PAIR_WORK = {"raster_fwd": (23, 1), "raster_bwd": (43, 1)}
+# Algorithmic FP32 operations (an FMA counts as 2) and SFU operations per (pixel, Gaussian) pair inside
+# the cutoff, with the per-column terms of the quadratic form counted once per column:
+#   forward  num 4, t 2, D 3, D^-1 and E 2, V 2, accumulate 1 = 14; rsqrt + exp2 = 2 SFU
+#   backward the forward's 9 up to E, V/amp 1, then the ten record-gradient sums 23 = 33; 2 SFU
+PAIR_WORK = {"raster_fwd": (14, 2), "raster_bwd": (33, 2)}
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM_CLK = 16
 
