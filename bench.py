@@ -46,10 +46,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=16, help="projections per step")
-    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--tile", type=int, default=0, help="raster tile edge (0: autotuned)")
+    ap.add_argument("--lanes", type=int, default=0, help="backward lanes per Gaussian, 16 or 32 (0: autotuned)")
     ap.add_argument("--n", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time direct calls instead of graph replays")
+    ap.add_argument("--no-batching", action="store_true", help="skip the four-scan batching measurement")
     return ap.parse_args()
 
 
@@ -175,11 +178,93 @@ def cpu_baseline(wl):
                       f"{dt:.1f} s"}
 
 
+def make_rec_factory(pkg, D, wl, device, total=10_000, scan_sizes=None):
+    lr0, lr1, _ = adam_defaults(total)
+
+    def make(tile, lanes):
+        return pkg.Reconstruction(wl["mu0"], wl["scale"], wl["quat"], wl["rho"], wl["phi"], wl["w"], wl["lattice"],
+                                  D.adam_config(lr0, lr1, total), tile=tile, bwd_lanes=lanes, device=device,
+                                  scan_sizes=scan_sizes)
+    return make
+
+
+def batching_measurement(pkg, D, device, steps=6, warmup=3):
+    """Four thorax scans with uneven Gaussian counts in one state; each step renders 64 (scan, projection)
+    items -- 16 distinct angles and times per scan -- with one launch per stage (a captured CUDA graph),
+    against the plain method: one digs_step per projection on each scan's own state."""
+    import torch
+    import synth
+    scans = synth.thorax_batch()
+    sizes = [w.n for w in scans]
+    meas = [render_measured(pkg, w, device) for w in scans]
+    n_proj = len(scans[0].views)
+    cat = lambda k: np.concatenate([getattr(w, k) for w in scans], 0)
+    state = dict(mu0=cat("mu0"), scale=cat("scale"), quat=cat("quat"), rho=cat("rho"),
+                 phi=np.stack([w.phi for w in scans], 0), w=cat("w"), lattice=scans[0].lattice)
+    per_scan = 16
+
+    def items(step):
+        out = []
+        for s in range(len(scans)):
+            for j in batch_ids(step * len(scans) + s, per_scan, n_proj):
+                out.append((s, j))
+        return out
+
+    def make_batch(B, step):
+        its = items(step)[:B]
+        M = torch.stack([meas[s][j] for s, j in its]).contiguous()
+        return M, [n_proj * s + j for s, j in its], [dict(scans[s].views[j], scan=s) for s, j in its]
+
+    from paper_2506_22280_gb300 import autotune
+    make = make_rec_factory(pkg, D, state, device, scan_sizes=sizes)
+    tuned = autotune.tune(make, make_batch, tiles=(8, 16, 32), lanes=(16, 32), batch_sizes=(64,), steps=2, warmup=1)
+    rec = make(tuned["tile"], tuned["bwd_lanes"])
+    B = len(scans) * per_scan
+    for s in range(warmup):
+        rec.step(*make_batch(B, s))
+    batches = [make_batch(B, warmup + s) for s in range(steps)]
+    graphs = rec.capture(batches)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for g in graphs:
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    batched = steps * B / (e0.elapsed_time(e1) / 1e3)
+    status = rec.status()
+    del rec, graphs
+    # plain: one projection per call on each scan's own state, same items
+    plain_recs = []
+    for s, w in enumerate(scans):
+        st = dict(mu0=w.mu0, scale=w.scale, quat=w.quat, rho=w.rho, phi=w.phi, w=w.w, lattice=w.lattice)
+        plain_recs.append(make_rec_factory(pkg, D, st, device)(16, 16))
+    its = [it for k in range(warmup + steps) for it in items(k)]
+    for s, j in its[:len(scans) * 2]:
+        plain_recs[s].step(meas[s][j:j + 1].contiguous(), [j], [scans[s].views[j]])
+    torch.cuda.synchronize()
+    timed = its[warmup * B:(warmup + steps) * B]
+    e0.record()
+    for s, j in timed:
+        plain_recs[s].step(meas[s][j:j + 1].contiguous(), [j], [scans[s].views[j]])
+    e1.record()
+    torch.cuda.synchronize()
+    plain = len(timed) / (e0.elapsed_time(e1) / 1e3)
+    status = status or max(r.status() for r in plain_recs)
+    return {"workload": f"4 synthetic thorax scans of {'/'.join(str(k // 1000) + 'k' for k in sizes)} Gaussians "
+                        f"(per-scan surrogates, 680 projections each, 256x256); {B} (scan, projection) items per "
+                        "step, 16 per scan, one launch per stage, CUDA-graph-replayed step",
+            "value": batched, "unit": UNIT, "plain_per_projection": plain, "speedup": batched / plain,
+            "tile": tuned["tile"], "bwd_lanes": tuned["bwd_lanes"], "autotune_trials": tuned["trials"],
+            "device_status": status}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
     import paper_2506_22280_gb300 as pkg
     from paper_2506_22280_gb300 import digs as D
+    from paper_2506_22280_gb300 import autotune
     import synth
 
     rank, world, local = dist_env()
@@ -192,27 +277,48 @@ def run_ours(args):
     n_proj = len(wl.views)
     meas = render_measured(pkg, wl, device)
     B = args.batch
-    lr0, lr1, total = adam_defaults(10_000)
-    rec = pkg.Reconstruction(wl.mu0, wl.scale, wl.quat, wl.rho, wl.phi, wl.w, wl.lattice,
-                             D.adam_config(lr0, lr1, total), tile=args.tile, device=device)
     K, W = args.steps, args.warmup
-    plan = [batch_ids(s, B, n_proj) for s in range(W + K)]
+    plan = [batch_ids(s, B, n_proj) for s in range(W + K + 8)]
     views = [[wl.views[i] for i in ids] for ids in plan]
     varrs = [D.views_array(v) for v in views]
     mb = [meas[torch.as_tensor(ids, device=device)].contiguous() for ids in plan]
+    init = dict(mu0=wl.mu0, scale=wl.scale, quat=wl.quat, rho=wl.rho, phi=wl.phi, w=wl.w, lattice=wl.lattice)
+    make = make_rec_factory(pkg, D, init, device)
+    # launch shape: the autotuner's pick unless given
+    tuned = None
+    if args.tile and args.lanes:
+        tile, lanes = args.tile, args.lanes
+    else:
+        tuned = autotune.tune(make, lambda b, s: (mb[s], plan[s], views[s]),
+                              tiles=(args.tile,) if args.tile else (8, 16, 32),
+                              lanes=(args.lanes,) if args.lanes else (16, 32), batch_sizes=(B,), steps=2, warmup=1)
+        tile, lanes = tuned["tile"], tuned["bwd_lanes"]
+    rec = make(tile, lanes)
     for s in range(W):
         rec.step(mb[s], plan[s], views[s], varr=varrs[s])
     torch.cuda.synchronize()
     if rec.status() != 0:
         raise RuntimeError("device status after warm-up: %d" % rec.status())
+    # stage times (CUDA events around each stage, on the launching stream) from direct calls
+    n_stage = min(K, 5)
+    stages = {k: 0.0 for k in D.STAGES}
+    l0 = D.kernel_launches()
+    for s in range(n_stage):
+        rec.step(mb[W + s], plan[W + s], views[W + s], time_stages=True, varr=varrs[W + s])
+        st = D.stage_times()
+        for k in stages:
+            stages[k] += st[k] / n_stage
+    launches_per_step = (D.kernel_launches() - l0) // n_stage
+    T0 = W + n_stage
+    use_graph = not args.no_graph
+    if use_graph:
+        graphs = rec.capture([(mb[T0 + s], plan[T0 + s], views[T0 + s]) for s in range(K)])
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=device)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    stages = {k: 0.0 for k in D.STAGES}
     clocks = ClockSampler(visible_gpu_index(local))
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    launches0 = D.kernel_launches()
     clocks.start()
     torch.cuda.profiler.start()  # ncu --profile-from-start off captures the timed steps only
     t_wall0 = time.perf_counter()
@@ -220,29 +326,29 @@ def run_ours(args):
         flush.fill_(float(s))
         e0, e1 = ev[s]
         e0.record()
-        rec.step(mb[W + s], plan[W + s], views[W + s], time_stages=True, varr=varrs[W + s])
+        if use_graph:
+            graphs[s].replay()
+        else:
+            rec.step(mb[T0 + s], plan[T0 + s], views[T0 + s], varr=varrs[T0 + s])
         e1.record()
-        st = D.stage_times()
-        for k in stages:
-            stages[k] += st[k]
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     t_wall = time.perf_counter() - t_wall0
-    launches = D.kernel_launches() - launches0
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
     dev_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
     status = rec.status()
     # pair statistics of one forward of the last batch (for the roofline's algorithmic work)
-    pj = pkg.Projector(wl.lattice, views[-1], tile=args.tile, device=device)
-    ins = [rec.mu0, rec.scale, rec.quat, rec.rho, rec.phi, rec.w[torch.as_tensor(plan[-1], device=device)].contiguous()]
+    pj = pkg.Projector(wl.lattice, views[T0 + K - 1], tile=tile, device=device)
+    ins = [rec.mu0, rec.scale, rec.quat, rec.rho, rec.phi,
+           rec.w[torch.as_tensor(plan[T0 + K - 1], device=device)].contiguous()]
     pj.forward(*ins)
     pairs = D.pair_stats(pj.ws)
     # end to end: pinned host measured projections -> device, step, loss -> host
     e2e = None
     if not args.no_e2e:
-        host = [m.cpu().pin_memory() for m in mb[W:]]
+        host = [m.cpu().pin_memory() for m in mb[T0:T0 + K]]
         dev_buf = torch.empty_like(mb[0])
         torch.cuda.synchronize()
         if world > 1:
@@ -250,7 +356,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for s in range(K):
             dev_buf.copy_(host[s], non_blocking=True)
-            loss = rec.step(dev_buf, plan[W + s], views[W + s], varr=varrs[W + s])
+            loss = rec.step(dev_buf, plan[T0 + s], views[T0 + s], varr=varrs[T0 + s])
             float(loss.item())
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
@@ -258,6 +364,9 @@ def run_ours(args):
     if world > 1:
         dist.all_reduce(red, op=dist.ReduceOp.MAX)
     dev_ms, t_wall, e2e_s = [float(x) for x in red.tolist()]
+    batching = None
+    if world == 1 and not args.no_batching:
+        batching = batching_measurement(pkg, D, device)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -276,13 +385,13 @@ def run_ours(args):
     dom = max(("raster_fwd", "raster_bwd"), key=lambda k: stages[k])
     flops, mufu = PAIR_WORK[dom]
     pair_rate_peak = n_sm * f_max * min(2 * FP32_LANES_PER_SM / flops, MUFU_PER_SM_CLK / mufu)
-    per_launch_ms = stages[dom] / K
+    per_launch_ms = stages[dom]
     achieved = pairs["cutoff_pairs"] * flops / (per_launch_ms / 1e3) / 1e12
     peak = pair_rate_peak * flops / 1e12
     roofline = {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_for("k_" + dom),
                 "peak_basis": (f"{n_sm} SMs x {f_max / 1e6:.0f} MHz; per in-cutoff pair {flops} FP32 ops "
-                               f"(128 lanes/SM, FMA = 2) and {mufu} MUFU ops (16/clk/SM): the slower pipe bounds"),
+                               f"(128 lanes/SM, FMA = 2) and {mufu} SFU ops (16/clk/SM): the slower pipe bounds"),
                 "pairs_per_launch": pairs["cutoff_pairs"], "box_pairs_per_launch": pairs["box_pairs"],
                 "tile_pairs_per_launch": pairs["tile_pairs"], "launch_ms": per_launch_ms}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -291,10 +400,16 @@ def run_ours(args):
             "config": {"workload": (f"synthetic thorax, {args.n} Gaussians, 256x256 detector (1.6 mm), R=3, "
                                     f"lattice 19^3 at 16 mm, 680-projection scan; {B} projections per step "
                                     "(fwd + bwd + Adam)"),
-                       "batch_projections": B, "tile": args.tile, "l2": "flushed between steps (512 MB write)",
+                       "batch_projections": B, "tile": tile, "bwd_lanes": lanes,
+                       "launch": "CUDA-graph replay of the whole step" if use_graph else "direct calls",
+                       "autotuned": tuned is not None, "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"{world} independent scans (replicas)", "wall_s_timed": t_wall},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "stages_ms_per_step": {k: v / K for k, v in stages.items()}, "device_status": status}
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * K, "clocks": clk,
+            "stages_ms_per_step": stages, "device_status": status}
+    if tuned is not None:
+        line["config"]["autotune_trials"] = tuned["trials"]
+    if batching is not None:
+        line["batching"] = batching
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)

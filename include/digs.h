@@ -38,6 +38,7 @@ extern "C" {
 
 #define DIGS_MAX_R 4        /* ranks N_r of the low-rank motion model (the paper uses 2)            */
 #define DIGS_MAX_VIEWS 128  /* projections per call                                                 */
+#define DIGS_MAX_SCANS 8    /* independent scans rendered together by one digs_step call             */
 
 typedef enum {
   DIGS_OK = 0,
@@ -72,15 +73,19 @@ typedef struct {
   double src[3], det_c[3], e_u[3], e_v[3];
   double du, dv, off_u, off_v;
   int nu, nv, parallel;
+  int scan;          /* digs_step: which scan of the state this projection belongs to (0 otherwise) */
 } DigsView;
 
 /* Options.  cutoff: a (ray, Gaussian) pair contributes iff the squared Mahalanobis distance E from the
  * ray to the deformed mean is <= cutoff^2 (default 3.5).  tile: square raster tile edge in pixels (8, 16
- * or 32; 0 = 16).  flags: DIGS_FLAG_* bits. */
+ * or 32; 0 = 16).  flags: DIGS_FLAG_* bits.  bwd_lanes: lanes that share one (projection, Gaussian) pair
+ * in the backward raster, 16 (two Gaussians per warp) or 32 (one); 0 = 16.  Tile and lanes change the
+ * speed, not the result beyond rounding. */
 typedef struct {
   float cutoff;
   int tile;
   int flags;
+  int bwd_lanes;
 } DigsOpts;
 
 #define DIGS_FLAG_REUSE_BINNING 1  /* project_bwd: reuse the per-pair records left in `ws` (same size)
@@ -150,11 +155,17 @@ typedef struct {
 
 /* Reconstruction state in caller-owned device memory.  Parameters are updated in place.  m and v are
  * Adam moments laid out like the parameters, concatenated in group order
- * (mu0 3n, log-scale 3n, quat 4n, density n, phi R*nz*ny*nx*3, w n_w*R), zero before the first step. */
+ * (mu0 3n, log-scale 3n, quat 4n, density n, phi S*R*nz*ny*nx*3, w n_w*R), zero before the first step.
+ * Several independent scans (S = n_scans <= DIGS_MAX_SCANS, e.g. scans of different patients with uneven
+ * Gaussian counts) may share one state so that one digs_step renders projections of all of them in one
+ * launch per stage: scan s owns Gaussians [scan_off[s], scan_off[s+1]) (scan_off[0] = 0,
+ * scan_off[S] = n), control points phi[s] ([S][R][nz][ny][nx][3], one lattice geometry for all scans),
+ * and the rows of w that its projections name; each view passed to digs_step says its scan.
+ * n_scans <= 1 means one scan holding all n Gaussians (scan_off is then ignored). */
 typedef struct {
   int n;
   float *mu0, *scale, *quat, *rho;  /* physical parameters (scale > 0, rho > 0)     */
-  float *phi;                        /* [R][nz][ny][nx][3]                           */
+  float *phi;                        /* [S][R][nz][ny][nx][3]                        */
   float *w;                          /* [n_w][R]: weights of every time point of the scan */
   int n_w;
   float *m, *v;                      /* Adam moments                                 */
@@ -162,16 +173,29 @@ typedef struct {
   int iter;                          /* completed steps; digs_step increments it     */
   DigsLattice lat;
   DigsAdamConfig adam;
+  int n_scans;
+  int scan_off[DIGS_MAX_SCANS + 1];
+  int* iter_dev;                     /* optional device int: when set, the step count (learning-rate
+                                        schedule, Adam bias correction) is read from and incremented on
+                                        the device, so a captured CUDA graph of a step can be replayed;
+                                        `iter` is then neither read nor changed                        */
 } DigsState;
 
-/* Number of floats in DigsState.m (and v, grad). */
-size_t digs_state_moments(int n, const DigsLattice* lat, int n_w);
+/* Number of floats in DigsState.m (and v, grad) for n Gaussians in n_scans (>= 1) scans. */
+size_t digs_state_moments(int n, const DigsLattice* lat, int n_w, int n_scans);
+
+/* Bytes of workspace digs_step needs for the state's scans, B projections of nu x nv pixels and room for
+ * max_pairs (tile, Gaussian) pairs (records are laid out [B][largest scan's Gaussian count]). */
+size_t digs_state_workspace_size(const DigsState* st, int B, int nu, int nv, long long max_pairs,
+                                 const DigsOpts* opts);
 
 /* One optimisation step over a batch of B projections (Eq. 1 with the L2 loss of Sec. 4.2):
  * render the projections `proj_ids` (host int array [B], rows of st->w) with geometry views[B] (host),
  * loss = mean over the batch's pixels of (I - meas)^2 written to loss_out (device float), gradients of
  * every parameter, then one fused Adam update of all groups with the learning rates of iteration st->iter.
- * meas: [B][nv][nu].  The workspace must be sized for n Gaussians and B projections. */
+ * meas: [B][nv][nu].  views[b].scan names the scan projection b belongs to (all 0 for one scan); every
+ * stage is one launch over all B projections of all scans.  The workspace must be sized by
+ * digs_state_workspace_size (for one scan, digs_workspace_size with n Gaussians and B projections). */
 digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, const DigsView* views, int B,
                       const DigsOpts* opts, float* loss_out, void* ws, size_t ws_bytes, void* stream);
 

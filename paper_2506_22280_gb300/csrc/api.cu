@@ -17,10 +17,10 @@ void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, long long cap, int tile,
-              size_t /*grad_floats*/) {
+              int n_total) {
   Workspace w;
   memset(&w, 0, sizeof(w));
-  w.n = n; w.P = P; w.nu = nu; w.nv = nv; w.R = R; w.cap = cap; w.tile = tile;
+  w.n = n; w.n_total = n_total; w.P = P; w.nu = nu; w.nv = nv; w.R = R; w.cap = cap; w.tile = tile;
   w.tiles_x = (nu + tile - 1) / tile;
   w.tiles_y = (nv + tile - 1) / tile;
   w.T = w.tiles_x * w.tiles_y;
@@ -53,9 +53,9 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.order = (uint32_t*)take((size_t)P * w.T * 4);
   w.grec = (float4*)take(PN * DIGS_PARTIAL_F4 * sizeof(float4));
   w.gw_part = (float*)take((size_t)std::max(w.n_gauss_blocks, 32) * P * R * 4 + 4);  // >= kGwSplit partials per (b, r)
-  w.loss_part = (float*)take((size_t)P * w.T * fwd_warps(tile) * 4 + 4);
-  w.ffd = (float*)take((size_t)12 * R * n * 4 + 4);
-  w.ffd2 = (float*)take((size_t)18 * R * n * 4 + 4);
+  w.loss_part = (float*)take((size_t)P * w.T * fwd_blocks(tile) * 4 + 4);
+  w.ffd = (float*)take((size_t)12 * R * n_total * 4 + 4);
+  w.ffd2 = (float*)take((size_t)18 * R * n_total * 4 + 4);
   w.padj = (float*)take((size_t)(kPairAdj + R) * P * n * 4 + 4);
   w.proj = (float*)take((size_t)P * nu * nv * 4);
   w.dldi = (float*)take((size_t)P * nu * nv * 4);
@@ -84,8 +84,8 @@ float opt_c2(const DigsOpts* o) {
 bool opt_valid(const DigsOpts* o) {
   if (!o) return true;
   if (!(o->cutoff >= 0.f) || !isfinite(o->cutoff)) return false;
-  int t = o->tile;
-  return t == 0 || t == 8 || t == 16 || t == 32;
+  int t = o->tile, l = o->bwd_lanes;
+  return (t == 0 || t == 8 || t == 16 || t == 32) && (l == 0 || l == 16 || l == 32);
 }
 
 double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
@@ -140,16 +140,46 @@ digs_status make_lattice(const DigsLattice* lat, LatticeC& L) {
   return DIGS_OK;
 }
 
-// Largest pair capacity whose layout fits `bytes`.
-long long capacity_for(size_t bytes, int n, int P, int nu, int nv, int R, int tile) {
-  if (layout(nullptr, nullptr, n, P, nu, nv, R, 0, tile, 0) > bytes) return -1;
+// Largest pair capacity whose layout fits `bytes` (n: record stride, n_total: all Gaussians).
+long long capacity_for(size_t bytes, int n, int P, int nu, int nv, int R, int tile, int n_total) {
+  if (layout(nullptr, nullptr, n, P, nu, nv, R, 0, tile, n_total) > bytes) return -1;
   long long lo = 0, hi = 1;
-  while (layout(nullptr, nullptr, n, P, nu, nv, R, hi, tile, 0) <= bytes && hi < (1LL << 32)) hi *= 2;
+  while (layout(nullptr, nullptr, n, P, nu, nv, R, hi, tile, n_total) <= bytes && hi < (1LL << 32)) hi *= 2;
   while (hi - lo > 1) {
     long long mid = (lo + hi) / 2;
-    if (layout(nullptr, nullptr, n, P, nu, nv, R, mid, tile, 0) <= bytes) lo = mid; else hi = mid;
+    if (layout(nullptr, nullptr, n, P, nu, nv, R, mid, tile, n_total) <= bytes) lo = mid; else hi = mid;
   }
   return std::min(lo, (long long)0xffffffffLL);
+}
+
+size_t phi_floats(const LatticeC& L) { return (size_t)L.nx * L.ny * L.nz * 3 * L.R; }
+
+ScanTable one_scan(int n, const LatticeC& L) {
+  ScanTable t;
+  memset(&t, 0, sizeof(t));
+  t.S = 1;
+  t.off[1] = n;
+  for (int k = 2; k <= DIGS_MAX_SCANS; ++k) t.off[k] = n;
+  t.nmax = n;
+  t.phi_stride = (long long)phi_floats(L);
+  return t;
+}
+
+// The scans of a state: n_scans <= 1 is one scan of all n Gaussians.
+digs_status state_scans(const DigsState* st, const LatticeC& L, ScanTable& t) {
+  t = one_scan(st->n, L);
+  if (st->n_scans <= 1) return DIGS_OK;
+  if (st->n_scans > DIGS_MAX_SCANS) return DIGS_ERR_ARG;
+  if (st->scan_off[0] != 0 || st->scan_off[st->n_scans] != st->n) return DIGS_ERR_ARG;
+  t.S = st->n_scans;
+  t.nmax = 0;
+  for (int s = 0; s < t.S; ++s) {
+    if (st->scan_off[s + 1] < st->scan_off[s]) return DIGS_ERR_ARG;
+    t.off[s] = st->scan_off[s];
+    t.nmax = std::max(t.nmax, st->scan_off[s + 1] - st->scan_off[s]);
+  }
+  for (int k = t.S; k <= DIGS_MAX_SCANS; ++k) t.off[k] = st->n;
+  return DIGS_OK;
 }
 
 int key_bits(long long nkeys) {
@@ -160,6 +190,7 @@ int key_bits(long long nkeys) {
 
 struct Call {
   GaussPtrs g;
+  ScanTable sc;
   LatticeC L;
   ViewsParam views;
   Workspace ws;
@@ -186,20 +217,30 @@ void mark(const Call& c, int i) {
   g_ev_marked |= 1u << i;
 }
 
+// scans: the state's scan table (digs_step), else nullptr for one scan of all g->n Gaussians.
 digs_status prepare(const DigsGaussians* g, const DigsLattice* lat, const float* phi, const float* w,
                     const DigsView* views, int P, const DigsOpts* opts, const int* rows, void* wsp, size_t ws_bytes,
-                    void* stream, Call& c) {
+                    void* stream, Call& c, const DigsState* scans = nullptr) {
   if (!g || !views || P < 0 || P > DIGS_MAX_VIEWS || g->n < 0 || !opt_valid(opts)) return DIGS_ERR_ARG;
   if (g->n > 0 && (!g->mu0 || !g->scale || !g->quat || !g->rho)) return DIGS_ERR_ARG;
   if (!phi || !w || !wsp) return DIGS_ERR_ARG;
   if (((uintptr_t)wsp & 255) != 0) return DIGS_ERR_ARG;
   digs_status s = make_lattice(lat, c.L);
   if (s != DIGS_OK) return s;
+  if (scans) {
+    s = state_scans(scans, c.L, c.sc);
+    if (s != DIGS_OK) return s;
+  } else {
+    c.sc = one_scan(g->n, c.L);
+  }
   int nu = P > 0 ? views[0].nu : 1, nv = P > 0 ? views[0].nv : 1;
   for (int b = 0; b < P; ++b) {
     if (views[b].nu != nu || views[b].nv != nv) return DIGS_ERR_ARG;
     s = make_view(views[b], rows ? rows[b] : b, c.views.v[b]);
     if (s != DIGS_OK) return s;
+    const int sc = scans ? views[b].scan : 0;
+    if (sc < 0 || sc >= c.sc.S) return DIGS_ERR_ARG;
+    c.views.v[b].scan = sc;
   }
   c.g = GaussPtrs{g->mu0, g->scale, g->quat, g->rho, g->n};
   c.c2 = opt_c2(opts);
@@ -207,9 +248,10 @@ digs_status prepare(const DigsGaussians* g, const DigsLattice* lat, const float*
   c.flags = opts ? opts->flags : 0;
   c.st = (cudaStream_t)stream;
   int tile = opt_tile(opts);
-  long long cap = capacity_for(ws_bytes, g->n, P, nu, nv, c.L.R, tile);
+  long long cap = capacity_for(ws_bytes, c.sc.nmax, P, nu, nv, c.L.R, tile, g->n);
   if (cap < 0) return DIGS_ERR_ARG;
-  layout(&c.ws, wsp, g->n, P, nu, nv, c.L.R, cap, tile, 0);
+  layout(&c.ws, wsp, c.sc.nmax, P, nu, nv, c.L.R, cap, tile, g->n);
+  c.ws.bwd_lanes = (opts && opts->bwd_lanes == 32) ? 32 : 16;
   return DIGS_OK;
 }
 
@@ -218,7 +260,7 @@ digs_status prep(Call& c, const float* phi, const float* w) {
   Workspace& ws = c.ws;
   mark(c, 0);
   DIGS_TRY(cudaMemsetAsync(ws.counters, 0, 2 * sizeof(unsigned long long), c.st));
-  DIGS_TRY(launch_prep_fwd(c.g, c.L, phi, w, c.views, c.P, c.c2, ws, c.st));
+  DIGS_TRY(launch_prep_fwd(c.g, c.sc, c.L, phi, w, c.views, c.P, c.c2, ws, c.st));
   mark(c, 1);
   return DIGS_OK;
 }
@@ -228,7 +270,7 @@ digs_status bin(Call& c, const float* phi, const float* w) {
   Workspace& ws = c.ws;
   digs_status s = prep(c, phi, w);
   if (s != DIGS_OK) return s;
-  DIGS_TRY(exclusive_scan(ws.counts, ws.offsets, c.P * c.g.n, ws.scan_tmp, c.st));
+  DIGS_TRY(exclusive_scan(ws.counts, ws.offsets, c.P * ws.n, ws.scan_tmp, c.st));
   DIGS_TRY(launch_emit(ws, c.st));
   mark(c, 2);
   uint32_t *sk = nullptr, *sv = nullptr;
@@ -243,13 +285,12 @@ digs_status bin(Call& c, const float* phi, const float* w) {
 // grad_proj = dL/dI, or nullptr when ws.dldi already holds dL/dI * |X - s|.
 digs_status backward(Call& c, const float* phi, const float* w, const float* grad_proj, float* g_mu0,
                      float* g_scale, float* g_quat, float* g_rho, float* g_phi, float* g_w, int w_rows) {
-  size_t nphi = (size_t)c.L.nx * c.L.ny * c.L.nz * 3 * c.L.R;
-  DIGS_TRY(cudaMemsetAsync(g_phi, 0, nphi * sizeof(float), c.st));
+  DIGS_TRY(cudaMemsetAsync(g_phi, 0, c.sc.S * phi_floats(c.L) * sizeof(float), c.st));
   mark(c, 5);
   if (c.g.n > 0) DIGS_TRY(launch_raster_bwd(c.ws, c.views, c.c2, grad_proj, c.st));
   mark(c, 6);
   if (c.g.n > 0)
-    DIGS_TRY(launch_chain_bwd(c.g, c.L, phi, w, c.views, c.P, c.c2, c.ws, g_mu0, g_scale, g_quat, g_rho, g_phi, c.st));
+    DIGS_TRY(launch_chain_bwd(c.g, c.sc, c.L, phi, w, c.views, c.P, c.ws, g_mu0, g_scale, g_quat, g_rho, g_phi, c.st));
   DIGS_TRY(launch_gw_reduce(c.ws, c.views, c.P, c.L.R, g_w, w_rows, c.st));
   mark(c, 7);
   return DIGS_OK;
@@ -261,7 +302,16 @@ extern "C" {
 
 size_t digs_workspace_size(int n, int P, int nu, int nv, int R, long long max_pairs, const DigsOpts* opts) {
   if (n < 0 || P < 0 || nu < 1 || nv < 1 || R < 1 || R > DIGS_MAX_R || max_pairs < 0 || !opt_valid(opts)) return 0;
-  return layout(nullptr, nullptr, n, P, nu, nv, R, max_pairs, opt_tile(opts), 0);
+  return layout(nullptr, nullptr, n, P, nu, nv, R, max_pairs, opt_tile(opts), n);
+}
+
+size_t digs_state_workspace_size(const DigsState* st, int B, int nu, int nv, long long max_pairs,
+                                 const DigsOpts* opts) {
+  if (!st || B < 0 || nu < 1 || nv < 1 || max_pairs < 0 || !opt_valid(opts)) return 0;
+  LatticeC L;
+  ScanTable t;
+  if (make_lattice(&st->lat, L) != DIGS_OK || state_scans(st, L, t) != DIGS_OK) return 0;
+  return layout(nullptr, nullptr, t.nmax, B, nu, nv, L.R, max_pairs, opt_tile(opts), st->n);
 }
 
 digs_status digs_ffd_eval(const DigsLattice* lat, const float* phi, const float* x, int n, float* U, float* dU,
@@ -281,10 +331,10 @@ digs_status digs_count_pairs(const DigsGaussians* g, const DigsLattice* lat, con
   Call c;
   digs_status s = prepare(g, lat, phi, w, views, P, opts, nullptr, ws, ws_bytes, stream, c);
   if (s != DIGS_OK) return s;
-  DIGS_TRY(launch_prep_fwd(c.g, c.L, phi, w, c.views, c.P, c.c2, c.ws, c.st));
-  DIGS_TRY(exclusive_scan(c.ws.counts, c.ws.offsets, c.P * c.g.n, c.ws.scan_tmp, c.st));
+  DIGS_TRY(launch_prep_fwd(c.g, c.sc, c.L, phi, w, c.views, c.P, c.c2, c.ws, c.st));
+  DIGS_TRY(exclusive_scan(c.ws.counts, c.ws.offsets, c.P * c.ws.n, c.ws.scan_tmp, c.st));
   uint32_t total = 0;
-  DIGS_TRY(cudaMemcpyAsync(&total, c.ws.offsets + (size_t)c.P * c.g.n, 4, cudaMemcpyDeviceToHost, c.st));
+  DIGS_TRY(cudaMemcpyAsync(&total, c.ws.offsets + (size_t)c.P * c.ws.n, 4, cudaMemcpyDeviceToHost, c.st));
   DIGS_TRY(cudaStreamSynchronize(c.st));
   *count_host = (long long)total;
   return DIGS_OK;
@@ -315,8 +365,7 @@ digs_status digs_project_bwd(const DigsGaussians* g, const DigsLattice* lat, con
   if (!g_phi || (P > 0 && (!g_w || !grad_proj))) return DIGS_ERR_ARG;
   if (g->n > 0 && (!g_mu0 || !g_scale || !g_quat || !g_rho)) return DIGS_ERR_ARG;
   if (P == 0) {
-    size_t nphi = (size_t)c.L.nx * c.L.ny * c.L.nz * 3 * c.L.R;
-    DIGS_TRY(cudaMemsetAsync(g_phi, 0, nphi * 4, c.st));
+    DIGS_TRY(cudaMemsetAsync(g_phi, 0, phi_floats(c.L) * 4, c.st));
     if (g->n > 0) {
       DIGS_TRY(cudaMemsetAsync(g_mu0, 0, (size_t)g->n * 12, c.st));
       DIGS_TRY(cudaMemsetAsync(g_scale, 0, (size_t)g->n * 12, c.st));
@@ -332,9 +381,10 @@ digs_status digs_project_bwd(const DigsGaussians* g, const DigsLattice* lat, con
   return backward(c, phi, w, grad_proj, g_mu0, g_scale, g_quat, g_rho, g_phi, g_w, P);
 }
 
-size_t digs_state_moments(int n, const DigsLattice* lat, int n_w) {
-  if (!lat || n < 0 || n_w < 0) return 0;
-  return (size_t)n * 11 + (size_t)lat->nx * lat->ny * lat->nz * 3 * lat->R + (size_t)n_w * lat->R;
+size_t digs_state_moments(int n, const DigsLattice* lat, int n_w, int n_scans) {
+  if (!lat || n < 0 || n_w < 0 || n_scans > DIGS_MAX_SCANS) return 0;
+  const size_t S = n_scans > 1 ? (size_t)n_scans : 1;
+  return (size_t)n * 11 + S * lat->nx * lat->ny * lat->nz * 3 * lat->R + (size_t)n_w * lat->R;
 }
 
 digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, const DigsView* views, int B,
@@ -344,10 +394,10 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
     if (proj_ids[b] < 0 || proj_ids[b] >= st->n_w) return DIGS_ERR_ARG;
   Call c;
   DigsGaussians g{st->n, st->mu0, st->scale, st->quat, st->rho};
-  digs_status s = prepare(&g, &st->lat, st->phi, st->w, views, B, opts, proj_ids, ws, ws_bytes, stream, c);
+  digs_status s = prepare(&g, &st->lat, st->phi, st->w, views, B, opts, proj_ids, ws, ws_bytes, stream, c, st);
   if (s != DIGS_OK) return s;
   const int n = st->n, R = st->lat.R;
-  const size_t nphi = (size_t)st->lat.nx * st->lat.ny * st->lat.nz * 3 * R;
+  const size_t nphi = c.sc.S * phi_floats(c.L);  // all scans' control points
   float* gr = st->grad;
   float *g_mu0 = gr, *g_ls = gr + 3 * (size_t)n, *g_q = gr + 6 * (size_t)n, *g_rho = gr + 10 * (size_t)n;
   float *g_phi = gr + 11 * (size_t)n, *g_w = g_phi + nphi;
@@ -356,7 +406,7 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
   float inv_count = 1.f / ((float)B * c.ws.nu * c.ws.nv);
   DIGS_TRY(launch_raster_fwd(c.ws, c.views, c.c2, c.ws.proj, meas, c.ws.dldi, inv_count, c.st));
   mark(c, 4);
-  DIGS_TRY(launch_loss_reduce(c.ws.loss_part, B * c.ws.T * fwd_warps(c.ws.tile), loss_out, inv_count, c.st));
+  DIGS_TRY(launch_loss_reduce(c.ws.loss_part, B * c.ws.T * fwd_blocks(c.ws.tile), loss_out, inv_count, c.st));
   s = backward(c, st->phi, st->w, nullptr, g_mu0, g_ls, g_q, g_rho, g_phi, g_w, st->n_w);
   if (s != DIGS_OK) return s;
   const DigsAdamConfig& a = st->adam;
@@ -372,12 +422,14 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
   AdamGroup groups[6];
   size_t off = 0;
   for (int k = 0; k < 6; ++k) {
-    groups[k] = AdamGroup{params[k], grads[k], st->m + off, st->v + off, (long long)sizes[k], 0, kinds[k], lr[k]};
+    const float lr_k = st->iter_dev ? a.lr0[k] : lr[k];
+    groups[k] = AdamGroup{params[k], grads[k], st->m + off, st->v + off, (long long)sizes[k], 0, kinds[k], lr_k,
+                          a.lr1[k]};
     off += sizes[k];
   }
-  DIGS_TRY(launch_adam(groups, 6, a.beta1, a.beta2, a.eps, st->iter + 1, c.st));
+  DIGS_TRY(launch_adam(groups, 6, a.beta1, a.beta2, a.eps, st->iter + 1, st->iter_dev, a.total_iters, c.st));
   mark(c, 8);
-  st->iter += 1;
+  if (!st->iter_dev) st->iter += 1;
   return DIGS_OK;
 }
 

@@ -43,8 +43,9 @@ __device__ __forceinline__ void warp_reduce_scatter48(float v[48], int lane) {
 // dL/d(grad u_r), read from shared memory at stride `st`.  Lanes with valid == false contribute nothing
 // but take part in the warp collectives.
 template <int R>
-__device__ __forceinline__ void ffd_scatter_warp(float* __restrict__ g_phi, const LatticeC& L, const float x[3],
-                                                 bool valid, const float* GU, const float* GdU, int st) {
+__device__ __forceinline__ void ffd_scatter_warp(float* __restrict__ g_phi_all, long long phi_stride, int scan,
+                                                 const LatticeC& L, const float x[3], bool valid, const float* GU,
+                                                 const float* GdU, int st) {
   const int lane = threadIdx.x & 31;
   int f[3];
   float u[3];
@@ -57,10 +58,13 @@ __device__ __forceinline__ void ffd_scatter_warp(float* __restrict__ g_phi, cons
 #pragma unroll
     for (int l = 0; l < 4; ++l) dB[a][l] *= L.inv_h[a];
   }
-  const unsigned key = valid ? ((unsigned)(f[0] + 1024) | ((unsigned)(f[1] + 1024) << 11) |
-                                ((unsigned)(f[2] + 512) << 22))
-                             : 0xffffffffu - (unsigned)lane;
-  // Lanes sharing a lattice cell share the 64 nodes: group them (up to kMaxGroups groups per warp) and
+  const unsigned long long key =
+      valid ? ((unsigned long long)((unsigned)(f[0] + 1024) | ((unsigned)(f[1] + 1024) << 11) |
+                                    ((unsigned)(f[2] + 512) << 22)) |
+               ((unsigned long long)scan << 32))
+            : ~0ull - (unsigned long long)lane;
+  float* g_phi = g_phi_all + scan * phi_stride;
+  // Lanes sharing a scan and a lattice cell share the 64 nodes: group them (up to 4 groups per warp) and
   // let each group sum its values over the warp before one atomic per node component.
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const unsigned leaders = __ballot_sync(0xffffffffu, (peers & ((1u << lane) - 1u)) == 0u);
@@ -103,6 +107,7 @@ __device__ __forceinline__ void ffd_scatter_warp(float* __restrict__ g_phi, cons
           const int gi = __shfl_sync(0xffffffffu, f[0], ld), gj = __shfl_sync(0xffffffffu, f[1], ld);
           const int gk = __shfl_sync(0xffffffffu, f[2], ld) + n3;
           const bool gvalid = __shfl_sync(0xffffffffu, valid ? 1 : 0, ld) != 0;
+          float* gphi = g_phi_all + __shfl_sync(0xffffffffu, scan, ld) * phi_stride;
           float v[48];
           slab(v, ((gmask >> lane) & 1u) != 0u);
           warp_reduce_scatter48(v, lane);
@@ -113,7 +118,7 @@ __device__ __forceinline__ void ffd_scatter_warp(float* __restrict__ g_phi, cons
               const int idx = base + jj, node = idx / 3, c = idx % 3;
               const int i = gi + (node & 3), j = gj + (node >> 2);
               if (i >= 0 && i < L.nx && j >= 0 && j < L.ny)
-                atomicAdd(g_phi + r * rank_stride + (((size_t)gk * L.ny + j) * L.nx + i) * 3 + c, v[jj]);
+                atomicAdd(gphi + r * rank_stride + (((size_t)gk * L.ny + j) * L.nx + i) * 3 + c, v[jj]);
             }
           }
         }
@@ -145,16 +150,17 @@ __device__ __forceinline__ void ffd_scatter_warp(float* __restrict__ g_phi, cons
 
 // (1) Adjoint of one (projection, Gaussian) pair.
 template <int R>
-__global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, const float* __restrict__ ffd,
+__global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, ScanTable sc, const float* __restrict__ ffd,
                                                       const float* __restrict__ w,
                                                       const __grid_constant__ ViewsParam views, int P,
                                                       const uint32_t* __restrict__ counts,
                                                       const float4* __restrict__ sums, float* __restrict__ padj) {
-  const int N = g.n;
-  const size_t PN = (size_t)P * N;
+  const int N = g.n, NM = sc.nmax;  // per-Gaussian arrays are [.][N]; records [P][NM]
+  const size_t PN = (size_t)P * NM;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= PN) return;
-  const int b = (int)(i / N), n = (int)(i - (size_t)b * N);
+  const int b = (int)(i / NM);
+  const int n = sc.off[views.v[b].scan] + (int)(i - (size_t)b * NM);  // global Gaussian (valid if counted)
   float out[kPairAdj + R];
 #pragma unroll
   for (int q = 0; q < kPairAdj + R; ++q) out[q] = 0.f;
@@ -248,13 +254,13 @@ __global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, const float* 
 
 // Second derivatives of u_r at each mean ([18 R][n], see ffd_hessian_point), for the mean's gradient.
 template <int R>
-__global__ void __launch_bounds__(128) k_ffd_hessian(GaussPtrs g, LatticeC L, const float* __restrict__ phi,
-                                                    float* __restrict__ out) {
+__global__ void __launch_bounds__(128) k_ffd_hessian(GaussPtrs g, ScanTable sc, LatticeC L,
+                                                    const float* __restrict__ phi, float* __restrict__ out) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.n) return;
   const float x[3] = {g.mu0[3 * n], g.mu0[3 * n + 1], g.mu0[3 * n + 2]};
   float H[R][18];
-  ffd_hessian_point<R>(phi, L, x, H);
+  ffd_hessian_point<R>(phi + scan_of(sc, n) * sc.phi_stride, L, x, H);
 #pragma unroll
   for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -264,16 +270,17 @@ __global__ void __launch_bounds__(128) k_ffd_hessian(GaussPtrs g, LatticeC L, co
 // (2) Per Gaussian: sum the pair adjoints over the projections, then the FFD backward.
 template <int R>
 __global__ void __launch_bounds__(kChainThreads) k_gauss_bwd(
-    GaussPtrs g, LatticeC L, const float* __restrict__ ffd, const float* __restrict__ ffd2,
+    GaussPtrs g, ScanTable sc, LatticeC L, const float* __restrict__ ffd, const float* __restrict__ ffd2,
     const float* __restrict__ w, const __grid_constant__ ViewsParam views, int P, const float* __restrict__ padj,
     float* __restrict__ g_mu0,
     float* __restrict__ g_scale, float* __restrict__ g_quat, float* __restrict__ g_rho, float* __restrict__ g_phi) {
   __shared__ float Gs[12 * R * kChainThreads];  // dL/du_r (3R) then dL/d(grad u_r) (9R), thread-fastest
   constexpr int ST = kChainThreads;
   const int N = g.n;
-  const size_t PN = (size_t)P * N;
+  const size_t PN = (size_t)P * sc.nmax;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = n < N;
+  const int scan = valid ? scan_of(sc, n) : 0, nl = n - sc.off[scan];  // scan-local index
   float GU[R][3], GdU[R][9], gmu0[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gR[9], grho = 0.f;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -286,7 +293,8 @@ __global__ void __launch_bounds__(kChainThreads) k_gauss_bwd(
   for (int c = 0; c < 9; ++c) gR[c] = 0.f;
   if (valid) {
     for (int b = 0; b < P; ++b) {
-      const size_t i = (size_t)b * N + n;
+      if (views.v[b].scan != scan) continue;
+      const size_t i = (size_t)b * sc.nmax + nl;
       const float* wb = w + (size_t)views.v[b].w_row * R;
       float gmu[3], gK[9];
 #pragma unroll
@@ -338,7 +346,8 @@ __global__ void __launch_bounds__(kChainThreads) k_gauss_bwd(
     }
   }
   // each thread reads back only its own column of Gs, so no barrier is needed
-  ffd_scatter_warp<R>(g_phi, L, mu0, valid, Gs + threadIdx.x, Gs + 3 * R * ST + threadIdx.x, ST);
+  ffd_scatter_warp<R>(g_phi, sc.phi_stride, scan, L, mu0, valid, Gs + threadIdx.x, Gs + 3 * R * ST + threadIdx.x,
+                      ST);
   if (!valid) return;
   float qh[4], gq[4];
   const float q0 = g.quat[4 * n], q1 = g.quat[4 * n + 1], q2 = g.quat[4 * n + 2], q3 = g.quat[4 * n + 3];
@@ -355,19 +364,18 @@ __global__ void __launch_bounds__(kChainThreads) k_gauss_bwd(
   g_rho[n] = grho;
 }
 
-cudaError_t launch_chain_bwd(const GaussPtrs& g, const LatticeC& L, const float* phi, const float* w,
-                             const ViewsParam& views, int P, float c2, const Workspace& ws, float* g_mu0,
+cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const LatticeC& L, const float* phi,
+                             const float* w, const ViewsParam& views, int P, const Workspace& ws, float* g_mu0,
                              float* g_scale, float* g_quat, float* g_rho, float* g_phi, cudaStream_t st) {
-  (void)c2;
   if (g.n <= 0) return cudaSuccess;
-  const size_t PN = (size_t)P * g.n;
+  const size_t PN = (size_t)P * sc.nmax;
   const unsigned ga = (unsigned)((PN + 255) / 256);
   dim3 gb(chain_blocks(g.n));
 #define DIGS_CH(RR)                                                                                             \
-  k_ffd_hessian<RR><<<gb, 128, 0, st>>>(g, L, phi, ws.ffd2);                                                    \
+  k_ffd_hessian<RR><<<gb, 128, 0, st>>>(g, sc, L, phi, ws.ffd2);                                                \
   if (PN > 0)                                                                                                   \
-    k_pair_adjoint<RR><<<ga, 256, 0, st>>>(g, ws.ffd, w, views, P, ws.counts, ws.grec, ws.padj);                 \
-  k_gauss_bwd<RR><<<gb, kChainThreads, 0, st>>>(g, L, ws.ffd, ws.ffd2, w, views, P, ws.padj, g_mu0, g_scale,     \
+    k_pair_adjoint<RR><<<ga, 256, 0, st>>>(g, sc, ws.ffd, w, views, P, ws.counts, ws.grec, ws.padj);             \
+  k_gauss_bwd<RR><<<gb, kChainThreads, 0, st>>>(g, sc, L, ws.ffd, ws.ffd2, w, views, P, ws.padj, g_mu0, g_scale, \
                                                g_quat, g_rho, g_phi)
   switch (L.R) {
     case 1: DIGS_CH(1); break;

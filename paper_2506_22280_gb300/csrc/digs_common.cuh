@@ -28,11 +28,28 @@ struct ViewC {
   int nu, nv;
   int parallel;
   int w_row;         // row of the temporal-weight table used by this projection
+  int scan;          // scan whose Gaussians and control points this projection renders
 };
 
 struct ViewsParam {
   ViewC v[DIGS_MAX_VIEWS];
 };
+
+// Scans sharing one call: scan s owns Gaussians [off[s], off[s+1]); records are laid out
+// [projection][nmax]; phi of scan s starts phi_stride floats after that of scan s - 1.
+struct ScanTable {
+  int S;
+  int off[DIGS_MAX_SCANS + 1];
+  int nmax;
+  long long phi_stride;
+};
+
+__device__ __forceinline__ int scan_of(const ScanTable& T, int g) {
+  int s = 0;
+#pragma unroll
+  for (int k = 1; k < DIGS_MAX_SCANS; ++k) s += (k < T.S && g >= T.off[k]) ? 1 : 0;
+  return s;
+}
 
 struct LatticeC {
   float origin[3];

@@ -35,23 +35,25 @@ struct Workspace {
   uint32_t* order;        // [P * T] forward launch order (longest lists first)
   float4* grec;           // [P * n * 3] backward: the ten pixel sums of each (projection, Gaussian) record
   float* gw_part;         // [gauss blocks][P * R]
-  float* ffd;             // [12 R][n]: u_r (3R components) then grad u_r (9R) at each mean
-  float* ffd2;            // [18 R][n]: second derivatives of u_r (6 per component)
+  float* ffd;             // [12 R][n_total]: u_r (3R components) then grad u_r (9R) at each mean
+  float* ffd2;            // [18 R][n_total]: second derivatives of u_r (6 per component)
   float* padj;            // [kPairAdj + R][P * n]: per-(projection, Gaussian) adjoints
-  float* loss_part;       // [P * T * fwd_warps(tile)] forward: squared residuals per warp
+  float* loss_part;       // [P * T * fwd_blocks(tile)] forward: squared residuals per 8 x 8 block (warp)
   float* proj;            // [P * nv * nu] (digs_step)
   float* dldi;            // [P * nv * nu] (digs_step)
   float* grads;           // all parameter gradients (digs_step)
   size_t bytes;
   long long cap;
-  int n, P, nu, nv, R, tile, tiles_x, tiles_y, T;
+  int n, P, nu, nv, R, tile, tiles_x, tiles_y, T;  // n: record stride (largest scan's Gaussian count)
+  int n_total;                                     // Gaussians of all scans
+  int bwd_lanes;                                   // lanes per record in the backward raster (16 or 32)
   int n_sort_blocks, n_gauss_blocks;
 };
 
-// Warps per forward CTA (one per 8 x 8 block of a tile).
-inline int fwd_warps(int tile) { return (tile / 8) * (tile / 8); }
+// Forward work items (8 x 8 pixel blocks) per tile.
+inline int fwd_blocks(int tile) { return (tile / 8) * (tile / 8); }
 
-size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, long long cap, int tile, size_t grad_floats);
+size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, long long cap, int tile, int n_total);
 
 // scan.cu
 cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int n, uint32_t* tmp, cudaStream_t st);
@@ -73,8 +75,9 @@ cudaError_t tile_order(const uint2* ranges, int n, uint32_t* order, cudaStream_t
 // prep.cu
 cudaError_t launch_ffd_eval(const LatticeC& L, const float* phi, const float* x, int n, float* U, float* dU,
                             cudaStream_t st);
-cudaError_t launch_prep_fwd(const GaussPtrs& g, const LatticeC& L, const float* phi, const float* w,
-                            const ViewsParam& views, int P, float c2, const Workspace& ws, cudaStream_t st);
+cudaError_t launch_prep_fwd(const GaussPtrs& g, const ScanTable& sc, const LatticeC& L, const float* phi,
+                            const float* w, const ViewsParam& views, int P, float c2, const Workspace& ws,
+                            cudaStream_t st);
 cudaError_t launch_emit(const Workspace& ws, cudaStream_t st);
 
 // raster.cu
@@ -86,8 +89,8 @@ cudaError_t launch_raster_bwd(const Workspace& ws, const ViewsParam& views, floa
 cudaError_t launch_loss_reduce(const float* part, int n, float* out, float scale, cudaStream_t st);
 
 // chain.cu
-cudaError_t launch_chain_bwd(const GaussPtrs& g, const LatticeC& L, const float* phi, const float* w,
-                             const ViewsParam& views, int P, float c2, const Workspace& ws, float* g_mu0,
+cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const LatticeC& L, const float* phi,
+                             const float* w, const ViewsParam& views, int P, const Workspace& ws, float* g_mu0,
                              float* g_scale, float* g_quat, float* g_rho, float* g_phi, cudaStream_t st);
 cudaError_t launch_gw_reduce(const Workspace& ws, const ViewsParam& views, int P, int R, float* g_w, int w_rows,
                              cudaStream_t st);
@@ -102,9 +105,12 @@ struct AdamGroup {
   long long n;
   long long off;   // offset of this group inside m / v
   int kind;        // 0 plain, 1 log-parameterised (scale), 2 softplus-parameterised (density)
-  float lr;
+  float lr;        // learning rate of this step, or (iter_dev set) of step 0
+  float lr_end;    // (iter_dev set) learning rate of step total_iters - 1, linear in between
 };
+// step: 1-based Adam step (bias correction) when iter_dev is null; else the step count is read from
+// *iter_dev (0-based) on the device and a following kernel increments it.
 cudaError_t launch_adam(const AdamGroup* groups, int ngroups, float beta1, float beta2, float eps, int step,
-                        cudaStream_t st);
+                        int* iter_dev, int total_iters, cudaStream_t st);
 
 }  // namespace digs

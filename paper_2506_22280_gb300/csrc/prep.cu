@@ -61,32 +61,35 @@ __device__ __forceinline__ void load_gauss(const GaussPtrs& g, int n, GaussLocal
   o.rho = g.rho[n];
 }
 
-// One thread per Gaussian; loops over the call's projections so the FFD is evaluated once.
+// One thread per Gaussian; loops over the call's projections of its scan so the FFD is evaluated once.
+// Record (b, n) of scan-local Gaussian n sits at b * nmax + n.
 template <int R>
-__global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, LatticeC L, const float* __restrict__ phi,
+__global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, ScanTable sc, LatticeC L, const float* __restrict__ phi,
                                                   const float* __restrict__ w, const __grid_constant__ ViewsParam views,
                                                   int P, float c2, int tile, int tiles_x, float4* __restrict__ rec,
                                                   uint32_t* __restrict__ counts, float* __restrict__ ffd_out,
                                                   int* status) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= g.n) return;
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= g.n) return;
+  const int s = scan_of(sc, gi), n = gi - sc.off[s];
   GaussLocal G;
-  load_gauss(g, n, G);
+  load_gauss(g, gi, G);
   float U[R][3], dU[R][9];
-  ffd_eval_point<R>(phi, L, G.mu0, U, dU);
+  ffd_eval_point<R>(phi + s * sc.phi_stride, L, G.mu0, U, dU);
   // keep u_r and grad u_r for the backward, component-major ([12 R][n]: coalesced for both passes)
 #pragma unroll
   for (int r = 0; r < R; ++r) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) ffd_out[(size_t)(r * 3 + c) * g.n + n] = U[r][c];
+    for (int c = 0; c < 3; ++c) ffd_out[(size_t)(r * 3 + c) * g.n + gi] = U[r][c];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) ffd_out[(size_t)(3 * R + r * 9 + c) * g.n + n] = dU[r][c];
+    for (int c = 0; c < 9; ++c) ffd_out[(size_t)(3 * R + r * 9 + c) * g.n + gi] = dU[r][c];
   }
 
   bool finite_in = isfinite(G.mu0[0] + G.mu0[1] + G.mu0[2] + G.s[0] + G.s[1] + G.s[2] + G.qnorm + G.rho);
   if (!finite_in) set_status(status, DIGS_ERR_NONFINITE);
   for (int b = 0; b < P; ++b) {
     const ViewC& v = views.v[b];
+    if (v.scan != s) continue;
     const float* wb = w + (size_t)v.w_row * R;
     float mu[3], K[9];
 #pragma unroll
@@ -116,18 +119,23 @@ __global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, LatticeC L, const
     } else {
       r = Rec{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0, 0};
     }
-    size_t idx = (size_t)b * g.n + n;
+    size_t idx = (size_t)b * sc.nmax + n;
     store_rec(rec + idx * DIGS_REC_F4, r);
     counts[idx] = cnt;
   }
 }
 
-cudaError_t launch_prep_fwd(const GaussPtrs& g, const LatticeC& L, const float* phi, const float* w,
-                            const ViewsParam& views, int P, float c2, const Workspace& ws, cudaStream_t st) {
+cudaError_t launch_prep_fwd(const GaussPtrs& g, const ScanTable& sc, const LatticeC& L, const float* phi,
+                            const float* w, const ViewsParam& views, int P, float c2, const Workspace& ws,
+                            cudaStream_t st) {
   if (g.n <= 0 || P <= 0) return cudaSuccess;
+  if (sc.S > 1) {  // records of projections whose scan is smaller than nmax are padding: no tiles
+    cudaError_t e = cudaMemsetAsync(ws.counts, 0, (size_t)P * sc.nmax * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+  }
   dim3 grid((g.n + 127) / 128);
-#define DIGS_PREP(RR)                                                                                      \
-  k_prep_fwd<RR><<<grid, 128, 0, st>>>(g, L, phi, w, views, P, c2, ws.tile, ws.tiles_x, ws.rec, ws.counts, \
+#define DIGS_PREP(RR)                                                                                          \
+  k_prep_fwd<RR><<<grid, 128, 0, st>>>(g, sc, L, phi, w, views, P, c2, ws.tile, ws.tiles_x, ws.rec, ws.counts, \
                                        ws.ffd, ws.status)
   switch (L.R) {
     case 1: DIGS_PREP(1); break;

@@ -21,6 +21,8 @@
 // rows.  Each lane accumulates seven sums per pixel of its pair and turns them into the ten sufficient
 // statistics of the record gradient; the half-warp reduces them with an 11-shuffle recursive halving
 // and ten lanes write them to the record's slot (no atomics).
+#include <algorithm>
+
 #include "digs_internal.h"
 
 namespace digs {
@@ -86,31 +88,34 @@ __device__ __forceinline__ f2 f2_rsqrt(f2 x) {
 
 // ---- lane layouts (forward and backward) ---------------------------------------------------------
 
-// Half-warp lane layout of a box slice w <= 16 pixels wide, per w: cw | s << 5 | m << 10, where cw is
-// the number of lane columns, s the rows covered per pass and m = ceil(256 / cw), so that
-// (l * m) >> 8 = l / cw exactly for l < 16.  w <= 8: lane l takes column l mod w and the row pair
-// (r, r + s), s = 16 div w, stepping 2s rows.  8 < w <= 16: the column pair (c, c + ceil(w/2)),
-// stepping s = 16 div ceil(w/2) rows.
-struct HalfLaneTable {
-  int v[17];
-  constexpr HalfLaneTable() : v() {
-    for (int w = 1; w <= 16; ++w) {
-      const int cw = w <= 8 ? w : (w + 1) / 2;
-      v[w] = cw | ((16 / cw) << 5) | (((256 + cw - 1) / cw) << 10);
+// Lane layout of a box slice w <= LPR pixels wide for a group of LPR lanes (16 or 32) sharing one
+// record, per w: cw | s << 6 | m << 12, where cw is the number of lane columns, s the rows covered per
+// pass and m = ceil(1024 / cw), so that (l * m) >> 10 = l / cw exactly for l < 32 (cw <= 16).
+// w <= LPR/2: lane l takes column l mod w and the row pair (r, r + s), s = LPR div w, stepping 2s rows.
+// LPR/2 < w <= LPR: the column pair (c, c + ceil(w/2)), stepping s = LPR div ceil(w/2) rows.
+template <int LPR>
+struct LaneTable {
+  int v[LPR + 1];
+  constexpr LaneTable() : v() {
+    for (int w = 1; w <= LPR; ++w) {
+      const int cw = w <= LPR / 2 ? w : (w + 1) / 2;
+      v[w] = cw | ((LPR / cw) << 6) | (((1024 + cw - 1) / cw) << 12);
     }
   }
 };
-__constant__ HalfLaneTable kHalfLanes = HalfLaneTable();
+__constant__ LaneTable<16> kLanes16 = LaneTable<16>();
+__constant__ LaneTable<32> kLanes32 = LaneTable<32>();
 
 struct HalfLanes {
   int c, r0, pdx, pdy, ystep;
   bool active, col2;
 };
-__device__ __forceinline__ HalfLanes half_lanes(int w, int h, int hl) {
-  const int t = kHalfLanes.v[w];
-  const int cw = t & 31, s = (t >> 5) & 31, m = t >> 10;
-  const int q = (hl * m) >> 8;
-  const bool rows = w <= 8;
+template <int LPR>
+__device__ __forceinline__ HalfLanes group_lanes(int w, int h, int hl) {
+  const int t = LPR == 16 ? kLanes16.v[w] : kLanes32.v[w];
+  const int cw = t & 63, s = (t >> 6) & 63, m = t >> 12;
+  const int q = (hl * m) >> 10;
+  const bool rows = w <= LPR / 2;
   HalfLanes L;
   L.c = hl - q * cw;
   L.r0 = q;
@@ -285,7 +290,6 @@ __global__ void __launch_bounds__(FwdCfg<TS>::threads) k_raster_fwd(
 // ---- backward: one half-warp per (projection, Gaussian) record, over the record's whole pixel box ----
 
 constexpr int kBwdThreads = 256;
-constexpr int kBwdRecords = kBwdThreads / 16;  // records per CTA
 
 // Adds the lane's share of the ten record-gradient sums, all but the first divided by amp / 2:
 // sum g V/amp; sum dL/dnum (dx^2, dx dy, dy^2); sum dL/dnum (dx, dy); sum dL/dt (1, dx, dy);
@@ -355,12 +359,14 @@ __device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const HalfLanes& B
   }
 }
 
-// Sum ten per-lane values over each half-warp (lanes hl = 0..15) and store them to out[0..9].
+// Sum ten per-lane values over each group of LPR lanes and store them to out[0..9]: first over each
+// half-warp (lanes hl = 0..15), then, for LPR = 32, across the two halves.
 // Recursive halving over an uneven split, 5 + 3 + 2 + 1 shuffles: after the xor-8 exchange a lane
 // holds five values (0-4 or 5-9), after xor-4 three of those five (local 0-2, or 3-4 plus a pad),
 // after xor-2 two, after xor-1 one, the value 5 b3 + 3 b2 + 2 b1 + b0 (b_k = bit k of hl) when that
 // lies inside its group of five.
-__device__ __forceinline__ void half_reduce_store10(const float v[10], float* out, int hl, bool store) {
+template <int LPR>
+__device__ __forceinline__ void group_reduce_store10(const float v[10], float* out, int hl, bool store) {
   const unsigned full = 0xffffffffu;
   float a[5];
   {
@@ -389,22 +395,26 @@ __device__ __forceinline__ void half_reduce_store10(const float v[10], float* ou
     c1 = k1 + __shfl_xor_sync(full, s1, 2);
   }
   const bool hi = (hl & 1) != 0;
-  const float d = (hi ? c1 : c0) + __shfl_xor_sync(full, hi ? c0 : c1, 1);
+  float d = (hi ? c1 : c0) + __shfl_xor_sync(full, hi ? c0 : c1, 1);
+  if (LPR == 32) d += __shfl_xor_sync(full, d, 16);
   const int bit2 = (hl >> 2) & 1;
   const int local = 3 * bit2 + 2 * ((hl >> 1) & 1) + (hl & 1);
-  if (store && local < (bit2 ? 5 : 3)) out[((hl & 8) ? 5 : 0) + local] = d;
+  if (store && (LPR == 16 || (threadIdx.x & 16) == 0) && local < (bit2 ? 5 : 3)) out[((hl & 8) ? 5 : 0) + local] = d;
 }
 
-// One half-warp per (projection, Gaussian) record: the ten sums over every pixel of the record's box,
-// reduced over the half-warp and written to grec[record] (12 floats, the last two unused).  Records
-// whose Gaussian was culled get zeros.  Grid: (ceil(N / 16), P).
+// One group of LPR lanes (16: two records per warp, 32: one) per (projection, Gaussian) record: the ten
+// sums over every pixel of the record's box, reduced over the group and written to grec[record] (12
+// floats, the last two unused).  Records whose Gaussian was culled get zeros.
+// Grid: (ceil(N / (256 / LPR)), P).
+template <int LPR>
 __global__ void __launch_bounds__(kBwdThreads, 4) k_raster_bwd(const float4* __restrict__ rec,
                                                                 const uint32_t* __restrict__ counts, int N, int nu,
                                                                 int nv, const float* __restrict__ gpix, float c2,
                                                                 float* __restrict__ grec) {
-  const int hl = threadIdx.x & 15;
+  constexpr int kRecords = kBwdThreads / LPR;  // records per CTA
+  const int hl = threadIdx.x & (LPR - 1);
   const int b = blockIdx.y;
-  const int n = blockIdx.x * kBwdRecords + (threadIdx.x >> 4);
+  const int n = blockIdx.x * kRecords + (int)(threadIdx.x / LPR);
   const bool valid = n < N;
   const size_t i = (size_t)b * N + (valid ? n : 0);
   float Sv[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -413,8 +423,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_raster_bwd(const float4* __r
     const int x0 = R0.bx & 0xffff, x1 = R0.bx >> 16, y0 = R0.by & 0xffff, y1 = R0.by >> 16;
     const int w = x1 - x0 + 1, h = y1 - y0 + 1;
     const float* gimg = gpix + (size_t)b * nv * nu;
-    for (int cx = 0; cx < w; cx += 16) {  // boxes wider than 16 pixels: 16-column slices
-      const HalfLanes B = half_lanes(min(16, w - cx), h, hl);
+    for (int cx = 0; cx < w; cx += LPR) {  // boxes wider than LPR pixels: LPR-column slices
+      const HalfLanes B = group_lanes<LPR>(min(LPR, w - cx), h, hl);
       if (B.active) {
         const int px = x0 + cx + B.c, py = y0 + B.r0;
         const float* gp = gimg + (size_t)py * nu + px;
@@ -425,7 +435,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_raster_bwd(const float4* __r
 #pragma unroll
     for (int q = 1; q < 10; ++q) Sv[q] *= amph;
   }
-  half_reduce_store10(Sv, grec + i * (DIGS_PARTIAL_F4 * 4), hl, valid);
+  group_reduce_store10<LPR>(Sv, grec + i * (DIGS_PARTIAL_F4 * 4), threadIdx.x & 15, valid);
 }
 
 // g = dL/dI * |X - s| for every pixel (the per-pixel factor of the line integral, applied once).
@@ -482,8 +492,15 @@ cudaError_t launch_raster_bwd(const Workspace& ws, const ViewsParam& views, floa
     k_gpix<<<g, 256, 0, st>>>(grad_proj, views, ws.nu, ws.nv, ws.dldi);
     note_launches(1);
   }
-  dim3 grid((ws.n + kBwdRecords - 1) / kBwdRecords, ws.P);
-  k_raster_bwd<<<grid, kBwdThreads, 0, st>>>(ws.rec, ws.counts, ws.n, ws.nu, ws.nv, ws.dldi, c2, (float*)ws.grec);
+  if (ws.bwd_lanes == 32) {
+    dim3 grid((ws.n + kBwdThreads / 32 - 1) / (kBwdThreads / 32), ws.P);
+    k_raster_bwd<32><<<grid, kBwdThreads, 0, st>>>(ws.rec, ws.counts, ws.n, ws.nu, ws.nv, ws.dldi, c2,
+                                                   (float*)ws.grec);
+  } else {
+    dim3 grid((ws.n + kBwdThreads / 16 - 1) / (kBwdThreads / 16), ws.P);
+    k_raster_bwd<16><<<grid, kBwdThreads, 0, st>>>(ws.rec, ws.counts, ws.n, ws.nu, ws.nv, ws.dldi, c2,
+                                                   (float*)ws.grec);
+  }
   note_launches(1);
   return cudaGetLastError();
 }

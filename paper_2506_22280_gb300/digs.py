@@ -9,7 +9,7 @@ from __future__ import annotations
 import ctypes as C
 import math
 import os
-from typing import Dict, List, Optional, Sequence
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import torch
 
@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libdigs.so")
 
 DIGS_MAX_R = 4
 DIGS_MAX_VIEWS = 128
+DIGS_MAX_SCANS = 8
 DIGS_FLAG_REUSE_BINNING = 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "workspace too small for the pairs",
           4: "device-side wait timed out", 5: "non-finite input"}
@@ -41,11 +42,11 @@ class DigsLattice(C.Structure):
 class DigsView(C.Structure):
     _fields_ = [("src", C.c_double * 3), ("det_c", C.c_double * 3), ("e_u", C.c_double * 3), ("e_v", C.c_double * 3),
                 ("du", C.c_double), ("dv", C.c_double), ("off_u", C.c_double), ("off_v", C.c_double),
-                ("nu", C.c_int), ("nv", C.c_int), ("parallel", C.c_int)]
+                ("nu", C.c_int), ("nv", C.c_int), ("parallel", C.c_int), ("scan", C.c_int)]
 
 
 class DigsOpts(C.Structure):
-    _fields_ = [("cutoff", C.c_float), ("tile", C.c_int), ("flags", C.c_int)]
+    _fields_ = [("cutoff", C.c_float), ("tile", C.c_int), ("flags", C.c_int), ("bwd_lanes", C.c_int)]
 
 
 class DigsAdamConfig(C.Structure):
@@ -56,7 +57,8 @@ class DigsAdamConfig(C.Structure):
 class DigsState(C.Structure):
     _fields_ = [("n", C.c_int), ("mu0", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("rho", C.c_void_p),
                 ("phi", C.c_void_p), ("w", C.c_void_p), ("n_w", C.c_int), ("m", C.c_void_p), ("v", C.c_void_p),
-                ("grad", C.c_void_p), ("iter", C.c_int), ("lat", DigsLattice), ("adam", DigsAdamConfig)]
+                ("grad", C.c_void_p), ("iter", C.c_int), ("lat", DigsLattice), ("adam", DigsAdamConfig),
+                ("n_scans", C.c_int), ("scan_off", C.c_int * (DIGS_MAX_SCANS + 1)), ("iter_dev", C.c_void_p)]
 
 
 _lib = None
@@ -77,7 +79,8 @@ def lib() -> C.CDLL:
         "digs_count_pairs": (I, [P, P, P, P, P, I, P, P, S, C.POINTER(LL), P]),
         "digs_project_fwd": (I, [P, P, P, P, P, I, P, P, P, S, P]),
         "digs_project_bwd": (I, [P, P, P, P, P, I, P, P, P, P, P, P, P, P, P, S, P]),
-        "digs_state_moments": (S, [I, P, I]),
+        "digs_state_moments": (S, [I, P, I, I]),
+        "digs_state_workspace_size": (S, [P, I, I, I, LL, P]),
         "digs_step": (I, [P, P, P, P, I, P, P, P, S, P]),
         "digs_sync_status": (I, [P, P]),
         "digs_status_string": (C.c_char_p, [I]),
@@ -95,7 +98,7 @@ def lib() -> C.CDLL:
 
 def exported_symbols() -> List[str]:
     return ["digs_workspace_size", "digs_ffd_eval", "digs_count_pairs", "digs_project_fwd", "digs_project_bwd",
-            "digs_state_moments", "digs_step", "digs_sync_status", "digs_status_string", "digs_stage_times",
+            "digs_state_moments", "digs_state_workspace_size", "digs_step", "digs_sync_status", "digs_status_string", "digs_stage_times",
             "digs_kernel_launches", "digs_pair_stats"]
 
 
@@ -168,11 +171,12 @@ def views_array(views: Sequence[Dict]):
         d.off_u, d.off_v = float(v.get("off_u", 0.0)), float(v.get("off_v", 0.0))
         d.nu, d.nv = int(v["nu"]), int(v["nv"])
         d.parallel = 1 if v.get("parallel", False) else 0
+        d.scan = int(v.get("scan", 0))
     return arr
 
 
-def opts_struct(cutoff: float = 3.5, tile: int = 16, flags: int = 0) -> DigsOpts:
-    return DigsOpts(float(cutoff), int(tile), int(flags))
+def opts_struct(cutoff: float = 3.5, tile: int = 16, flags: int = 0, bwd_lanes: int = 16) -> DigsOpts:
+    return DigsOpts(float(cutoff), int(tile), int(flags), int(bwd_lanes))
 
 
 def gauss_struct(mu0, scale, quat, rho) -> DigsGaussians:
@@ -231,7 +235,7 @@ class Projector:
     by the pair count of the inputs it last saw (recounted when a call reports overflow)."""
 
     def __init__(self, lattice: Dict, views: Sequence[Dict], cutoff: float = 3.5, tile: int = 16,
-                 headroom: float = 1.25, device="cuda"):
+                 headroom: float = 1.25, device="cuda", bwd_lanes: int = 16):
         if len(views) > DIGS_MAX_VIEWS:
             raise ValueError(f"at most {DIGS_MAX_VIEWS} views per call")
         self.lattice = dict(lattice)
@@ -241,8 +245,8 @@ class Projector:
         self.P = len(self.views)
         self.nu = int(self.views[0]["nu"]) if self.views else 1
         self.nv = int(self.views[0]["nv"]) if self.views else 1
-        self.opts = opts_struct(cutoff, tile)
-        self.cutoff, self.tile, self.headroom = cutoff, tile, headroom
+        self.opts = opts_struct(cutoff, tile, 0, bwd_lanes)
+        self.cutoff, self.tile, self.headroom, self.bwd_lanes = cutoff, tile, headroom, bwd_lanes
         self.ws = Workspace(device)
         self.cap = -1
 
@@ -288,7 +292,7 @@ class Projector:
         g_phi = torch.empty_like(phi)
         g_w = torch.empty(self.P, int(self.lattice["R"]), device=dev)
         g = gauss_struct(mu0, scale, quat, rho)
-        o = opts_struct(self.cutoff, self.tile, DIGS_FLAG_REUSE_BINNING if reuse else 0)
+        o = opts_struct(self.cutoff, self.tile, DIGS_FLAG_REUSE_BINNING if reuse else 0, self.bwd_lanes)
         _check(lib().digs_project_bwd(C.byref(g), C.byref(self.lat), _ptr(_f32(phi, "phi")), _ptr(_f32(w, "w")),
                                       self.varr, self.P, C.byref(o), _ptr(_f32(grad_proj.contiguous(), "grad_proj")),
                                       _ptr(g_mu0), _ptr(g_scale), _ptr(g_quat), _ptr(g_rho), _ptr(g_phi), _ptr(g_w),
@@ -329,10 +333,15 @@ def adam_config(lr0: Sequence[float], lr1: Sequence[float], total_iters: int, be
 
 class Reconstruction:
     """Parameters, Adam moments and gradient scratch of one reconstruction in device memory, stepped by
-    ``digs_step`` (render a batch, L2 loss, backward, fused Adam)."""
+    ``digs_step`` (render a batch, L2 loss, backward, fused Adam).
+
+    Several independent scans may share the state (``scan_sizes`` = their Gaussian counts, stacked in that
+    order in mu0 / scale / quat / rho; ``phi`` is then [S][R][nz][ny][nx][3] and ``w`` holds the weight rows
+    of every scan's projections); each view of a batch names its scan in ``view["scan"]``, and one step
+    renders the projections of all scans with one launch per stage."""
 
     def __init__(self, mu0, scale, quat, rho, phi, w, lattice: Dict, adam: DigsAdamConfig, cutoff=3.5, tile=16,
-                 headroom=1.3, device="cuda"):
+                 headroom=1.3, device="cuda", scan_sizes: Optional[Sequence[int]] = None, bwd_lanes: int = 16):
         dev = torch.device(device)
         f = lambda a: torch.as_tensor(a, dtype=torch.float32, device=dev).contiguous().clone()
         self.mu0, self.scale, self.quat, self.rho = f(mu0), f(scale), f(quat), f(rho)
@@ -340,8 +349,17 @@ class Reconstruction:
         self.lattice = dict(lattice)
         self.lat = lattice_struct(lattice)
         n = int(self.mu0.shape[0])
+        sizes = [n] if scan_sizes is None else [int(k) for k in scan_sizes]
+        if sum(sizes) != n or not 1 <= len(sizes) <= DIGS_MAX_SCANS:
+            raise ValueError("scan_sizes must add up to the number of Gaussians (at most %d scans)" % DIGS_MAX_SCANS)
+        self.scan_off = [0]
+        for k in sizes:
+            self.scan_off.append(self.scan_off[-1] + k)
+        self.S = len(sizes)
+        if self.S > 1:
+            self.phi = self.phi.reshape(self.S, -1)
         self.n_w = int(self.w.shape[0])
-        nm = int(lib().digs_state_moments(n, C.byref(self.lat), self.n_w))
+        nm = int(lib().digs_state_moments(n, C.byref(self.lat), self.n_w, self.S))
         self.m = torch.zeros(nm, device=dev)
         self.v = torch.zeros(nm, device=dev)
         self.grad = torch.zeros(nm, device=dev)
@@ -354,22 +372,46 @@ class Reconstruction:
         self.state.iter = 0
         self.state.lat = self.lat
         self.state.adam = adam
-        self.cutoff, self.tile, self.headroom = cutoff, tile, headroom
+        self.state.n_scans = self.S if self.S > 1 else 0
+        for k, o in enumerate(self.scan_off):
+            self.state.scan_off[k] = o
+        self.cutoff, self.tile, self.headroom, self.bwd_lanes = cutoff, tile, headroom, bwd_lanes
         self.ws = Workspace(dev)
         self.cap = {}
         self.loss = torch.zeros(1, device=dev)
+
+    def scan_params(self, s: int) -> Dict[str, torch.Tensor]:
+        """Views of scan s's Gaussians and control points inside the state."""
+        a, b = self.scan_off[s], self.scan_off[s + 1]
+        phi = self.phi[s] if self.S > 1 else self.phi
+        return dict(mu0=self.mu0[a:b], scale=self.scale[a:b], quat=self.quat[a:b], rho=self.rho[a:b],
+                    phi=phi.reshape(-1))
+
+    def count_pairs(self, views, proj_ids) -> int:
+        """(tile, Gaussian) pairs of one batch with the current parameters (synchronises)."""
+        total = 0
+        for s in range(self.S):
+            sel = [k for k, v in enumerate(views) if int(v.get("scan", 0)) == s]
+            if not sel:
+                continue
+            pj = Projector(self.lattice, [views[k] for k in sel], self.cutoff, self.tile, self.headroom,
+                           self.mu0.device)
+            p = self.scan_params(s)
+            w_rows = self.w[torch.as_tensor([proj_ids[k] for k in sel], device=self.w.device)].contiguous()
+            total += pj.count_pairs(p["mu0"], p["scale"], p["quat"], p["rho"], p["phi"], w_rows)
+        return total
+
+    def workspace_bytes(self, B: int, nu: int, nv: int, max_pairs: int) -> int:
+        o = opts_struct(self.cutoff, self.tile)
+        return int(lib().digs_state_workspace_size(C.byref(self.state), B, nu, nv, int(max_pairs), C.byref(o)))
 
     def _reserve(self, views, B, proj_ids):
         key = B
         if key in self.cap:
             return
-        pj = Projector(self.lattice, views, self.cutoff, self.tile, self.headroom, self.mu0.device)
-        w_rows = self.w[torch.as_tensor(proj_ids, device=self.w.device)].contiguous()
-        cnt = pj.count_pairs(self.mu0, self.scale, self.quat, self.rho, self.phi, w_rows)
-        cap = int(math.ceil(cnt * self.headroom)) + 4096
+        cap = int(math.ceil(self.count_pairs(views, proj_ids) * self.headroom)) + 4096
         nu, nv = int(views[0]["nu"]), int(views[0]["nv"])
-        self.ws.ensure(workspace_size(self.mu0.shape[0], B, nu, nv, int(self.lattice["R"]), cap, self.cutoff,
-                                      self.tile))
+        self.ws.ensure(self.workspace_bytes(B, nu, nv, cap))
         self.cap[key] = cap
 
     def step(self, meas: torch.Tensor, proj_ids: Sequence[int], views: Sequence[Dict], time_stages: bool = False,
@@ -381,13 +423,45 @@ class Reconstruction:
         ids = (C.c_int * B)(*[int(i) for i in proj_ids])
         if varr is None:
             varr = views_array(views)
-        o = opts_struct(self.cutoff, self.tile, DIGS_FLAG_TIME_STAGES if time_stages else 0)
+        o = opts_struct(self.cutoff, self.tile, DIGS_FLAG_TIME_STAGES if time_stages else 0, self.bwd_lanes)
         _check(lib().digs_step(C.byref(self.state), _ptr(_f32(meas, "meas")), ids, varr, B, C.byref(o),
                                _ptr(self.loss), self.ws.ptr, self.ws.nbytes, _stream()), "digs_step")
         return self.loss
 
+    # ---- graph-captured iterations -------------------------------------------------------------
+    def use_device_counter(self) -> None:
+        """Keep the step count on the device (the learning-rate schedule and Adam's bias correction then
+        come from it), so that a captured step can be replayed."""
+        if getattr(self, "iter_dev", None) is None:
+            self.iter_dev = torch.full((1,), int(self.state.iter), dtype=torch.int32, device=self.mu0.device)
+            self.state.iter_dev = self.iter_dev.data_ptr()
+
+    def capture(self, batches: Sequence[Tuple[torch.Tensor, Sequence[int], Sequence[Dict]]]) -> List["torch.cuda.CUDAGraph"]:
+        """One CUDA graph per (measured projections, projection ids, views) batch, each holding a whole
+        step (set-up, binning, both rasters, chain, Adam); ``graph.replay()`` runs the step again with the
+        current parameters.  The measured tensors are captured by address and kept alive here.  Run at
+        least one eager step first (it sizes the workspace and initialises the kernels)."""
+        self.use_device_counter()
+        for M, ids, views in batches:
+            self._reserve(views, len(ids), ids)
+        torch.cuda.synchronize()
+        graphs = []
+        keep = []
+        for M, ids, views in batches:
+            M = _f32(M, "meas")
+            varr = views_array(views)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self.step(M, ids, views, varr=varr)
+            graphs.append(g)
+            keep.append((M, varr))
+        self._graph_inputs = getattr(self, "_graph_inputs", []) + keep
+        return graphs
+
     @property
     def iter(self) -> int:
+        if getattr(self, "iter_dev", None) is not None:
+            return int(self.iter_dev.item())
         return int(self.state.iter)
 
     def status(self) -> int:

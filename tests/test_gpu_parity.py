@@ -132,10 +132,10 @@ def tiny_grad_ref():
     return wl, gp, grads
 
 
-@pytest.mark.parametrize("tile", [16, 32])
-def test_project_bwd_tiny(dev, P, tiny_grad_ref, tile):
+@pytest.mark.parametrize("tile,lanes", [(16, 16), (32, 16), (16, 32), (8, 32)])
+def test_project_bwd_tiny(dev, P, tiny_grad_ref, tile, lanes):
     wl, gp, ref = tiny_grad_ref
-    pj = P.Projector(wl.lattice, wl.views, tile=tile)
+    pj = P.Projector(wl.lattice, wl.views, tile=tile, bwd_lanes=lanes)
     g = pj.backward(*gpu_inputs(wl, dev), T(gp, dev))
     assert pj.status() == 0
     for k in ("mu0", "scale", "quat", "rho", "phi", "w"):
