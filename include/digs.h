@@ -203,6 +203,40 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
  * clear it. */
 digs_status digs_sync_status(void* ws, void* stream);
 
+/* ---- Weight-predictor CNN (warm start of the temporal weights) ---------------------------------
+ * The paper has no counterpart: this network learns, from (projection, weights) pairs that the forward
+ * model above renders, to map one projection to its R temporal weights, so that a reconstruction can
+ * start its per-projection weights near their values.  Input: the projection 2x2-averaged to 128 x 128
+ * (digs_cnn_prepare_input) and (cos theta, sin theta) of its gantry angle; four 3x3 stride-2 convolutions
+ * (1 -> 32 -> 64 -> 128 -> 128 channels, ReLU), a 128-unit ReLU layer, a linear layer to R outputs.
+ * Parameters: one FP32 array of digs_cnn_params(R) floats, in this order per layer: conv weights
+ * [Co][3][3][Ci] and biases [Co] for the four convolutions, then W1 [128][8194] (the 8 x 8 x 128
+ * features in (y, x, c) order, then cos, sin), b1 [128], W2 [R][128], b2 [R].  Images: [B][128][128];
+ * angle features cs: [B][2]; weights: [B][R].  B <= 1024.  The workspace (digs_cnn_workspace_size)
+ * holds the activations of the last forward, which digs_cnn_backward differentiates. */
+size_t digs_cnn_params(int R);
+size_t digs_cnn_workspace_size(int B, int R);
+/* He-normal weights (std sqrt(2 / fan-in)) from a counter-based generator of `seed`; zero biases. */
+digs_status digs_cnn_init(float* params, int R, unsigned long long seed, void* stream);
+/* img[b] = scale * the 2x2 means of proj[b] ([B][256][256] -> [B][128][128]). */
+digs_status digs_cnn_prepare_input(const float* proj, int B, int nu, int nv, float scale, float* img, void* stream);
+/* FP32 forward: w_out[B][R]. */
+digs_status digs_cnn_forward(const float* params, int R, const float* img, const float* cs, int B, float* w_out,
+                             void* ws, size_t ws_bytes, void* stream);
+/* Gradient of every parameter (grad_params, laid out like params) for dL/dw = grad_w [B][R], through the
+ * activations of the preceding digs_cnn_forward on the same workspace and batch size. */
+digs_status digs_cnn_backward(const float* params, int R, int B, const float* grad_w, float* grad_params, void* ws,
+                              size_t ws_bytes, void* stream);
+/* One training step on the mean squared error between the predicted and target weights ([B][R]):
+ * forward, loss (device float, written to loss_out), backward into grad, Adam (beta 0.9 / 0.999,
+ * eps 1e-8, learning rate lr, 1-based step) on params with moments m, v (zero-initialised). */
+digs_status digs_cnn_train_step(float* params, float* m, float* v, float* grad, int step, float lr, int R,
+                                const float* img, const float* cs, const float* target, int B, float* loss_out,
+                                void* ws, size_t ws_bytes, void* stream);
+/* Inference with BF16 weights and activations and FP32 accumulation (biases FP32): w_out[B][R]. */
+digs_status digs_cnn_infer_bf16(const float* params, int R, const float* img, const float* cs, int B, float* w_out,
+                                void* ws, size_t ws_bytes, void* stream);
+
 /* ---- Diagnostics (not part of the method; used to measure it) ---------------------------------- */
 
 /* Stage timing: a call whose opts->flags has DIGS_FLAG_TIME_STAGES records CUDA events around each of

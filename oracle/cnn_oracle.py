@@ -1,0 +1,92 @@
+"""FP64 CPU oracle of the weight-predictor CNN.  TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/`` and ``bench.py``'s baseline legs may import or run this module.  It shares no code with
+the CUDA path.  The network is the one the warm start of the temporal weights uses (the paper has no
+counterpart; it maps one projection to its R low-rank weights):
+
+* input: a [B][256][256] projection stack averaged over 2 x 2 pixel blocks to [B][128][128] and scaled;
+* four 3 x 3 convolutions of stride 2 and padding 1 (1 -> 32 -> 64 -> 128 -> 128 channels), each
+  followed by ReLU (128^2 -> 64^2 -> 32^2 -> 16^2 -> 8^2);
+* the 8 x 8 x 128 features flattened in (y, x, channel) order, then (cos theta, sin theta) of the
+  projection's gantry angle: 8194 inputs to a 128-unit ReLU layer, then a linear layer to R outputs;
+* training loss: mean over the batch's B x R outputs of (prediction - target)^2.
+
+Parameters are one flat vector, per layer: convolution weights [Co][ky][kx][Ci] and biases [Co] for the
+four convolutions, then W1 [128][8194], b1 [128], W2 [R][128], b2 [R].  The steps are library
+primitives in float64 (``torch.nn.functional.conv2d`` / ``linear`` / ``relu``), and autograd gives the
+gradient of the same definition.  Pins: ``tests/test_oracle_cnn.py`` (convolution against an explicit
+loop, the feature order, finite differences of the gradient, the 2 x 2 average).
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Tuple
+
+import numpy as np
+import torch
+import torch.nn.functional as F
+
+DT = torch.float64
+CH = [1, 32, 64, 128, 128]
+HID = 128
+FEAT = 8 * 8 * 128
+FEAT_IN = FEAT + 2
+
+
+def param_shapes(R: int) -> List[Tuple[str, Tuple[int, ...]]]:
+    out = []
+    for l in range(4):
+        out.append((f"w{l}", (CH[l + 1], 3, 3, CH[l])))
+        out.append((f"b{l}", (CH[l + 1],)))
+    out += [("w_fc1", (HID, FEAT_IN)), ("b_fc1", (HID,)), ("w_fc2", (R, HID)), ("b_fc2", (R,))]
+    return out
+
+
+def n_params(R: int) -> int:
+    return int(sum(np.prod(s) for _, s in param_shapes(R)))
+
+
+def unpack(flat: torch.Tensor, R: int) -> Dict[str, torch.Tensor]:
+    """Views of the flat parameter vector, in the layouts of the module docstring."""
+    out, off = {}, 0
+    for name, shape in param_shapes(R):
+        n = int(np.prod(shape))
+        out[name] = flat[off:off + n].reshape(shape)
+        off += n
+    return out
+
+
+def downsample(proj, scale: float) -> np.ndarray:
+    """scale * the 2 x 2 block means of [B][nv][nu] -> [B][nv/2][nu/2]."""
+    p = np.asarray(proj, dtype=np.float64)
+    return scale * 0.25 * (p[:, 0::2, 0::2] + p[:, 0::2, 1::2] + p[:, 1::2, 0::2] + p[:, 1::2, 1::2])
+
+
+def forward_tensors(flat: torch.Tensor, R: int, img: torch.Tensor, cs: torch.Tensor) -> torch.Tensor:
+    P = unpack(flat, R)
+    x = img.reshape(img.shape[0], 1, 128, 128)                       # NCHW for the library convolution
+    for l in range(4):
+        w = P[f"w{l}"].permute(0, 3, 1, 2)                           # [Co][Ci][ky][kx]
+        x = F.relu(F.conv2d(x, w, P[f"b{l}"], stride=2, padding=1))
+    feat = torch.cat([x.permute(0, 2, 3, 1).reshape(x.shape[0], FEAT), cs], 1)   # (y, x, c) order, cos, sin
+    h = F.relu(F.linear(feat, P["w_fc1"], P["b_fc1"]))
+    return F.linear(h, P["w_fc2"], P["b_fc2"])
+
+
+def forward(flat, R: int, img, cs) -> np.ndarray:
+    with torch.no_grad():
+        t = lambda a: torch.as_tensor(np.asarray(a), dtype=DT)
+        return forward_tensors(t(flat), R, t(img), t(cs)).numpy()
+
+
+def vjp(flat, R: int, img, cs, grad_w) -> np.ndarray:
+    """Gradient of sum(grad_w * forward) with respect to the flat parameter vector."""
+    t = lambda a: torch.as_tensor(np.asarray(a), dtype=DT)
+    p = t(flat).clone().requires_grad_(True)
+    out = forward_tensors(p, R, t(img), t(cs))
+    (out * t(grad_w)).sum().backward()
+    return p.grad.numpy()
+
+
+def mse(flat, R: int, img, cs, target) -> float:
+    out = forward(flat, R, img, cs)
+    return float(((out - np.asarray(target, dtype=np.float64)) ** 2).mean())

@@ -8,6 +8,7 @@ from .digs import (  # noqa: F401
     DigsRender,
     Projector,
     Reconstruction,
+    WeightPredictor,
     Workspace,
     adam_config,
     exported_symbols,

@@ -87,6 +87,14 @@ def lib() -> C.CDLL:
         "digs_stage_times": (I, [P]),
         "digs_kernel_launches": (LL, []),
         "digs_pair_stats": (I, [P, P, P]),
+        "digs_cnn_params": (S, [I]),
+        "digs_cnn_workspace_size": (S, [I, I]),
+        "digs_cnn_init": (I, [P, I, C.c_ulonglong, P]),
+        "digs_cnn_prepare_input": (I, [P, I, I, I, C.c_float, P, P]),
+        "digs_cnn_forward": (I, [P, I, P, P, I, P, P, S, P]),
+        "digs_cnn_backward": (I, [P, I, I, P, P, P, S, P]),
+        "digs_cnn_train_step": (I, [P, P, P, P, I, C.c_float, I, P, P, P, I, P, P, S, P]),
+        "digs_cnn_infer_bf16": (I, [P, I, P, P, I, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -99,7 +107,9 @@ def lib() -> C.CDLL:
 def exported_symbols() -> List[str]:
     return ["digs_workspace_size", "digs_ffd_eval", "digs_count_pairs", "digs_project_fwd", "digs_project_bwd",
             "digs_state_moments", "digs_state_workspace_size", "digs_step", "digs_sync_status", "digs_status_string", "digs_stage_times",
-            "digs_kernel_launches", "digs_pair_stats"]
+            "digs_kernel_launches", "digs_pair_stats", "digs_cnn_params", "digs_cnn_workspace_size", "digs_cnn_init",
+            "digs_cnn_prepare_input", "digs_cnn_forward", "digs_cnn_backward", "digs_cnn_train_step",
+            "digs_cnn_infer_bf16"]
 
 
 DIGS_FLAG_TIME_STAGES = 2
@@ -466,3 +476,76 @@ class Reconstruction:
 
     def status(self) -> int:
         return sync_status(self.ws)
+
+
+class WeightPredictor:
+    """The weight-predictor CNN (include/digs.h, "Weight-predictor CNN"): parameters, Adam moments and
+    a workspace in device memory; training and inference run in the library's kernels."""
+
+    def __init__(self, R: int, seed: int = 0, input_scale: float = 1.0, device="cuda"):
+        self.R = int(R)
+        self.dev = torch.device(device)
+        n = int(lib().digs_cnn_params(self.R))
+        if n == 0:
+            raise ValueError("unsupported R")
+        self.params = torch.empty(n, device=self.dev)
+        self.m = torch.zeros(n, device=self.dev)
+        self.v = torch.zeros(n, device=self.dev)
+        self.grad = torch.zeros(n, device=self.dev)
+        self.step_count = 0
+        self.input_scale = float(input_scale)
+        self.loss = torch.zeros(1, device=self.dev)
+        self.ws = Workspace(self.dev)
+        _check(lib().digs_cnn_init(_ptr(self.params), self.R, int(seed), _stream()), "digs_cnn_init")
+
+    def _ws(self, B: int):
+        nb = int(lib().digs_cnn_workspace_size(B, self.R))
+        if nb == 0:
+            raise ValueError("batch size out of range")
+        self.ws.ensure(nb)
+
+    def prepare(self, proj: torch.Tensor) -> torch.Tensor:
+        """[B][256][256] projections -> [B][128][128] network inputs (2x2 means times input_scale)."""
+        proj = _f32(proj, "proj")
+        B, nv, nu = proj.shape
+        img = torch.empty(B, nv // 2, nu // 2, device=proj.device)
+        _check(lib().digs_cnn_prepare_input(_ptr(proj), B, nu, nv, self.input_scale, _ptr(img), _stream()),
+               "digs_cnn_prepare_input")
+        return img
+
+    def forward(self, img: torch.Tensor, cs: torch.Tensor) -> torch.Tensor:
+        B = int(img.shape[0])
+        self._ws(B)
+        out = torch.empty(B, self.R, device=self.dev)
+        _check(lib().digs_cnn_forward(_ptr(self.params), self.R, _ptr(_f32(img, "img")), _ptr(_f32(cs, "cs")), B,
+                                      _ptr(out), self.ws.ptr, self.ws.nbytes, _stream()), "digs_cnn_forward")
+        return out
+
+    def backward(self, grad_w: torch.Tensor) -> torch.Tensor:
+        """Parameter gradient for dL/dw of the preceding forward (same batch size)."""
+        B = int(grad_w.shape[0])
+        g = torch.empty_like(self.params)
+        _check(lib().digs_cnn_backward(_ptr(self.params), self.R, B, _ptr(_f32(grad_w, "grad_w")), _ptr(g),
+                                       self.ws.ptr, self.ws.nbytes, _stream()), "digs_cnn_backward")
+        return g
+
+    def train_step(self, img: torch.Tensor, cs: torch.Tensor, target: torch.Tensor, lr: float) -> torch.Tensor:
+        B = int(img.shape[0])
+        self._ws(B)
+        self.step_count += 1
+        _check(lib().digs_cnn_train_step(_ptr(self.params), _ptr(self.m), _ptr(self.v), _ptr(self.grad),
+                                         self.step_count, float(lr), self.R, _ptr(_f32(img, "img")),
+                                         _ptr(_f32(cs, "cs")), _ptr(_f32(target, "target")), B, _ptr(self.loss),
+                                         self.ws.ptr, self.ws.nbytes, _stream()), "digs_cnn_train_step")
+        return self.loss
+
+    def predict(self, img: torch.Tensor, cs: torch.Tensor, batch: int = 512) -> torch.Tensor:
+        """BF16-weight, FP32-accumulate inference in batches."""
+        out = torch.empty(int(img.shape[0]), self.R, device=self.dev)
+        for s in range(0, int(img.shape[0]), batch):
+            B = min(batch, int(img.shape[0]) - s)
+            self._ws(B)
+            _check(lib().digs_cnn_infer_bf16(_ptr(self.params), self.R, _ptr(_f32(img[s:s + B], "img")),
+                                             _ptr(_f32(cs[s:s + B], "cs")), B, _ptr(out[s:s + B]), self.ws.ptr,
+                                             self.ws.nbytes, _stream()), "digs_cnn_infer_bf16")
+        return out

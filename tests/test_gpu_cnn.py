@@ -1,0 +1,109 @@
+"""The weight-predictor CNN's kernels (through the C-ABI) against the FP64 oracle: FP32 forward and
+parameter gradient, BF16-in / FP32-accumulate inference, the input 2x2 average, initialisation
+statistics, and training that fits a fixed batch."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cnn_oracle as C
+
+pytestmark = pytest.mark.gpu
+
+R = 3
+
+
+def relL2(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def P():
+    assert torch.cuda.is_available()
+    import paper_2506_22280_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def _inputs(B, seed=0):
+    rng = np.random.default_rng(seed)
+    img = rng.uniform(0.0, 1.0, size=(B, 128, 128)).astype(np.float32)
+    th = rng.uniform(0, 2 * np.pi, size=B)
+    cs = np.stack([np.cos(th), np.sin(th)], 1).astype(np.float32)
+    return img, cs
+
+
+def _biased(net):
+    """Non-zero biases so that the test also covers them."""
+    n = net.params.numel()
+    off = 0
+    p = net.params.cpu().numpy()
+    rng = np.random.default_rng(5)
+    for name, shape in C.param_shapes(R):
+        k = int(np.prod(shape))
+        if name.startswith("b"):
+            p[off:off + k] = rng.normal(0, 0.05, size=k)
+        off += k
+    assert off == n
+    net.params.copy_(torch.as_tensor(p))
+
+
+def test_init_statistics(P):
+    net = P.WeightPredictor(R, seed=3)
+    p = net.params.cpu().numpy().astype(np.float64)
+    off = 0
+    for name, shape in C.param_shapes(R):
+        k = int(np.prod(shape))
+        x = p[off:off + k]
+        if name.startswith("b"):
+            assert np.all(x == 0)
+        elif k > 2000:
+            std = np.sqrt(2.0 / np.prod(shape[1:]))
+            assert abs(x.std() / std - 1) < 0.05 and abs(x.mean()) < 0.05 * std, name
+        off += k
+
+
+def test_forward_and_gradient_match_oracle(P):
+    net = P.WeightPredictor(R, seed=1)
+    _biased(net)
+    img, cs = _inputs(6)
+    out = net.forward(torch.as_tensor(img, device="cuda"), torch.as_tensor(cs, device="cuda"))
+    flat = net.params.cpu().numpy().astype(np.float64)
+    ref = C.forward(flat, R, img, cs)
+    assert relL2(out.cpu().numpy(), ref) < 1e-5
+    gw = np.random.default_rng(2).normal(size=(6, R)).astype(np.float32)
+    g = net.backward(torch.as_tensor(gw, device="cuda")).cpu().numpy()
+    gref = C.vjp(flat, R, img, cs, gw)
+    off = 0
+    for name, shape in C.param_shapes(R):
+        k = int(np.prod(shape))
+        assert relL2(g[off:off + k], gref[off:off + k]) < 1e-4, name
+        off += k
+
+
+def test_bf16_inference_matches_oracle(P):
+    net = P.WeightPredictor(R, seed=4)
+    _biased(net)
+    img, cs = _inputs(40, seed=7)
+    out = net.predict(torch.as_tensor(img, device="cuda"), torch.as_tensor(cs, device="cuda"), batch=16)
+    ref = C.forward(net.params.cpu().numpy().astype(np.float64), R, img, cs)
+    assert relL2(out.cpu().numpy(), ref) < 3e-2
+
+
+def test_prepare_input_is_the_block_mean(P):
+    net = P.WeightPredictor(R, input_scale=0.5)
+    proj = np.random.default_rng(9).normal(size=(3, 256, 256)).astype(np.float32)
+    img = net.prepare(torch.as_tensor(proj, device="cuda")).cpu().numpy()
+    assert np.allclose(img, C.downsample(proj, 0.5), rtol=1e-5, atol=1e-6)
+
+
+def test_training_fits_a_fixed_batch(P):
+    net = P.WeightPredictor(R, seed=2)
+    img, cs = _inputs(32, seed=11)
+    target = np.random.default_rng(12).normal(size=(32, R)).astype(np.float32)
+    I, Cs, Tg = (torch.as_tensor(a, device="cuda") for a in (img, cs, target))
+    loss0 = C.mse(net.params.cpu().numpy().astype(np.float64), R, img, cs, target)
+    losses = [float(net.train_step(I, Cs, Tg, 1e-3).item()) for _ in range(100)]
+    assert abs(losses[0] - loss0) < 1e-4 * loss0, (losses[0], loss0)  # the step reports its starting loss
+    final = C.mse(net.params.cpu().numpy().astype(np.float64), R, img, cs, target)
+    assert final < 0.1 * loss0, (loss0, final)
