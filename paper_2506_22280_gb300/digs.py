@@ -260,6 +260,14 @@ class Projector:
         self.ws = Workspace(device)
         self.cap = -1
 
+    def set_views(self, views: Sequence[Dict]) -> None:
+        """Project along other views of the same count and detector (the workspace is kept; call
+        reserve(force=True) if the pair count may have grown)."""
+        if len(views) != self.P:
+            raise ValueError("set_views keeps the number of views")
+        self.views = list(views)
+        self.varr = views_array(self.views)
+
     def _size(self, n, cap):
         return workspace_size(n, self.P, self.nu, self.nv, int(self.lattice["R"]), cap, self.cutoff, self.tile)
 
@@ -437,6 +445,17 @@ class Reconstruction:
         _check(lib().digs_step(C.byref(self.state), _ptr(_f32(meas, "meas")), ids, varr, B, C.byref(o),
                                _ptr(self.loss), self.ws.ptr, self.ws.nbytes, _stream()), "digs_step")
         return self.loss
+
+    def clone(self) -> "Reconstruction":
+        """An independent copy of the state (parameters, Adam moments, step count)."""
+        sizes = [self.scan_off[k + 1] - self.scan_off[k] for k in range(self.S)]
+        r = Reconstruction(self.mu0, self.scale, self.quat, self.rho, self.phi, self.w, self.lattice, self.state.adam,
+                           self.cutoff, self.tile, self.headroom, self.mu0.device, sizes if self.S > 1 else None,
+                           self.bwd_lanes)
+        r.m.copy_(self.m)
+        r.v.copy_(self.v)
+        r.state.iter = self.iter
+        return r
 
     # ---- graph-captured iterations -------------------------------------------------------------
     def use_device_counter(self) -> None:
