@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time direct calls instead of graph replays")
     ap.add_argument("--no-batching", action="store_true", help="skip the four-scan batching measurement")
+    ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start measurement")
     return ap.parse_args()
 
 
@@ -259,6 +260,75 @@ def batching_measurement(pkg, D, device, steps=6, warmup=3):
             "device_status": status}
 
 
+def warmstart_measurement(pkg, D, wl, meas, device, tile, lanes, B=16, warmup_iters=150, plain_iters=2150,
+                          n_pairs=10_000, epochs=3):
+    """Wall time for the plain batched optimisation to reach its final full-scan loss after `plain_iters`
+    steps, against the learned warm start (render training pairs with the model, train the CNN, propose
+    all weights, keep them if the scan loss falls) followed by the same optimisation until its scan loss
+    is within 1 % of the plain final loss.  Both start from the same state after a short plain warm-up."""
+    import torch
+    import synth
+    from paper_2506_22280_gb300 import warmstart as WS
+    n_proj = len(wl.views)
+    init = dict(mu0=wl.mu0, scale=wl.scale, quat=wl.quat, rho=wl.rho, phi=wl.phi, w=wl.w, lattice=wl.lattice)
+    rec = make_rec_factory(pkg, D, init, device, total=warmup_iters + plain_iters)(tile, lanes)
+    plan = [batch_ids(s, B, n_proj) for s in range(warmup_iters + plain_iters)]
+
+    def step(r, s):
+        ids = plan[s]
+        r.step(meas[torch.as_tensor(ids, device=device)].contiguous(), ids, [wl.views[i] for i in ids])
+
+    for s in range(warmup_iters):
+        step(rec, s)
+    plain, warm = rec.clone(), rec.clone()
+    del rec
+    chunk = n_proj // B
+    curve = []
+    torch.cuda.synchronize()
+    t_plain = 0.0
+    for k0 in range(0, plain_iters, chunk):
+        t0 = time.perf_counter()
+        for k in range(k0, min(k0 + chunk, plain_iters)):
+            step(plain, warmup_iters + k)
+        torch.cuda.synchronize()
+        t_plain += time.perf_counter() - t0
+        if (k0 // chunk) % 10 == 9 or k0 + chunk >= plain_iters:
+            curve.append([min(k0 + chunk, plain_iters), round(t_plain, 3), WS.scan_loss(plain, meas, wl.views, plain.w)])
+    final = curve[-1][2]
+    target = 1.01 * final
+    t0 = time.perf_counter()
+    pred = pkg.WeightPredictor(int(wl.lattice["R"]), seed=0, input_scale=0.25)
+    make_views = lambda a: synth.circular_views(a, 1000.0, 1500.0, 256, 256, 1.6, 1.6)
+    imgs, cs, W = WS.render_training_pairs(warm, make_views, n_pairs, pred, seed=1)
+    losses = WS.train(pred, imgs, cs, W, epochs, batch=256, lr=1e-3)
+    res = WS.warm_start(warm, pred, meas, wl.views, np.asarray(wl.angles), list(range(n_proj)))
+    torch.cuda.synchronize()
+    t_cnn = time.perf_counter() - t0
+    t_warm, iters, reached, wcurve = t_cnn, 0, None, []
+    while iters < plain_iters:
+        t0 = time.perf_counter()
+        for k in range(iters, min(iters + chunk, plain_iters)):
+            step(warm, warmup_iters + k)
+        torch.cuda.synchronize()
+        t_warm += time.perf_counter() - t0
+        iters = min(iters + chunk, plain_iters)
+        L = WS.scan_loss(warm, meas, wl.views, warm.w)
+        wcurve.append([iters, round(t_warm, 3), L])
+        if L <= target:
+            reached = iters
+            break
+    status = max(plain.status(), warm.status())
+    return {"protocol": (f"{warmup_iters} shared plain steps, then plain for {plain_iters} steps vs CNN warm start "
+                         f"({n_pairs} rendered pairs, {epochs} epochs, BF16 inference, accept if the scan loss "
+                         f"falls) + the same steps until the scan loss is within 1% of the plain final; "
+                         f"B = {B}, wall time, scan-loss evaluations excluded"),
+            "plain_s": t_plain, "plain_final_scan_loss": final, "warm_s": t_warm if reached else None,
+            "cnn_s": t_cnn, "warm_steps_to_target": reached, "speedup": (t_plain / t_warm) if reached else None,
+            "accepted": res["accepted"], "scan_loss_before": res["loss_plain"],
+            "scan_loss_proposal": res["loss_proposal"], "cnn_train_loss": losses, "plain_curve": curve,
+            "warm_curve": wcurve, "device_status": status}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -367,6 +437,9 @@ def run_ours(args):
     batching = None
     if world == 1 and not args.no_batching:
         batching = batching_measurement(pkg, D, device)
+    warm = None
+    if world == 1 and not args.no_warmstart:
+        warm = warmstart_measurement(pkg, D, wl, meas, device, tile, lanes)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -410,6 +483,8 @@ def run_ours(args):
         line["config"]["autotune_trials"] = tuned["trials"]
     if batching is not None:
         line["batching"] = batching
+    if warm is not None:
+        line["warm_start"] = warm
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
