@@ -179,10 +179,23 @@ typedef struct {
                                         schedule, Adam bias correction) is read from and incremented on
                                         the device, so a captured CUDA graph of a step can be replayed;
                                         `iter` is then neither read nor changed                        */
+  float* w_ctrl;                     /* optional [n_ctrl][R]: temporal B-spline control points of the
+                                        weights (Sec. 4.2; one scan only).  When set, each step first
+                                        writes the rows proj_ids of w from them -- projection p at
+                                        tau = p / t_step + 1 control-point units, f = floor(tau) - 1,
+                                        u = tau - floor(tau), w(p) = sum_l B_l(u) w_ctrl[f + l], outside
+                                        nodes zero -- and Adam updates w_ctrl instead of w (the last
+                                        group of m / v / grad is then n_ctrl * R floats)              */
+  int n_ctrl;
+  float t_step;                      /* control-point spacing in projection indices (e.g. 4)          */
 } DigsState;
 
-/* Number of floats in DigsState.m (and v, grad) for n Gaussians in n_scans (>= 1) scans. */
+/* Number of floats in DigsState.m (and v, grad) for n Gaussians in n_scans (>= 1) scans with per-row
+ * weights w (for temporal control points use digs_state_size). */
 size_t digs_state_moments(int n, const DigsLattice* lat, int n_w, int n_scans);
+
+/* Number of floats in m (and v, grad) for the state as configured (scans, temporal control points). */
+size_t digs_state_size(const DigsState* st);
 
 /* Bytes of workspace digs_step needs for the state's scans, B projections of nu x nv pixels and room for
  * max_pairs (tile, Gaussian) pairs (records are laid out [B][largest scan's Gaussian count]). */

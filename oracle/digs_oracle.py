@@ -90,6 +90,27 @@ def bspline(u: torch.Tensor, deriv: int = 0) -> torch.Tensor:
     raise ValueError(deriv)
 
 
+def temporal_weights(ctrl, t_step: float, rows) -> torch.Tensor:
+    """Weights w[rows][R] from temporal control points ctrl[n_ctrl][R] (Sec. 4.2: a cubic B-spline over
+    the time axis, control points every t_step time points, with the basis of Eq. 10): projection p sits
+    at tau = p / t_step + 1 control-point units; with f = floor(tau) - 1 and u = tau - floor(tau),
+    w(p) = sum_l B_l(u) ctrl[f + l]; control points outside [0, n_ctrl) read as zero.  Differentiable in
+    ctrl (torch input)."""
+    c = ctrl if isinstance(ctrl, torch.Tensor) else torch.as_tensor(np.asarray(ctrl), dtype=DT)
+    out = []
+    for p in rows:
+        tau = float(p) / float(t_step) + 1.0
+        fl = math.floor(tau)
+        B = bspline(torch.tensor(tau - fl, dtype=DT))
+        acc = torch.zeros(c.shape[1], dtype=DT)
+        for l in range(4):
+            j = fl - 1 + l
+            if 0 <= j < c.shape[0]:
+                acc = acc + B[l] * c[j]
+        out.append(acc)
+    return torch.stack(out, 0)
+
+
 def lattice_coords(lattice: Dict, x: torch.Tensor):
     """p = (x - origin) / spacing, its floor and fractional part (Eq. 10)."""
     origin = _t(lattice["origin"])

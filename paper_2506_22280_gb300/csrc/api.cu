@@ -17,7 +17,7 @@ void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, long long cap, int tile,
-              int n_total) {
+              int n_total, int w_rows) {
   Workspace w;
   memset(&w, 0, sizeof(w));
   w.n = n; w.n_total = n_total; w.P = P; w.nu = nu; w.nv = nv; w.R = R; w.cap = cap; w.tile = tile;
@@ -59,6 +59,7 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.padj = (float*)take((size_t)(kPairAdj + R) * P * n * 4 + 4);
   w.proj = (float*)take((size_t)P * nu * nv * 4);
   w.dldi = (float*)take((size_t)P * nu * nv * 4);
+  w.gw_rows = (float*)take((size_t)w_rows * R * 4 + 4);
   w.bytes = off;
   if (ws) *ws = w;
   return off;
@@ -141,13 +142,13 @@ digs_status make_lattice(const DigsLattice* lat, LatticeC& L) {
 }
 
 // Largest pair capacity whose layout fits `bytes` (n: record stride, n_total: all Gaussians).
-long long capacity_for(size_t bytes, int n, int P, int nu, int nv, int R, int tile, int n_total) {
-  if (layout(nullptr, nullptr, n, P, nu, nv, R, 0, tile, n_total) > bytes) return -1;
+long long capacity_for(size_t bytes, int n, int P, int nu, int nv, int R, int tile, int n_total, int w_rows) {
+  if (layout(nullptr, nullptr, n, P, nu, nv, R, 0, tile, n_total, w_rows) > bytes) return -1;
   long long lo = 0, hi = 1;
-  while (layout(nullptr, nullptr, n, P, nu, nv, R, hi, tile, n_total) <= bytes && hi < (1LL << 32)) hi *= 2;
+  while (layout(nullptr, nullptr, n, P, nu, nv, R, hi, tile, n_total, w_rows) <= bytes && hi < (1LL << 32)) hi *= 2;
   while (hi - lo > 1) {
     long long mid = (lo + hi) / 2;
-    if (layout(nullptr, nullptr, n, P, nu, nv, R, mid, tile, n_total) <= bytes) lo = mid; else hi = mid;
+    if (layout(nullptr, nullptr, n, P, nu, nv, R, mid, tile, n_total, w_rows) <= bytes) lo = mid; else hi = mid;
   }
   return std::min(lo, (long long)0xffffffffLL);
 }
@@ -248,9 +249,10 @@ digs_status prepare(const DigsGaussians* g, const DigsLattice* lat, const float*
   c.flags = opts ? opts->flags : 0;
   c.st = (cudaStream_t)stream;
   int tile = opt_tile(opts);
-  long long cap = capacity_for(ws_bytes, c.sc.nmax, P, nu, nv, c.L.R, tile, g->n);
+  const int w_rows = (scans && scans->w_ctrl) ? scans->n_w : 0;
+  long long cap = capacity_for(ws_bytes, c.sc.nmax, P, nu, nv, c.L.R, tile, g->n, w_rows);
   if (cap < 0) return DIGS_ERR_ARG;
-  layout(&c.ws, wsp, c.sc.nmax, P, nu, nv, c.L.R, cap, tile, g->n);
+  layout(&c.ws, wsp, c.sc.nmax, P, nu, nv, c.L.R, cap, tile, g->n, w_rows);
   c.ws.bwd_lanes = (opts && opts->bwd_lanes == 32) ? 32 : 16;
   return DIGS_OK;
 }
@@ -311,7 +313,15 @@ size_t digs_state_workspace_size(const DigsState* st, int B, int nu, int nv, lon
   LatticeC L;
   ScanTable t;
   if (make_lattice(&st->lat, L) != DIGS_OK || state_scans(st, L, t) != DIGS_OK) return 0;
-  return layout(nullptr, nullptr, t.nmax, B, nu, nv, L.R, max_pairs, opt_tile(opts), st->n);
+  return layout(nullptr, nullptr, t.nmax, B, nu, nv, L.R, max_pairs, opt_tile(opts), st->n,
+                st->w_ctrl ? st->n_w : 0);
+}
+
+size_t digs_state_size(const DigsState* st) {
+  if (!st) return 0;
+  const size_t wg = st->w_ctrl ? (size_t)st->n_ctrl * st->lat.R : (size_t)st->n_w * st->lat.R;
+  const size_t S = st->n_scans > 1 ? (size_t)st->n_scans : 1;
+  return (size_t)st->n * 11 + S * st->lat.nx * st->lat.ny * st->lat.nz * 3 * st->lat.R + wg;
 }
 
 digs_status digs_ffd_eval(const DigsLattice* lat, const float* phi, const float* x, int n, float* U, float* dU,
@@ -401,22 +411,32 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
   float* gr = st->grad;
   float *g_mu0 = gr, *g_ls = gr + 3 * (size_t)n, *g_q = gr + 6 * (size_t)n, *g_rho = gr + 10 * (size_t)n;
   float *g_phi = gr + 11 * (size_t)n, *g_w = g_phi + nphi;
+  const bool temporal = st->w_ctrl != nullptr;
+  RowsParam rowsp;
+  if (temporal) {
+    if (c.sc.S > 1 || st->n_ctrl < 1 || !(st->t_step > 0.f)) return DIGS_ERR_ARG;
+    for (int b = 0; b < B; ++b) rowsp.v[b] = proj_ids[b];
+    DIGS_TRY(launch_temporal_eval(st->w_ctrl, st->n_ctrl, R, st->t_step, rowsp, B, st->w, c.st));
+  }
+  float* g_w_rows = temporal ? c.ws.gw_rows : g_w;  // dL/dw per row; with control points, their adjoint follows
   s = bin(c, st->phi, st->w);
   if (s != DIGS_OK) return s;
   float inv_count = 1.f / ((float)B * c.ws.nu * c.ws.nv);
   DIGS_TRY(launch_raster_fwd(c.ws, c.views, c.c2, c.ws.proj, meas, c.ws.dldi, inv_count, c.st));
   mark(c, 4);
   DIGS_TRY(launch_loss_reduce(c.ws.loss_part, B * c.ws.T * fwd_blocks(c.ws.tile), loss_out, inv_count, c.st));
-  s = backward(c, st->phi, st->w, nullptr, g_mu0, g_ls, g_q, g_rho, g_phi, g_w, st->n_w);
+  s = backward(c, st->phi, st->w, nullptr, g_mu0, g_ls, g_q, g_rho, g_phi, g_w_rows, st->n_w);
   if (s != DIGS_OK) return s;
+  if (temporal) DIGS_TRY(launch_temporal_bwd(g_w_rows, st->n_ctrl, R, st->t_step, rowsp, B, g_w, c.st));
   const DigsAdamConfig& a = st->adam;
   float lr[6];
   for (int k = 0; k < 6; ++k) {
     float t = a.total_iters > 1 ? std::min(std::max((float)st->iter / (float)(a.total_iters - 1), 0.f), 1.f) : 0.f;
     lr[k] = a.lr0[k] + (a.lr1[k] - a.lr0[k]) * t;
   }
-  size_t sizes[6] = {3 * (size_t)n, 3 * (size_t)n, 4 * (size_t)n, (size_t)n, nphi, (size_t)st->n_w * R};
-  float* params[6] = {st->mu0, st->scale, st->quat, st->rho, st->phi, st->w};
+  size_t sizes[6] = {3 * (size_t)n, 3 * (size_t)n, 4 * (size_t)n, (size_t)n, nphi,
+                     temporal ? (size_t)st->n_ctrl * R : (size_t)st->n_w * R};
+  float* params[6] = {st->mu0, st->scale, st->quat, st->rho, st->phi, temporal ? st->w_ctrl : st->w};
   const float* grads[6] = {g_mu0, g_ls, g_q, g_rho, g_phi, g_w};
   int kinds[6] = {0, 1, 0, 2, 0, 0};
   AdamGroup groups[6];

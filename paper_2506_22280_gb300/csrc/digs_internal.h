@@ -41,6 +41,7 @@ struct Workspace {
   float* loss_part;       // [P * T * fwd_blocks(tile)] forward: squared residuals per 8 x 8 block (warp)
   float* proj;            // [P * nv * nu] (digs_step)
   float* dldi;            // [P * nv * nu] (digs_step)
+  float* gw_rows;         // [w rows][R] (digs_step with temporal control points): dL/dw before the adjoint
   float* grads;           // all parameter gradients (digs_step)
   size_t bytes;
   long long cap;
@@ -53,7 +54,8 @@ struct Workspace {
 // Forward work items (8 x 8 pixel blocks) per tile.
 inline int fwd_blocks(int tile) { return (tile / 8) * (tile / 8); }
 
-size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, long long cap, int tile, int n_total);
+size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, long long cap, int tile, int n_total,
+              int w_rows = 0);
 
 // scan.cu
 cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int n, uint32_t* tmp, cudaStream_t st);
@@ -95,6 +97,15 @@ cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const Latt
 cudaError_t launch_gw_reduce(const Workspace& ws, const ViewsParam& views, int P, int R, float* g_w, int w_rows,
                              cudaStream_t st);
 int chain_blocks(int n);
+
+// temporal.cu: w rows of a step from the temporal B-spline control points, and the adjoint.
+struct RowsParam {
+  int v[DIGS_MAX_VIEWS];
+};
+cudaError_t launch_temporal_eval(const float* ctrl, int n_ctrl, int R, float t_step, const RowsParam& rows, int B,
+                                 float* w, cudaStream_t st);
+cudaError_t launch_temporal_bwd(const float* g_w, int n_ctrl, int R, float t_step, const RowsParam& rows, int B,
+                                float* g_ctrl, cudaStream_t st);
 
 // adam.cu
 struct AdamGroup {

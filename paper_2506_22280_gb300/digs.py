@@ -58,7 +58,8 @@ class DigsState(C.Structure):
     _fields_ = [("n", C.c_int), ("mu0", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("rho", C.c_void_p),
                 ("phi", C.c_void_p), ("w", C.c_void_p), ("n_w", C.c_int), ("m", C.c_void_p), ("v", C.c_void_p),
                 ("grad", C.c_void_p), ("iter", C.c_int), ("lat", DigsLattice), ("adam", DigsAdamConfig),
-                ("n_scans", C.c_int), ("scan_off", C.c_int * (DIGS_MAX_SCANS + 1)), ("iter_dev", C.c_void_p)]
+                ("n_scans", C.c_int), ("scan_off", C.c_int * (DIGS_MAX_SCANS + 1)), ("iter_dev", C.c_void_p),
+                ("w_ctrl", C.c_void_p), ("n_ctrl", C.c_int), ("t_step", C.c_float)]
 
 
 _lib = None
@@ -81,6 +82,7 @@ def lib() -> C.CDLL:
         "digs_project_bwd": (I, [P, P, P, P, P, I, P, P, P, P, P, P, P, P, P, S, P]),
         "digs_state_moments": (S, [I, P, I, I]),
         "digs_state_workspace_size": (S, [P, I, I, I, LL, P]),
+        "digs_state_size": (S, [P]),
         "digs_step": (I, [P, P, P, P, I, P, P, P, S, P]),
         "digs_sync_status": (I, [P, P]),
         "digs_status_string": (C.c_char_p, [I]),
@@ -106,7 +108,7 @@ def lib() -> C.CDLL:
 
 def exported_symbols() -> List[str]:
     return ["digs_workspace_size", "digs_ffd_eval", "digs_count_pairs", "digs_project_fwd", "digs_project_bwd",
-            "digs_state_moments", "digs_state_workspace_size", "digs_step", "digs_sync_status", "digs_status_string", "digs_stage_times",
+            "digs_state_moments", "digs_state_workspace_size", "digs_state_size", "digs_step", "digs_sync_status", "digs_status_string", "digs_stage_times",
             "digs_kernel_launches", "digs_pair_stats", "digs_cnn_params", "digs_cnn_workspace_size", "digs_cnn_init",
             "digs_cnn_prepare_input", "digs_cnn_forward", "digs_cnn_backward", "digs_cnn_train_step",
             "digs_cnn_infer_bf16"]
@@ -359,7 +361,8 @@ class Reconstruction:
     renders the projections of all scans with one launch per stage."""
 
     def __init__(self, mu0, scale, quat, rho, phi, w, lattice: Dict, adam: DigsAdamConfig, cutoff=3.5, tile=16,
-                 headroom=1.3, device="cuda", scan_sizes: Optional[Sequence[int]] = None, bwd_lanes: int = 16):
+                 headroom=1.3, device="cuda", scan_sizes: Optional[Sequence[int]] = None, bwd_lanes: int = 16,
+                 w_ctrl=None, t_step: float = 4.0):
         dev = torch.device(device)
         f = lambda a: torch.as_tensor(a, dtype=torch.float32, device=dev).contiguous().clone()
         self.mu0, self.scale, self.quat, self.rho = f(mu0), f(scale), f(quat), f(rho)
@@ -377,22 +380,27 @@ class Reconstruction:
         if self.S > 1:
             self.phi = self.phi.reshape(self.S, -1)
         self.n_w = int(self.w.shape[0])
-        nm = int(lib().digs_state_moments(n, C.byref(self.lat), self.n_w, self.S))
-        self.m = torch.zeros(nm, device=dev)
-        self.v = torch.zeros(nm, device=dev)
-        self.grad = torch.zeros(nm, device=dev)
+        self.w_ctrl = None if w_ctrl is None else f(w_ctrl)
+        self.t_step = float(t_step)
         self.state = DigsState()
         self.state.n = n
         self.state.mu0, self.state.scale = self.mu0.data_ptr(), self.scale.data_ptr()
         self.state.quat, self.state.rho = self.quat.data_ptr(), self.rho.data_ptr()
         self.state.phi, self.state.w, self.state.n_w = self.phi.data_ptr(), self.w.data_ptr(), self.n_w
-        self.state.m, self.state.v, self.state.grad = self.m.data_ptr(), self.v.data_ptr(), self.grad.data_ptr()
         self.state.iter = 0
         self.state.lat = self.lat
         self.state.adam = adam
         self.state.n_scans = self.S if self.S > 1 else 0
         for k, o in enumerate(self.scan_off):
             self.state.scan_off[k] = o
+        if self.w_ctrl is not None:  # weights from temporal B-spline control points (one scan)
+            self.state.w_ctrl, self.state.n_ctrl = self.w_ctrl.data_ptr(), int(self.w_ctrl.shape[0])
+            self.state.t_step = self.t_step
+        nm = int(lib().digs_state_size(C.byref(self.state)))
+        self.m = torch.zeros(nm, device=dev)
+        self.v = torch.zeros(nm, device=dev)
+        self.grad = torch.zeros(nm, device=dev)
+        self.state.m, self.state.v, self.state.grad = self.m.data_ptr(), self.v.data_ptr(), self.grad.data_ptr()
         self.cutoff, self.tile, self.headroom, self.bwd_lanes = cutoff, tile, headroom, bwd_lanes
         self.ws = Workspace(dev)
         self.cap = {}
@@ -451,7 +459,7 @@ class Reconstruction:
         sizes = [self.scan_off[k + 1] - self.scan_off[k] for k in range(self.S)]
         r = Reconstruction(self.mu0, self.scale, self.quat, self.rho, self.phi, self.w, self.lattice, self.state.adam,
                            self.cutoff, self.tile, self.headroom, self.mu0.device, sizes if self.S > 1 else None,
-                           self.bwd_lanes)
+                           self.bwd_lanes, self.w_ctrl, self.t_step)
         r.m.copy_(self.m)
         r.v.copy_(self.v)
         r.state.iter = self.iter

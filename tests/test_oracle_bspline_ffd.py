@@ -165,3 +165,28 @@ def test_separable_field_axis_order():
     assert torch.allclose(U[:, 0, 0], torch.zeros(50, dtype=DT)) and torch.allclose(U[:, 0, 2], torch.zeros(50, dtype=DT))
     dF = _spline1d(f, p[:, 0], 1) / lat["spacing"][0]
     assert torch.allclose(dU[:, 0, 1, 0], dF * G * H, atol=1e-13)
+
+
+# ---- temporal B-spline of the weights (Sec. 4.2) ------------------------------------------------
+def test_temporal_weights_reproduce_constants_lines_and_knot_values():
+    from oracle import digs_oracle as O
+    t_step = 4.0
+    n_ctrl = 12
+    rows = list(range(0, 30))
+    const = np.full((n_ctrl, 2), 1.7)
+    w = O.temporal_weights(const, t_step, rows).numpy()
+    assert np.allclose(w, 1.7, atol=1e-12)                     # partition of unity (all nodes inside)
+    j = np.arange(n_ctrl, dtype=float)
+    lin = np.stack([0.5 * j - 2.0, -1.5 * j + 0.25], 1)
+    w = O.temporal_weights(lin, t_step, rows).numpy()
+    tau = np.asarray(rows) / t_step + 1.0
+    assert np.allclose(w[:, 0], 0.5 * tau - 2.0, atol=1e-12)  # linear precision: w = line(tau)
+    assert np.allclose(w[:, 1], -1.5 * tau + 0.25, atol=1e-12)
+    spike = np.zeros((n_ctrl, 1))
+    spike[5, 0] = 6.0
+    # at a knot (u = 0) the basis is (1/6, 4/6, 1/6, 0): p = 16 -> tau = 5, f = 4, nodes 4..7
+    assert np.allclose(O.temporal_weights(spike, t_step, [16]).numpy(), [[4.0]])
+    assert np.allclose(O.temporal_weights(spike, t_step, [12]).numpy(), [[1.0]])   # tau = 4: node 5 is f + 2
+    # nodes past the end read as zero
+    # p = 40: tau = 11, nodes 10..13 of which 10, 11 exist (1/6 + 4/6); p = 44: only node 11 (1/6)
+    assert np.allclose(O.temporal_weights(const, t_step, [40, 44]).numpy(), [[1.7 * 5 / 6] * 2, [1.7 / 6] * 2])
