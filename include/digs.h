@@ -216,6 +216,27 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
  * clear it. */
 digs_status digs_sync_status(void* ws, void* stream);
 
+/* ---- Evaluation volumes at one time point ------------------------------------------------------ */
+
+/* Voxel grid: centre of voxel (i, j, k) = origin + (i, j, k) * spacing (mm), i (x) fastest. */
+typedef struct {
+  int nx, ny, nz;
+  float origin[3], spacing[3];
+} DigsGrid;
+
+/* Attenuation volume of the cloud deformed with the weights w[R] of one time point (Eq. 3 with the warp
+ * of Eq. 7-8): vol[nz][ny][nx] = sum_n rho_n exp(-E_n / 2) at the voxel centres, E_n the squared
+ * Mahalanobis distance to the deformed mean, each Gaussian taken where E_n <= cutoff^2 (opts->cutoff,
+ * default 3.5); folded Gaussians (det K <= 1e-6) are dropped.  Sums use float atomics, so the result
+ * varies between runs within rounding.  w: device [R]. */
+digs_status digs_voxelize(const DigsGaussians* g, const DigsLattice* lat, const float* phi, const float* w,
+                          const DigsGrid* grid, const DigsOpts* opts, float* vol, void* stream);
+
+/* Displacement field of one time point, D(x, t) - x = sum_r w_r u_r(x) (Eq. 9-10), at the voxel centres:
+ * dvf[nz][ny][nx][3] mm.  w: device [R]. */
+digs_status digs_dvf(const DigsLattice* lat, const float* phi, const float* w, const DigsGrid* grid, float* dvf,
+                     void* stream);
+
 /* ---- Weight-predictor CNN (warm start of the temporal weights) ---------------------------------
  * The paper has no counterpart: this network learns, from (projection, weights) pairs that the forward
  * model above renders, to map one projection to its R temporal weights, so that a reconstruction can

@@ -166,6 +166,48 @@ def deform(mu0: torch.Tensor, sigma0: torch.Tensor, U: torch.Tensor, dU: torch.T
     return mu, sigma, K
 
 
+# ----------------------------------------------------------------------------- volumes (evaluation)
+def grid_centres(grid: Dict) -> torch.Tensor:
+    """Voxel centres [nz][ny][nx][3] of a grid: origin + (i, j, k) * spacing, i (x) fastest."""
+    o, h = _t(grid["origin"]), _t(grid["spacing"])
+    k, j, i = torch.meshgrid(torch.arange(grid["nz"], dtype=DT), torch.arange(grid["ny"], dtype=DT),
+                             torch.arange(grid["nx"], dtype=DT), indexing="ij")
+    return torch.stack([o[0] + i * h[0], o[1] + j * h[1], o[2] + k * h[2]], -1)
+
+
+def voxelize(gauss: Dict, lattice: Dict, phi, w_row, grid: Dict, cutoff: Optional[float] = 3.5) -> np.ndarray:
+    """Attenuation volume of the cloud deformed with weights w_row [R] (Eq. 3 with the warp of Eq. 7-8):
+    vol[k][j][i] = sum_n rho_n exp(-E_n / 2), E_n = (x - mu'_n)^T Sigma'_n^-1 (x - mu'_n), at the voxel
+    centres, each Gaussian taken where E_n <= cutoff^2 (all of it when cutoff is None); folded Gaussians
+    (det K <= 1e-6) are dropped as in the projector."""
+    with torch.no_grad():
+        T = _inputs(gauss, phi, np.asarray(w_row)[None])
+        sigma0 = covariance(T["scale"], T["quat"])
+        U, dU = ffd_eval(T["phi"], lattice, T["mu0"])
+        mu, sigma, K = deform(T["mu0"], sigma0, U, dU, T["w"][0])
+        P = torch.linalg.inv(sigma)
+        keep = torch.linalg.det(K) > FOLD_EPS
+        X = grid_centres(grid).reshape(-1, 3)
+        vol = torch.zeros(X.shape[0], dtype=DT)
+        for n in torch.nonzero(keep).flatten().tolist():
+            d = X - mu[n]
+            E = torch.einsum("vi,ij,vj->v", d, P[n], d)
+            val = T["rho"][n] * torch.exp(-0.5 * E)
+            if cutoff is not None:
+                val = torch.where(E <= cutoff * cutoff, val, torch.zeros_like(val))
+            vol += val
+        return vol.reshape(grid["nz"], grid["ny"], grid["nx"]).numpy()
+
+
+def dvf(lattice: Dict, phi, w_row, grid: Dict) -> np.ndarray:
+    """Displacement D(x, t) - x = sum_r w_r u_r(x) at the voxel centres, [nz][ny][nx][3] (Eq. 9-10)."""
+    with torch.no_grad():
+        X = grid_centres(grid).reshape(-1, 3)
+        U, _ = ffd_eval(_t(phi), lattice, X)
+        d = torch.einsum("r,nri->ni", _t(w_row), U)
+        return d.reshape(grid["nz"], grid["ny"], grid["nx"], 3).numpy()
+
+
 # ----------------------------------------------------------------------------- geometry
 def view_tensors(view: Dict):
     v = {k: _t(view[k]) for k in ("src", "det_c", "e_u", "e_v")}

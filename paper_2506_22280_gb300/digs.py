@@ -89,6 +89,8 @@ def lib() -> C.CDLL:
         "digs_stage_times": (I, [P]),
         "digs_kernel_launches": (LL, []),
         "digs_pair_stats": (I, [P, P, P]),
+        "digs_voxelize": (I, [P, P, P, P, P, P, P, P]),
+        "digs_dvf": (I, [P, P, P, P, P, P]),
         "digs_cnn_params": (S, [I]),
         "digs_cnn_workspace_size": (S, [I, I]),
         "digs_cnn_init": (I, [P, I, C.c_ulonglong, P]),
@@ -109,7 +111,7 @@ def lib() -> C.CDLL:
 def exported_symbols() -> List[str]:
     return ["digs_workspace_size", "digs_ffd_eval", "digs_count_pairs", "digs_project_fwd", "digs_project_bwd",
             "digs_state_moments", "digs_state_workspace_size", "digs_state_size", "digs_step", "digs_sync_status", "digs_status_string", "digs_stage_times",
-            "digs_kernel_launches", "digs_pair_stats", "digs_cnn_params", "digs_cnn_workspace_size", "digs_cnn_init",
+            "digs_kernel_launches", "digs_pair_stats", "digs_voxelize", "digs_dvf", "digs_cnn_params", "digs_cnn_workspace_size", "digs_cnn_init",
             "digs_cnn_prepare_input", "digs_cnn_forward", "digs_cnn_backward", "digs_cnn_train_step",
             "digs_cnn_infer_bf16"]
 
@@ -576,3 +578,37 @@ class WeightPredictor:
                                              _ptr(_f32(cs[s:s + B], "cs")), B, _ptr(out[s:s + B]), self.ws.ptr,
                                              self.ws.nbytes, _stream()), "digs_cnn_infer_bf16")
         return out
+
+
+class DigsGrid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("origin", C.c_float * 3),
+                ("spacing", C.c_float * 3)]
+
+
+def grid_struct(grid: Dict) -> DigsGrid:
+    g = DigsGrid()
+    g.nx, g.ny, g.nz = int(grid["nx"]), int(grid["ny"]), int(grid["nz"])
+    for a in range(3):
+        g.origin[a] = float(grid["origin"][a])
+        g.spacing[a] = float(grid["spacing"][a])
+    return g
+
+
+def voxelize(mu0, scale, quat, rho, phi, w_row, lattice: Dict, grid: Dict, cutoff: float = 3.5) -> torch.Tensor:
+    """Attenuation volume [nz][ny][nx] of the cloud deformed with weights w_row [R] (one time point)."""
+    g = gauss_struct(mu0, scale, quat, rho)
+    lat, gr = lattice_struct(lattice), grid_struct(grid)
+    vol = torch.empty(gr.nz, gr.ny, gr.nx, device=mu0.device)
+    o = opts_struct(cutoff)
+    _check(lib().digs_voxelize(C.byref(g), C.byref(lat), _ptr(_f32(phi, "phi")), _ptr(_f32(w_row, "w")), C.byref(gr),
+                               C.byref(o), _ptr(vol), _stream()), "digs_voxelize")
+    return vol
+
+
+def dvf(phi, w_row, lattice: Dict, grid: Dict) -> torch.Tensor:
+    """Displacement field [nz][ny][nx][3] (mm) of one time point at the voxel centres."""
+    lat, gr = lattice_struct(lattice), grid_struct(grid)
+    out = torch.empty(gr.nz, gr.ny, gr.nx, 3, device=phi.device)
+    _check(lib().digs_dvf(C.byref(lat), _ptr(_f32(phi, "phi")), _ptr(_f32(w_row, "w")), C.byref(gr), _ptr(out),
+                          _stream()), "digs_dvf")
+    return out
