@@ -88,6 +88,12 @@ typedef struct {
   int bwd_lanes;
 } DigsOpts;
 
+#define DIGS_FLAG_EWA 4            /* cone-beam views: the paper's 2D-Gaussian approximation of each projected
+                                      Gaussian (Sec. 3.1, Eq. 4: EWA covariance of J W Sigma W^T J^T with
+                                      its third row and column dropped, density scaled by the integration
+                                      bias factor) instead of the exact line integral; a pair contributes
+                                      where its 2D Mahalanobis distance is <= cutoff.  Parallel views are
+                                      exact either way (the two models coincide there).               */
 #define DIGS_FLAG_REUSE_BINNING 1  /* project_bwd: reuse the per-pair records left in `ws` (same size)
                                       by the immediately preceding project_fwd with identical inputs   */
 

@@ -391,6 +391,79 @@ def render_tensors(T: Dict, lattice: Dict, views: Sequence[Dict], cutoff: Option
     return torch.stack(out) if out else torch.zeros(0, dtype=DT)
 
 
+def ewa_view(v, mu: torch.Tensor, sigma: torch.Tensor, rho: torch.Tensor, keep: torch.Tensor,
+             cutoff: Optional[float], chunk: int = 256) -> torch.Tensor:
+    """The paper's 2D-Gaussian model of one cone-beam view (Sec. 3.1, Eq. 4), brute force over every pixel:
+    each Gaussian becomes rho~ exp(-1/2 Delta^T Sig2^-1 Delta) around its projected mean, where
+    Sig2 = J Sigma' J^T with J the 2 x 3 Jacobian of the world-to-pixel perspective map at mu' (the EWA
+    covariance with its depth row and column dropped), and rho~ = rho sqrt(2 pi) |det J3| sqrt(det Sigma'
+    / det Sig2) with J3 = [J; d^T / |d|], d = mu' - src: the integration bias factor that makes the
+    ray-space Gaussian's integral along the ray the line integral.  A pair contributes where
+    Delta^T Sig2^-1 Delta <= cutoff^2."""
+    s, n = v["src"], v["n_d"]
+    sdd = torch.dot(v["det_c"] - s, n)
+    d = mu - s[None]
+    dn = d @ n
+    sc = sdd / dn
+    Ju = sc[:, None] / v["du"] * (v["e_u"][None] - ((d @ v["e_u"]) / dn)[:, None] * n[None])
+    Jv = sc[:, None] / v["dv"] * (v["e_v"][None] - ((d @ v["e_v"]) / dn)[:, None] * n[None])
+    J = torch.stack([Ju, Jv], 1)                                            # [N][2][3]
+    sig2 = J @ sigma @ J.transpose(-1, -2)
+    J3 = torch.cat([J, (d / d.norm(dim=1, keepdim=True))[:, None, :]], 1)
+    amp = rho * math.sqrt(2 * math.pi) * torch.linalg.det(J3).abs() * torch.sqrt(
+        torch.linalg.det(sigma) / torch.linalg.det(sig2))
+    mpix = project_to_pixel(v, mu)
+    jj, ii = torch.meshgrid(torch.arange(v["nv"], dtype=DT), torch.arange(v["nu"], dtype=DT), indexing="ij")
+    pix = torch.stack([ii.reshape(-1), jj.reshape(-1)], -1)                 # [npix][2]
+    out = torch.zeros(pix.shape[0], dtype=DT)
+    inv2 = torch.linalg.inv(sig2)
+    for a in range(0, mu.shape[0], chunk):
+        sl = slice(a, a + chunk)
+        D = pix[None] - mpix[sl, None, :]                                   # [c][npix][2]
+        E = torch.einsum("cpi,cij,cpj->cp", D, inv2[sl], D)
+        val = amp[sl, None] * torch.exp(-0.5 * E)
+        mask = keep[sl, None] & (dn[sl, None] > 0)
+        if cutoff is not None:
+            mask = mask & (E <= cutoff * cutoff)
+        out = out + torch.where(mask, val, torch.zeros_like(val)).sum(0)
+    return out
+
+
+def render_ewa(gauss: Dict, lattice: Dict, phi, w, views: Sequence[Dict], cutoff: Optional[float] = 3.5,
+               grad: bool = False):
+    """Projections [P][nv][nu] with the 2D-Gaussian model for cone-beam views (parallel views are the
+    exact model, which the 2D Gaussian equals there).  With grad=True returns the float64 tensors' graph
+    inputs and output for autograd."""
+    T = _inputs(gauss, phi, w)
+    if grad:
+        for k in T:
+            T[k].requires_grad_(True)
+    sigma0 = covariance(T["scale"], T["quat"])
+    U, dU = ffd_eval(T["phi"], lattice, T["mu0"])
+    out = []
+    for b, view in enumerate(views):
+        v = view_tensors(view)
+        mu, sigma, K = deform(T["mu0"], sigma0, U, dU, T["w"][b])
+        keep = torch.linalg.det(K).detach() > FOLD_EPS
+        if v["parallel"]:
+            P = torch.linalg.inv(sigma)
+            alive = alive_mask(v, mu.detach(), P.detach(), K.detach(), cutoff)
+            img = render_view_brute(v, mu, P, T["rho"], alive, cutoff)
+        else:
+            img = ewa_view(v, mu, sigma, T["rho"], keep, cutoff)
+        out.append(img.reshape(v["nv"], v["nu"]))
+    I = torch.stack(out)
+    return (T, I) if grad else I.detach().numpy()
+
+
+def project_vjp_ewa(gauss: Dict, lattice: Dict, phi, w, views: Sequence[Dict], grad_proj,
+                    cutoff: Optional[float] = 3.5) -> Dict[str, np.ndarray]:
+    """Gradients of sum(grad_proj * render_ewa) with respect to every input (autograd)."""
+    T, I = render_ewa(gauss, lattice, phi, w, views, cutoff, grad=True)
+    (I * _t(grad_proj)).sum().backward()
+    return {k: T[k].grad.numpy() for k in ("mu0", "scale", "quat", "rho", "phi", "w")}
+
+
 def render(gauss: Dict, lattice: Dict, phi, w, views: Sequence[Dict], cutoff: Optional[float] = 3.5,
            mode: str = "bbox") -> np.ndarray:
     """Projections [P][nv][nu] as float64 numpy.  ``gauss`` holds mu0, scale, quat, rho."""

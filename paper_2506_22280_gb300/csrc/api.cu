@@ -239,6 +239,7 @@ digs_status prepare(const DigsGaussians* g, const DigsLattice* lat, const float*
     if (views[b].nu != nu || views[b].nv != nv) return DIGS_ERR_ARG;
     s = make_view(views[b], rows ? rows[b] : b, c.views.v[b]);
     if (s != DIGS_OK) return s;
+    c.views.v[b].ewa = (opts && (opts->flags & DIGS_FLAG_EWA) && !views[b].parallel) ? 1 : 0;
     const int sc = scans ? views[b].scan : 0;
     if (sc < 0 || sc >= c.sc.S) return DIGS_ERR_ARG;
     c.views.v[b].scan = sc;

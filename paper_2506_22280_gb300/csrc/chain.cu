@@ -194,8 +194,6 @@ __global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, ScanTable sc,
     float Ki[9], A[9];
     inv3(K, Ki);
     make_A(inv_s, Rm, Ki, A);
-    SetupState st;
-    setup_core(v, mu, A, rho, st);
     float S[10];
     {
       const float4* p = sums + i * DIGS_PARTIAL_F4;
@@ -204,11 +202,21 @@ __global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, ScanTable sc,
       S[4] = c.x; S[5] = c.y; S[6] = c.z; S[7] = c.w;
       S[8] = d.x; S[9] = d.y;
     }
-    // record-parameter gradients (see the raster's pair formulas)
-    const float g_xc = -(2.f * (st.n00 * S[4] + st.n01 * S[5]) - st.w0 * S[6]);
-    const float g_yc = -(2.f * (st.n01 * S[4] + st.n11 * S[5]) - st.w1 * S[6]);
     float gmu[3], gA[9], grho;
-    setup_adjoint(v, st, rho, g_xc, g_yc, S[1], 2.f * S[2], S[3], -S[7], -S[8], S[9], S[0], gmu, gA, grho);
+    // record-parameter gradients (see the raster's pair formulas)
+    if (v.ewa) {  // the 2D-Gaussian model: w = kappa = 0
+      EwaState es;
+      ewa_core(v, mu, A, rho, es);
+      const float id = 1.f / es.det2, n00 = es.s11 * id, n01 = -es.s01 * id, n11 = es.s00 * id;
+      const float g_xc = -2.f * (n00 * S[4] + n01 * S[5]), g_yc = -2.f * (n01 * S[4] + n11 * S[5]);
+      ewa_adjoint(v, es, rho, g_xc, g_yc, S[1], 2.f * S[2], S[3], S[0], gmu, gA, grho);
+    } else {
+      SetupState st;
+      setup_core(v, mu, A, rho, st);
+      const float g_xc = -(2.f * (st.n00 * S[4] + st.n01 * S[5]) - st.w0 * S[6]);
+      const float g_yc = -(2.f * (st.n01 * S[4] + st.n11 * S[5]) - st.w1 * S[6]);
+      setup_adjoint(v, st, rho, g_xc, g_yc, S[1], 2.f * S[2], S[3], -S[7], -S[8], S[9], S[0], gmu, gA, grho);
+    }
     // A = S^-1 R^T K^-1: dL/ds, dL/dR, dL/dK = -A^T gA K^-T
     float gK[9];
 #pragma unroll

@@ -29,6 +29,7 @@ struct ViewC {
   int parallel;
   int w_row;         // row of the temporal-weight table used by this projection
   int scan;          // scan whose Gaussians and control points this projection renders
+  int ewa;           // 1: the paper's 2D-Gaussian (EWA) projection model instead of the exact line integral
 };
 
 struct ViewsParam {
@@ -92,9 +93,10 @@ __device__ __forceinline__ void store_rec(float4* r3, const Rec& r) {
   r3[2] = make_float4(r.amp, __int_as_float(r.bx), __int_as_float(r.by), __int_as_float(r.poly));
 }
 
-// |pixel centre - source| for pixel (px, py) (cone beam); 1 for parallel beams.
+// |pixel centre - source| for pixel (px, py) (cone beam, exact model); 1 for parallel beams and for the
+// 2D-Gaussian model, whose amplitude already holds the whole line integral.
 __device__ __forceinline__ float pixel_ray_length(const ViewC& v, float px, float py) {
-  if (v.parallel) return 1.f;
+  if (v.parallel || v.ewa) return 1.f;
   float a = (px - v.cx0) * v.du - v.su;
   float b = (py - v.cy0) * v.dv - v.sv;
   return sqrtf(fmaf(a, a, fmaf(b, b, v.sdd_n * v.sdd_n)));

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, ScanTable sc, Lat
     bool alive = finite_in && detK > DIGS_FOLD_EPS;
     if (alive) {
       make_A(G.inv_s, G.R, Ki, A);
-      alive = setup_record(v, mu, A, G.rho, c2, r);
+      alive = v.ewa ? ewa_record(v, mu, A, G.rho, c2, r) : setup_record(v, mu, A, G.rho, c2, r);
     }
     if (alive) {
       int x0 = r.bx & 0xffff, x1 = r.bx >> 16, y0 = r.by & 0xffff, y1 = r.by >> 16;

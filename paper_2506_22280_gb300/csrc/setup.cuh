@@ -248,3 +248,138 @@ __device__ __forceinline__ void setup_adjoint(const ViewC& v, const SetupState& 
     for (int k = 0; k < 3; ++k)
       gA[3 * i + k] = gAd[3 * i] * v.F[k] + gAd[3 * i + 1] * v.F[3 + k] + gAd[3 * i + 2] * v.F[6 + k];
 }
+
+// ---- the paper's 2D-Gaussian projection model (Sec. 3.1, Eq. 4) ----------------------------------
+// In the detector frame, t = mu' - src; the perspective map to pixels has the Jacobian
+//   J = [[a / tz, 0, -a tu / tz^2], [0, b / tz, -b tv / tz^2]],  a = SDD_n / du, b = SDD_n / dv,
+// and the projected covariance is Sig2 = J C J^T with C = Sigma' in the detector frame (the EWA covariance
+// J W Sigma W^T J^T with its third row and column dropped).  The integration bias factor follows from the
+// affine ray-space map (x, y, l = |t|) with Jacobian J3 = [J; t^T / |t|], |det J3| = a b |t| / tz^3:
+// the line integral of the ray-space Gaussian over l at fixed (x, y) is
+//   rho sqrt(2 pi det(J3 C J3^T) / det Sig2) exp(-Delta^T Sig2^-1 Delta / 2),
+// so amp = rho sqrt(2 pi) |det J3| sqrt(det C / det Sig2) = rho sqrt(2 pi) |det J3| / (|det A| sqrt(det Sig2)).
+// The record then has N = Sig2^-1, w = 0, kappa = 0 and no per-pixel |X - s| factor.
+struct EwaState {
+  float t[3], Ai[9], Bm[9], Q0[3], Q1[3], s00, s01, s11, det2, detA, a, b, ell, detJ3, amp, xc, yc;
+};
+
+__device__ __forceinline__ bool ewa_core(const ViewC& v, const float mu[3], const float A[9], float rho, EwaState& e) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    e.t[c] = v.F[3 * c] * mu[0] + v.F[3 * c + 1] * mu[1] + v.F[3 * c + 2] * mu[2] - v.src_d[c];
+  const float tz = e.t[2];
+  if (!(tz > 0.f)) return false;
+  e.detA = inv3(A, e.Ai);  // returns det A; Ai = A^-1, so Sigma' = Ai Ai^T
+  if (!(fabsf(e.detA) > 0.f)) return false;
+  // Bm = F Ai: Sigma' in the detector frame is C = Bm Bm^T
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      e.Bm[3 * c + k] = v.F[3 * c] * e.Ai[k] + v.F[3 * c + 1] * e.Ai[3 + k] + v.F[3 * c + 2] * e.Ai[6 + k];
+  e.a = v.sdd_n * v.inv_du;
+  e.b = v.sdd_n * v.inv_dv;
+  const float itz = 1.f / tz;
+  const float j00 = e.a * itz, j02 = -e.a * e.t[0] * itz * itz, j11 = e.b * itz, j12 = -e.b * e.t[1] * itz * itz;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    e.Q0[k] = j00 * e.Bm[k] + j02 * e.Bm[6 + k];
+    e.Q1[k] = j11 * e.Bm[3 + k] + j12 * e.Bm[6 + k];
+  }
+  e.s00 = e.Q0[0] * e.Q0[0] + e.Q0[1] * e.Q0[1] + e.Q0[2] * e.Q0[2];
+  e.s01 = e.Q0[0] * e.Q1[0] + e.Q0[1] * e.Q1[1] + e.Q0[2] * e.Q1[2];
+  e.s11 = e.Q1[0] * e.Q1[0] + e.Q1[1] * e.Q1[1] + e.Q1[2] * e.Q1[2];
+  e.det2 = e.s00 * e.s11 - e.s01 * e.s01;
+  if (!(e.det2 > 0.f)) return false;
+  e.ell = sqrtf(e.t[0] * e.t[0] + e.t[1] * e.t[1] + tz * tz);
+  e.detJ3 = e.a * e.b * e.ell * itz * itz * itz;
+  e.amp = rho * DIGS_SQRT_2PI * e.detJ3 / (fabsf(e.detA) * sqrtf(e.det2));
+  e.xc = v.cx0 + (v.su + v.sdd_n * e.t[0] * itz) * v.inv_du;
+  e.yc = v.cy0 + (v.sv + v.sdd_n * e.t[1] * itz) * v.inv_dv;
+  return isfinite(e.xc) && isfinite(e.yc) && isfinite(e.amp) && isfinite(e.det2);
+}
+
+// Record and pixel box of { Delta : Delta^T Sig2^-1 Delta <= c2 } (half widths sqrt(c2 Sig2_ii)).
+__device__ __forceinline__ bool ewa_record(const ViewC& v, const float mu[3], const float A[9], float rho, float c2,
+                                           Rec& r) {
+  EwaState e;
+  if (!ewa_core(v, mu, A, rho, e)) return false;
+  const float hx = sqrtf(c2 * e.s00) * 1.0001f + 1e-3f, hy = sqrtf(c2 * e.s11) * 1.0001f + 1e-3f;
+  float fx0 = fmaxf(ceilf(e.xc - hx), 0.f), fx1 = fminf(floorf(e.xc + hx), (float)(v.nu - 1));
+  float fy0 = fmaxf(ceilf(e.yc - hy), 0.f), fy1 = fminf(floorf(e.yc + hy), (float)(v.nv - 1));
+  if (!(fx0 <= fx1) || !(fy0 <= fy1)) return false;
+  const float id = 1.f / e.det2;
+  r.xc = e.xc; r.yc = e.yc;
+  r.n00 = e.s11 * id; r.n01x2 = -2.f * e.s01 * id; r.n11 = e.s00 * id;
+  r.wn0 = 0.f; r.wn1 = 0.f; r.kappa = 0.f; r.amp = e.amp;
+  r.bx = (int)fx0 | ((int)fx1 << 16);
+  r.by = (int)fy0 | ((int)fy1 << 16);
+  r.poly = 1;
+  return true;
+}
+
+// Adjoint of ewa_core: from dL/d(xc, yc, n00, n01, n11, amp) (n01 the off-diagonal of N = Sig2^-1) to
+// dL/dmu (world), dL/dA and dL/drho.
+__device__ __forceinline__ void ewa_adjoint(const ViewC& v, const EwaState& e, float rho, float g_xc, float g_yc,
+                                            float g_n00, float g_n01, float g_n11, float gamp, float gmu[3],
+                                            float gA[9], float& grho) {
+  const float id = 1.f / e.det2, ga = gamp * e.amp;  // dL/damp * amp
+  grho = gamp * e.amp / rho;
+  // N = [[s11, -s01], [-s01, s00]] / det2; amp ~ det2^-1/2
+  const float gdet = -(g_n00 * e.s11 - g_n01 * e.s01 + g_n11 * e.s00) * id * id - 0.5f * ga * id;
+  const float g00 = g_n11 * id + gdet * e.s11, g11 = g_n00 * id + gdet * e.s00;
+  const float g01 = -g_n01 * id - 2.f * gdet * e.s01;
+  // Sig2 = Q Q^T
+  float gQ0[3], gQ1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gQ0[k] = 2.f * g00 * e.Q0[k] + g01 * e.Q1[k];
+    gQ1[k] = 2.f * g11 * e.Q1[k] + g01 * e.Q0[k];
+  }
+  // Q0 = j00 Bm[0,:] + j02 Bm[2,:], Q1 = j11 Bm[1,:] + j12 Bm[2,:]
+  const float tz = e.t[2], itz = 1.f / tz;
+  const float j00 = e.a * itz, j02 = -e.a * e.t[0] * itz * itz, j11 = e.b * itz, j12 = -e.b * e.t[1] * itz * itz;
+  float gBm[9];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gBm[k] = j00 * gQ0[k];
+    gBm[3 + k] = j11 * gQ1[k];
+    gBm[6 + k] = j02 * gQ0[k] + j12 * gQ1[k];
+  }
+  float gj00 = 0.f, gj02 = 0.f, gj11 = 0.f, gj12 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gj00 += gQ0[k] * e.Bm[k];
+    gj02 += gQ0[k] * e.Bm[6 + k];
+    gj11 += gQ1[k] * e.Bm[3 + k];
+    gj12 += gQ1[k] * e.Bm[6 + k];
+  }
+  // t: the Jacobian entries, the projected mean and |det J3| = a b |t| / tz^3
+  float gt[3];
+  gt[0] = gj02 * (-e.a * itz * itz) + g_xc * e.a * itz + ga * e.t[0] / (e.ell * e.ell);
+  gt[1] = gj12 * (-e.b * itz * itz) + g_yc * e.b * itz + ga * e.t[1] / (e.ell * e.ell);
+  gt[2] = gj00 * (-e.a * itz * itz) + gj02 * (2.f * e.a * e.t[0] * itz * itz * itz) + gj11 * (-e.b * itz * itz) +
+          gj12 * (2.f * e.b * e.t[1] * itz * itz * itz) - g_xc * e.a * e.t[0] * itz * itz -
+          g_yc * e.b * e.t[1] * itz * itz + ga * (tz / (e.ell * e.ell) - 3.f * itz);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) gmu[k] = v.F[k] * gt[0] + v.F[3 + k] * gt[1] + v.F[6 + k] * gt[2];
+  // Bm = F Ai  ->  gAi = F^T gBm;  Ai = A^-1  ->  gA = -Ai^T gAi Ai^T;  |det A|^-1 in amp -> -ga Ai^T
+  float gAi[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      gAi[3 * i + k] = v.F[i] * gBm[k] + v.F[3 + i] * gBm[3 + k] + v.F[6 + i] * gBm[6 + k];
+  float T1[9];  // Ai^T gAi
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      T1[3 * i + k] = e.Ai[i] * gAi[k] + e.Ai[3 + i] * gAi[3 + k] + e.Ai[6 + i] * gAi[6 + k];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      gA[3 * i + k] = -(T1[3 * i] * e.Ai[k * 3] + T1[3 * i + 1] * e.Ai[k * 3 + 1] + T1[3 * i + 2] * e.Ai[k * 3 + 2]) -
+                      ga * e.Ai[3 * k + i];
+}

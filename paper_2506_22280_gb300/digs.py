@@ -20,6 +20,7 @@ DIGS_MAX_R = 4
 DIGS_MAX_VIEWS = 128
 DIGS_MAX_SCANS = 8
 DIGS_FLAG_REUSE_BINNING = 1
+DIGS_FLAG_EWA = 4
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "workspace too small for the pairs",
           4: "device-side wait timed out", 5: "non-finite input"}
 
@@ -249,7 +250,7 @@ class Projector:
     by the pair count of the inputs it last saw (recounted when a call reports overflow)."""
 
     def __init__(self, lattice: Dict, views: Sequence[Dict], cutoff: float = 3.5, tile: int = 16,
-                 headroom: float = 1.25, device="cuda", bwd_lanes: int = 16):
+                 headroom: float = 1.25, device="cuda", bwd_lanes: int = 16, ewa: bool = False):
         if len(views) > DIGS_MAX_VIEWS:
             raise ValueError(f"at most {DIGS_MAX_VIEWS} views per call")
         self.lattice = dict(lattice)
@@ -259,7 +260,8 @@ class Projector:
         self.P = len(self.views)
         self.nu = int(self.views[0]["nu"]) if self.views else 1
         self.nv = int(self.views[0]["nv"]) if self.views else 1
-        self.opts = opts_struct(cutoff, tile, 0, bwd_lanes)
+        self.model = DIGS_FLAG_EWA if ewa else 0  # the paper's 2D-Gaussian model instead of the exact integral
+        self.opts = opts_struct(cutoff, tile, self.model, bwd_lanes)
         self.cutoff, self.tile, self.headroom, self.bwd_lanes = cutoff, tile, headroom, bwd_lanes
         self.ws = Workspace(device)
         self.cap = -1
@@ -314,7 +316,8 @@ class Projector:
         g_phi = torch.empty_like(phi)
         g_w = torch.empty(self.P, int(self.lattice["R"]), device=dev)
         g = gauss_struct(mu0, scale, quat, rho)
-        o = opts_struct(self.cutoff, self.tile, DIGS_FLAG_REUSE_BINNING if reuse else 0, self.bwd_lanes)
+        o = opts_struct(self.cutoff, self.tile, self.model | (DIGS_FLAG_REUSE_BINNING if reuse else 0),
+                        self.bwd_lanes)
         _check(lib().digs_project_bwd(C.byref(g), C.byref(self.lat), _ptr(_f32(phi, "phi")), _ptr(_f32(w, "w")),
                                       self.varr, self.P, C.byref(o), _ptr(_f32(grad_proj.contiguous(), "grad_proj")),
                                       _ptr(g_mu0), _ptr(g_scale), _ptr(g_quat), _ptr(g_rho), _ptr(g_phi), _ptr(g_w),
