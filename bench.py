@@ -260,6 +260,36 @@ def batching_measurement(pkg, D, device, steps=6, warmup=3):
             "device_status": status}
 
 
+def model_comparison(pkg, wl, device, tile, lanes, B=16, reps=10):
+    """The exact line-integral model against the paper's 2D-Gaussian (EWA) model on one batch of the
+    workload: forward + backward throughput (CUDA events; the backward reuses the forward's records) and
+    the relative L2 difference of the two models' projections."""
+    import torch
+    f = lambda a: torch.as_tensor(a, dtype=torch.float32, device=device).contiguous()
+    ids = batch_ids(0, B, len(wl.views))
+    views = [wl.views[i] for i in ids]
+    ins = [f(wl.mu0), f(wl.scale), f(wl.quat), f(wl.rho), f(wl.phi), f(wl.w[ids])]
+    gp = torch.randn(B, 256, 256, device=device, generator=torch.Generator(device=device).manual_seed(0))
+    out, imgs = {}, {}
+    for name, ewa in (("exact", False), ("ewa", True)):
+        pj = pkg.Projector(wl.lattice, views, tile=tile, device=device, bwd_lanes=lanes, ewa=ewa)
+        I = pj.forward(*ins)
+        pj.backward(*ins, gp, reuse=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            pj.forward(*ins, out=I)
+            pj.backward(*ins, gp, reuse=True)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"proj_per_s_fwd_bwd": reps * B / (e0.elapsed_time(e1) / 1e3), "status": pj.status()}
+        imgs[name] = I.clone()
+    out["rel_l2_ewa_vs_exact"] = float((imgs["ewa"] - imgs["exact"]).norm() / imgs["exact"].norm())
+    out["workload"] = f"{B} projections of the thorax workload, projector forward + backward"
+    return out
+
+
 def warmstart_measurement(pkg, D, wl, meas, device, tile, lanes, B=16, warmup_iters=150, plain_iters=2150,
                           n_pairs=10_000, epochs=3):
     """Wall time for the plain batched optimisation to reach its final full-scan loss after `plain_iters`
@@ -437,6 +467,9 @@ def run_ours(args):
     batching = None
     if world == 1 and not args.no_batching:
         batching = batching_measurement(pkg, D, device)
+    models = None
+    if world == 1 and not args.no_batching:
+        models = model_comparison(pkg, wl, device, tile, lanes, B=B)
     warm = None
     if world == 1 and not args.no_warmstart:
         warm = warmstart_measurement(pkg, D, wl, meas, device, tile, lanes)
@@ -485,6 +518,8 @@ def run_ours(args):
         line["batching"] = batching
     if warm is not None:
         line["warm_start"] = warm
+    if models is not None:
+        line["projection_models"] = models
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
