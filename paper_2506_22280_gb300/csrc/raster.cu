@@ -158,6 +158,37 @@ __device__ __forceinline__ void derive_entry(const float4* raw, float4* ent) {
   ent[4] = make_float4(-a.y, -a.y, 0.f, 0.f);
 }
 
+// Whether the pixel rectangle [x0, x1] x [y0, y1] (a block's part of the record's box) can hold a pixel
+// with E <= c2: E = num / D with D <= Dmax = (1 + tau)^2 / (1 - c2 kappa) over the box (|t - 1| <= tau,
+// kappa num <= c2 kappa D), so no pixel qualifies when min over the rectangle of the quadratic form num
+// exceeds c2 Dmax.  The minimum of a positive definite form over a rectangle not holding its centre lies
+// on an edge, where it is a clamped one-dimensional minimum.  Conservative (small relative margin); a
+// culled block's entries would only have added zeros, so sums are unchanged.
+__device__ __forceinline__ bool ellipse_meets(const float4* r3, int x0, int x1, int y0, int y1, float c2_const) {
+  const float4 a = r3[0], b = r3[1], c = r3[2];
+  const float xc = a.x, yc = a.y, n00 = a.z, n01 = 0.5f * a.w, n11 = b.x;
+  const float X0 = (float)x0 - xc, X1 = (float)x1 - xc, Y0 = (float)y0 - yc, Y1 = (float)y1 - yc;
+  if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
+  const int bx = __float_as_int(c.y), by = __float_as_int(c.z);
+  const float mdx = fmaxf(fabsf((float)(bx & 0xffff) - xc), fabsf((float)(bx >> 16) - xc));
+  const float mdy = fmaxf(fabsf((float)(by & 0xffff) - yc), fabsf((float)(by >> 16) - yc));
+  const float tau = fabsf(b.y) * mdx + fabsf(b.z) * mdy;
+  const float ck = 1.f - c2_const * b.w;  // > 0: the source lies outside the cutoff ellipsoid
+  if (!(ck > 0.f)) return true;
+  const float lim = c2_const * (1.f + tau) * (1.f + tau) / ck * 1.001f + 1e-4f;
+  auto q = [&](float dx, float dy) { return dy * (n11 * dy + 2.f * n01 * dx) + n00 * dx * dx; };
+  auto edge_x = [&](float dx) {  // min over dy in [Y0, Y1] at fixed dx
+    const float dy = fminf(fmaxf(-n01 * dx / n11, Y0), Y1);
+    return q(dx, dy);
+  };
+  auto edge_y = [&](float dy) {
+    const float dx = fminf(fmaxf(-n01 * dy / n00, X0), X1);
+    return q(dx, dy);
+  };
+  const float m = fminf(fminf(edge_x(X0), edge_x(X1)), fminf(edge_y(Y0), edge_y(Y1)));
+  return !(m > lim);
+}
+
 __device__ __forceinline__ f2 f2_lo(const float4& v) { return f2_pack(v.x, v.y); }
 __device__ __forceinline__ f2 f2_hi(const float4& v) { return f2_pack(v.z, v.w); }
 
@@ -225,10 +256,9 @@ __global__ void __launch_bounds__(FwdCfg<TS>::threads) k_raster_fwd(
       const int x0 = max(bx & 0xffff, qx), x1 = min(bx >> 16, qx + 7);
       const int y0 = max(by & 0xffff, qy), y1 = min(by >> 16, qy + 7);
       meets = x0 <= x1 && y0 <= y1;
-      if (meets) {
-        derive_entry(r3, ent + lane * 5);
-        if (COUNT) n_box += (unsigned)((x1 - x0 + 1) * (y1 - y0 + 1));
-      }
+      if (COUNT && meets) n_box += (unsigned)((x1 - x0 + 1) * (y1 - y0 + 1));
+      meets = meets && ellipse_meets(r3, x0, x1, y0, y1, c2);
+      if (meets) derive_entry(r3, ent + lane * 5);
     }
     unsigned mask = __ballot_sync(0xffffffffu, meets);
     __syncwarp();
