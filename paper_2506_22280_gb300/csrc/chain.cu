@@ -150,7 +150,7 @@ __device__ __forceinline__ void ffd_scatter_warp(float* __restrict__ g_phi_all, 
 
 // (1) Adjoint of one (projection, Gaussian) pair.
 template <int R>
-__global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, ScanTable sc, const float* __restrict__ ffd,
+__global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, const __grid_constant__ ScanTable sc, const float* __restrict__ ffd,
                                                       const float* __restrict__ w,
                                                       const __grid_constant__ ViewsParam views, int P,
                                                       const uint32_t* __restrict__ counts,
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, ScanTable sc,
 
 // Second derivatives of u_r at each mean ([18 R][n], see ffd_hessian_point), for the mean's gradient.
 template <int R>
-__global__ void __launch_bounds__(128) k_ffd_hessian(GaussPtrs g, ScanTable sc, LatticeC L,
+__global__ void __launch_bounds__(128) k_ffd_hessian(GaussPtrs g, const __grid_constant__ ScanTable sc, LatticeC L,
                                                     const float* __restrict__ phi, float* __restrict__ out) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.n) return;
@@ -278,7 +278,8 @@ __global__ void __launch_bounds__(128) k_ffd_hessian(GaussPtrs g, ScanTable sc, 
 // (2) Per Gaussian: sum the pair adjoints over the projections, then the FFD backward.
 template <int R>
 __global__ void __launch_bounds__(kChainThreads) k_gauss_bwd(
-    GaussPtrs g, ScanTable sc, LatticeC L, const float* __restrict__ ffd, const float* __restrict__ ffd2,
+    GaussPtrs g, const __grid_constant__ ScanTable sc, LatticeC L, const float* __restrict__ ffd,
+    const float* __restrict__ ffd2,
     const float* __restrict__ w, const __grid_constant__ ViewsParam views, int P, const float* __restrict__ padj,
     float* __restrict__ g_mu0,
     float* __restrict__ g_scale, float* __restrict__ g_quat, float* __restrict__ g_rho, float* __restrict__ g_phi) {

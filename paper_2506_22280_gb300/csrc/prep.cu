@@ -64,7 +64,7 @@ __device__ __forceinline__ void load_gauss(const GaussPtrs& g, int n, GaussLocal
 // One thread per Gaussian; loops over the call's projections of its scan so the FFD is evaluated once.
 // Record (b, n) of scan-local Gaussian n sits at b * nmax + n.
 template <int R>
-__global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, ScanTable sc, LatticeC L, const float* __restrict__ phi,
+__global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, const __grid_constant__ ScanTable sc, LatticeC L, const float* __restrict__ phi,
                                                   const float* __restrict__ w, const __grid_constant__ ViewsParam views,
                                                   int P, float c2, int tile, int tiles_x, float4* __restrict__ rec,
                                                   uint32_t* __restrict__ counts, float* __restrict__ ffd_out,
