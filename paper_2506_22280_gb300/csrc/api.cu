@@ -46,8 +46,6 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.vals = (uint32_t*)take((size_t)cap * 4);
   w.keys_alt = (uint32_t*)take((size_t)cap * 4);
   w.vals_alt = (uint32_t*)take((size_t)cap * 4);
-  w.rid = (uint32_t*)take((size_t)cap * 4);
-  w.srid = (uint32_t*)take((size_t)cap * 4);
   w.hist = (uint32_t*)take(((size_t)256 * w.n_sort_blocks + 1) * 4);
   w.ranges = (uint2*)take((size_t)P * w.T * sizeof(uint2));
   w.order = (uint32_t*)take((size_t)P * w.T * 4);
@@ -279,7 +277,8 @@ digs_status bin(Call& c, const float* phi, const float* w) {
   uint32_t *sk = nullptr, *sv = nullptr;
   DIGS_TRY(radix_sort(ws.keys, ws.vals, ws.keys_alt, ws.vals_alt, ws.n_pairs, ws.cap, key_bits((long long)c.P * ws.T),
                       ws.hist, ws.scan_tmp, ws.n_sort_blocks, &sk, &sv, c.st));
-  DIGS_TRY(tile_ranges(sk, sv, ws.rid, ws.n_pairs, ws.cap, ws.ranges, c.P * ws.T, ws.srid, c.st));
+  DIGS_TRY(tile_ranges(sk, ws.n_pairs, ws.cap, ws.ranges, c.P * ws.T, c.st));
+  ws.srid = sv;
   DIGS_TRY(tile_order(ws.ranges, c.P * ws.T, ws.order, c.st));
   mark(c, 3);
   return DIGS_OK;

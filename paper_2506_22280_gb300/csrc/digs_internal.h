@@ -25,11 +25,10 @@ struct Workspace {
   uint32_t* offsets;      // [P * n + 1] exclusive scan of counts (offsets[P*n] = total)
   uint32_t* scan_tmp;     // block sums of the scans
   uint32_t* keys;         // [cap] (projection, tile) key per pair
-  uint32_t* vals;         // [cap] slot of the pair (its position before sorting)
+  uint32_t* vals;         // [cap] (projection, Gaussian) record of the pair
   uint32_t* keys_alt;     // [cap]
   uint32_t* vals_alt;     // [cap]
-  uint32_t* rid;          // [cap] (projection, Gaussian) record of each slot
-  uint32_t* srid;         // [cap] record of each sorted position
+  uint32_t* srid;         // record of each sorted position (the sorted values: vals or vals_alt)
   uint32_t* hist;         // radix histograms [256][sort blocks]
   uint2* ranges;          // [P * T] sorted-range of each (projection, tile)
   uint32_t* order;        // [P * T] forward launch order (longest lists first)
@@ -66,10 +65,9 @@ size_t scan_tmp_words(int n);
 cudaError_t radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, const uint32_t* n_dev,
                        long long cap, int bits, uint32_t* hist, uint32_t* scan_tmp, int n_sort_blocks,
                        uint32_t** out_keys, uint32_t** out_vals, cudaStream_t st);
-// Per-(projection, tile) ranges of the sorted keys, plus srid[k] = rid[slot(k)].
-cudaError_t tile_ranges(const uint32_t* sorted_keys, const uint32_t* sorted_vals, const uint32_t* rid,
-                        const uint32_t* n_dev, long long cap, uint2* ranges, int n_ranges, uint32_t* srid,
-                        cudaStream_t st);
+// Per-(projection, tile) ranges of the sorted keys.
+cudaError_t tile_ranges(const uint32_t* sorted_keys, const uint32_t* n_dev, long long cap, uint2* ranges,
+                        int n_ranges, cudaStream_t st);
 int sort_blocks(long long cap);
 // order[P * T]: (projection, tile) indices by descending range length (power-of-two classes).
 cudaError_t tile_order(const uint2* ranges, int n, uint32_t* order, cudaStream_t st);

@@ -149,13 +149,13 @@ cudaError_t launch_prep_fwd(const GaussPtrs& g, const ScanTable& sc, const Latti
   return cudaGetLastError();
 }
 
-// One thread per (projection, Gaussian): write key = b * T + tile and slot index for each tile of its
-// box, at the slots [offsets[i], offsets[i + 1]) reserved by the scan.  Pairs beyond the capacity are
-// dropped and flagged.
+// One thread per (projection, Gaussian) record i: write key = b * T + tile and value i for each tile of
+// its box, at the slots [offsets[i], offsets[i + 1]) reserved by the scan (so after the stable sort the
+// values are the record of each sorted position).  Pairs beyond the capacity are dropped and flagged.
 __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ rec, const uint32_t* __restrict__ offsets,
                                               int PN, int n, int tile, int tiles_x, int T, uint32_t* __restrict__ keys,
-                                              uint32_t* __restrict__ vals, uint32_t* __restrict__ rid, long long cap,
-                                              uint32_t* n_pairs, int* status) {
+                                              uint32_t* __restrict__ vals, long long cap, uint32_t* n_pairs,
+                                              int* status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     uint32_t total = offsets[PN];
@@ -175,16 +175,15 @@ __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ rec, co
     for (int tx = tx0; tx <= tx1; ++tx, ++k) {
       if ((long long)k >= cap) return;
       keys[k] = base + (uint32_t)(ty * tiles_x + tx);
-      vals[k] = k;
-      rid[k] = (uint32_t)i;
+      vals[k] = (uint32_t)i;
     }
 }
 
 cudaError_t launch_emit(const Workspace& ws, cudaStream_t st) {
   int PN = ws.P * ws.n;
   dim3 grid((PN + 255) / 256 > 0 ? (PN + 255) / 256 : 1);
-  k_emit<<<grid, 256, 0, st>>>(ws.rec, ws.offsets, PN, ws.n, ws.tile, ws.tiles_x, ws.T, ws.keys, ws.vals, ws.rid,
-                               ws.cap, ws.n_pairs, ws.status);
+  k_emit<<<grid, 256, 0, st>>>(ws.rec, ws.offsets, PN, ws.n, ws.tile, ws.tiles_x, ws.T, ws.keys, ws.vals, ws.cap,
+                               ws.n_pairs, ws.status);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -107,27 +107,23 @@ cudaError_t radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint3
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys,
-                                                     const uint32_t* __restrict__ vals, const uint32_t* __restrict__ rid,
-                                                     const uint32_t* n_dev, uint2* __restrict__ ranges,
-                                                     uint32_t* __restrict__ srid) {
+__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys, const uint32_t* n_dev,
+                                                     uint2* __restrict__ ranges) {
   uint32_t n = n_dev[1];
   size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   uint32_t key = keys[k];
   if (k == 0 || keys[k - 1] != key) ranges[key].x = (uint32_t)k;
   if (k + 1 == n || keys[k + 1] != key) ranges[key].y = (uint32_t)(k + 1);
-  srid[k] = rid[vals[k]];
 }
 
-cudaError_t tile_ranges(const uint32_t* sorted_keys, const uint32_t* sorted_vals, const uint32_t* rid,
-                        const uint32_t* n_dev, long long cap, uint2* ranges, int n_ranges, uint32_t* srid,
-                        cudaStream_t st) {
+cudaError_t tile_ranges(const uint32_t* sorted_keys, const uint32_t* n_dev, long long cap, uint2* ranges,
+                        int n_ranges, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_ranges, st);
   if (e != cudaSuccess) return e;
   if (cap <= 0) return cudaSuccess;
   long long blocks = (cap + 255) / 256;
-  k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(sorted_keys, sorted_vals, rid, n_dev, ranges, srid);
+  k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(sorted_keys, n_dev, ranges);
   note_launches(1);
   return cudaGetLastError();
 }
