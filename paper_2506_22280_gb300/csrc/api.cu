@@ -24,7 +24,7 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.tiles_x = (nu + tile - 1) / tile;
   w.tiles_y = (nv + tile - 1) / tile;
   w.T = w.tiles_x * w.tiles_y;
-  w.n_sort_blocks = sort_blocks(cap);
+  w.n_sort_blocks = sort_blocks(cap, P);
   w.n_gauss_blocks = chain_blocks(n);
   size_t PN = (size_t)P * n;
   size_t off = 0;
@@ -47,6 +47,7 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.keys_alt = (uint32_t*)take((size_t)cap * 4);
   w.vals_alt = (uint32_t*)take((size_t)cap * 4);
   w.hist = (uint32_t*)take(((size_t)256 * w.n_sort_blocks + 1) * 4);
+  w.seg = (uint32_t*)take(((size_t)2 * P + 2) * 4);
   w.ranges = (uint2*)take((size_t)P * w.T * sizeof(uint2));
   w.order = (uint32_t*)take((size_t)P * w.T * 4);
   w.grec = (float4*)take(PN * DIGS_PARTIAL_F4 * sizeof(float4));
@@ -181,12 +182,6 @@ digs_status state_scans(const DigsState* st, const LatticeC& L, ScanTable& t) {
   return DIGS_OK;
 }
 
-int key_bits(long long nkeys) {
-  int b = 1;
-  while ((1LL << b) < nkeys) ++b;
-  return b;
-}
-
 struct Call {
   GaussPtrs g;
   ScanTable sc;
@@ -275,9 +270,8 @@ digs_status bin(Call& c, const float* phi, const float* w) {
   DIGS_TRY(launch_emit(ws, c.st));
   mark(c, 2);
   uint32_t *sk = nullptr, *sv = nullptr;
-  DIGS_TRY(radix_sort(ws.keys, ws.vals, ws.keys_alt, ws.vals_alt, ws.n_pairs, ws.cap, key_bits((long long)c.P * ws.T),
-                      ws.hist, ws.scan_tmp, ws.n_sort_blocks, &sk, &sv, c.st));
-  DIGS_TRY(tile_ranges(sk, ws.n_pairs, ws.cap, ws.ranges, c.P * ws.T, c.st));
+  DIGS_TRY(sort_pairs(ws.keys, ws.vals, ws.keys_alt, ws.vals_alt, ws.n_pairs, ws.cap, ws.offsets, ws.n, c.P, ws.T,
+                      ws.n_sort_blocks, ws.seg, ws.hist, ws.scan_tmp, ws.ranges, &sk, &sv, c.st));
   ws.srid = sv;
   DIGS_TRY(tile_order(ws.ranges, c.P * ws.T, ws.order, c.st));
   mark(c, 3);

@@ -30,6 +30,7 @@ struct Workspace {
   uint32_t* vals_alt;     // [cap]
   uint32_t* srid;         // record of each sorted position (the sorted values: vals or vals_alt)
   uint32_t* hist;         // radix histograms [256][sort blocks]
+  uint32_t* seg;          // [2P + 2] each projection's first pair and first sort block
   uint2* ranges;          // [P * T] sorted-range of each (projection, tile)
   uint32_t* order;        // [P * T] forward launch order (longest lists first)
   float4* grec;           // [P * n * 3] backward: the ten pixel sums of each (projection, Gaussian) record
@@ -60,15 +61,18 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
 cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int n, uint32_t* tmp, cudaStream_t st);
 size_t scan_tmp_words(int n);
 
-// sort.cu: LSD radix sort of (key, value) pairs on the low `bits` bits; count read from the device.
-// Returns via *out_keys / *out_vals which of the two buffers holds the result.
-cudaError_t radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, const uint32_t* n_dev,
-                       long long cap, int bits, uint32_t* hist, uint32_t* scan_tmp, int n_sort_blocks,
-                       uint32_t** out_keys, uint32_t** out_vals, cudaStream_t st);
+// sort.cu: stable sort of the pair keys (projection * T + tile) with their record values, the pairs being
+// grouped by projection as the emit step writes them (projection b's start is offsets[b * n]); count
+// read from the device; also writes ranges[P * T].  Returns via *out_keys / *out_vals which of the two
+// buffers holds the result.  seg: 2P + 2 words; hist: 256 * n_blocks + 1 words, n_blocks = sort_blocks.
+cudaError_t sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, const uint32_t* n_dev,
+                       long long cap, const uint32_t* offsets, int n, int P, int T, int n_blocks, uint32_t* seg,
+                       uint32_t* hist, uint32_t* scan_tmp, uint2* ranges, uint32_t** out_keys, uint32_t** out_vals,
+                       cudaStream_t st);
 // Per-(projection, tile) ranges of the sorted keys.
 cudaError_t tile_ranges(const uint32_t* sorted_keys, const uint32_t* n_dev, long long cap, uint2* ranges,
                         int n_ranges, cudaStream_t st);
-int sort_blocks(long long cap);
+int sort_blocks(long long cap, int P);
 // order[P * T]: (projection, tile) indices by descending range length (power-of-two classes).
 cudaError_t tile_order(const uint2* ranges, int n, uint32_t* order, cudaStream_t st);
 

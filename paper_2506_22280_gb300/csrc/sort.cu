@@ -1,11 +1,15 @@
-// Stable LSD radix sort of (projection, tile) keys with their slot values, 8 bits per pass, and the
-// per-(projection, tile) ranges of the sorted list.  The pair count lives on the device (it comes out
-// of the prefix sum), so every kernel is launched for the workspace capacity and reads the count.
+// Stable sort of the (projection, tile) pair keys with their record values, and the per-(projection,
+// tile) ranges of the sorted list.  The pairs come out of the emit step projection by projection, so
+// only the tile part of each key needs sorting, inside each projection's run: an LSD radix sort on the
+// tile index, 8 bits per pass (one pass when a projection has at most 256 tiles), whose blocks never
+// straddle two projections.  The pair count lives on the device (it comes out of the prefix sum), so
+// every kernel is launched for the workspace capacity and reads the counts.
 //
-// Each pass: (1) per-block digit histograms, stored digit-major; (2) an exclusive scan of that
-// [256][blocks] array gives every (digit, block) its output base; (3) each block ranks its keys stably --
-// each warp walks a contiguous run of 512 keys in order, ranking equal digits inside a 32-key step with
-// __match_any_sync and across steps with per-warp digit counters -- and scatters them.
+// Each pass: (1) per-block digit histograms, stored projection-major, then digit-major, then by block,
+// so that (2) one exclusive scan of the whole array gives every (projection, digit, block) its output
+// base; (3) each block ranks its keys stably -- each warp walks a contiguous run of 512 keys in order,
+// ranking equal digits inside a 32-key step with __match_any_sync and across steps with per-warp digit
+// counters -- and scatters them.  With one pass the ranges follow from the scanned histograms.
 #include "digs_internal.h"
 
 namespace digs {
@@ -16,49 +20,116 @@ constexpr int kSortItems = 16;                               // keys per thread
 constexpr int kSortTile = kSortThreads * kSortItems;         // 4096 keys per block
 constexpr int kWarpRun = kSortTile / kSortWarps;             // 512 keys per warp
 
-int sort_blocks(long long cap) { return (int)((cap + kSortTile - 1) / kSortTile); }
+// Upper bound of the sort blocks: every projection's run may end in a partial block.
+int sort_blocks(long long cap, int P) { return (int)((cap + kSortTile - 1) / kSortTile) + P; }
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys, const uint32_t* n_dev,
-                                                             int shift, uint32_t* __restrict__ hist, int nblk) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0u;
+// seg[0..P]: start of each projection's pairs (seg[P] = pairs kept); seg[P+1..2P+1]: first sort block of
+// each projection (seg[2P+1] = blocks in use).  One CTA of 256 threads, P <= 255.
+__global__ void __launch_bounds__(256) k_sort_segments(const uint32_t* __restrict__ offsets,
+                                                       const uint32_t* __restrict__ n_dev, int n, int P,
+                                                       uint32_t* __restrict__ seg) {
+  __shared__ uint32_t start[257], nb[256];
+  const int t = threadIdx.x;
+  const uint32_t kept = n_dev[1];
+  if (t <= P) start[t] = t < P ? min(offsets[(size_t)t * n], kept) : kept;
   __syncthreads();
-  uint32_t n = n_dev[1];
-  size_t base = (size_t)blockIdx.x * kSortTile;
-#pragma unroll 4
-  for (int i = 0; i < kSortItems; ++i) {
-    size_t idx = base + (size_t)i * kSortThreads + threadIdx.x;
-    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+  uint32_t x = t < P ? (start[t + 1] - start[t] + kSortTile - 1) / kSortTile : 0u;
+  nb[t] = x;
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {  // inclusive scan of the block counts
+    const uint32_t y = t >= o ? nb[t - o] : 0u;
+    __syncthreads();
+    x += y;
+    nb[t] = x;
+    __syncthreads();
   }
-  __syncthreads();
-  hist[(size_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+  if (t <= P) {
+    seg[t] = start[t];
+    seg[P + 1 + t] = t == 0 ? 0u : nb[t - 1];
+  }
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
-                                                                const uint32_t* __restrict__ vin,
-                                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                                const uint32_t* n_dev, int shift,
-                                                                const uint32_t* __restrict__ hist_scan, int nblk) {
+// The projection whose sort blocks hold block g (the last b with first block <= g; g < blocks in use).
+__device__ __forceinline__ int block_projection(const uint32_t* sblk, int P, uint32_t g) {
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sblk[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct SortBlock {
+  bool idle;
+  int b;            // projection
+  uint32_t j, nb;   // block within the projection, blocks of the projection
+  uint32_t lo, hi;  // keys [lo, hi)
+  uint32_t hbase;   // first histogram entry of the projection
+};
+
+__device__ __forceinline__ SortBlock sort_block(const uint32_t* seg, int P) {
+  const uint32_t* sblk = seg + P + 1;
+  SortBlock s;
+  const uint32_t g = blockIdx.x;
+  s.idle = g >= sblk[P];
+  if (s.idle) return s;
+  s.b = block_projection(sblk, P, g);
+  s.j = g - sblk[s.b];
+  s.nb = sblk[s.b + 1] - sblk[s.b];
+  s.lo = seg[s.b] + s.j * kSortTile;
+  s.hi = min(s.lo + (uint32_t)kSortTile, seg[s.b + 1]);
+  s.hbase = 256u * sblk[s.b];
+  return s;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys,
+                                                            const uint32_t* __restrict__ seg, int P, int T, int shift,
+                                                            uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[256];
+  const SortBlock s = sort_block(seg, P);
+  if (s.idle) {  // idle blocks zero the tail of the histogram array, which the scan covers
+    hist[(size_t)blockIdx.x * 256 + threadIdx.x] = 0u;
+    return;
+  }
+  h[threadIdx.x] = 0u;
+  __syncthreads();
+  const uint32_t kb = (uint32_t)s.b * (uint32_t)T;
+#pragma unroll 4
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint32_t idx = s.lo + (uint32_t)(i * kSortThreads) + threadIdx.x;
+    if (idx < s.hi) atomicAdd(&h[((keys[idx] - kb) >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[s.hbase + threadIdx.x * s.nb + s.j] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
+                                                               const uint32_t* __restrict__ vin,
+                                                               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                               const uint32_t* __restrict__ seg, int P, int T, int shift,
+                                                               const uint32_t* __restrict__ hist_scan) {
   __shared__ uint32_t wcnt[kSortWarps][256];
   __shared__ uint32_t dbase[256];
+  const SortBlock s = sort_block(seg, P);
+  if (s.idle) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) wcnt[w][threadIdx.x] = 0u;
-  dbase[threadIdx.x] = hist_scan[(size_t)threadIdx.x * nblk + blockIdx.x];
+  dbase[threadIdx.x] = hist_scan[s.hbase + threadIdx.x * s.nb + s.j];
   __syncthreads();
-  const uint32_t n = n_dev[1];
-  const size_t run = (size_t)blockIdx.x * kSortTile + (size_t)warp * kWarpRun;
+  const uint32_t kb = (uint32_t)s.b * (uint32_t)T;
+  const uint32_t run = s.lo + (uint32_t)(warp * kWarpRun);
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
-    size_t idx = run + (size_t)it * 32 + lane;
-    bool valid = idx < n;
+    const uint32_t idx = run + (uint32_t)(it * 32 + lane);
+    const bool valid = idx < s.hi;
     key[it] = valid ? kin[idx] : 0u;
     val[it] = valid ? vin[idx] : 0u;
-    uint32_t d = valid ? ((key[it] >> shift) & 255u) : 256u;  // 256: sentinel for the ragged tail
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t before = __popc(peers & lt_mask);
+    const uint32_t d = valid ? (((key[it] - kb) >> shift) & 255u) : 256u;  // 256: sentinel for the ragged tail
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t before = __popc(peers & lt_mask);
     rank[it] = valid ? wcnt[warp][d] + before : 0u;
     __syncwarp();
     if (valid && before == 0) wcnt[warp][d] += __popc(peers);
@@ -69,7 +140,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
     uint32_t acc = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) {
-      uint32_t c = wcnt[w][threadIdx.x];
+      const uint32_t c = wcnt[w][threadIdx.x];
       wcnt[w][threadIdx.x] = acc;
       acc += c;
     }
@@ -77,34 +148,66 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
   __syncthreads();
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
-    size_t idx = run + (size_t)it * 32 + lane;
-    if (idx < n) {
-      uint32_t d = (key[it] >> shift) & 255u;
-      uint32_t pos = dbase[d] + wcnt[warp][d] + rank[it];
+    const uint32_t idx = run + (uint32_t)(it * 32 + lane);
+    if (idx < s.hi) {
+      const uint32_t d = ((key[it] - kb) >> shift) & 255u;
+      const uint32_t pos = dbase[d] + wcnt[warp][d] + rank[it];
       kout[pos] = key[it];
       vout[pos] = val[it];
     }
   }
 }
 
-cudaError_t radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, const uint32_t* n_dev,
-                       long long cap, int bits, uint32_t* hist, uint32_t* scan_tmp, int nblk, uint32_t** out_keys,
-                       uint32_t** out_vals, cudaStream_t st) {
+// With one pass (T <= 256) the digit is the tile, so the scanned histogram entry of (projection, tile,
+// first block) is where the tile's run starts.
+__global__ void __launch_bounds__(256) k_sort_ranges(const uint32_t* __restrict__ hist_scan,
+                                                     const uint32_t* __restrict__ seg, int P, int T,
+                                                     uint2* __restrict__ ranges) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P * T) return;
+  const int b = i / T, t = i - b * T;
+  const uint32_t* sblk = seg + P + 1;
+  const uint32_t nb = sblk[b + 1] - sblk[b], hb = 256u * sblk[b];
+  uint2 r;
+  if (nb == 0) {
+    r.x = r.y = seg[b];
+  } else {
+    r.x = hist_scan[hb + (uint32_t)t * nb];
+    r.y = t + 1 < 256 ? hist_scan[hb + (uint32_t)(t + 1) * nb] : seg[b + 1];
+  }
+  ranges[i] = r;
+}
+
+cudaError_t sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, const uint32_t* n_dev,
+                       long long cap, const uint32_t* offsets, int n, int P, int T, int n_blocks, uint32_t* seg,
+                       uint32_t* hist,
+                       uint32_t* scan_tmp, uint2* ranges, uint32_t** out_keys, uint32_t** out_vals, cudaStream_t st) {
   uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
-  if (cap > 0 && nblk > 0) {
-    for (int shift = 0; shift < bits; shift += 8) {
-      k_radix_hist<<<nblk, kSortThreads, 0, st>>>(ki, n_dev, shift, hist, nblk);
-      cudaError_t e = exclusive_scan(hist, hist, 256 * nblk, scan_tmp, st);
-      if (e != cudaSuccess) return e;
-      k_radix_scatter<<<nblk, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_dev, shift, hist, nblk);
-      note_launches(2);
-      uint32_t* t = ki; ki = ko; ko = t;
-      t = vi; vi = vo; vo = t;
-    }
+  *out_keys = ki;
+  *out_vals = vi;
+  if (P <= 0 || T <= 0) return cudaSuccess;
+  if (P > 255) return cudaErrorInvalidValue;
+  int bits = 1;
+  while ((1 << bits) < T) ++bits;
+  k_sort_segments<<<1, 256, 0, st>>>(offsets, n_dev, n, P, seg);
+  note_launches(1);
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_sort_hist<<<n_blocks, kSortThreads, 0, st>>>(ki, seg, P, T, shift, hist);
+    cudaError_t e = exclusive_scan(hist, hist, 256 * n_blocks, scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    k_sort_scatter<<<n_blocks, kSortThreads, 0, st>>>(ki, vi, ko, vo, seg, P, T, shift, hist);
+    note_launches(2);
+    uint32_t* t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
   }
   *out_keys = ki;
   *out_vals = vi;
-  return cudaGetLastError();
+  if (bits <= 8) {
+    k_sort_ranges<<<(P * T + 255) / 256, 256, 0, st>>>(hist, seg, P, T, ranges);
+    note_launches(1);
+    return cudaGetLastError();
+  }
+  return tile_ranges(ki, n_dev, cap, ranges, P * T, st);
 }
 
 __global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys, const uint32_t* n_dev,
