@@ -25,7 +25,6 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.tiles_y = (nv + tile - 1) / tile;
   w.T = w.tiles_x * w.tiles_y;
   w.n_sort_blocks = sort_blocks(cap, P);
-  w.n_gauss_blocks = chain_blocks(n);
   size_t PN = (size_t)P * n;
   size_t off = 0;
   char* b = (char*)base;
@@ -51,11 +50,11 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.ranges = (uint2*)take((size_t)P * w.T * sizeof(uint2));
   w.order = (uint32_t*)take((size_t)P * w.T * 4);
   w.grec = (float4*)take(PN * DIGS_PARTIAL_F4 * sizeof(float4));
-  w.gw_part = (float*)take((size_t)std::max(w.n_gauss_blocks, 32) * P * R * 4 + 4);  // >= kGwSplit partials per (b, r)
+  w.gw_part = (float*)take((size_t)pair_sum_blocks(n_total) * P * R * 4 + 4);
   w.loss_part = (float*)take((size_t)P * w.T * fwd_blocks(tile) * 4 + 4);
   w.ffd = (float*)take((size_t)12 * R * n_total * 4 + 4);
   w.ffd2 = (float*)take((size_t)18 * R * n_total * 4 + 4);
-  w.padj = (float*)take((size_t)(kPairAdj + R) * P * n * 4 + 4);
+  w.gsum = (float*)take((size_t)(16 + 12 * R) * n_total * 4 + 4);
   w.proj = (float*)take((size_t)P * nu * nv * 4);
   w.dldi = (float*)take((size_t)P * nu * nv * 4);
   w.gw_rows = (float*)take((size_t)w_rows * R * 4 + 4);

@@ -2,14 +2,15 @@
 // and precision factor A -> K, S, R -> reference Gaussian; then through the DI warp (Eq. 7-8) and the
 // FFD (Eq. 9-11) to the control points phi and the temporal weights w.
 //
-// Three kernels.  (1) One thread per (projection, Gaussian) pair takes the pair's ten pixel sums, runs the
-// adjoint of the projection set-up and of A = S^-1 R^T K^-1, and
-// writes 25 + R numbers (dL/dmu', dL/dK, dL/ds, dL/dR, dL/drho, dL/dw_r) component-major.  (2) One thread
-// per Gaussian sums them over the projections, forms dL/du_r and dL/d(grad u_r), and scatters the FFD
-// backward to the control points: when all 32 Gaussians of a warp sit in the same lattice cell (the
-// usual case for spatially ordered clouds) the warp first sums its 64 x 3R values with a transposed
-// shuffle reduction and issues one atomic per control-point component; otherwise each lane adds its own.
-// (3) dL/dw is a tree reduction over the Gaussians of each (projection, rank), in a fixed order.
+// Three kernels.  (1) For 32 Gaussians per CTA, each warp takes a slot of the projections: one thread per
+// (projection, Gaussian) pair takes the pair's ten pixel sums and runs the adjoint of the projection
+// set-up and of A = S^-1 R^T K^-1; the pair adjoints (and their w-weighted sums, what the FFD backward
+// needs) are added up per Gaussian in shared memory, and dL/dw per projection is summed over the CTA's
+// Gaussians.  (2) One thread per Gaussian forms dL/du_r and dL/d(grad u_r) from those sums and scatters
+// the FFD backward to the control points: when all 32 Gaussians of a warp sit in the same lattice cell
+// (the usual case for spatially ordered clouds) the warp first sums its 64 x 3R values with a
+// transposed shuffle reduction and issues one atomic per control-point component; otherwise each lane
+// adds its own.  (3) dL/dw adds the per-CTA sums in a fixed order.
 #include "digs_internal.h"
 #include "ffd.cuh"
 #include "setup.cuh"
@@ -148,25 +149,109 @@ __device__ __forceinline__ void ffd_scatter_warp(float* __restrict__ g_phi_all, 
   }
 }
 
-// (1) Adjoint of one (projection, Gaussian) pair.
+// Adjoint of one (projection b, Gaussian n) pair from its ten pixel sums S: dL/dmu' (gmu), dL/dK (gK),
+// dL/ds (gs), dL/dR (gR), dL/drho (grho) and dL/dw_r (gw).  mu0, inv_s = 1 / s, Rm, rho: the Gaussian.
 template <int R>
-__global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, const __grid_constant__ ScanTable sc, const float* __restrict__ ffd,
-                                                      const float* __restrict__ w,
-                                                      const __grid_constant__ ViewsParam views, int P,
-                                                      const uint32_t* __restrict__ counts,
-                                                      const float4* __restrict__ sums, float* __restrict__ padj) {
-  const int N = g.n, NM = sc.nmax;  // per-Gaussian arrays are [.][N]; records [P][NM]
-  const size_t PN = (size_t)P * NM;
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= PN) return;
-  const int b = (int)(i / NM);
-  const int n = sc.off[views.v[b].scan] + (int)(i - (size_t)b * NM);  // global Gaussian (valid if counted)
-  float out[kPairAdj + R];
+__device__ __forceinline__ void pair_adjoint(const ViewC& v, const float* __restrict__ ffd, int N, int n,
+                                             const float* wr, const float mu0[3], const float inv_s[3],
+                                             const float Rm[9], float rho, const float S[10], float gmu[3],
+                                             float gK[9], float gs[3], float gR[9], float& grho, float gw[R]) {
+  float mu[3], K[9];
 #pragma unroll
-  for (int q = 0; q < kPairAdj + R; ++q) out[q] = 0.f;
-  if (counts[i] != 0u) {  // else the pair was culled by the projection set-up
-    const ViewC& v = views.v[b];
-    float mu0[3], inv_s[3], qh[4], Rm[9];
+  for (int c = 0; c < 3; ++c) mu[c] = mu0[c];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) K[c] = (c % 4 == 0) ? 1.f : 0.f;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) mu[c] = fmaf(wr[r], __ldg(ffd + (size_t)(r * 3 + c) * N + n), mu[c]);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) K[c] = fmaf(wr[r], __ldg(ffd + (size_t)(3 * R + r * 9 + c) * N + n), K[c]);
+  }
+  float Ki[9], A[9];
+  inv3(K, Ki);
+  make_A(inv_s, Rm, Ki, A);
+  float gA[9];
+  // record-parameter gradients (see the raster's pair formulas)
+  if (v.ewa) {  // the 2D-Gaussian model: w = kappa = 0
+    EwaState es;
+    ewa_core(v, mu, A, rho, es);
+    const float id = 1.f / es.det2, n00 = es.s11 * id, n01 = -es.s01 * id, n11 = es.s00 * id;
+    const float g_xc = -2.f * (n00 * S[4] + n01 * S[5]), g_yc = -2.f * (n01 * S[4] + n11 * S[5]);
+    ewa_adjoint(v, es, rho, g_xc, g_yc, S[1], 2.f * S[2], S[3], S[0], gmu, gA, grho);
+  } else {
+    SetupState st;
+    setup_core(v, mu, A, rho, st);
+    const float g_xc = -(2.f * (st.n00 * S[4] + st.n01 * S[5]) - st.w0 * S[6]);
+    const float g_yc = -(2.f * (st.n01 * S[4] + st.n11 * S[5]) - st.w1 * S[6]);
+    setup_adjoint(v, st, rho, g_xc, g_yc, S[1], 2.f * S[2], S[3], -S[7], -S[8], S[9], S[0], gmu, gA, grho);
+  }
+  // A = S^-1 R^T K^-1: dL/ds, dL/dR, dL/dK = -A^T gA K^-T
+#pragma unroll
+  for (int ii = 0; ii < 3; ++ii)
+    gs[ii] = -inv_s[ii] * (gA[3 * ii] * A[3 * ii] + gA[3 * ii + 1] * A[3 * ii + 1] + gA[3 * ii + 2] * A[3 * ii + 2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb)
+      gR[3 * a + bb] =
+          inv_s[bb] * (gA[3 * bb] * Ki[3 * a] + gA[3 * bb + 1] * Ki[3 * a + 1] + gA[3 * bb + 2] * Ki[3 * a + 2]);
+  {
+    float Tm[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Tm[3 * a + j] = A[a] * gA[j] + A[3 + a] * gA[3 + j] + A[6 + a] * gA[6 + j];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 3; ++bb)
+        gK[3 * a + bb] = -(Tm[3 * a] * Ki[3 * bb] + Tm[3 * a + 1] * Ki[3 * bb + 1] + Tm[3 * a + 2] * Ki[3 * bb + 2]);
+  }
+  // dL/dw_r = dL/dmu' . u_r + dL/dK : grad u_r
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc = fmaf(gmu[c], __ldg(ffd + (size_t)(r * 3 + c) * N + n), acc);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc = fmaf(gK[c], __ldg(ffd + (size_t)(3 * R + r * 9 + c) * N + n), acc);
+    gw[r] = acc;
+  }
+}
+
+// (1) Per Gaussian, the pair adjoints summed over its projections.  A CTA takes 32 Gaussians (its lanes)
+// and kSlots projection slots (its warps): warp k handles projections k, k + kSlots, ..., each thread
+// adding its pair's adjoint into its own shared-memory column; the slots are then summed in order.
+// gsum [16 + 12 R][N]: dL/dmu' (3), dL/ds (3), dL/dR (9), dL/drho (1), sum_b w_br dL/dmu'_b (3R) and
+// sum_b w_br dL/dK_b (9R).  gw_part [CTA][P][R]: dL/dw_r of each projection summed over the CTA's
+// Gaussians (a warp sum; each (CTA, projection) is written by one warp).
+constexpr int kSlots = 8;
+template <int R>
+__host__ __device__ constexpr int gauss_sum_count() { return 16 + 12 * R; }
+template <int R>
+constexpr size_t pair_sum_smem() { return (size_t)gauss_sum_count<R>() * kSlots * 32 * sizeof(float); }
+int pair_sum_blocks(int n) { return (n + 31) / 32; }
+
+template <int R>
+__global__ void __launch_bounds__(kSlots * 32, 2) k_pair_sum(GaussPtrs g, const __grid_constant__ ScanTable sc,
+                                                             const float* __restrict__ ffd, const float* __restrict__ w,
+                                                             const __grid_constant__ ViewsParam views, int P,
+                                                             const uint32_t* __restrict__ counts,
+                                                             const float4* __restrict__ sums, float* __restrict__ gsum,
+                                                             float* __restrict__ gw_part) {
+  constexpr int Q = gauss_sum_count<R>(), QS = kSlots * 32;
+  extern __shared__ float acc[];  // [Q][kSlots][32]
+  const int lane = threadIdx.x & 31, slot = threadIdx.x >> 5;
+  const int N = g.n, NM = sc.nmax;
+  const int n = blockIdx.x * 32 + lane;
+  const bool valid = n < N;
+  const int scan = valid ? scan_of(sc, n) : 0, nl = n - sc.off[scan];
+  float* my = acc + slot * 32 + lane;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) my[q * QS] = 0.f;
+  float mu0[3] = {0.f, 0.f, 0.f}, inv_s[3] = {1.f, 1.f, 1.f}, Rm[9], rho = 0.f;
+  if (valid) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       mu0[c] = g.mu0[3 * n + c];
@@ -174,90 +259,62 @@ __global__ void __launch_bounds__(256) k_pair_adjoint(GaussPtrs g, const __grid_
     }
     const float q0 = g.quat[4 * n], q1 = g.quat[4 * n + 1], q2 = g.quat[4 * n + 2], q3 = g.quat[4 * n + 3];
     const float iq = 1.f / sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
-    qh[0] = q0 * iq; qh[1] = q1 * iq; qh[2] = q2 * iq; qh[3] = q3 * iq;
+    const float qh[4] = {q0 * iq, q1 * iq, q2 * iq, q3 * iq};
     quat_to_R(qh, Rm);
-    const float rho = g.rho[n];
+    rho = g.rho[n];
+  }
+  for (int b0 = 0; b0 < P; b0 += kSlots) {
+    const int b = b0 + slot;  // the same for the whole warp
+    if (b >= P) break;
+    const ViewC& v = views.v[b];
     const float* wb = w + (size_t)v.w_row * R;
-    float wr[R], mu[3], K[9];
+    float gw[R];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) mu[c] = mu0[c];
+    for (int r = 0; r < R; ++r) gw[r] = 0.f;
+    const size_t i = (size_t)b * NM + nl;
+    if (valid && v.scan == scan && counts[i] != 0u) {  // else the pair was culled by the projection set-up
+      float S[10];
+      {
+        const float4* p = sums + i * DIGS_PARTIAL_F4;
+        const float4 a = p[0], c = p[1], d = p[2];
+        S[0] = a.x; S[1] = a.y; S[2] = a.z; S[3] = a.w;
+        S[4] = c.x; S[5] = c.y; S[6] = c.z; S[7] = c.w;
+        S[8] = d.x; S[9] = d.y;
+      }
+      float wr[R], gmu[3], gK[9], gs[3], gR[9], grho;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) K[c] = (c % 4 == 0) ? 1.f : 0.f;
+      for (int r = 0; r < R; ++r) wr[r] = __ldg(wb + r);
+      pair_adjoint<R>(v, ffd, N, n, wr, mu0, inv_s, Rm, rho, S, gmu, gK, gs, gR, grho, gw);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        my[c * QS] += gmu[c];
+        my[(3 + c) * QS] += gs[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 9; ++c) my[(6 + c) * QS] += gR[c];
+      my[15 * QS] += grho;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) my[(16 + 3 * r + c) * QS] += wr[r] * gmu[c];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) my[(16 + 3 * R + 9 * r + c) * QS] += wr[r] * gK[c];
+      }
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      wr[r] = __ldg(wb + r);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) mu[c] = fmaf(wr[r], __ldg(ffd + (size_t)(r * 3 + c) * N + n), mu[c]);
-#pragma unroll
-      for (int c = 0; c < 9; ++c) K[c] = fmaf(wr[r], __ldg(ffd + (size_t)(3 * R + r * 9 + c) * N + n), K[c]);
-    }
-    float Ki[9], A[9];
-    inv3(K, Ki);
-    make_A(inv_s, Rm, Ki, A);
-    float S[10];
-    {
-      const float4* p = sums + i * DIGS_PARTIAL_F4;
-      const float4 a = p[0], c = p[1], d = p[2];
-      S[0] = a.x; S[1] = a.y; S[2] = a.z; S[3] = a.w;
-      S[4] = c.x; S[5] = c.y; S[6] = c.z; S[7] = c.w;
-      S[8] = d.x; S[9] = d.y;
-    }
-    float gmu[3], gA[9], grho;
-    // record-parameter gradients (see the raster's pair formulas)
-    if (v.ewa) {  // the 2D-Gaussian model: w = kappa = 0
-      EwaState es;
-      ewa_core(v, mu, A, rho, es);
-      const float id = 1.f / es.det2, n00 = es.s11 * id, n01 = -es.s01 * id, n11 = es.s00 * id;
-      const float g_xc = -2.f * (n00 * S[4] + n01 * S[5]), g_yc = -2.f * (n01 * S[4] + n11 * S[5]);
-      ewa_adjoint(v, es, rho, g_xc, g_yc, S[1], 2.f * S[2], S[3], S[0], gmu, gA, grho);
-    } else {
-      SetupState st;
-      setup_core(v, mu, A, rho, st);
-      const float g_xc = -(2.f * (st.n00 * S[4] + st.n01 * S[5]) - st.w0 * S[6]);
-      const float g_yc = -(2.f * (st.n01 * S[4] + st.n11 * S[5]) - st.w1 * S[6]);
-      setup_adjoint(v, st, rho, g_xc, g_yc, S[1], 2.f * S[2], S[3], -S[7], -S[8], S[9], S[0], gmu, gA, grho);
-    }
-    // A = S^-1 R^T K^-1: dL/ds, dL/dR, dL/dK = -A^T gA K^-T
-    float gK[9];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) out[c] = gmu[c];
-#pragma unroll
-    for (int ii = 0; ii < 3; ++ii)
-      out[12 + ii] = -inv_s[ii] * (gA[3 * ii] * A[3 * ii] + gA[3 * ii + 1] * A[3 * ii + 1] + gA[3 * ii + 2] * A[3 * ii + 2]);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int bb = 0; bb < 3; ++bb)
-        out[15 + 3 * a + bb] =
-            inv_s[bb] * (gA[3 * bb] * Ki[3 * a] + gA[3 * bb + 1] * Ki[3 * a + 1] + gA[3 * bb + 2] * Ki[3 * a + 2]);
-    {
-      float Tm[9];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) Tm[3 * a + j] = A[a] * gA[j] + A[3 + a] * gA[3 + j] + A[6 + a] * gA[6 + j];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int bb = 0; bb < 3; ++bb)
-          gK[3 * a + bb] = -(Tm[3 * a] * Ki[3 * bb] + Tm[3 * a + 1] * Ki[3 * bb + 1] + Tm[3 * a + 2] * Ki[3 * bb + 2]);
-    }
-#pragma unroll
-    for (int c = 0; c < 9; ++c) out[3 + c] = gK[c];
-    out[24] = grho;
-    // dL/dw_r = dL/dmu' . u_r + dL/dK : grad u_r
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      float acc = 0.f;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc = fmaf(gmu[c], __ldg(ffd + (size_t)(r * 3 + c) * N + n), acc);
-#pragma unroll
-      for (int c = 0; c < 9; ++c) acc = fmaf(gK[c], __ldg(ffd + (size_t)(3 * R + r * 9 + c) * N + n), acc);
-      out[kPairAdj + r] = acc;
+      const float t = warp_sum(gw[r]);
+      if (lane == 0) gw_part[((size_t)blockIdx.x * P + b) * R + r] = t;
     }
   }
+  __syncthreads();
+  for (int o = threadIdx.x; o < Q * 32; o += QS) {
+    const int q = o >> 5, l = o & 31, nn = blockIdx.x * 32 + l;
+    float t = 0.f;
 #pragma unroll
-  for (int q = 0; q < kPairAdj + R; ++q) padj[(size_t)q * PN + i] = out[q];
+    for (int k = 0; k < kSlots; ++k) t += acc[q * QS + k * 32 + l];
+    if (nn < N) gsum[(size_t)q * N + nn] = t;
+  }
 }
 
 // Second derivatives of u_r at each mean ([18 R][n], see ffd_hessian_point), for the mean's gradient.
@@ -275,21 +332,19 @@ __global__ void __launch_bounds__(128) k_ffd_hessian(GaussPtrs g, const __grid_c
     for (int c = 0; c < 18; ++c) out[(size_t)(r * 18 + c) * g.n + n] = H[r][c];
 }
 
-// (2) Per Gaussian: sum the pair adjoints over the projections, then the FFD backward.
+// (2) Per Gaussian: from the summed pair adjoints, the FFD backward and the reference-parameter gradients.
 template <int R>
 __global__ void __launch_bounds__(kChainThreads) k_gauss_bwd(
     GaussPtrs g, const __grid_constant__ ScanTable sc, LatticeC L, const float* __restrict__ ffd,
     const float* __restrict__ ffd2,
-    const float* __restrict__ w, const __grid_constant__ ViewsParam views, int P, const float* __restrict__ padj,
-    float* __restrict__ g_mu0,
+    const float* __restrict__ gsum, float* __restrict__ g_mu0,
     float* __restrict__ g_scale, float* __restrict__ g_quat, float* __restrict__ g_rho, float* __restrict__ g_phi) {
   __shared__ float Gs[12 * R * kChainThreads];  // dL/du_r (3R) then dL/d(grad u_r) (9R), thread-fastest
   constexpr int ST = kChainThreads;
   const int N = g.n;
-  const size_t PN = (size_t)P * sc.nmax;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = n < N;
-  const int scan = valid ? scan_of(sc, n) : 0, nl = n - sc.off[scan];  // scan-local index
+  const int scan = valid ? scan_of(sc, n) : 0;
   float GU[R][3], GdU[R][9], gmu0[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gR[9], grho = 0.f;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -301,30 +356,21 @@ __global__ void __launch_bounds__(kChainThreads) k_gauss_bwd(
 #pragma unroll
   for (int c = 0; c < 9; ++c) gR[c] = 0.f;
   if (valid) {
-    for (int b = 0; b < P; ++b) {
-      if (views.v[b].scan != scan) continue;
-      const size_t i = (size_t)b * sc.nmax + nl;
-      const float* wb = w + (size_t)views.v[b].w_row * R;
-      float gmu[3], gK[9];
+    const float* q = gsum + n;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) gmu[c] = padj[(size_t)c * PN + i];
+    for (int c = 0; c < 3; ++c) {
+      gmu0[c] = q[(size_t)c * N];
+      gs[c] = q[(size_t)(3 + c) * N];
+    }
 #pragma unroll
-      for (int c = 0; c < 9; ++c) gK[c] = padj[(size_t)(3 + c) * PN + i];
+    for (int c = 0; c < 9; ++c) gR[c] = q[(size_t)(6 + c) * N];
+    grho = q[(size_t)15 * N];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) gs[c] += padj[(size_t)(12 + c) * PN + i];
+    for (int r = 0; r < R; ++r) {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) gR[c] += padj[(size_t)(15 + c) * PN + i];
-      grho += padj[(size_t)24 * PN + i];
+      for (int c = 0; c < 3; ++c) GU[r][c] = q[(size_t)(16 + 3 * r + c) * N];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) gmu0[c] += gmu[c];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float wr = __ldg(wb + r);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) GU[r][c] = fmaf(wr, gmu[c], GU[r][c]);
-#pragma unroll
-        for (int c = 0; c < 9; ++c) GdU[r][c] = fmaf(wr, gK[c], GdU[r][c]);
-      }
+      for (int c = 0; c < 9; ++c) GdU[r][c] = q[(size_t)(16 + 3 * R + 9 * r + c) * N];
     }
   }
 #pragma unroll
@@ -377,15 +423,20 @@ cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const Latt
                              const float* w, const ViewsParam& views, int P, const Workspace& ws, float* g_mu0,
                              float* g_scale, float* g_quat, float* g_rho, float* g_phi, cudaStream_t st) {
   if (g.n <= 0) return cudaSuccess;
-  const size_t PN = (size_t)P * sc.nmax;
-  const unsigned ga = (unsigned)((PN + 255) / 256);
-  dim3 gb(chain_blocks(g.n));
+  dim3 gb(chain_blocks(g.n)), gp(pair_sum_blocks(g.n));
 #define DIGS_CH(RR)                                                                                             \
+  {                                                                                                             \
+    static bool configured = false;                                                                             \
+    if (!configured) {                                                                                          \
+      cudaFuncSetAttribute(k_pair_sum<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_sum_smem<RR>()); \
+      configured = true;                                                                                        \
+    }                                                                                                           \
+  }                                                                                                             \
   k_ffd_hessian<RR><<<gb, 128, 0, st>>>(g, sc, L, phi, ws.ffd2);                                                \
-  if (PN > 0)                                                                                                   \
-    k_pair_adjoint<RR><<<ga, 256, 0, st>>>(g, sc, ws.ffd, w, views, P, ws.counts, ws.grec, ws.padj);             \
-  k_gauss_bwd<RR><<<gb, kChainThreads, 0, st>>>(g, sc, L, ws.ffd, ws.ffd2, w, views, P, ws.padj, g_mu0, g_scale, \
-                                               g_quat, g_rho, g_phi)
+  k_pair_sum<RR><<<gp, kSlots * 32, pair_sum_smem<RR>(), st>>>(g, sc, ws.ffd, w, views, P, ws.counts, ws.grec,   \
+                                                              ws.gsum, ws.gw_part);                            \
+  k_gauss_bwd<RR><<<gb, kChainThreads, 0, st>>>(g, sc, L, ws.ffd, ws.ffd2, ws.gsum, g_mu0, g_scale, g_quat,    \
+                                               g_rho, g_phi)
   switch (L.R) {
     case 1: DIGS_CH(1); break;
     case 2: DIGS_CH(2); break;
@@ -394,53 +445,35 @@ cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const Latt
     default: return cudaErrorInvalidValue;
   }
 #undef DIGS_CH
-  note_launches(PN > 0 ? 3 : 2);
+  note_launches(3);
   return cudaGetLastError();
 }
 
-// (3) dL/dw[row(b)][r] = sum over the Gaussians of the pair adjoints: kGwSplit blocks per (projection,
-// rank) sum contiguous ranges (strided, then a fixed-order tree), and a second kernel adds the kGwSplit
-// partials in order.  Rows of w that no projection of the call uses get zero.
-constexpr int kGwSplit = 32;
-
-__global__ void __launch_bounds__(256) k_gw_partial(const float* __restrict__ padj, int N, int P, int R,
-                                                    float* __restrict__ part) {
+// (3) dL/dw[row(b)][r]: the per-CTA sums of k_pair_sum added in CTA order (strided over the block's
+// threads, then a fixed-order tree), one block per (projection, rank).  Rows of w that no projection of
+// the call uses get zero.
+__global__ void __launch_bounds__(256) k_gw_final(const float* __restrict__ part, int n_cta, int P, int R,
+                                                  float* __restrict__ g_w, const __grid_constant__ ViewsParam views) {
   __shared__ float red[8];
-  const int pr = blockIdx.x / kGwSplit, j = blockIdx.x % kGwSplit;
-  const int b = pr / R, r = pr % R;
-  const size_t PN = (size_t)P * N;
-  const int chunk = (N + kGwSplit - 1) / kGwSplit;
-  const int n0 = j * chunk, n1 = min(N, n0 + chunk);
-  const float* src = padj + (size_t)(kPairAdj + r) * PN + (size_t)b * N;
+  const int b = blockIdx.x / R, r = blockIdx.x % R;
   float s = 0.f;
-  for (int n = n0 + threadIdx.x; n < n1; n += blockDim.x) s += src[n];
+  for (int k = threadIdx.x; k < n_cta; k += blockDim.x) s += part[((size_t)k * P + b) * R + r];
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     float t = 0.f;
     for (int k = 0; k < 8; ++k) t += red[k];
-    part[blockIdx.x] = t;
+    atomicAdd(&g_w[(size_t)views.v[b].w_row * R + r], t);  // rows repeat only if a time point repeats
   }
-}
-
-__global__ void k_gw_final(const float* __restrict__ part, int P, int R, float* __restrict__ g_w,
-                           const __grid_constant__ ViewsParam views) {
-  const int pr = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pr >= P * R) return;
-  const int b = pr / R, r = pr % R;
-  float t = 0.f;
-  for (int j = 0; j < kGwSplit; ++j) t += part[(size_t)pr * kGwSplit + j];
-  atomicAdd(&g_w[(size_t)views.v[b].w_row * R + r], t);  // rows repeat only if a time point repeats
 }
 
 cudaError_t launch_gw_reduce(const Workspace& ws, const ViewsParam& views, int P, int R, float* g_w, int w_rows,
                              cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(g_w, 0, sizeof(float) * (size_t)w_rows * R, st);
-  if (e != cudaSuccess || P * R == 0 || ws.n == 0) return e;
-  k_gw_partial<<<P * R * kGwSplit, 256, 0, st>>>(ws.padj, ws.n, P, R, ws.gw_part);
-  k_gw_final<<<(P * R + 127) / 128, 128, 0, st>>>(ws.gw_part, P, R, g_w, views);
-  note_launches(2);
+  if (e != cudaSuccess || P * R == 0 || ws.n_total == 0) return e;
+  k_gw_final<<<P * R, 256, 0, st>>>(ws.gw_part, pair_sum_blocks(ws.n_total), P, R, g_w, views);
+  note_launches(1);
   return cudaGetLastError();
 }
 

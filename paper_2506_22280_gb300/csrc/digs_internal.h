@@ -8,10 +8,6 @@
 
 namespace digs {
 
-// Per-(projection, Gaussian) adjoint record of the backward: dL/dmu' (3), dL/dK (9), dL/ds (3),
-// dL/dR (9), dL/drho (1), followed by R entries of dL/dw_r.
-constexpr int kPairAdj = 25;
-
 // Kernel-launch bookkeeping (diagnostic): every launcher reports how many kernels it enqueued.
 void note_launches(int k);
 
@@ -34,10 +30,10 @@ struct Workspace {
   uint2* ranges;          // [P * T] sorted-range of each (projection, tile)
   uint32_t* order;        // [P * T] forward launch order (longest lists first)
   float4* grec;           // [P * n * 3] backward: the ten pixel sums of each (projection, Gaussian) record
-  float* gw_part;         // [gauss blocks][P * R]
+  float* gw_part;         // [pair-sum CTAs][P][R] dL/dw partial sums
   float* ffd;             // [12 R][n_total]: u_r (3R components) then grad u_r (9R) at each mean
   float* ffd2;            // [18 R][n_total]: second derivatives of u_r (6 per component)
-  float* padj;            // [kPairAdj + R][P * n]: per-(projection, Gaussian) adjoints
+  float* gsum;            // [16 + 12 R][n_total]: each Gaussian's pair adjoints summed over its projections
   float* loss_part;       // [P * T * fwd_blocks(tile)] forward: squared residuals per 8 x 8 block (warp)
   float* proj;            // [P * nv * nu] (digs_step)
   float* dldi;            // [P * nv * nu] (digs_step)
@@ -48,7 +44,7 @@ struct Workspace {
   int n, P, nu, nv, R, tile, tiles_x, tiles_y, T;  // n: record stride (largest scan's Gaussian count)
   int n_total;                                     // Gaussians of all scans
   int bwd_lanes;                                   // lanes per record in the backward raster (16 or 32)
-  int n_sort_blocks, n_gauss_blocks;
+  int n_sort_blocks;
 };
 
 // Forward work items (8 x 8 pixel blocks) per tile.
@@ -99,6 +95,7 @@ cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const Latt
 cudaError_t launch_gw_reduce(const Workspace& ws, const ViewsParam& views, int P, int R, float* g_w, int w_rows,
                              cudaStream_t st);
 int chain_blocks(int n);
+int pair_sum_blocks(int n);
 
 // temporal.cu: w rows of a step from the temporal B-spline control points, and the adjoint.
 struct RowsParam {
