@@ -15,7 +15,10 @@ Parameters are one flat vector, per layer: convolution weights [Co][ky][kx][Ci] 
 four convolutions, then W1 [128][8194], b1 [128], W2 [R][128], b2 [R].  The steps are library
 primitives in float64 (``torch.nn.functional.conv2d`` / ``linear`` / ``relu``), and autograd gives the
 gradient of the same definition.  Pins: ``tests/test_oracle_cnn.py`` (convolution against an explicit
-loop, the feature order, finite differences of the gradient, the 2 x 2 average).
+loop, the feature order, finite differences of the gradient, the 2 x 2 average, bfloat16 rounding).
+
+``bf16_round`` / ``gemm_bf16``: the tensor-core GEMM's definition -- both operands rounded to bfloat16
+(round to nearest, ties to even), then an exact product in float64.
 """
 from __future__ import annotations
 
@@ -90,3 +93,23 @@ def vjp(flat, R: int, img, cs, grad_w) -> np.ndarray:
 def mse(flat, R: int, img, cs, target) -> float:
     out = forward(flat, R, img, cs)
     return float(((out - np.asarray(target, dtype=np.float64)) ** 2).mean())
+
+
+def bf16_round(x) -> np.ndarray:
+    """Nearest bfloat16 of each float32 value (ties to even), as float64.  A bfloat16 is the upper 16 bits
+    of a binary32 pattern: add 0x7FFF plus the lowest kept bit (so that exact halves go to the even
+    neighbour) and clear the 16 dropped bits.  Finite inputs only."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = a.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def gemm_bf16(A, B, trans_a: bool = False, trans_b: bool = False, bias=None, relu: bool = False) -> np.ndarray:
+    """op(A) op(B) (+ bias per column, ReLU) with A and B rounded to bfloat16 and everything after in
+    float64; op(X) = X.T when its flag is set."""
+    a, b = bf16_round(A), bf16_round(B)
+    c = (a.T if trans_a else a) @ (b.T if trans_b else b)
+    if bias is not None:
+        c = c + np.asarray(bias, dtype=np.float64)[None, :]
+    return np.maximum(c, 0.0) if relu else c

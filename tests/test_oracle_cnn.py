@@ -83,3 +83,29 @@ def test_downsample_is_the_block_mean():
     d = C.downsample(p, 2.0)
     assert d.shape == (3, 4, 3)
     assert np.isclose(d[1, 2, 1], 2.0 * p[1, 4:6, 2:4].mean())
+
+
+def test_bf16_rounding_ties_to_even_and_matches_torch():
+    u = 2.0 ** -8  # half a bfloat16 ulp at 1
+    x = np.array([1.0, -2.5, 1 + u, 1 + 3 * u, 1 + u + 2.0 ** -20, 1 - 2.0 ** -9], dtype=np.float32)
+    want = np.array([1.0, -2.5, 1.0, 1 + 4 * u, 1 + 2 * u, 1.0])
+    assert np.array_equal(C.bf16_round(x), want)
+    rng = np.random.default_rng(3)
+    y = (rng.normal(size=10000) * 10.0 ** rng.uniform(-30, 30, size=10000)).astype(np.float32)
+    ref = torch.tensor(y).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(C.bf16_round(y), ref)
+
+
+def test_gemm_bf16_definition():
+    rng = np.random.default_rng(4)
+    A = rng.normal(size=(5, 7)).astype(np.float32)
+    B = rng.normal(size=(7, 3)).astype(np.float32)
+    bias = rng.normal(size=3)
+    ref = C.bf16_round(A) @ C.bf16_round(B) + bias
+    assert np.allclose(C.gemm_bf16(A, B, bias=bias), ref, rtol=0, atol=1e-12)
+    assert np.allclose(C.gemm_bf16(A.T.copy(), B.T.copy(), True, True, bias, True), np.maximum(ref, 0), atol=1e-12)
+    # exact on values that bfloat16 holds: small integers
+    Ai = rng.integers(-8, 9, size=(4, 6)).astype(np.float32)
+    Bi = rng.integers(-8, 9, size=(6, 2)).astype(np.float32)
+    assert np.array_equal(C.gemm_bf16(Ai, Bi), Ai.astype(np.float64) @ Bi.astype(np.float64))
+
