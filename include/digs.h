@@ -277,6 +277,19 @@ digs_status digs_cnn_train_step(float* params, float* m, float* v, float* grad, 
 digs_status digs_cnn_infer_bf16(const float* params, int R, const float* img, const float* cs, int B, float* w_out,
                                 void* ws, size_t ws_bytes, void* stream);
 
+/* ---- Dense GEMM on the tensor cores ------------------------------------------------------------
+ * The paper has no counterpart: the weight-predictor CNN's layers run on this.  C = op(A) op(B) (+ bias
+ * per column, ReLU if relu != 0) on the fifth-generation tensor cores: A and B are FP32 in device memory,
+ * rounded to BF16 (round to nearest even) as they are read; products are exact and accumulate in FP32.
+ * op(A) is M x K: A[m lda + k], or A[k lda + m] if trans_a; op(B) is K x N: B[k ldb + n], or
+ * B[n ldb + k] if trans_b; C is M x N with row pitch ldc (FP32).  splits > 1 (<= 64) divides K into
+ * that many ranges computed in parallel into partial[splits][M][N] (device scratch the caller owns),
+ * then added in a fixed order.  status: optional device int set to 1 if an internal bounded wait gave
+ * up (the output is then undefined).  DIGS_ERR_ARG on bad sizes or pitches. */
+digs_status digs_gemm_bf16(int trans_a, int trans_b, int M, int N, int K, const float* A, int lda, const float* B,
+                           int ldb, const float* bias, int relu, float* C, int ldc, int splits, float* partial,
+                           int* status, void* stream);
+
 /* ---- Diagnostics (not part of the method; used to measure it) ---------------------------------- */
 
 /* Stage timing: a call whose opts->flags has DIGS_FLAG_TIME_STAGES records CUDA events around each of

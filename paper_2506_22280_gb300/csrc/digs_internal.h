@@ -97,6 +97,14 @@ cudaError_t launch_gw_reduce(const Workspace& ws, const ViewsParam& views, int P
 int chain_blocks(int n);
 int pair_sum_blocks(int n);
 
+// umma.cu: tensor-core GEMM (BF16 operands rounded from FP32, FP32 accumulation); C(m, n) = sum_k
+// A(m, k) B(k, n) with A(m, k) = at ? A[k lda + m] : A[m lda + k], B(k, n) = bt ? B[n ldb + k] :
+// B[k ldb + n]; splits > 1: partial sums over K ranges into C + z zstride (bias and ReLU not applied).
+// *status (optional) is set to 1 if a bounded wait gave up.
+cudaError_t gemm_tc(bool at, bool bt, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
+                    int ldc, const float* bias, bool relu, int splits, long long zstride, int* status,
+                    cudaStream_t st);
+
 // temporal.cu: w rows of a step from the temporal B-spline control points, and the adjoint.
 struct RowsParam {
   int v[DIGS_MAX_VIEWS];

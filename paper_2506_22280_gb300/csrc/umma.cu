@@ -1,0 +1,313 @@
+// Dense GEMM on the fifth-generation tensor cores (tcgen05, sm_103a): C = op(A) op(B) with BF16 operands
+// and FP32 accumulation in tensor memory, for the weight-predictor CNN's layers.
+//
+// C(m, n) = sum_k A(m, k) B(k, n); A(m, k) = AT ? A[k lda + m] : A[m lda + k] and
+// B(k, n) = BT ? B[n ldb + k] : B[k ldb + n], FP32 or BF16 in global memory.  One CTA of 128 threads per
+// 128 x 64 tile of C:
+//   * all four warps stage 64-deep K slices of A (128 x 64) and B (64 x 64) into shared memory,
+//     rounding to BF16 (round to nearest even) and writing the K-major, non-swizzled layout the tensor
+//     core reads: 8-row x 16-byte core matrices, core matrix (row group g, k chunk kc) at
+//     (8 g + kc) 128 bytes, so that 8-row groups lie 1024 bytes apart and K chunks 128 bytes apart;
+//   * one thread issues four 128 x 64 x 16 tcgen05.mma per slice into a 128-lane x 64-column FP32
+//     accumulator in tensor memory and commits them to the slice's mbarrier; the slice buffers are
+//     double-buffered, so staging slice k + 1 overlaps the MMAs of slice k;
+//   * each warp reads its 32 accumulator lanes (rows) back with tcgen05.ld and writes them out, adding
+//     the bias and applying ReLU when asked.
+// gridDim.z > 1 splits K: block z sums k in [z kchunk, (z + 1) kchunk) into C + z zstride (no bias).
+// Every mbarrier wait is bounded; a wait that gives up sets *status to 1 and the block still waits
+// (bounded) for its own MMAs, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "digs_internal.h"
+
+namespace digs {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kBM = 128, kBN = 64, kBK = 64;
+constexpr int kStageA = kBM * kBK * 2;  // bytes of one A slice (16 KB)
+constexpr int kStageB = kBN * kBK * 2;  // bytes of one B slice (8 KB)
+constexpr int kTmemCols = 64;           // FP32 accumulator columns (= kBN)
+constexpr size_t kTcSmem = 1024 + 2 * kStageA + 2 * kStageB + 64;  // 1 KB alignment slack, buffers, barriers
+constexpr unsigned kWaitLimit = 1u << 22;                          // x ~100 ns
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Waits for the completion of the mbarrier phase with the given parity: non-blocking tests with a short
+// sleep between them, false after kWaitLimit tests (well under a second).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (unsigned it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it >= 64) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major without swizzle: start address, leading-dimension byte
+// offset (between core matrices adjacent in K), stride-dimension byte offset (between 8-row groups),
+// all in 16-byte units; descriptor version 1 (bits 46-47); layout type 0 (no swizzle, bits 61-63).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits 7-9 and
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 in bits 17-22, M / 16 in bits 24-28.
+constexpr uint32_t kIdesc =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's accumulator lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float ld_f(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_f(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void st_c(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_c(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// One 8-element K chunk of row `row` of an operand, K-range [k, k + 8) clipped to [.., kend), rows
+// beyond `rows` zero; T (transposed) reads element (row, kk) at P[kk ld + row], else P[row ld + kk].
+template <bool T, typename TP>
+__device__ __forceinline__ uint4 load_chunk(const TP* __restrict__ P, int ld, int row, int rows, int k, int kend) {
+  float x[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int kk = k + e;
+    x[e] = (row < rows && kk < kend) ? ld_f(T ? P + (size_t)kk * ld + row : P + (size_t)row * ld + kk) : 0.f;
+  }
+  return make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
+}
+
+// Stage the K slice [k0, k0 + 64) of the block's A rows and B columns.  Consecutive threads take
+// consecutive K chunks when K is the contiguous global index, else consecutive rows.
+template <bool AT, bool BT, typename TA, typename TB>
+__device__ __forceinline__ void stage(const TA* __restrict__ A, int lda, const TB* __restrict__ B, int ldb, int M,
+                                      int N, int m0, int n0, int k0, int kend, uint8_t* sA, uint8_t* sB) {
+#pragma unroll
+  for (int i = 0; i < (kBM * 8) / kTcThreads; ++i) {
+    const int c = threadIdx.x + i * kTcThreads;
+    const int kc = AT ? c / kBM : c & 7, mm = AT ? c % kBM : c >> 3;
+    const uint4 v = load_chunk<AT>(A, lda, m0 + mm, M, k0 + kc * 8, kend);
+    *reinterpret_cast<uint4*>(sA + ((mm >> 3) * 8 + kc) * 128 + (mm & 7) * 16) = v;
+  }
+#pragma unroll
+  for (int i = 0; i < (kBN * 8) / kTcThreads; ++i) {
+    const int c = threadIdx.x + i * kTcThreads;
+    const int kc = BT ? c & 7 : c / kBN, nn = BT ? c >> 3 : c % kBN;
+    const uint4 v = load_chunk<!BT>(B, ldb, n0 + nn, N, k0 + kc * 8, kend);
+    *reinterpret_cast<uint4*>(sB + ((nn >> 3) * 8 + kc) * 128 + (nn & 7) * 16) = v;
+  }
+}
+
+template <bool AT, bool BT, typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, const TA* __restrict__ A, int lda,
+                                                        const TB* __restrict__ B, int ldb, TC* __restrict__ C,
+                                                        int ldc, int kchunk, long long zstride,
+                                                        const float* __restrict__ bias, int relu, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = sm;
+  uint8_t* sB = sm + 2 * kStageA;
+  uint64_t* bar = (uint64_t*)(sB + 2 * kStageB);
+  uint32_t* tslot = (uint32_t*)(bar + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  const int nk = ke > kb ? (ke - kb + kBK - 1) / kBK : 0;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  int ok = 1;
+  int issued = 0;  // slices whose MMAs were committed
+  for (int s = 0; s < nk; ++s) {
+    const int buf = s & 1;
+    if (s >= 2) ok = __syncthreads_and(ok && mbar_wait(bar + buf, (uint32_t)(((s >> 1) - 1) & 1)));
+    if (!ok) break;
+    stage<AT, BT>(A, lda, B, ldb, M, N, m0, n0, kb + s * kBK, ke, sA + buf * kStageA, sB + buf * kStageB);
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA + buf * kStageA), b0 = smem_u32(sB + buf * kStageB);
+#pragma unroll
+      for (int j = 0; j < kBK / 16; ++j) {
+        // MMA j covers k chunks 2j and 2j + 1 (256 bytes in): K chunks 128 bytes apart, row groups 1024
+        const uint64_t da = smem_desc(a0 + j * 256, 128, 1024);
+        const uint64_t db = smem_desc(b0 + j * 256, 128, 1024);
+        mma_bf16(tmem, da, db, (s > 0 || j > 0) ? 1u : 0u);
+      }
+      mma_commit(bar + buf);
+    }
+    issued = s + 1;
+  }
+  // the last commit tracks every MMA issued before it
+  if (issued > 0 && !mbar_wait(bar + ((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1))) ok = 0;
+  tc_fence_after();
+  const int m = m0 + warp * 32 + lane;
+  TC* Cz = C + (size_t)blockIdx.z * zstride;
+#pragma unroll
+  for (int c0 = 0; c0 < kBN; c0 += 16) {
+    float v[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (m < M && ok) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int n = n0 + c0 + j;
+        if (n >= N) break;
+        float x = issued > 0 ? v[j] : 0.f;
+        if (gridDim.z == 1) {
+          if (bias) x += bias[n];
+          if (relu) x = fmaxf(x, 0.f);
+        }
+        st_c(Cz + (size_t)m * ldc + n, x);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+  if (!ok && threadIdx.x == 0 && status) atomicExch(status, 1);
+}
+
+template <bool AT, bool BT, typename TA, typename TB, typename TC>
+cudaError_t launch_tc(int M, int N, int K, const TA* A, int lda, const TB* B, int ldb, TC* C, int ldc,
+                      const float* bias, bool relu, int splits, long long zstride, int* status, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<AT, BT, TA, TB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (splits < 1) splits = 1;
+  const int kchunk = ((K + splits - 1) / splits + kBK - 1) / kBK * kBK;
+  dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, splits);
+  k_gemm_tc<AT, BT, TA, TB, TC><<<grid, kTcThreads, kTcSmem, st>>>(M, N, K, A, lda, B, ldb, C, ldc, kchunk, zstride,
+                                                                   bias, relu ? 1 : 0, status);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// C[m][n] = act(sum_z part[z][m][n] + bias[n]), the splits added in order.
+__global__ void k_tc_sum(const float* __restrict__ part, int splits, int M, int N, float* __restrict__ C, int ldc,
+                         const float* __restrict__ bias, int relu) {
+  const long long MN = (long long)M * N;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < MN; i += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[(size_t)z * MN + i];
+    const int n = (int)(i % N);
+    if (bias) s += bias[n];
+    if (relu) s = fmaxf(s, 0.f);
+    C[(size_t)(i / N) * ldc + n] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t gemm_tc(bool at, bool bt, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
+                    int ldc, const float* bias, bool relu, int splits, long long zstride, int* status,
+                    cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (!at && !bt) return launch_tc<false, false>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, splits, zstride, status, st);
+  if (!at && bt) return launch_tc<false, true>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, splits, zstride, status, st);
+  if (at && !bt) return launch_tc<true, false>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, splits, zstride, status, st);
+  return launch_tc<true, true>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, splits, zstride, status, st);
+}
+
+cudaError_t gemm_tc_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
+                         __nv_bfloat16* C, int ldc, const float* bias, bool relu, int* status, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  return launch_tc<false, true>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, 1, 0, status, st);
+}
+
+}  // namespace digs
+
+extern "C" digs_status digs_gemm_bf16(int trans_a, int trans_b, int M, int N, int K, const float* A, int lda,
+                                      const float* B, int ldb, const float* bias, int relu, float* C, int ldc,
+                                      int splits, float* partial, int* status, void* stream) {
+  using namespace digs;
+  if (M < 0 || N < 0 || K < 0 || splits < 1 || splits > 64) return DIGS_ERR_ARG;
+  if (M == 0 || N == 0) return DIGS_OK;
+  if (!C || ldc < N || (K > 0 && (!A || !B))) return DIGS_ERR_ARG;
+  if (K > 0 && (lda < (trans_a ? M : K) || ldb < (trans_b ? K : N))) return DIGS_ERR_ARG;
+  if (splits > 1 && !partial) return DIGS_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (splits == 1) {
+    e = gemm_tc(trans_a != 0, trans_b != 0, M, N, K, A, lda, B, ldb, C, ldc, bias, relu != 0, 1, 0, status, st);
+  } else {
+    e = gemm_tc(trans_a != 0, trans_b != 0, M, N, K, A, lda, B, ldb, partial, N, nullptr, false, splits,
+                (long long)M * N, status, st);
+    if (e == cudaSuccess) {
+      const long long MN = (long long)M * N;
+      k_tc_sum<<<(unsigned)std::min<long long>((MN + 255) / 256, 152LL * 16), 256, 0, st>>>(partial, splits, M, N, C,
+                                                                                         ldc, bias, relu);
+      note_launches(1);
+      e = cudaGetLastError();
+    }
+  }
+  return e == cudaSuccess ? DIGS_OK : DIGS_ERR_CUDA;
+}

@@ -100,6 +100,7 @@ def lib() -> C.CDLL:
         "digs_cnn_backward": (I, [P, I, I, P, P, P, S, P]),
         "digs_cnn_train_step": (I, [P, P, P, P, I, C.c_float, I, P, P, P, I, P, P, S, P]),
         "digs_cnn_infer_bf16": (I, [P, I, P, P, I, P, P, S, P]),
+        "digs_gemm_bf16": (I, [I, I, I, I, I, P, I, P, I, P, I, P, I, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -114,7 +115,7 @@ def exported_symbols() -> List[str]:
             "digs_state_moments", "digs_state_workspace_size", "digs_state_size", "digs_step", "digs_sync_status", "digs_status_string", "digs_stage_times",
             "digs_kernel_launches", "digs_pair_stats", "digs_voxelize", "digs_dvf", "digs_cnn_params", "digs_cnn_workspace_size", "digs_cnn_init",
             "digs_cnn_prepare_input", "digs_cnn_forward", "digs_cnn_backward", "digs_cnn_train_step",
-            "digs_cnn_infer_bf16"]
+            "digs_cnn_infer_bf16", "digs_gemm_bf16"]
 
 
 DIGS_FLAG_TIME_STAGES = 2
@@ -508,6 +509,25 @@ class Reconstruction:
 
     def status(self) -> int:
         return sync_status(self.ws)
+
+
+def gemm_bf16(a: torch.Tensor, b: torch.Tensor, trans_a: bool = False, trans_b: bool = False,
+              bias: Optional[torch.Tensor] = None, relu: bool = False, splits: int = 1) -> Tuple[torch.Tensor, torch.Tensor]:
+    """C = op(a) op(b) (+ bias, ReLU) on the tensor cores: BF16 operands rounded from a, b (FP32), FP32
+    accumulation (include/digs.h, digs_gemm_bf16).  op(a) = a.T if trans_a; op(b) = b.T if trans_b.
+    Returns (C [M][N] float32, status [1] int32: nonzero if a bounded wait in the kernel gave up)."""
+    a, b = _f32(a, "a").contiguous(), _f32(b, "b").contiguous()
+    M, K = (a.shape[1], a.shape[0]) if trans_a else (a.shape[0], a.shape[1])
+    Kb, N = (b.shape[1], b.shape[0]) if trans_b else (b.shape[0], b.shape[1])
+    if K != Kb:
+        raise ValueError(f"inner dimensions differ: {K} vs {Kb}")
+    out = torch.empty(M, N, device=a.device, dtype=torch.float32)
+    part = torch.empty(splits, M, N, device=a.device, dtype=torch.float32) if splits > 1 else None
+    status = torch.zeros(1, device=a.device, dtype=torch.int32)
+    _check(lib().digs_gemm_bf16(int(trans_a), int(trans_b), M, N, K, _ptr(a), int(a.shape[1]), _ptr(b),
+                                int(b.shape[1]), _ptr(bias), int(relu), _ptr(out), N, int(splits), _ptr(part),
+                                _ptr(status), _stream()), "digs_gemm_bf16")
+    return out, status
 
 
 class WeightPredictor:
