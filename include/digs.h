@@ -260,20 +260,25 @@ size_t digs_cnn_workspace_size(int B, int R);
 digs_status digs_cnn_init(float* params, int R, unsigned long long seed, void* stream);
 /* img[b] = scale * the 2x2 means of proj[b] ([B][256][256] -> [B][128][128]). */
 digs_status digs_cnn_prepare_input(const float* proj, int B, int nu, int nv, float scale, float* img, void* stream);
-/* FP32 forward: w_out[B][R]. */
+/* flags of the forward, backward and training step: DIGS_CNN_TENSOR_CORES runs the convolutions' and the
+ * 8194-wide layer's GEMMs on the tensor cores (BF16 operands rounded from FP32, FP32 accumulation); without
+ * it every GEMM is FP32 on the SIMT pipes. */
+#define DIGS_CNN_TENSOR_CORES 1
+/* Forward: w_out[B][R]. */
 digs_status digs_cnn_forward(const float* params, int R, const float* img, const float* cs, int B, float* w_out,
-                             void* ws, size_t ws_bytes, void* stream);
+                             int flags, void* ws, size_t ws_bytes, void* stream);
 /* Gradient of every parameter (grad_params, laid out like params) for dL/dw = grad_w [B][R], through the
  * activations of the preceding digs_cnn_forward on the same workspace and batch size. */
-digs_status digs_cnn_backward(const float* params, int R, int B, const float* grad_w, float* grad_params, void* ws,
-                              size_t ws_bytes, void* stream);
+digs_status digs_cnn_backward(const float* params, int R, int B, const float* grad_w, float* grad_params, int flags,
+                              void* ws, size_t ws_bytes, void* stream);
 /* One training step on the mean squared error between the predicted and target weights ([B][R]):
  * forward, loss (device float, written to loss_out), backward into grad, Adam (beta 0.9 / 0.999,
  * eps 1e-8, learning rate lr, 1-based step) on params with moments m, v (zero-initialised). */
 digs_status digs_cnn_train_step(float* params, float* m, float* v, float* grad, int step, float lr, int R,
                                 const float* img, const float* cs, const float* target, int B, float* loss_out,
-                                void* ws, size_t ws_bytes, void* stream);
-/* Inference with BF16 weights and activations and FP32 accumulation (biases FP32): w_out[B][R]. */
+                                int flags, void* ws, size_t ws_bytes, void* stream);
+/* Inference with BF16 weights and activations, the large GEMMs on the tensor cores with FP32 accumulation
+ * (biases and the output layer FP32): w_out[B][R]. */
 digs_status digs_cnn_infer_bf16(const float* params, int R, const float* img, const float* cs, int B, float* w_out,
                                 void* ws, size_t ws_bytes, void* stream);
 

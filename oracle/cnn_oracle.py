@@ -64,34 +64,76 @@ def downsample(proj, scale: float) -> np.ndarray:
     return scale * 0.25 * (p[:, 0::2, 0::2] + p[:, 0::2, 1::2] + p[:, 1::2, 0::2] + p[:, 1::2, 1::2])
 
 
-def forward_tensors(flat: torch.Tensor, R: int, img: torch.Tensor, cs: torch.Tensor) -> torch.Tensor:
+def _bf16_t(t: torch.Tensor) -> torch.Tensor:
+    """bf16_round of a tensor's values taken as float32 (no gradient)."""
+    return torch.as_tensor(bf16_round(t.detach().numpy().astype(np.float32)), dtype=DT)
+
+
+class _Bf16Conv(torch.autograd.Function):
+    """The stride-2, padding-1 convolution with bfloat16-rounded operands in both directions: forward
+    conv(r(x), r(w)) + b; backward dx from r(dy) and r(w), dw from r(x) and r(dy), db = sum dy."""
+
+    @staticmethod
+    def forward(ctx, x, w, b):
+        ctx.save_for_backward(x, w)
+        return F.conv2d(_bf16_t(x), _bf16_t(w), b, stride=2, padding=1)
+
+    @staticmethod
+    def backward(ctx, g):
+        x, w = ctx.saved_tensors
+        gr = _bf16_t(g)
+        gx = torch.nn.grad.conv2d_input(x.shape, _bf16_t(w), gr, stride=2, padding=1)
+        gw = torch.nn.grad.conv2d_weight(_bf16_t(x), w.shape, gr, stride=2, padding=1)
+        return gx, gw, g.sum((0, 2, 3))
+
+
+class _Bf16Linear(torch.autograd.Function):
+    """x W^T + b with bfloat16-rounded operands in both directions (as _Bf16Conv)."""
+
+    @staticmethod
+    def forward(ctx, x, w, b):
+        ctx.save_for_backward(x, w)
+        return _bf16_t(x) @ _bf16_t(w).T + b
+
+    @staticmethod
+    def backward(ctx, g):
+        x, w = ctx.saved_tensors
+        gr = _bf16_t(g)
+        return gr @ _bf16_t(w), gr.T @ _bf16_t(x), g.sum(0)
+
+
+def forward_tensors(flat: torch.Tensor, R: int, img: torch.Tensor, cs: torch.Tensor, bf16: bool = False) -> torch.Tensor:
+    """bf16: every operand of the four convolutions and of the 8194-wide layer rounded to bfloat16, in
+    the forward (inputs, weights) and in the backward (incoming gradients, inputs, weights) -- the
+    tensor-core GEMMs' operands; biases, bias gradients and the output layer unrounded."""
     P = unpack(flat, R)
     x = img.reshape(img.shape[0], 1, 128, 128)                       # NCHW for the library convolution
     for l in range(4):
         w = P[f"w{l}"].permute(0, 3, 1, 2)                           # [Co][Ci][ky][kx]
-        x = F.relu(F.conv2d(x, w, P[f"b{l}"], stride=2, padding=1))
+        x = F.relu(_Bf16Conv.apply(x, w, P[f"b{l}"]) if bf16 else F.conv2d(x, w, P[f"b{l}"], stride=2, padding=1))
     feat = torch.cat([x.permute(0, 2, 3, 1).reshape(x.shape[0], FEAT), cs], 1)   # (y, x, c) order, cos, sin
-    h = F.relu(F.linear(feat, P["w_fc1"], P["b_fc1"]))
+    h = F.relu(_Bf16Linear.apply(feat, P["w_fc1"], P["b_fc1"]) if bf16 else F.linear(feat, P["w_fc1"], P["b_fc1"]))
     return F.linear(h, P["w_fc2"], P["b_fc2"])
 
 
-def forward(flat, R: int, img, cs) -> np.ndarray:
+def forward(flat, R: int, img, cs, bf16: bool = False) -> np.ndarray:
     with torch.no_grad():
         t = lambda a: torch.as_tensor(np.asarray(a), dtype=DT)
-        return forward_tensors(t(flat), R, t(img), t(cs)).numpy()
+        return forward_tensors(t(flat), R, t(img), t(cs), bf16).numpy()
 
 
-def vjp(flat, R: int, img, cs, grad_w) -> np.ndarray:
-    """Gradient of sum(grad_w * forward) with respect to the flat parameter vector."""
+def vjp(flat, R: int, img, cs, grad_w, bf16: bool = False) -> np.ndarray:
+    """Gradient of sum(grad_w * forward) with respect to the flat parameter vector (bf16: with the
+    rounded operands of forward_tensors in both directions)."""
     t = lambda a: torch.as_tensor(np.asarray(a), dtype=DT)
     p = t(flat).clone().requires_grad_(True)
-    out = forward_tensors(p, R, t(img), t(cs))
+    out = forward_tensors(p, R, t(img), t(cs), bf16)
     (out * t(grad_w)).sum().backward()
     return p.grad.numpy()
 
 
-def mse(flat, R: int, img, cs, target) -> float:
-    out = forward(flat, R, img, cs)
+def mse(flat, R: int, img, cs, target, bf16: bool = False) -> float:
+    out = forward(flat, R, img, cs, bf16)
     return float(((out - np.asarray(target, dtype=np.float64)) ** 2).mean())
 
 

@@ -11,7 +11,10 @@
 //   forward      Y[M][N]  = X[M][K] W[N][K]^T      (+ bias, ReLU)
 //   data grad    dX[M][K] = dY[M][N] W[N][K]
 //   weight grad  dW[N][K] = dY[M][N]^T X[M][K]     (split over M, partials summed in a fixed order)
-// Training runs in FP32; inference reads BF16 weights and activations and accumulates in FP32.
+// The forward and backward run either in FP32 on the SIMT pipes or, with DIGS_CNN_TENSOR_CORES, with the
+// large GEMMs (the convolutions and the 8194-wide layer) on the tensor cores: BF16 operands rounded from
+// the FP32 activations, gradients and weights, FP32 accumulation; the R-wide output layer stays FP32.
+// Inference reads BF16 weights and activations and runs its large GEMMs on the tensor cores.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -19,6 +22,11 @@
 #include "digs_internal.h"
 
 namespace digs {
+
+// umma.cu: the tensor-core GEMM with BF16 operands and output, B K-major (B(k, n) = B[n ldb + k]).
+cudaError_t gemm_tc_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
+                         __nv_bfloat16* C, int ldc, const float* bias, bool relu, int* status, cudaStream_t st);
+
 namespace {
 
 constexpr int kConvs = 4;
@@ -66,6 +74,12 @@ struct CnnWs {
 
 constexpr int kSplits = 32;
 
+// Floats of the split-K partial buffer: 32 splits of the largest dW (128 x 1152) or 16 splits of the
+// B x 128 hidden layer, whichever is more.
+long long part_floats(int B) {
+  return std::max<long long>((long long)kSplits * 128 * 1152, 16LL * B * 128);
+}
+
 CnnWs cnn_layout(void* base, int B, int R) {
   CnnWs w;
   size_t off = 0;
@@ -75,13 +89,12 @@ CnnWs cnn_layout(void* base, int B, int R) {
     off += (bytes + 255) & ~(size_t)255;
     return q;
   };
-  size_t max_act = 0, max_col = 0, max_dw = 0;
+  size_t max_act = 0, max_col = 0;
   for (int l = 0; l < kConvs; ++l) {
     w.col[l] = (float*)take(rows(l, B) * kdim(l) * 4);
     w.act[l] = (float*)take(rows(l, B) * kCh[l + 1] * 4);
     max_act = std::max(max_act, rows(l, B) * kCh[l + 1]);
     max_col = std::max(max_col, rows(l, B) * kdim(l));
-    max_dw = std::max(max_dw, (size_t)kCh[l + 1] * kdim(l));
   }
   max_act = std::max(max_act, (size_t)B * kFeatIn);
   w.feat = (float*)take((size_t)B * kFeatIn * 4);
@@ -93,7 +106,7 @@ CnnWs cnn_layout(void* base, int B, int R) {
   w.dact0 = (float*)take(max_act * 4);
   w.dact1 = (float*)take(max_act * 4);
   w.dcol = (float*)take(max_col * 4);
-  w.part = (float*)take((size_t)kSplits * std::max(max_dw, (size_t)kFeatIn) * 4);  // conv dW / bias partials
+  w.part = (float*)take((size_t)part_floats(B) * 4);  // split-K and bias partials
   w.loss = (float*)take(256);
   const ParamOffsets po = param_offsets(R);
   w.pb = (__nv_bfloat16*)take(po.total * 2);
@@ -198,6 +211,14 @@ cudaError_t gemm(int M, int N, int K, const TA* A, int lda, const TB* B, int ldb
   return cudaGetLastError();
 }
 
+// An FP32-in / FP32-out GEMM of the training path: on the tensor cores (BF16 operands) if tc, else SIMT.
+template <bool AT, bool BT>
+cudaError_t gemm_f32(bool tc, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                     const float* bias, bool relu, cudaStream_t st, int splits = 1, long long zstride = 0) {
+  if (tc) return gemm_tc(AT, BT, M, N, K, A, lda, B, ldb, C, ldc, bias, relu, splits, zstride, nullptr, st);
+  return gemm<AT, BT>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, st, splits, zstride);
+}
+
 // out[i] (+)= sum_z part[z][i], z in a fixed order.
 __global__ void k_sum_splits(const float* __restrict__ part, int splits, long long n, float* __restrict__ out,
                              int accumulate) {
@@ -230,10 +251,12 @@ __global__ void __launch_bounds__(256) k_colsum(const float* __restrict__ dY, in
 }
 
 cudaError_t colsum(const float* dY, int M, int N, float* part, float* db, cudaStream_t st) {
-  const int rows_per = (M + kSplits - 1) / kSplits;
-  dim3 grid((N + 31) / 32, kSplits);
+  // about 4096 rows per slice (at least kSplits slices), so that tall thin dY fill the GPU
+  const int splits = std::max(kSplits, std::min((M + 4095) / 4096, 1024));
+  const int rows_per = (M + splits - 1) / splits;
+  dim3 grid((N + 31) / 32, splits);
   k_colsum<<<grid, 256, 0, st>>>(dY, M, N, rows_per, part);
-  k_sum_splits<<<(N + 255) / 256, 256, 0, st>>>(part, kSplits, N, db, 0);
+  k_sum_splits<<<(N + 255) / 256, 256, 0, st>>>(part, splits, N, db, 0);
   note_launches(2);
   return cudaGetLastError();
 }
@@ -389,27 +412,31 @@ NetPtrs<T> net_ptrs(const T* wp, const float* bp, const ParamOffsets& o) {
 
 // FP32 forward keeping every activation in the workspace for the backward.
 cudaError_t forward_f32(const NetPtrs<float>& N, int R, const float* img, const float* cs, int B, const CnnWs& w,
-                        cudaStream_t st) {
+                        bool tc, cudaStream_t st) {
   const float* in = img;
   for (int l = 0; l < kConvs; ++l) {
     const int H = kEdge[l], C = kCh[l];
     const long long ncol = (long long)rows(l, B) * kdim(l);
     k_im2col<float, float><<<grid_for(ncol), 256, 0, st>>>(in, B, H, H, C, w.col[l]);
     note_launches(1);
-    CNN_TRY(gemm<false, true>((int)rows(l, B), kCh[l + 1], (int)kdim(l), w.col[l], (int)kdim(l), N.w[l],
-                              (int)kdim(l), w.act[l], kCh[l + 1], N.b[l], true, st));
+    CNN_TRY(gemm_f32<false, true>(tc, (int)rows(l, B), kCh[l + 1], (int)kdim(l), w.col[l], (int)kdim(l), N.w[l],
+                                  (int)kdim(l), w.act[l], kCh[l + 1], N.b[l], true, st));
     in = w.act[l];
   }
   k_features<float, float><<<grid_for((long long)B * kFeatIn), 256, 0, st>>>(w.act[kConvs - 1], cs, B, w.feat);
   note_launches(1);
-  CNN_TRY(gemm<false, true>(B, kHid, kFeatIn, w.feat, kFeatIn, N.w1, kFeatIn, w.h, kHid, N.b1, true, st));
+  if (tc)  // 8194-deep and only B x 128 wide: split K over 16 blocks per tile
+    CNN_TRY(gemm_tc_sum(false, true, B, kHid, kFeatIn, w.feat, kFeatIn, N.w1, kFeatIn, w.h, kHid, N.b1, true, 16,
+                        w.part, nullptr, st));
+  else
+    CNN_TRY(gemm<false, true>(B, kHid, kFeatIn, w.feat, kFeatIn, N.w1, kFeatIn, w.h, kHid, N.b1, true, st));
   CNN_TRY(gemm<false, true>(B, R, kHid, w.h, kHid, N.w2, kHid, w.out, R, N.b2, false, st));
   return cudaGetLastError();
 }
 
 // Backward of forward_f32 for dL/dout in w.dout; writes every parameter gradient to grad (layout as params).
 cudaError_t backward_f32(const NetPtrs<float>& N, const ParamOffsets& o, int R, int B, const CnnWs& w, float* grad,
-                         cudaStream_t st) {
+                         bool tc, cudaStream_t st) {
   // output layer
   CNN_TRY(gemm<true, false>(R, kHid, B, w.dout, R, w.h, kHid, grad + o.w2, kHid, nullptr, false, st));
   CNN_TRY(colsum(w.dout, B, R, w.part, grad + o.b2, st));
@@ -417,9 +444,11 @@ cudaError_t backward_f32(const NetPtrs<float>& N, const ParamOffsets& o, int R, 
   k_relu_bwd<<<grid_for((long long)B * kHid), 256, 0, st>>>(w.h, (long long)B * kHid, w.dh);
   note_launches(1);
   // hidden layer
-  CNN_TRY(gemm<true, false>(kHid, kFeatIn, B, w.dh, kHid, w.feat, kFeatIn, grad + o.w1, kFeatIn, nullptr, false, st));
+  CNN_TRY(gemm_f32<true, false>(tc, kHid, kFeatIn, B, w.dh, kHid, w.feat, kFeatIn, grad + o.w1, kFeatIn, nullptr,
+                                false, st));
   CNN_TRY(colsum(w.dh, B, kHid, w.part, grad + o.b1, st));
-  CNN_TRY(gemm<false, false>(B, kFeatIn, kHid, w.dh, kHid, N.w1, kFeatIn, w.dfeat, kFeatIn, nullptr, false, st));
+  CNN_TRY(gemm_f32<false, false>(tc, B, kFeatIn, kHid, w.dh, kHid, N.w1, kFeatIn, w.dfeat, kFeatIn, nullptr, false,
+                                 st));
   k_feat_grad<<<grid_for((long long)B * kFeat), 256, 0, st>>>(w.dfeat, B, w.dact0);
   note_launches(1);
   // convolutions, last to first; dact0 holds dL/d(output of conv l)
@@ -430,12 +459,17 @@ cudaError_t backward_f32(const NetPtrs<float>& N, const ParamOffsets& o, int R, 
     k_relu_bwd<<<grid_for((long long)M * Nn), 256, 0, st>>>(w.act[l], (long long)M * Nn, dY);
     note_launches(1);
     const long long ndw = (long long)Nn * K;
-    CNN_TRY(gemm<true, false>(Nn, K, M, dY, Nn, w.col[l], K, w.part, K, nullptr, false, st, kSplits, ndw));
-    k_sum_splits<<<(unsigned)((ndw + 255) / 256), 256, 0, st>>>(w.part, kSplits, ndw, grad + o.w[l], 0);
+    // split K (the B x H x W rows): the tensor-core path takes ~2048 rows per split, as many as the
+    // partial buffer holds (its tiles are few: Nn <= 128 rows, K <= 1152 columns of dW)
+    const int splits = tc ? (int)std::max<long long>(
+                                1, std::min<long long>({(M + 2047) / 2048, part_floats(B) / ndw, 1024}))
+                          : kSplits;
+    CNN_TRY(gemm_f32<true, false>(tc, Nn, K, M, dY, Nn, w.col[l], K, w.part, K, nullptr, false, st, splits, ndw));
+    k_sum_splits<<<(unsigned)((ndw + 255) / 256), 256, 0, st>>>(w.part, splits, ndw, grad + o.w[l], 0);
     note_launches(1);
     CNN_TRY(colsum(dY, M, Nn, w.part, grad + o.b[l], st));
     if (l > 0) {
-      CNN_TRY(gemm<false, false>(M, K, Nn, dY, Nn, N.w[l], K, w.dcol, K, nullptr, false, st));
+      CNN_TRY(gemm_f32<false, false>(tc, M, K, Nn, dY, Nn, N.w[l], K, w.dcol, K, nullptr, false, st));
       const int H = kEdge[l], C = kCh[l];
       k_col2im<<<grid_for((long long)B * H * H * C), 256, 0, st>>>(w.dcol, B, H, H, C, dX);
       note_launches(1);
@@ -487,20 +521,21 @@ digs_status digs_cnn_prepare_input(const float* proj, int B, int nu, int nv, flo
 }
 
 digs_status digs_cnn_forward(const float* params, int R, const float* img, const float* cs, int B, float* w_out,
-                             void* ws, size_t ws_bytes, void* stream) {
+                             int flags, void* ws, size_t ws_bytes, void* stream) {
   if (!params || !img || !cs || !w_out || !ws || !args_ok(R, B)) return DIGS_ERR_ARG;
   const CnnWs w = cnn_layout(ws, B, R);
   if (w.bytes > ws_bytes) return DIGS_ERR_ARG;
   const ParamOffsets o = param_offsets(R);
   cudaStream_t st = (cudaStream_t)stream;
-  if (forward_f32(net_ptrs<float>(params, params, o), R, img, cs, B, w, st) != cudaSuccess) return DIGS_ERR_CUDA;
+  const bool tc = (flags & DIGS_CNN_TENSOR_CORES) != 0;
+  if (forward_f32(net_ptrs<float>(params, params, o), R, img, cs, B, w, tc, st) != cudaSuccess) return DIGS_ERR_CUDA;
   if (cudaMemcpyAsync(w_out, w.out, (size_t)B * R * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return DIGS_ERR_CUDA;
   return DIGS_OK;
 }
 
-digs_status digs_cnn_backward(const float* params, int R, int B, const float* grad_w, float* grad_params, void* ws,
-                              size_t ws_bytes, void* stream) {
+digs_status digs_cnn_backward(const float* params, int R, int B, const float* grad_w, float* grad_params, int flags,
+                              void* ws, size_t ws_bytes, void* stream) {
   if (!params || !grad_w || !grad_params || !ws || !args_ok(R, B)) return DIGS_ERR_ARG;
   const CnnWs w = cnn_layout(ws, B, R);
   if (w.bytes > ws_bytes) return DIGS_ERR_ARG;
@@ -508,14 +543,15 @@ digs_status digs_cnn_backward(const float* params, int R, int B, const float* gr
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemcpyAsync(w.dout, grad_w, (size_t)B * R * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return DIGS_ERR_CUDA;
-  if (backward_f32(net_ptrs<float>(params, params, o), o, R, B, w, grad_params, st) != cudaSuccess)
+  const bool tc = (flags & DIGS_CNN_TENSOR_CORES) != 0;
+  if (backward_f32(net_ptrs<float>(params, params, o), o, R, B, w, grad_params, tc, st) != cudaSuccess)
     return DIGS_ERR_CUDA;
   return DIGS_OK;
 }
 
 digs_status digs_cnn_train_step(float* params, float* m, float* v, float* grad, int step, float lr, int R,
                                 const float* img, const float* cs, const float* target, int B, float* loss_out,
-                                void* ws, size_t ws_bytes, void* stream) {
+                                int flags, void* ws, size_t ws_bytes, void* stream) {
   if (!params || !m || !v || !grad || !img || !cs || !target || !loss_out || !ws || step < 1 || !args_ok(R, B))
     return DIGS_ERR_ARG;
   const CnnWs w = cnn_layout(ws, B, R);
@@ -523,10 +559,11 @@ digs_status digs_cnn_train_step(float* params, float* m, float* v, float* grad, 
   const ParamOffsets o = param_offsets(R);
   cudaStream_t st = (cudaStream_t)stream;
   const NetPtrs<float> N = net_ptrs<float>(params, params, o);
-  if (forward_f32(N, R, img, cs, B, w, st) != cudaSuccess) return DIGS_ERR_CUDA;
+  const bool tc = (flags & DIGS_CNN_TENSOR_CORES) != 0;
+  if (forward_f32(N, R, img, cs, B, w, tc, st) != cudaSuccess) return DIGS_ERR_CUDA;
   k_mse<<<1, 256, 0, st>>>(w.out, target, B * R, w.dout, loss_out);
   note_launches(1);
-  if (backward_f32(N, o, R, B, w, grad, st) != cudaSuccess) return DIGS_ERR_CUDA;
+  if (backward_f32(N, o, R, B, w, grad, tc, st) != cudaSuccess) return DIGS_ERR_CUDA;
   AdamGroup g{params, grad, m, v, (long long)o.total, 0, 0, lr, lr};
   if (launch_adam(&g, 1, 0.9f, 0.999f, 1e-8f, step, nullptr, 0, st) != cudaSuccess) return DIGS_ERR_CUDA;
   return DIGS_OK;
@@ -550,15 +587,16 @@ digs_status digs_cnn_infer_bf16(const float* params, int R, const float* img, co
     const long long ncol = (long long)rows(l, B) * kdim(l);
     k_im2col<__nv_bfloat16, __nv_bfloat16><<<grid_for(ncol), 256, 0, st>>>(in, B, H, H, C, w.colb);
     note_launches(1);
-    if (gemm<false, true>((int)rows(l, B), kCh[l + 1], (int)kdim(l), w.colb, (int)kdim(l), N.w[l], (int)kdim(l),
-                          out_act, kCh[l + 1], N.b[l], true, st) != cudaSuccess)
+    if (gemm_tc_bf16((int)rows(l, B), kCh[l + 1], (int)kdim(l), w.colb, (int)kdim(l), N.w[l], (int)kdim(l), out_act,
+                     kCh[l + 1], N.b[l], true, nullptr, st) != cudaSuccess)
       return DIGS_ERR_CUDA;
     in = out_act;
     out_act = (out_act == w.actb0) ? w.actb1 : w.actb0;
   }
   k_features<__nv_bfloat16, __nv_bfloat16><<<grid_for((long long)B * kFeatIn), 256, 0, st>>>(in, cs, B, w.featb);
   note_launches(1);
-  if (gemm<false, true>(B, kHid, kFeatIn, w.featb, kFeatIn, N.w1, kFeatIn, w.hb, kHid, N.b1, true, st) != cudaSuccess)
+  if (gemm_tc_bf16(B, kHid, kFeatIn, w.featb, kFeatIn, N.w1, kFeatIn, w.hb, kHid, N.b1, true, nullptr, st) !=
+      cudaSuccess)
     return DIGS_ERR_CUDA;
   if (gemm<false, true>(B, R, kHid, w.hb, kHid, N.w2, kHid, w_out, R, N.b2, false, st) != cudaSuccess)
     return DIGS_ERR_CUDA;

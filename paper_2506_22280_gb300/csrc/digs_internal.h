@@ -104,6 +104,11 @@ int pair_sum_blocks(int n);
 cudaError_t gemm_tc(bool at, bool bt, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
                     int ldc, const float* bias, bool relu, int splits, long long zstride, int* status,
                     cudaStream_t st);
+// The same with the K splits (splits > 1) summed in order into C by a second kernel, adding the bias and
+// applying ReLU there; part: splits * M * N floats.
+cudaError_t gemm_tc_sum(bool at, bool bt, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                        float* C, int ldc, const float* bias, bool relu, int splits, float* part, int* status,
+                        cudaStream_t st);
 
 // temporal.cu: w rows of a step from the temporal B-spline control points, and the adjoint.
 struct RowsParam {

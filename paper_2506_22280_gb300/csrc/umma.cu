@@ -11,8 +11,8 @@
 //   * one thread issues four 128 x 64 x 16 tcgen05.mma per slice into a 128-lane x 64-column FP32
 //     accumulator in tensor memory and commits them to the slice's mbarrier; the slice buffers are
 //     double-buffered, so staging slice k + 1 overlaps the MMAs of slice k;
-//   * each warp reads its 32 accumulator lanes (rows) back with tcgen05.ld and writes them out, adding
-//     the bias and applying ReLU when asked.
+//   * each warp reads its 32 accumulator lanes (rows) back with tcgen05.ld, adds the bias and applies
+//     ReLU when asked, and puts them in shared memory, from where whole rows go out with 16-byte stores.
 // gridDim.z > 1 splits K: block z sums k in [z kchunk, (z + 1) kchunk) into C + z zstride (no bias).
 // Every mbarrier wait is bounded; a wait that gives up sets *status to 1 and the block still waits
 // (bounded) for its own MMAs, frees its tensor memory and returns.
@@ -112,11 +112,24 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&h);
 }
+__device__ __forceinline__ void st_c4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void st_c4(__nv_bfloat16* p, float4 v) {
+  *reinterpret_cast<uint2*>(p) = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
+}
+
+// A whole 8-element chunk with 16-byte loads (vec: the operand's base and pitch allow them).
+__device__ __forceinline__ uint4 load_vec8(const float* p) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  return make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(b.x, b.y), pack_bf16(b.z, b.w));
+}
+__device__ __forceinline__ uint4 load_vec8(const __nv_bfloat16* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
 
 // One 8-element K chunk of row `row` of an operand, K-range [k, k + 8) clipped to [.., kend), rows
 // beyond `rows` zero; T (transposed) reads element (row, kk) at P[kk ld + row], else P[row ld + kk].
 template <bool T, typename TP>
-__device__ __forceinline__ uint4 load_chunk(const TP* __restrict__ P, int ld, int row, int rows, int k, int kend) {
+__device__ __forceinline__ uint4 load_chunk(const TP* __restrict__ P, int ld, int row, int rows, int k, int kend,
+                                            bool vec) {
+  if (!T && vec && row < rows && k + 8 <= kend) return load_vec8(P + (size_t)row * ld + k);
   float x[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
@@ -130,19 +143,19 @@ __device__ __forceinline__ uint4 load_chunk(const TP* __restrict__ P, int ld, in
 // consecutive K chunks when K is the contiguous global index, else consecutive rows.
 template <bool AT, bool BT, typename TA, typename TB>
 __device__ __forceinline__ void stage(const TA* __restrict__ A, int lda, const TB* __restrict__ B, int ldb, int M,
-                                      int N, int m0, int n0, int k0, int kend, uint8_t* sA, uint8_t* sB) {
+                                      int N, int m0, int n0, int k0, int kend, uint8_t* sA, uint8_t* sB, int vec) {
 #pragma unroll
   for (int i = 0; i < (kBM * 8) / kTcThreads; ++i) {
     const int c = threadIdx.x + i * kTcThreads;
     const int kc = AT ? c / kBM : c & 7, mm = AT ? c % kBM : c >> 3;
-    const uint4 v = load_chunk<AT>(A, lda, m0 + mm, M, k0 + kc * 8, kend);
+    const uint4 v = load_chunk<AT>(A, lda, m0 + mm, M, k0 + kc * 8, kend, (vec & 1) != 0);
     *reinterpret_cast<uint4*>(sA + ((mm >> 3) * 8 + kc) * 128 + (mm & 7) * 16) = v;
   }
 #pragma unroll
   for (int i = 0; i < (kBN * 8) / kTcThreads; ++i) {
     const int c = threadIdx.x + i * kTcThreads;
     const int kc = BT ? c & 7 : c / kBN, nn = BT ? c >> 3 : c % kBN;
-    const uint4 v = load_chunk<!BT>(B, ldb, n0 + nn, N, k0 + kc * 8, kend);
+    const uint4 v = load_chunk<!BT>(B, ldb, n0 + nn, N, k0 + kc * 8, kend, (vec & 2) != 0);
     *reinterpret_cast<uint4*>(sB + ((nn >> 3) * 8 + kc) * 128 + (nn & 7) * 16) = v;
   }
 }
@@ -151,7 +164,8 @@ template <bool AT, bool BT, typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, const TA* __restrict__ A, int lda,
                                                         const TB* __restrict__ B, int ldb, TC* __restrict__ C,
                                                         int ldc, int kchunk, long long zstride,
-                                                        const float* __restrict__ bias, int relu, int* status) {
+                                                        const float* __restrict__ bias, int relu, int vec,
+                                                        int* status) {
   extern __shared__ unsigned char smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = sm;
@@ -183,7 +197,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
     const int buf = s & 1;
     if (s >= 2) ok = __syncthreads_and(ok && mbar_wait(bar + buf, (uint32_t)(((s >> 1) - 1) & 1)));
     if (!ok) break;
-    stage<AT, BT>(A, lda, B, ldb, M, N, m0, n0, kb + s * kBK, ke, sA + buf * kStageA, sB + buf * kStageB);
+    stage<AT, BT>(A, lda, B, ldb, M, N, m0, n0, kb + s * kBK, ke, sA + buf * kStageA, sB + buf * kStageB, vec);
     fence_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -203,23 +217,47 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
   // the last commit tracks every MMA issued before it
   if (issued > 0 && !mbar_wait(bar + ((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1))) ok = 0;
   tc_fence_after();
-  const int m = m0 + warp * 32 + lane;
-  TC* Cz = C + (size_t)blockIdx.z * zstride;
+  // epilogue: accumulator lanes -> registers (+ bias, ReLU) -> the 128 x 64 tile in the (now idle)
+  // staging buffers -> global rows, 4 consecutive columns per thread, 16 threads per row
+  constexpr int TP = kBN + 4;  // tile row pitch in floats (16-byte aligned rows)
+  float* tile = reinterpret_cast<float*>(sm);
+  const int r = warp * 32 + lane;
 #pragma unroll
   for (int c0 = 0; c0 < kBN; c0 += 16) {
     float v[16];
     tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-    if (m < M && ok) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int n = n0 + c0 + j;
-        if (n >= N) break;
-        float x = issued > 0 ? v[j] : 0.f;
-        if (gridDim.z == 1) {
-          if (bias) x += bias[n];
-          if (relu) x = fmaxf(x, 0.f);
-        }
-        st_c(Cz + (size_t)m * ldc + n, x);
+    for (int j = 0; j < 16; ++j) {
+      const int n = n0 + c0 + j;
+      float x = issued > 0 ? v[j] : 0.f;
+      if (gridDim.z == 1 && n < N) {
+        if (bias) x += bias[n];
+        if (relu) x = fmaxf(x, 0.f);
+      }
+      v[j] = x;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      *reinterpret_cast<float4*>(tile + r * TP + c0 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  }
+  __syncthreads();
+  TC* Cz = C + (size_t)blockIdx.z * zstride;
+  const bool vec_c = (ldc % 4) == 0 && ((uintptr_t)Cz % (4 * sizeof(TC))) == 0;
+  const int cq = (threadIdx.x & 15) * 4;
+  if (ok) {
+#pragma unroll 4
+    for (int i = 0; i < kBM / 8; ++i) {
+      const int rr = (threadIdx.x >> 4) + 8 * i, m = m0 + rr, n = n0 + cq;
+      if (m >= M || n >= N) continue;
+      const float4 x = *reinterpret_cast<const float4*>(tile + rr * TP + cq);
+      TC* dst = Cz + (size_t)m * ldc + n;
+      if (vec_c && n + 3 < N) {
+        st_c4(dst, x);
+      } else {
+        st_c(dst, x.x);
+        if (n + 1 < N) st_c(dst + 1, x.y);
+        if (n + 2 < N) st_c(dst + 2, x.z);
+        if (n + 3 < N) st_c(dst + 3, x.w);
       }
     }
   }
@@ -245,8 +283,12 @@ cudaError_t launch_tc(int M, int N, int K, const TA* A, int lda, const TB* B, in
   if (splits < 1) splits = 1;
   const int kchunk = ((K + splits - 1) / splits + kBK - 1) / kBK * kBK;
   dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, splits);
+  // 16-byte loads of whole K chunks where K is the contiguous index and base and pitch are aligned
+  constexpr int per16a = 16 / (int)sizeof(TA), per16b = 16 / (int)sizeof(TB);
+  const int vec = ((!AT && ((uintptr_t)A & 15) == 0 && lda % per16a == 0) ? 1 : 0) |
+                  ((BT && ((uintptr_t)B & 15) == 0 && ldb % per16b == 0) ? 2 : 0);
   k_gemm_tc<AT, BT, TA, TB, TC><<<grid, kTcThreads, kTcSmem, st>>>(M, N, K, A, lda, B, ldb, C, ldc, kchunk, zstride,
-                                                                   bias, relu ? 1 : 0, status);
+                                                                   bias, relu ? 1 : 0, vec, status);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -277,6 +319,20 @@ cudaError_t gemm_tc(bool at, bool bt, int M, int N, int K, const float* A, int l
   return launch_tc<true, true>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, splits, zstride, status, st);
 }
 
+cudaError_t gemm_tc_sum(bool at, bool bt, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                        float* C, int ldc, const float* bias, bool relu, int splits, float* part, int* status,
+                        cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (splits <= 1) return gemm_tc(at, bt, M, N, K, A, lda, B, ldb, C, ldc, bias, relu, 1, 0, status, st);
+  cudaError_t e = gemm_tc(at, bt, M, N, K, A, lda, B, ldb, part, N, nullptr, false, splits, (long long)M * N, status, st);
+  if (e != cudaSuccess) return e;
+  const long long MN = (long long)M * N;
+  k_tc_sum<<<(unsigned)std::min<long long>((MN + 255) / 256, 152LL * 16), 256, 0, st>>>(part, splits, M, N, C, ldc,
+                                                                                     bias, relu ? 1 : 0);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t gemm_tc_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
                          __nv_bfloat16* C, int ldc, const float* bias, bool relu, int* status, cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
@@ -294,20 +350,7 @@ extern "C" digs_status digs_gemm_bf16(int trans_a, int trans_b, int M, int N, in
   if (!C || ldc < N || (K > 0 && (!A || !B))) return DIGS_ERR_ARG;
   if (K > 0 && (lda < (trans_a ? M : K) || ldb < (trans_b ? K : N))) return DIGS_ERR_ARG;
   if (splits > 1 && !partial) return DIGS_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e;
-  if (splits == 1) {
-    e = gemm_tc(trans_a != 0, trans_b != 0, M, N, K, A, lda, B, ldb, C, ldc, bias, relu != 0, 1, 0, status, st);
-  } else {
-    e = gemm_tc(trans_a != 0, trans_b != 0, M, N, K, A, lda, B, ldb, partial, N, nullptr, false, splits,
-                (long long)M * N, status, st);
-    if (e == cudaSuccess) {
-      const long long MN = (long long)M * N;
-      k_tc_sum<<<(unsigned)std::min<long long>((MN + 255) / 256, 152LL * 16), 256, 0, st>>>(partial, splits, M, N, C,
-                                                                                         ldc, bias, relu);
-      note_launches(1);
-      e = cudaGetLastError();
-    }
-  }
+  const cudaError_t e = gemm_tc_sum(trans_a != 0, trans_b != 0, M, N, K, A, lda, B, ldb, C, ldc, bias, relu != 0,
+                                    splits, partial, status, (cudaStream_t)stream);
   return e == cudaSuccess ? DIGS_OK : DIGS_ERR_CUDA;
 }

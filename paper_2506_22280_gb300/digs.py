@@ -96,9 +96,9 @@ def lib() -> C.CDLL:
         "digs_cnn_workspace_size": (S, [I, I]),
         "digs_cnn_init": (I, [P, I, C.c_ulonglong, P]),
         "digs_cnn_prepare_input": (I, [P, I, I, I, C.c_float, P, P]),
-        "digs_cnn_forward": (I, [P, I, P, P, I, P, P, S, P]),
-        "digs_cnn_backward": (I, [P, I, I, P, P, P, S, P]),
-        "digs_cnn_train_step": (I, [P, P, P, P, I, C.c_float, I, P, P, P, I, P, P, S, P]),
+        "digs_cnn_forward": (I, [P, I, P, P, I, P, I, P, S, P]),
+        "digs_cnn_backward": (I, [P, I, I, P, P, I, P, S, P]),
+        "digs_cnn_train_step": (I, [P, P, P, P, I, C.c_float, I, P, P, P, I, P, I, P, S, P]),
         "digs_cnn_infer_bf16": (I, [P, I, P, P, I, P, P, S, P]),
         "digs_gemm_bf16": (I, [I, I, I, I, I, P, I, P, I, P, I, P, I, I, P, P, P]),
     }
@@ -530,11 +530,16 @@ def gemm_bf16(a: torch.Tensor, b: torch.Tensor, trans_a: bool = False, trans_b: 
     return out, status
 
 
+DIGS_CNN_TENSOR_CORES = 1
+
+
 class WeightPredictor:
     """The weight-predictor CNN (include/digs.h, "Weight-predictor CNN"): parameters, Adam moments and
-    a workspace in device memory; training and inference run in the library's kernels."""
+    a workspace in device memory; training and inference run in the library's kernels.  tensor_cores:
+    the default of train_step (BF16-operand GEMMs on the tensor cores; False: FP32 SIMT)."""
 
-    def __init__(self, R: int, seed: int = 0, input_scale: float = 1.0, device="cuda"):
+    def __init__(self, R: int, seed: int = 0, input_scale: float = 1.0, device="cuda", tensor_cores: bool = True):
+        self.tensor_cores = bool(tensor_cores)
         self.R = int(R)
         self.dev = torch.device(device)
         n = int(lib().digs_cnn_params(self.R))
@@ -565,30 +570,35 @@ class WeightPredictor:
                "digs_cnn_prepare_input")
         return img
 
-    def forward(self, img: torch.Tensor, cs: torch.Tensor) -> torch.Tensor:
+    def forward(self, img: torch.Tensor, cs: torch.Tensor, tensor_cores: bool = False) -> torch.Tensor:
         B = int(img.shape[0])
         self._ws(B)
         out = torch.empty(B, self.R, device=self.dev)
+        flags = DIGS_CNN_TENSOR_CORES if tensor_cores else 0
         _check(lib().digs_cnn_forward(_ptr(self.params), self.R, _ptr(_f32(img, "img")), _ptr(_f32(cs, "cs")), B,
-                                      _ptr(out), self.ws.ptr, self.ws.nbytes, _stream()), "digs_cnn_forward")
+                                      _ptr(out), flags, self.ws.ptr, self.ws.nbytes, _stream()), "digs_cnn_forward")
         return out
 
-    def backward(self, grad_w: torch.Tensor) -> torch.Tensor:
+    def backward(self, grad_w: torch.Tensor, tensor_cores: bool = False) -> torch.Tensor:
         """Parameter gradient for dL/dw of the preceding forward (same batch size)."""
         B = int(grad_w.shape[0])
         g = torch.empty_like(self.params)
-        _check(lib().digs_cnn_backward(_ptr(self.params), self.R, B, _ptr(_f32(grad_w, "grad_w")), _ptr(g),
+        flags = DIGS_CNN_TENSOR_CORES if tensor_cores else 0
+        _check(lib().digs_cnn_backward(_ptr(self.params), self.R, B, _ptr(_f32(grad_w, "grad_w")), _ptr(g), flags,
                                        self.ws.ptr, self.ws.nbytes, _stream()), "digs_cnn_backward")
         return g
 
-    def train_step(self, img: torch.Tensor, cs: torch.Tensor, target: torch.Tensor, lr: float) -> torch.Tensor:
+    def train_step(self, img: torch.Tensor, cs: torch.Tensor, target: torch.Tensor, lr: float,
+                   tensor_cores: Optional[bool] = None) -> torch.Tensor:
         B = int(img.shape[0])
         self._ws(B)
         self.step_count += 1
+        tc = self.tensor_cores if tensor_cores is None else bool(tensor_cores)
         _check(lib().digs_cnn_train_step(_ptr(self.params), _ptr(self.m), _ptr(self.v), _ptr(self.grad),
                                          self.step_count, float(lr), self.R, _ptr(_f32(img, "img")),
                                          _ptr(_f32(cs, "cs")), _ptr(_f32(target, "target")), B, _ptr(self.loss),
-                                         self.ws.ptr, self.ws.nbytes, _stream()), "digs_cnn_train_step")
+                                         DIGS_CNN_TENSOR_CORES if tc else 0, self.ws.ptr, self.ws.nbytes,
+                                         _stream()), "digs_cnn_train_step")
         return self.loss
 
     def predict(self, img: torch.Tensor, cs: torch.Tensor, batch: int = 512) -> torch.Tensor:

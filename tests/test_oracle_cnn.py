@@ -109,3 +109,37 @@ def test_gemm_bf16_definition():
     Bi = rng.integers(-8, 9, size=(6, 2)).astype(np.float32)
     assert np.array_equal(C.gemm_bf16(Ai, Bi), Ai.astype(np.float64) @ Bi.astype(np.float64))
 
+
+def test_bf16_forward_is_exact_when_every_operand_is_representable_and_close_otherwise():
+    R = 2
+    shapes = dict(C.param_shapes(R))
+    P = {k: np.zeros(v) for k, v in shapes.items()}
+    for l, scale in zip(range(4), (1.0, 0.5, 0.5, 0.25)):
+        co, _, _, ci = shapes[f"w{l}"]
+        for o in range(co):
+            P[f"w{l}"][o, 1, 1, o % ci] = scale                       # the centre tap only
+    for j in range(C.HID):
+        P["w_fc1"][j, j] = 1.0
+    P["w_fc2"] = np.random.default_rng(0).normal(size=shapes["w_fc2"])
+    flat = np.concatenate([P[k].ravel() for k, _ in C.param_shapes(R)])
+    rng = np.random.default_rng(1)
+    img = rng.integers(0, 3, size=(2, 128, 128)) * 0.5                 # 0, 0.5, 1
+    cs = np.array([[1.0, 0.0], [0.0, 1.0]])
+    a, b = C.forward(flat, R, img, cs), C.forward(flat, R, img, cs, bf16=True)
+    assert np.array_equal(a, b) and np.abs(a).max() > 0
+    # the backward too: output weights and incoming gradients that bfloat16 holds keep every backward
+    # operand exact
+    P["w_fc2"] = np.random.default_rng(2).choice([-1.0, -0.5, 0.25, 0.5, 1.0], size=shapes["w_fc2"])
+    flat = np.concatenate([P[k].ravel() for k, _ in C.param_shapes(R)])
+    gw = np.array([[1.0, -2.0], [0.5, 3.0]])
+    ga, gb = C.vjp(flat, R, img, cs, gw), C.vjp(flat, R, img, cs, gw, bf16=True)
+    assert np.array_equal(ga, gb) and np.abs(ga).max() > 0
+    flat2 = rng.normal(size=flat.size) * 0.05
+    img2 = rng.uniform(size=(2, 128, 128))
+    a, b = C.forward(flat2, R, img2, cs), C.forward(flat2, R, img2, cs, bf16=True)
+    rel = np.linalg.norm(a - b) / np.linalg.norm(a)
+    assert 1e-5 < rel < 2e-2, rel
+    ga, gb = C.vjp(flat2, R, img2, cs, gw), C.vjp(flat2, R, img2, cs, gw, bf16=True)
+    rel = np.linalg.norm(ga - gb) / np.linalg.norm(ga)
+    assert 1e-5 < rel < 0.3, rel
+
