@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="time direct calls instead of graph replays")
     ap.add_argument("--no-batching", action="store_true", help="skip the four-scan batching measurement")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start measurement")
+    ap.add_argument("--only-cnn", action="store_true",
+                    help="time only the weight-predictor CNN's training step and inference, print that line")
     return ap.parse_args()
 
 
@@ -374,6 +376,69 @@ def warmstart_measurement(pkg, D, wl, meas, device, tile, lanes, B=16, warmup_it
             "warm_curve": wcurve, "device_status": status}
 
 
+def cnn_gemm_flops(B, R=3):
+    """FLOPs of the weight-predictor CNN's GEMMs in one training step of batch B: the forward (four
+    convolutions as im2col GEMMs, the 8194-wide and the R-wide layers), the weight gradients of all six
+    and the data gradients of all but the first convolution."""
+    ch, edge, k_feat, hid = [1, 32, 64, 128, 128], [128, 64, 32, 16, 8], 8194, 128
+    fwd = dw = dx = 0
+    for l in range(4):
+        mnk = B * edge[l + 1] ** 2 * ch[l + 1] * 9 * ch[l]
+        fwd += 2 * mnk
+        dw += 2 * mnk
+        dx += 2 * mnk if l > 0 else 0
+    for a, b in ((k_feat, hid), (hid, R)):
+        fwd += 2 * B * a * b
+        dw += 2 * B * a * b
+        dx += 2 * B * a * b
+    return fwd + dw + dx
+
+
+def cnn_measurement(pkg, device, B=256, R=3, reps=20):
+    """CUDA-event times of one CNN training step (batch B) with the tensor-core GEMMs and with FP32 SIMT
+    GEMMs, and of BF16 inference on 680 projections; the tensor-core step's GEMM work in TFLOP/s against
+    the measured dense BF16 peak."""
+    import torch
+    rng = np.random.default_rng(0)
+    img = torch.tensor(rng.uniform(size=(B, 128, 128)).astype(np.float32), device=device)
+    cs = torch.tensor(rng.normal(size=(B, 2)).astype(np.float32), device=device)
+    W = torch.tensor(rng.normal(size=(B, R)).astype(np.float32), device=device)
+    out = {"batch": B}
+    for tc in (True, False):
+        net = pkg.WeightPredictor(R, seed=0, tensor_cores=tc, device=device)
+        for _ in range(3):
+            net.train_step(img, cs, W, 1e-3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            net.train_step(img, cs, W, 1e-3)
+        e1.record()
+        torch.cuda.synchronize()
+        out["train_step_ms_tensor_cores" if tc else "train_step_ms_fp32_simt"] = e0.elapsed_time(e1) / reps
+    imgs = torch.tensor(rng.uniform(size=(680, 128, 128)).astype(np.float32), device=device)
+    css = torch.tensor(rng.normal(size=(680, 2)).astype(np.float32), device=device)
+    net.predict(imgs, css)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    net.predict(imgs, css)
+    e1.record()
+    torch.cuda.synchronize()
+    out["infer_680_ms"] = e0.elapsed_time(e1)
+    flops = cnn_gemm_flops(B, R)
+    achieved = flops / (out["train_step_ms_tensor_cores"] / 1e3) / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    out["train_step_speedup"] = out["train_step_ms_fp32_simt"] / out["train_step_ms_tensor_cores"]
+    out["roofline"] = {"bound": "tensor", "kernel": "k_gemm_tc (whole training step)", "achieved": achieved,
+                       "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                       "peak_basis": "measured dense BF16 burst" if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s",
+                       "flops_per_step": flops}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -385,6 +450,10 @@ def run_ours(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
+    if args.only_cnn:
+        if rank == 0:
+            print(json.dumps({"cnn": cnn_measurement(pkg, device)}), flush=True)
+        return
     if world > 1:
         dist.init_process_group("nccl", device_id=device)
     pkg.lib()
@@ -482,9 +551,10 @@ def run_ours(args):
     models = None
     if world == 1 and not args.no_batching:
         models = model_comparison(pkg, wl, device, tile, lanes, B=B)
-    warm = None
+    warm = cnn = None
     if world == 1 and not args.no_warmstart:
         warm = warmstart_measurement(pkg, D, wl, meas, device, tile, lanes)
+        cnn = cnn_measurement(pkg, device)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -530,6 +600,8 @@ def run_ours(args):
         line["batching"] = batching
     if warm is not None:
         line["warm_start"] = warm
+    if cnn is not None:
+        line["cnn"] = cnn
     if models is not None:
         line["projection_models"] = models
     if world == 1 and not args.no_cpu_baseline:

@@ -459,10 +459,13 @@ cudaError_t backward_f32(const NetPtrs<float>& N, const ParamOffsets& o, int R, 
     k_relu_bwd<<<grid_for((long long)M * Nn), 256, 0, st>>>(w.act[l], (long long)M * Nn, dY);
     note_launches(1);
     const long long ndw = (long long)Nn * K;
-    // split K (the B x H x W rows): the tensor-core path takes ~2048 rows per split, as many as the
-    // partial buffer holds (its tiles are few: Nn <= 128 rows, K <= 1152 columns of dW)
-    const int splits = tc ? (int)std::max<long long>(
-                                1, std::min<long long>({(M + 2047) / 2048, part_floats(B) / ndw, 1024}))
+    // split K (the B x H x W rows): dW has few 128 x 64 tiles (Nn <= 128 rows, K <= 1152 columns), so the
+    // tensor-core path splits until about 4 CTAs per SM are busy, keeping >= 256 rows per split and the
+    // partials within the buffer
+    const long long tiles = (long long)((K + 63) / 64) * ((Nn + 127) / 128);
+    const int splits = tc ? (int)std::max<long long>(1, std::min<long long>({(4LL * 152 + tiles - 1) / tiles,
+                                                                             (M + 255) / 256, part_floats(B) / ndw,
+                                                                             1024}))
                           : kSplits;
     CNN_TRY(gemm_f32<true, false>(tc, Nn, K, M, dY, Nn, w.col[l], K, w.part, K, nullptr, false, st, splits, ndw));
     k_sum_splits<<<(unsigned)((ndw + 255) / 256), 256, 0, st>>>(w.part, splits, ndw, grad + o.w[l], 0);

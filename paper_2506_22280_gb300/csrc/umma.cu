@@ -140,23 +140,36 @@ __device__ __forceinline__ uint4 load_chunk(const TP* __restrict__ P, int ld, in
 }
 
 // Stage the K slice [k0, k0 + 64) of the block's A rows and B columns.  Consecutive threads take
-// consecutive K chunks when K is the contiguous global index, else consecutive rows.
+// consecutive K chunks when K is the contiguous global index, else consecutive rows.  Every chunk is
+// loaded (and rounded) before any is stored, so that all of the thread's loads are in flight together.
 template <bool AT, bool BT, typename TA, typename TB>
 __device__ __forceinline__ void stage(const TA* __restrict__ A, int lda, const TB* __restrict__ B, int ldb, int M,
                                       int N, int m0, int n0, int k0, int kend, uint8_t* sA, uint8_t* sB, int vec) {
+  constexpr int CA = (kBM * 8) / kTcThreads, CB = (kBN * 8) / kTcThreads;
+  uint4 va[CA], vb[CB];
 #pragma unroll
-  for (int i = 0; i < (kBM * 8) / kTcThreads; ++i) {
+  for (int i = 0; i < CA; ++i) {
     const int c = threadIdx.x + i * kTcThreads;
     const int kc = AT ? c / kBM : c & 7, mm = AT ? c % kBM : c >> 3;
-    const uint4 v = load_chunk<AT>(A, lda, m0 + mm, M, k0 + kc * 8, kend, (vec & 1) != 0);
-    *reinterpret_cast<uint4*>(sA + ((mm >> 3) * 8 + kc) * 128 + (mm & 7) * 16) = v;
+    va[i] = load_chunk<AT>(A, lda, m0 + mm, M, k0 + kc * 8, kend, (vec & 1) != 0);
   }
 #pragma unroll
-  for (int i = 0; i < (kBN * 8) / kTcThreads; ++i) {
+  for (int i = 0; i < CB; ++i) {
     const int c = threadIdx.x + i * kTcThreads;
     const int kc = BT ? c & 7 : c / kBN, nn = BT ? c >> 3 : c % kBN;
-    const uint4 v = load_chunk<!BT>(B, ldb, n0 + nn, N, k0 + kc * 8, kend, (vec & 2) != 0);
-    *reinterpret_cast<uint4*>(sB + ((nn >> 3) * 8 + kc) * 128 + (nn & 7) * 16) = v;
+    vb[i] = load_chunk<!BT>(B, ldb, n0 + nn, N, k0 + kc * 8, kend, (vec & 2) != 0);
+  }
+#pragma unroll
+  for (int i = 0; i < CA; ++i) {
+    const int c = threadIdx.x + i * kTcThreads;
+    const int kc = AT ? c / kBM : c & 7, mm = AT ? c % kBM : c >> 3;
+    *reinterpret_cast<uint4*>(sA + ((mm >> 3) * 8 + kc) * 128 + (mm & 7) * 16) = va[i];
+  }
+#pragma unroll
+  for (int i = 0; i < CB; ++i) {
+    const int c = threadIdx.x + i * kTcThreads;
+    const int kc = BT ? c & 7 : c / kBN, nn = BT ? c >> 3 : c % kBN;
+    *reinterpret_cast<uint4*>(sB + ((nn >> 3) * 8 + kc) * 128 + (nn & 7) * 16) = vb[i];
   }
 }
 
