@@ -175,14 +175,16 @@ __device__ __forceinline__ bool ellipse_meets(const float4* r3, int x0, int x1, 
   const float tau = fabsf(b.y) * mdx + fabsf(b.z) * mdy;
   const float ck = 1.f - c2_const * b.w;  // > 0: the source lies outside the cutoff ellipsoid
   if (!(ck > 0.f)) return true;
-  const float lim = c2_const * (1.f + tau) * (1.f + tau) / ck * 1.001f + 1e-4f;
+  // fast (approximate) divisions: they move the clamped minimisers by a few ulps, far inside the margin
+  const float lim = __fdividef(c2_const * (1.f + tau) * (1.f + tau), ck) * 1.001f + 1e-4f;
+  const float s11 = __fdividef(-n01, n11), s00 = __fdividef(-n01, n00);
   auto q = [&](float dx, float dy) { return dy * (n11 * dy + 2.f * n01 * dx) + n00 * dx * dx; };
   auto edge_x = [&](float dx) {  // min over dy in [Y0, Y1] at fixed dx
-    const float dy = fminf(fmaxf(-n01 * dx / n11, Y0), Y1);
+    const float dy = fminf(fmaxf(s11 * dx, Y0), Y1);
     return q(dx, dy);
   };
   auto edge_y = [&](float dy) {
-    const float dx = fminf(fmaxf(-n01 * dy / n00, X0), X1);
+    const float dx = fminf(fmaxf(s00 * dy, X0), X1);
     return q(dx, dy);
   };
   const float m = fminf(fminf(edge_x(X0), edge_x(X1)), fminf(edge_y(Y0), edge_y(Y1)));
@@ -214,8 +216,9 @@ __device__ __forceinline__ f2 fwd_pair(const float4* en, f2 XX, f2 YY, float c2k
 
 // Each warp walks the tile's whole sorted list in batches of 32: lane l copies record l of the batch
 // into shared memory (cp.async), tests its box against the warp's block and, if they meet, writes the
-// entry; the next batch's copies are then issued and the warp sweeps the meeting entries in list order
-// (so the sums are deterministic).  No canvas, no atomics, no CTA barrier.
+// entry to the slot given by the number of meeting lanes below it (so the meeting entries lie packed,
+// in list order); the next batch's copies are then issued and the warp sweeps the packed entries in
+// order (so the sums are deterministic).  No canvas, no atomics, no CTA barrier.
 template <int TS, bool COUNT>
 __global__ void __launch_bounds__(FwdCfg<TS>::threads) k_raster_fwd(
     const float4* __restrict__ grec, const uint32_t* __restrict__ srid, const uint2* __restrict__ ranges,
@@ -258,25 +261,20 @@ __global__ void __launch_bounds__(FwdCfg<TS>::threads) k_raster_fwd(
       meets = x0 <= x1 && y0 <= y1;
       if (COUNT && meets) n_box += (unsigned)((x1 - x0 + 1) * (y1 - y0 + 1));
       meets = meets && ellipse_meets(r3, x0, x1, y0, y1, c2);
-      if (meets) derive_entry(r3, ent + lane * 5);
     }
-    unsigned mask = __ballot_sync(0xffffffffu, meets);
+    // the meeting entries, compacted in list order: lane -> slot popc(mask below the lane)
+    const unsigned mask = __ballot_sync(0xffffffffu, meets);
+    if (meets) derive_entry(raw + lane * DIGS_REC_F4, ent + __popc(mask & ((1u << lane) - 1u)) * 5);
     __syncwarp();
     issue(k0 + C::batch);  // lands while this batch is swept
-    while (mask) {  // two entries per step: two independent dependency chains
-      const int ea = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const float4* pa = ent + ea * 5;
-      if (mask) {
-        const int eb = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const float4* pb = ent + eb * 5;
-        const f2 va = fwd_pair<COUNT>(pa, XX, YY, c2k, n_cut), vb = fwd_pair<COUNT>(pb, XX, YY, c2k, n_cut);
-        ACC = f2_add(f2_add(ACC, va), vb);  // list order
-      } else {
-        ACC = f2_add(ACC, fwd_pair<COUNT>(pa, XX, YY, c2k, n_cut));
-      }
+    const int cnt = __popc(mask);
+    int e = 0;
+#pragma unroll 1
+    for (; e + 1 < cnt; e += 2) {  // two entries per step: two independent dependency chains
+      const f2 va = fwd_pair<COUNT>(ent + e * 5, XX, YY, c2k, n_cut), vb = fwd_pair<COUNT>(ent + e * 5 + 5, XX, YY, c2k, n_cut);
+      ACC = f2_add(f2_add(ACC, va), vb);  // list order
     }
+    if (e < cnt) ACC = f2_add(ACC, fwd_pair<COUNT>(ent + e * 5, XX, YY, c2k, n_cut));
     __syncwarp();
   }
   cp_async_wait_all();  // the last (empty) group
