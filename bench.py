@@ -308,7 +308,7 @@ def model_comparison(pkg, wl, device, tile, lanes, B=16, reps=10):
 
 
 def warmstart_measurement(pkg, D, wl, meas, device, tile, lanes, B=16, warmup_iters=150, plain_iters=2150,
-                          n_pairs=10_000, epochs=3):
+                          n_pairs=10_000, epochs=3, render_res=128):
     """Wall time for the plain batched optimisation to reach its final full-scan loss after `plain_iters`
     steps, against the learned warm start (render training pairs with the model, train the CNN, propose
     all weights, keep them if the scan loss falls) followed by the same optimisation until its scan loss
@@ -345,7 +345,8 @@ def warmstart_measurement(pkg, D, wl, meas, device, tile, lanes, B=16, warmup_it
     target = 1.01 * final
     t0 = time.perf_counter()
     pred = pkg.WeightPredictor(int(wl.lattice["R"]), seed=0, input_scale=0.25)
-    make_views = lambda a: synth.circular_views(a, 1000.0, 1500.0, 256, 256, 1.6, 1.6)
+    pitch = 1.6 * 256 / render_res  # the same 409.6 mm detector
+    make_views = lambda a: synth.circular_views(a, 1000.0, 1500.0, render_res, render_res, pitch, pitch)
     imgs, cs, W = WS.render_training_pairs(warm, make_views, n_pairs, pred, seed=1)
     losses = WS.train(pred, imgs, cs, W, epochs, batch=256, lr=1e-3)
     res = WS.warm_start(warm, pred, meas, wl.views, np.asarray(wl.angles), list(range(n_proj)))
@@ -366,7 +367,8 @@ def warmstart_measurement(pkg, D, wl, meas, device, tile, lanes, B=16, warmup_it
             break
     status = max(plain.status(), warm.status())
     return {"protocol": (f"{warmup_iters} shared plain steps, then plain for {plain_iters} steps vs CNN warm start "
-                         f"({n_pairs} rendered pairs, {epochs} epochs, BF16 inference, accept if the scan loss "
+                         f"({n_pairs} pairs rendered at {render_res}x{render_res}, {epochs} epochs, BF16 inference, "
+                         f"accept if the scan loss "
                          f"falls) + the same steps until the scan loss is within 1% of the plain final; "
                          f"B = {B}, wall time, scan-loss evaluations excluded"),
             "plain_s": t_plain, "plain_final_scan_loss": final, "warm_s": t_warm if reached else None,

@@ -258,7 +258,8 @@ size_t digs_cnn_params(int R);
 size_t digs_cnn_workspace_size(int B, int R);
 /* He-normal weights (std sqrt(2 / fan-in)) from a counter-based generator of `seed`; zero biases. */
 digs_status digs_cnn_init(float* params, int R, unsigned long long seed, void* stream);
-/* img[b] = scale * the 2x2 means of proj[b] ([B][256][256] -> [B][128][128]). */
+/* img[b] = scale * the 2x2 means of proj[b] ([B][256][256] -> [B][128][128]), or scale * proj[b] for
+ * [B][128][128] projections (a detector of half the pixels at twice the pitch). */
 digs_status digs_cnn_prepare_input(const float* proj, int B, int nu, int nv, float scale, float* img, void* stream);
 /* flags of the forward, backward and training step: DIGS_CNN_TENSOR_CORES runs the convolutions' and the
  * 8194-wide layer's GEMMs on the tensor cores (BF16 operands rounded from FP32, FP32 accumulation); without

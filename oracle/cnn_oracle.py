@@ -59,8 +59,11 @@ def unpack(flat: torch.Tensor, R: int) -> Dict[str, torch.Tensor]:
 
 
 def downsample(proj, scale: float) -> np.ndarray:
-    """scale * the 2 x 2 block means of [B][nv][nu] -> [B][nv/2][nu/2]."""
+    """The [B][128][128] network input: scale * the 2 x 2 block means of [B][256][256] projections, or
+    scale * [B][128][128] projections as they are."""
     p = np.asarray(proj, dtype=np.float64)
+    if p.shape[1] == 128:
+        return scale * p
     return scale * 0.25 * (p[:, 0::2, 0::2] + p[:, 0::2, 1::2] + p[:, 1::2, 0::2] + p[:, 1::2, 1::2])
 
 

@@ -348,15 +348,16 @@ __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ out, cons
   }
 }
 
-// 2 x 2 mean of a [B][nv][nu] projection stack into [B][nv/2][nu/2], times `scale`.
+// The network input [B][128][128] of a projection stack [B][nv][nu], times `scale`: the 2 x 2 means of
+// 256 x 256 projections, or 128 x 128 projections as they are.
 __global__ void k_downsample(const float* __restrict__ proj, int B, int nu, int nv, float scale,
                              float* __restrict__ img) {
-  const int wo = nu / 2, ho = nv / 2;
-  const long long total = (long long)B * wo * ho;
+  const int f = nu / 128;  // 2: 2 x 2 means of a 256 x 256 projection; 1: a 128 x 128 one, scaled
+  const long long total = (long long)B * 128 * 128;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % wo), y = (int)((i / wo) % ho), b = (int)(i / ((long long)wo * ho));
-    const float* p = proj + ((size_t)b * nv + 2 * y) * nu + 2 * x;
-    img[i] = 0.25f * scale * (p[0] + p[1] + p[nu] + p[nu + 1]);
+    const int x = (int)(i % 128), y = (int)((i / 128) % 128), b = (int)(i / (128LL * 128));
+    const float* p = proj + ((size_t)b * nv + f * y) * nu + f * x;
+    img[i] = f == 2 ? 0.25f * scale * (p[0] + p[1] + p[nu] + p[nu + 1]) : scale * p[0];
   }
 }
 
@@ -517,7 +518,7 @@ digs_status digs_cnn_init(float* params, int R, unsigned long long seed, void* s
 }
 
 digs_status digs_cnn_prepare_input(const float* proj, int B, int nu, int nv, float scale, float* img, void* stream) {
-  if (!proj || !img || B < 1 || nu != 256 || nv != 256) return DIGS_ERR_ARG;
+  if (!proj || !img || B < 1 || nu != nv || (nu != 256 && nu != 128)) return DIGS_ERR_ARG;
   k_downsample<<<grid_for((long long)B * 128 * 128), 256, 0, (cudaStream_t)stream>>>(proj, B, nu, nv, scale, img);
   note_launches(1);
   return cudaGetLastError() == cudaSuccess ? DIGS_OK : DIGS_ERR_CUDA;

@@ -562,10 +562,11 @@ class WeightPredictor:
         self.ws.ensure(nb)
 
     def prepare(self, proj: torch.Tensor) -> torch.Tensor:
-        """[B][256][256] projections -> [B][128][128] network inputs (2x2 means times input_scale)."""
+        """[B][256][256] projections -> [B][128][128] network inputs (2x2 means times input_scale);
+        [B][128][128] projections are only scaled."""
         proj = _f32(proj, "proj")
         B, nv, nu = proj.shape
-        img = torch.empty(B, nv // 2, nu // 2, device=proj.device)
+        img = torch.empty(B, 128, 128, device=proj.device)
         _check(lib().digs_cnn_prepare_input(_ptr(proj), B, nu, nv, self.input_scale, _ptr(img), _stream()),
                "digs_cnn_prepare_input")
         return img

@@ -120,6 +120,9 @@ def test_prepare_input_is_the_block_mean(P):
     proj = np.random.default_rng(9).normal(size=(3, 256, 256)).astype(np.float32)
     img = net.prepare(torch.as_tensor(proj, device="cuda")).cpu().numpy()
     assert np.allclose(img, C.downsample(proj, 0.5), rtol=1e-5, atol=1e-6)
+    small = np.random.default_rng(10).normal(size=(2, 128, 128)).astype(np.float32)
+    img2 = net.prepare(torch.as_tensor(small, device="cuda")).cpu().numpy()
+    assert np.allclose(img2, C.downsample(small, 0.5), rtol=1e-6, atol=0)
 
 
 @pytest.mark.parametrize("tc", [False, True])
