@@ -26,6 +26,8 @@ namespace digs {
 // umma.cu: the tensor-core GEMM with BF16 operands and output, B K-major (B(k, n) = B[n ldb + k]).
 cudaError_t gemm_tc_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
                          __nv_bfloat16* C, int ldc, const float* bias, bool relu, int* status, cudaStream_t st);
+cudaError_t gemm_tc_conv_fwd_bf16(int M, int N, int K, const __nv_bfloat16* act, ConvGeom g, const __nv_bfloat16* W,
+                                  int ldw, __nv_bfloat16* C, int ldc, const float* bias, bool relu, cudaStream_t st);
 
 namespace {
 
@@ -64,6 +66,13 @@ ParamOffsets param_offsets(int R) {
 
 size_t rows(int l, int B) { return (size_t)B * kEdge[l + 1] * kEdge[l + 1]; }  // output pixels of conv l
 size_t kdim(int l) { return (size_t)9 * kCh[l]; }
+int ilog2(int v) {
+  int k = 0;
+  while ((1 << k) < v) ++k;
+  return k;
+}
+// Input geometry of conv l for the tensor-core GEMM's implicit im2col.
+ConvGeom conv_geom(int l) { return ConvGeom{kEdge[l], kEdge[l], ilog2(kEdge[l + 1]), ilog2(kCh[l])}; }
 
 // Workspace of one batch: activations for the backward, gradients, split-K partials, BF16 copies.
 struct CnnWs {
@@ -417,11 +426,16 @@ cudaError_t forward_f32(const NetPtrs<float>& N, int R, const float* img, const 
   const float* in = img;
   for (int l = 0; l < kConvs; ++l) {
     const int H = kEdge[l], C = kCh[l];
-    const long long ncol = (long long)rows(l, B) * kdim(l);
-    k_im2col<float, float><<<grid_for(ncol), 256, 0, st>>>(in, B, H, H, C, w.col[l]);
-    note_launches(1);
-    CNN_TRY(gemm_f32<false, true>(tc, (int)rows(l, B), kCh[l + 1], (int)kdim(l), w.col[l], (int)kdim(l), N.w[l],
-                                  (int)kdim(l), w.act[l], kCh[l + 1], N.b[l], true, st));
+    if (tc && l > 0) {  // the tensor-core GEMM gathers the im2col matrix of act[l - 1] itself
+      CNN_TRY(gemm_tc_conv_fwd((int)rows(l, B), kCh[l + 1], (int)kdim(l), in, conv_geom(l), N.w[l], (int)kdim(l),
+                               w.act[l], kCh[l + 1], N.b[l], true, st));
+    } else {
+      const long long ncol = (long long)rows(l, B) * kdim(l);
+      k_im2col<float, float><<<grid_for(ncol), 256, 0, st>>>(in, B, H, H, C, w.col[l]);
+      note_launches(1);
+      CNN_TRY(gemm_f32<false, true>(tc, (int)rows(l, B), kCh[l + 1], (int)kdim(l), w.col[l], (int)kdim(l), N.w[l],
+                                    (int)kdim(l), w.act[l], kCh[l + 1], N.b[l], true, st));
+    }
     in = w.act[l];
   }
   k_features<float, float><<<grid_for((long long)B * kFeatIn), 256, 0, st>>>(w.act[kConvs - 1], cs, B, w.feat);
@@ -468,7 +482,10 @@ cudaError_t backward_f32(const NetPtrs<float>& N, const ParamOffsets& o, int R, 
                                                                              (M + 255) / 256, part_floats(B) / ndw,
                                                                              1024}))
                           : kSplits;
-    CNN_TRY(gemm_f32<true, false>(tc, Nn, K, M, dY, Nn, w.col[l], K, w.part, K, nullptr, false, st, splits, ndw));
+    if (tc && l > 0)  // the im2col matrix of act[l - 1], gathered by the GEMM (the forward stored none)
+      CNN_TRY(gemm_tc_conv_dw(Nn, K, M, dY, Nn, w.act[l - 1], conv_geom(l), w.part, K, splits, ndw, st));
+    else
+      CNN_TRY(gemm_f32<true, false>(tc, Nn, K, M, dY, Nn, w.col[l], K, w.part, K, nullptr, false, st, splits, ndw));
     k_sum_splits<<<(unsigned)((ndw + 255) / 256), 256, 0, st>>>(w.part, splits, ndw, grad + o.w[l], 0);
     note_launches(1);
     CNN_TRY(colsum(dY, M, Nn, w.part, grad + o.b[l], st));
@@ -588,12 +605,18 @@ digs_status digs_cnn_infer_bf16(const float* params, int R, const float* img, co
   __nv_bfloat16* out_act = w.actb0;
   for (int l = 0; l < kConvs; ++l) {
     const int H = kEdge[l], C = kCh[l];
-    const long long ncol = (long long)rows(l, B) * kdim(l);
-    k_im2col<__nv_bfloat16, __nv_bfloat16><<<grid_for(ncol), 256, 0, st>>>(in, B, H, H, C, w.colb);
-    note_launches(1);
-    if (gemm_tc_bf16((int)rows(l, B), kCh[l + 1], (int)kdim(l), w.colb, (int)kdim(l), N.w[l], (int)kdim(l), out_act,
-                     kCh[l + 1], N.b[l], true, nullptr, st) != cudaSuccess)
-      return DIGS_ERR_CUDA;
+    if (l > 0) {
+      if (gemm_tc_conv_fwd_bf16((int)rows(l, B), kCh[l + 1], (int)kdim(l), in, conv_geom(l), N.w[l], (int)kdim(l),
+                                out_act, kCh[l + 1], N.b[l], true, st) != cudaSuccess)
+        return DIGS_ERR_CUDA;
+    } else {
+      const long long ncol = (long long)rows(l, B) * kdim(l);
+      k_im2col<__nv_bfloat16, __nv_bfloat16><<<grid_for(ncol), 256, 0, st>>>(in, B, H, H, C, w.colb);
+      note_launches(1);
+      if (gemm_tc_bf16((int)rows(l, B), kCh[l + 1], (int)kdim(l), w.colb, (int)kdim(l), N.w[l], (int)kdim(l), out_act,
+                       kCh[l + 1], N.b[l], true, nullptr, st) != cudaSuccess)
+        return DIGS_ERR_CUDA;
+    }
     in = out_act;
     out_act = (out_act == w.actb0) ? w.actb1 : w.actb0;
   }

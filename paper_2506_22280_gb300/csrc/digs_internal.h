@@ -97,6 +97,18 @@ cudaError_t launch_gw_reduce(const Workspace& ws, const ViewsParam& views, int P
 int chain_blocks(int n);
 int pair_sum_blocks(int n);
 
+// Geometry of a 3 x 3, stride-2, padding-1 convolution input (NHWC, H x W x C) whose im2col matrix a
+// tensor-core GEMM reads implicitly: lwo = log2 of the output width W / 2 (= output height), lc = log2 C.
+struct ConvGeom {
+  int H, W, lwo, lc;
+};
+// umma.cu: implicit-im2col GEMMs: forward C[m][n] = act(sum_k im2col(act)[m][k] W[n][k] + bias[n]);
+// weight gradient C[m][n] (+ z zstride) = sum over the split's rows k of dY[k][m] im2col(act)[k][n].
+cudaError_t gemm_tc_conv_fwd(int M, int N, int K, const float* act, ConvGeom g, const float* W, int ldw, float* C,
+                             int ldc, const float* bias, bool relu, cudaStream_t st);
+cudaError_t gemm_tc_conv_dw(int M, int N, int K, const float* dY, int ldy, const float* act, ConvGeom g, float* C,
+                            int ldc, int splits, long long zstride, cudaStream_t st);
+
 // umma.cu: tensor-core GEMM (BF16 operands rounded from FP32, FP32 accumulation); C(m, n) = sum_k
 // A(m, k) B(k, n) with A(m, k) = at ? A[k lda + m] : A[m lda + k], B(k, n) = bt ? B[n ldb + k] :
 // B[k ldb + n]; splits > 1: partial sums over K ranges into C + z zstride (bias and ReLU not applied).

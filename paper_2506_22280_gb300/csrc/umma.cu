@@ -139,25 +139,72 @@ __device__ __forceinline__ uint4 load_chunk(const TP* __restrict__ P, int ld, in
   return make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
 }
 
+// Implicit im2col of a 3 x 3, stride-2, padding-1 convolution over an NHWC input of H x W x C (C and
+// the output width W / 2 powers of two): element (p, k) with p the output pixel (b, y, x) and
+// k = (ky 3 + kx) C + c is in[b][2y + ky - 1][2x + kx - 1][c], zero outside the input.
+__device__ __forceinline__ int conv_offset(const ConvGeom& g, int p, int k) {
+  const int lw = g.lwo, x = p & ((1 << lw) - 1), y = (p >> lw) & ((1 << lw) - 1), b = p >> (2 * lw);
+  const int tap = k >> g.lc, c = k & ((1 << g.lc) - 1), ky = tap / 3, kx = tap - 3 * ky;
+  const int iy = 2 * y + ky - 1, ix = 2 * x + kx - 1;
+  if (iy < 0 || iy >= g.H || ix < 0 || ix >= g.W) return -1;
+  return ((b * g.H + iy) * g.W + ix) << g.lc | c;
+}
+
+// Row p's K chunk [k, k + 8) of the implicit im2col matrix (rows < rows, k < kend), as BF16: with C a
+// multiple of 8 the chunk is 8 channels of one tap, contiguous in the input.
+template <typename TP>
+__device__ __forceinline__ uint4 conv_chunk_row(const ConvGeom& g, const TP* __restrict__ P, int p, int rows, int k,
+                                                int kend) {
+  if ((g.lc >= 3) && p < rows && k + 8 <= kend) {
+    const int o = conv_offset(g, p, k);
+    return o < 0 ? make_uint4(0u, 0u, 0u, 0u) : load_vec8(P + o);
+  }
+  float x[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int o = (p < rows && k + e < kend) ? conv_offset(g, p, k + e) : -1;
+    x[e] = o >= 0 ? ld_f(P + o) : 0.f;
+  }
+  return make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
+}
+
+// Column n's chunk of 8 consecutive rows [p, p + 8) of the implicit im2col matrix, as BF16.
+template <typename TP>
+__device__ __forceinline__ uint4 conv_chunk_col(const ConvGeom& g, const TP* __restrict__ P, int n, int cols, int p,
+                                                int pend) {
+  float x[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int o = (n < cols && p + e < pend) ? conv_offset(g, p + e, n) : -1;
+    x[e] = o >= 0 ? ld_f(P + o) : 0.f;
+  }
+  return make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
+}
+
 // Stage the K slice [k0, k0 + 64) of the block's A rows and B columns.  Consecutive threads take
 // consecutive K chunks when K is the contiguous global index, else consecutive rows.  Every chunk is
 // loaded (and rounded) before any is stored, so that all of the thread's loads are in flight together.
-template <bool AT, bool BT, typename TA, typename TB>
+// CA_ (CB_): A (B) is the implicit im2col matrix of the input at A (B) with geometry ga (gb): A(m, k) =
+// im2col[m][k] (AT false), B(k, n) = im2col[k][n] (BT false).
+template <bool AT, bool BT, bool CA_, bool CB_, typename TA, typename TB>
 __device__ __forceinline__ void stage(const TA* __restrict__ A, int lda, const TB* __restrict__ B, int ldb, int M,
-                                      int N, int m0, int n0, int k0, int kend, uint8_t* sA, uint8_t* sB, int vec) {
+                                      int N, int m0, int n0, int k0, int kend, uint8_t* sA, uint8_t* sB, int vec,
+                                      const ConvGeom& ga, const ConvGeom& gb) {
   constexpr int CA = (kBM * 8) / kTcThreads, CB = (kBN * 8) / kTcThreads;
   uint4 va[CA], vb[CB];
 #pragma unroll
   for (int i = 0; i < CA; ++i) {
     const int c = threadIdx.x + i * kTcThreads;
     const int kc = AT ? c / kBM : c & 7, mm = AT ? c % kBM : c >> 3;
-    va[i] = load_chunk<AT>(A, lda, m0 + mm, M, k0 + kc * 8, kend, (vec & 1) != 0);
+    va[i] = CA_ ? conv_chunk_row(ga, A, m0 + mm, M, k0 + kc * 8, kend)
+                : load_chunk<AT>(A, lda, m0 + mm, M, k0 + kc * 8, kend, (vec & 1) != 0);
   }
 #pragma unroll
   for (int i = 0; i < CB; ++i) {
     const int c = threadIdx.x + i * kTcThreads;
     const int kc = BT ? c & 7 : c / kBN, nn = BT ? c >> 3 : c % kBN;
-    vb[i] = load_chunk<!BT>(B, ldb, n0 + nn, N, k0 + kc * 8, kend, (vec & 2) != 0);
+    vb[i] = CB_ ? conv_chunk_col(gb, B, n0 + nn, N, k0 + kc * 8, kend)
+                : load_chunk<!BT>(B, ldb, n0 + nn, N, k0 + kc * 8, kend, (vec & 2) != 0);
   }
 #pragma unroll
   for (int i = 0; i < CA; ++i) {
@@ -173,12 +220,12 @@ __device__ __forceinline__ void stage(const TA* __restrict__ A, int lda, const T
   }
 }
 
-template <bool AT, bool BT, typename TA, typename TB, typename TC>
+template <bool AT, bool BT, bool CA_, bool CB_, typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, const TA* __restrict__ A, int lda,
                                                         const TB* __restrict__ B, int ldb, TC* __restrict__ C,
                                                         int ldc, int kchunk, long long zstride,
                                                         const float* __restrict__ bias, int relu, int vec,
-                                                        int* status) {
+                                                        int* status, const ConvGeom ga, const ConvGeom gb) {
   extern __shared__ unsigned char smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = sm;
@@ -210,7 +257,8 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
     const int buf = s & 1;
     if (s >= 2) ok = __syncthreads_and(ok && mbar_wait(bar + buf, (uint32_t)(((s >> 1) - 1) & 1)));
     if (!ok) break;
-    stage<AT, BT>(A, lda, B, ldb, M, N, m0, n0, kb + s * kBK, ke, sA + buf * kStageA, sB + buf * kStageB, vec);
+    stage<AT, BT, CA_, CB_>(A, lda, B, ldb, M, N, m0, n0, kb + s * kBK, ke, sA + buf * kStageA, sB + buf * kStageB,
+                            vec, ga, gb);
     fence_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -283,13 +331,14 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
   if (!ok && threadIdx.x == 0 && status) atomicExch(status, 1);
 }
 
-template <bool AT, bool BT, typename TA, typename TB, typename TC>
+template <bool AT, bool BT, typename TA, typename TB, typename TC, bool CA_ = false, bool CB_ = false>
 cudaError_t launch_tc(int M, int N, int K, const TA* A, int lda, const TB* B, int ldb, TC* C, int ldc,
-                      const float* bias, bool relu, int splits, long long zstride, int* status, cudaStream_t st) {
+                      const float* bias, bool relu, int splits, long long zstride, int* status, cudaStream_t st,
+                      ConvGeom ga = ConvGeom{}, ConvGeom gb = ConvGeom{}) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<AT, BT, TA, TB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kTcSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<AT, BT, CA_, CB_, TA, TB, TC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -300,8 +349,8 @@ cudaError_t launch_tc(int M, int N, int K, const TA* A, int lda, const TB* B, in
   constexpr int per16a = 16 / (int)sizeof(TA), per16b = 16 / (int)sizeof(TB);
   const int vec = ((!AT && ((uintptr_t)A & 15) == 0 && lda % per16a == 0) ? 1 : 0) |
                   ((BT && ((uintptr_t)B & 15) == 0 && ldb % per16b == 0) ? 2 : 0);
-  k_gemm_tc<AT, BT, TA, TB, TC><<<grid, kTcThreads, kTcSmem, st>>>(M, N, K, A, lda, B, ldb, C, ldc, kchunk, zstride,
-                                                                   bias, relu ? 1 : 0, vec, status);
+  k_gemm_tc<AT, BT, CA_, CB_, TA, TB, TC><<<grid, kTcThreads, kTcSmem, st>>>(
+      M, N, K, A, lda, B, ldb, C, ldc, kchunk, zstride, bias, relu ? 1 : 0, vec, status, ga, gb);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -344,6 +393,27 @@ cudaError_t gemm_tc_sum(bool at, bool bt, int M, int N, int K, const float* A, i
                                                                                      bias, relu ? 1 : 0);
   note_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t gemm_tc_conv_fwd(int M, int N, int K, const float* act, ConvGeom g, const float* W, int ldw, float* C,
+                             int ldc, const float* bias, bool relu, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  return launch_tc<false, true, float, float, float, true, false>(M, N, K, act, 0, W, ldw, C, ldc, bias, relu, 1, 0,
+                                                                  nullptr, st, g, ConvGeom{});
+}
+
+cudaError_t gemm_tc_conv_dw(int M, int N, int K, const float* dY, int ldy, const float* act, ConvGeom g, float* C,
+                            int ldc, int splits, long long zstride, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  return launch_tc<true, false, float, float, float, false, true>(M, N, K, dY, ldy, act, 0, C, ldc, nullptr, false,
+                                                                  splits, zstride, nullptr, st, ConvGeom{}, g);
+}
+
+cudaError_t gemm_tc_conv_fwd_bf16(int M, int N, int K, const __nv_bfloat16* act, ConvGeom g, const __nv_bfloat16* W,
+                                  int ldw, __nv_bfloat16* C, int ldc, const float* bias, bool relu, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  return launch_tc<false, true, __nv_bfloat16, __nv_bfloat16, __nv_bfloat16, true, false>(
+      M, N, K, act, 0, W, ldw, C, ldc, bias, relu, 1, 0, nullptr, st, g, ConvGeom{});
 }
 
 cudaError_t gemm_tc_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
