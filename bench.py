@@ -8,8 +8,9 @@ Gaussians, control points and temporal weights, and the fused Adam update of eve
 
 Prints ONE JSON line (rank 0).  ``value`` = projections processed by all ranks / max over ranks of the
 summed device time of the timed steps (CUDA events around each step; L2 is flushed between steps by a
-512 MB write outside the events).  ``e2e`` times the same steps end to end: host-to-device copy of the
-batch's measured projections from pinned memory, the step, and a device-to-host read of the loss.
+512 MB write outside the events).  ``e2e`` times the same steps end to end by the wall clock: every step's
+host-to-device copy of the batch's measured projections from pinned memory (on a copy stream, double
+buffered so that it overlaps the previous step), the step, and a device-to-host read of its loss.
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload instead.
 Multi-GPU (torchrun): every rank reconstructs its own independent scan (no data-path collective).
 """
@@ -541,18 +542,49 @@ def run_ours(args):
     # end to end: pinned host measured projections -> device, step, loss -> host
     e2e = None
     if not args.no_e2e:
+        # every step copies its measured projections from pinned host memory (on a copy stream, into one of
+        # two device buffers, so that step s + 1's copy overlaps step s) and reads its loss back to the host
+        # (step s's loss is read once step s + 1 has been launched)
         host = [m.cpu().pin_memory() for m in mb[T0:T0 + K]]
-        dev_buf = torch.empty_like(mb[0])
+        bufs = [torch.empty_like(mb[0]) for _ in range(2)]
+        loss_host = torch.empty(K, dtype=torch.float32).pin_memory()
+        copy_stream = torch.cuda.Stream(device=device)
+        main = torch.cuda.current_stream(device)
+        copied = [torch.cuda.Event() for _ in range(2)]
+        used = [torch.cuda.Event() for _ in range(2)]
+        read = [torch.cuda.Event() for _ in range(K)]
+        losses = []
+
+        def copy_in(s):
+            b = s % 2
+            with torch.cuda.stream(copy_stream):
+                if s >= 2:
+                    copy_stream.wait_event(used[b])  # step s - 2 has finished with this buffer
+                bufs[b].copy_(host[s], non_blocking=True)
+                copied[b].record(copy_stream)
+
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
+        copy_in(0)
         for s in range(K):
-            dev_buf.copy_(host[s], non_blocking=True)
-            loss = rec.step(dev_buf, plan[T0 + s], views[T0 + s], varr=varrs[T0 + s])
-            float(loss.item())
+            if s + 1 < K:
+                copy_in(s + 1)
+            main.wait_event(copied[s % 2])
+            loss = rec.step(bufs[s % 2], plan[T0 + s], views[T0 + s], varr=varrs[T0 + s])
+            used[s % 2].record(main)
+            loss_host[s:s + 1].copy_(loss.reshape(-1)[:1], non_blocking=True)
+            read[s].record(main)
+            if s >= 1:
+                read[s - 1].synchronize()
+                losses.append(float(loss_host[s - 1]))
+        read[K - 1].synchronize()
+        losses.append(float(loss_host[K - 1]))
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
+        if not all(math.isfinite(v) for v in losses):
+            raise RuntimeError("non-finite loss in the end-to-end steps")
     dev_ms, t_wall, e2e_s = reduce_timings([dev_ms, t_wall, e2e_s if not args.no_e2e else 0.0], world, device)
     batching = None
     if world == 1 and not args.no_batching:
