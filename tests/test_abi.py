@@ -61,3 +61,23 @@ def test_binding_marshals_views_and_lattice():
     lat = digs.lattice_struct(wl.lattice)
     assert (lat.nx, lat.ny, lat.nz, lat.R) == (8, 8, 8, 2) and abs(lat.origin[0] + 35) < 1e-6
     assert C.sizeof(digs.DigsView) == 8 * 16 + 4 * 3 + 4  # 16 doubles, 3 ints, tail padding
+
+
+def test_gemm_and_cnn_input_host_checks(lib):
+    """The tensor-core GEMM and the CNN input step reject bad sizes before any launch."""
+    P, I = C.c_void_p, C.c_int
+    f = lib.digs_gemm_bf16
+    f.restype = I
+    f.argtypes = [I, I, I, I, I, P, I, P, I, P, I, P, I, I, P, P, P]
+    dummy = C.c_void_p(16)
+    assert f(0, 0, -1, 4, 4, dummy, 4, dummy, 4, None, 0, dummy, 4, 1, None, None, None) == 1   # M < 0
+    assert f(0, 0, 4, 4, 4, dummy, 4, dummy, 4, None, 0, dummy, 2, 1, None, None, None) == 1    # ldc < N
+    assert f(0, 0, 4, 4, 8, dummy, 4, dummy, 4, None, 0, dummy, 4, 1, None, None, None) == 1    # lda < K
+    assert f(0, 0, 4, 4, 4, dummy, 4, dummy, 4, None, 0, dummy, 4, 2, None, None, None) == 1    # split, no scratch
+    assert f(0, 0, 4, 4, 4, dummy, 4, dummy, 4, None, 0, dummy, 4, 65, dummy, None, None) == 1  # splits > 64
+    assert f(0, 0, 0, 4, 4, None, 4, None, 4, None, 0, None, 4, 1, None, None, None) == 0       # empty: nothing to do
+    g = lib.digs_cnn_prepare_input
+    g.restype = I
+    g.argtypes = [P, I, I, I, C.c_float, P, P]
+    assert g(dummy, 2, 64, 64, 1.0, dummy, None) == 1     # only 256 x 256 or 128 x 128 projections
+    assert g(dummy, 2, 256, 128, 1.0, dummy, None) == 1
