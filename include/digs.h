@@ -194,6 +194,11 @@ typedef struct {
                                         group of m / v / grad is then n_ctrl * R floats)              */
   int n_ctrl;
   float t_step;                      /* control-point spacing in projection indices (e.g. 4)          */
+  float* dens_grad;                  /* optional [n]: when set, each step adds, for every Gaussian, the
+                                        sum over the batch's projections of |dL/dmu'_b| (the gradient of
+                                        the step's loss with respect to its deformed mean in projection b,
+                                        the deformed covariance held fixed): the statistic of
+                                        digs_densify_plan.  Single-scan states only.                    */
 } DigsState;
 
 /* Number of floats in DigsState.m (and v, grad) for n Gaussians in n_scans (>= 1) scans with per-row
@@ -282,6 +287,40 @@ digs_status digs_cnn_train_step(float* params, float* m, float* v, float* grad, 
  * (biases and the output layer FP32): w_out[B][R]. */
 digs_status digs_cnn_infer_bf16(const float* params, int R, const float* img, const float* cs, int B, float* w_out,
                                 void* ws, size_t ws_bytes, void* stream);
+
+/* ---- Adaptive density control -----------------------------------------------------------------
+ * Between optimisation steps the cloud is densified and pruned (Sec. 4.2 gives the gradient threshold,
+ * 5e-8 in its loss units, and defers the other settings to the method it builds on, whose values are not
+ * stated; the rules below are this library's reading, each a parameter).  Per Gaussian, with g = the
+ * DigsState.dens_grad sum over the n_projections projections rendered since it was last cleared:
+ *   prune if rho < rho_min; else, if g >= tau * n_projections (compared in float: the product is
+ *   rounded to float once), split if the largest scale exceeds s_split, otherwise clone; else keep.
+ * Clone: two copies, each with density rho / 2.  Split: two children at mu + R diag(s) z_k (z_k ~ N(0, I)
+ * drawn by the caller, z[n][2][3]) with scales s / 1.6, the parent's rotation and density
+ * rho * 1.6^3 / 2 (the integrated mass is conserved).  Output rows follow the parents' order, a clone's
+ * original first; src[j] is each output row's parent and is_new[j] marks the rows that are not the parent
+ * itself (the clone's second copy, both split children), whose optimiser moments should start at zero
+ * (digs_gather_rows). */
+typedef struct {
+  float tau;          /* threshold on the mean of |dL/dmu'| over the projections (paper: 5e-8)   */
+  int n_projections;  /* projections rendered since dens_grad was cleared (>= 1)                   */
+  float s_split;      /* largest scale above which a densified Gaussian is split (mm)              */
+  float rho_min;      /* density below which a Gaussian is pruned                                  */
+} DigsDensifyOpts;
+size_t digs_densify_workspace_size(int n);
+/* action[n]: -1 prune, 0 keep, 1 clone, 2 split; dst[n + 1] (device ints): each Gaussian's first output
+ * row, dst[n] = the number of output rows. */
+digs_status digs_densify_plan(int n, const float* grad_sum, const float* scale, const float* rho,
+                              const DigsDensifyOpts* opts, int* action, int* dst, void* ws, size_t ws_bytes,
+                              void* stream);
+/* Writes the new cloud (rows [0, dst[n]) of mu0 [.][3], scale [.][3], quat [.][4], rho, src, is_new;
+ * rows at or beyond cap are not written).  z: device [n][2][3]. */
+digs_status digs_densify_apply(const DigsGaussians* g, const int* action, const int* dst, const float* z, int cap,
+                               float* mu0, float* scale, float* quat, float* rho, int* src, int* is_new,
+                               void* stream);
+/* out[j][c] = is_new[j] ? 0 : in[src[j]][c] for j < n_out, c < dim (e.g. Adam moments of the new cloud). */
+digs_status digs_gather_rows(const int* src, const int* is_new, int n_out, int dim, const float* in, float* out,
+                             void* stream);
 
 /* ---- Dense GEMM on the tensor cores ------------------------------------------------------------
  * The paper has no counterpart: the weight-predictor CNN's layers run on this.  C = op(A) op(B) (+ bias

@@ -70,7 +70,7 @@ def densify_plan(grad_sum, n_projections: int, scale, rho, tau: float, s_split: 
     s = np.asarray(scale, dtype=np.float32)
     r = np.asarray(rho, dtype=np.float32)
     prune = r < np.float32(rho_min)
-    dens = ~prune & (g >= np.float32(tau * n_projections))
+    dens = ~prune & (g >= np.float32(float(np.float32(tau)) * n_projections))  # tau as the library's float
     split = dens & (s.max(axis=1) > np.float32(s_split))
     action = np.where(prune, PRUNE, np.where(split, SPLIT, np.where(dens, CLONE, KEEP)))
     size = np.where(action == PRUNE, 0, np.where(action == KEEP, 1, 2))

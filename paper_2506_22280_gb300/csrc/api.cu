@@ -54,7 +54,7 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.loss_part = (float*)take((size_t)P * w.T * fwd_blocks(tile) * 4 + 4);
   w.ffd = (float*)take((size_t)12 * R * n_total * 4 + 4);
   w.ffd2 = (float*)take((size_t)18 * R * n_total * 4 + 4);
-  w.gsum = (float*)take((size_t)(16 + 12 * R) * n_total * 4 + 4);
+  w.gsum = (float*)take((size_t)(17 + 12 * R) * n_total * 4 + 4);
   w.proj = (float*)take((size_t)P * nu * nv * 4);
   w.dldi = (float*)take((size_t)P * nu * nv * 4);
   w.gw_rows = (float*)take((size_t)w_rows * R * 4 + 4);
@@ -279,13 +279,15 @@ digs_status bin(Call& c, const float* phi, const float* w) {
 
 // grad_proj = dL/dI, or nullptr when ws.dldi already holds dL/dI * |X - s|.
 digs_status backward(Call& c, const float* phi, const float* w, const float* grad_proj, float* g_mu0,
-                     float* g_scale, float* g_quat, float* g_rho, float* g_phi, float* g_w, int w_rows) {
+                     float* g_scale, float* g_quat, float* g_rho, float* g_phi, float* g_w, int w_rows,
+                     float* dens_grad = nullptr) {
   DIGS_TRY(cudaMemsetAsync(g_phi, 0, c.sc.S * phi_floats(c.L) * sizeof(float), c.st));
   mark(c, 5);
   if (c.g.n > 0) DIGS_TRY(launch_raster_bwd(c.ws, c.views, c.c2, grad_proj, c.st));
   mark(c, 6);
   if (c.g.n > 0)
-    DIGS_TRY(launch_chain_bwd(c.g, c.sc, c.L, phi, w, c.views, c.P, c.ws, g_mu0, g_scale, g_quat, g_rho, g_phi, c.st));
+    DIGS_TRY(launch_chain_bwd(c.g, c.sc, c.L, phi, w, c.views, c.P, c.ws, g_mu0, g_scale, g_quat, g_rho, g_phi,
+                              dens_grad, c.st));
   DIGS_TRY(launch_gw_reduce(c.ws, c.views, c.P, c.L.R, g_w, w_rows, c.st));
   mark(c, 7);
   return DIGS_OK;
@@ -418,7 +420,7 @@ digs_status digs_step(DigsState* st, const float* meas, const int* proj_ids, con
   DIGS_TRY(launch_raster_fwd(c.ws, c.views, c.c2, c.ws.proj, meas, c.ws.dldi, inv_count, c.st));
   mark(c, 4);
   DIGS_TRY(launch_loss_reduce(c.ws.loss_part, B * c.ws.T * fwd_blocks(c.ws.tile), loss_out, inv_count, c.st));
-  s = backward(c, st->phi, st->w, nullptr, g_mu0, g_ls, g_q, g_rho, g_phi, g_w_rows, st->n_w);
+  s = backward(c, st->phi, st->w, nullptr, g_mu0, g_ls, g_q, g_rho, g_phi, g_w_rows, st->n_w, st->dens_grad);
   if (s != DIGS_OK) return s;
   if (temporal) DIGS_TRY(launch_temporal_bwd(g_w_rows, st->n_ctrl, R, st->t_step, rowsp, B, g_w, c.st));
   const DigsAdamConfig& a = st->adam;

@@ -223,12 +223,12 @@ __device__ __forceinline__ void pair_adjoint(const ViewC& v, const float* __rest
 // (1) Per Gaussian, the pair adjoints summed over its projections.  A CTA takes 32 Gaussians (its lanes)
 // and kSlots projection slots (its warps): warp k handles projections k, k + kSlots, ..., each thread
 // adding its pair's adjoint into its own shared-memory column; the slots are then summed in order.
-// gsum [16 + 12 R][N]: dL/dmu' (3), dL/ds (3), dL/dR (9), dL/drho (1), sum_b w_br dL/dmu'_b (3R) and
-// sum_b w_br dL/dK_b (9R).  gw_part [CTA][P][R]: dL/dw_r of each projection summed over the CTA's
+// gsum [17 + 12 R][N]: dL/dmu' (3), dL/ds (3), dL/dR (9), dL/drho (1), sum_b w_br dL/dmu'_b (3R),
+// sum_b w_br dL/dK_b (9R) and sum_b |dL/dmu'_b| (the density-control statistic).  gw_part [CTA][P][R]: dL/dw_r of each projection summed over the CTA's
 // Gaussians (a warp sum; each (CTA, projection) is written by one warp).
 constexpr int kSlots = 8;
 template <int R>
-__host__ __device__ constexpr int gauss_sum_count() { return 16 + 12 * R; }
+__host__ __device__ constexpr int gauss_sum_count() { return 17 + 12 * R; }
 template <int R>
 constexpr size_t pair_sum_smem() { return (size_t)gauss_sum_count<R>() * kSlots * 32 * sizeof(float); }
 int pair_sum_blocks(int n) { return (n + 31) / 32; }
@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(kSlots * 32, 3) k_pair_sum(GaussPtrs g, const 
 #pragma unroll
         for (int c = 0; c < 9; ++c) my[(16 + 3 * R + 9 * r + c) * QS] += wr[r] * gK[c];
       }
+      my[(16 + 12 * R) * QS] += sqrtf(gmu[0] * gmu[0] + gmu[1] * gmu[1] + gmu[2] * gmu[2]);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -337,7 +338,7 @@ template <int R>
 __global__ void __launch_bounds__(kChainThreads) k_gauss_bwd(
     GaussPtrs g, const __grid_constant__ ScanTable sc, LatticeC L, const float* __restrict__ ffd,
     const float* __restrict__ ffd2,
-    const float* __restrict__ gsum, float* __restrict__ g_mu0,
+    const float* __restrict__ gsum, float* __restrict__ dens_grad, float* __restrict__ g_mu0,
     float* __restrict__ g_scale, float* __restrict__ g_quat, float* __restrict__ g_rho, float* __restrict__ g_phi) {
   __shared__ float Gs[12 * R * kChainThreads];  // dL/du_r (3R) then dL/d(grad u_r) (9R), thread-fastest
   constexpr int ST = kChainThreads;
@@ -417,11 +418,13 @@ __global__ void __launch_bounds__(kChainThreads) k_gauss_bwd(
 #pragma unroll
   for (int c = 0; c < 4; ++c) g_quat[4 * n + c] = gq[c];
   g_rho[n] = grho;
+  if (dens_grad) dens_grad[n] += gsum[(size_t)(16 + 12 * R) * N + n];  // density-control statistic
 }
 
 cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const LatticeC& L, const float* phi,
                              const float* w, const ViewsParam& views, int P, const Workspace& ws, float* g_mu0,
-                             float* g_scale, float* g_quat, float* g_rho, float* g_phi, cudaStream_t st) {
+                             float* g_scale, float* g_quat, float* g_rho, float* g_phi, float* dens_grad,
+                             cudaStream_t st) {
   if (g.n <= 0) return cudaSuccess;
   dim3 gb(chain_blocks(g.n)), gp(pair_sum_blocks(g.n));
 #define DIGS_CH(RR)                                                                                             \
@@ -435,8 +438,8 @@ cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const Latt
   k_ffd_hessian<RR><<<gb, 128, 0, st>>>(g, sc, L, phi, ws.ffd2);                                                \
   k_pair_sum<RR><<<gp, kSlots * 32, pair_sum_smem<RR>(), st>>>(g, sc, ws.ffd, w, views, P, ws.counts, ws.grec,   \
                                                               ws.gsum, ws.gw_part);                            \
-  k_gauss_bwd<RR><<<gb, kChainThreads, 0, st>>>(g, sc, L, ws.ffd, ws.ffd2, ws.gsum, g_mu0, g_scale, g_quat,    \
-                                               g_rho, g_phi)
+  k_gauss_bwd<RR><<<gb, kChainThreads, 0, st>>>(g, sc, L, ws.ffd, ws.ffd2, ws.gsum, dens_grad, g_mu0, g_scale,  \
+                                               g_quat, g_rho, g_phi)
   switch (L.R) {
     case 1: DIGS_CH(1); break;
     case 2: DIGS_CH(2); break;

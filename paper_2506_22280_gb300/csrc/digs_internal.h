@@ -33,7 +33,7 @@ struct Workspace {
   float* gw_part;         // [pair-sum CTAs][P][R] dL/dw partial sums
   float* ffd;             // [12 R][n_total]: u_r (3R components) then grad u_r (9R) at each mean
   float* ffd2;            // [18 R][n_total]: second derivatives of u_r (6 per component)
-  float* gsum;            // [16 + 12 R][n_total]: each Gaussian's pair adjoints summed over its projections
+  float* gsum;            // [17 + 12 R][n_total]: each Gaussian's pair adjoints summed over its projections
   float* loss_part;       // [P * T * fwd_blocks(tile)] forward: squared residuals per 8 x 8 block (warp)
   float* proj;            // [P * nv * nu] (digs_step)
   float* dldi;            // [P * nv * nu] (digs_step)
@@ -91,7 +91,8 @@ cudaError_t launch_loss_reduce(const float* part, int n, float* out, float scale
 // chain.cu
 cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const LatticeC& L, const float* phi,
                              const float* w, const ViewsParam& views, int P, const Workspace& ws, float* g_mu0,
-                             float* g_scale, float* g_quat, float* g_rho, float* g_phi, cudaStream_t st);
+                             float* g_scale, float* g_quat, float* g_rho, float* g_phi, float* dens_grad,
+                             cudaStream_t st);
 cudaError_t launch_gw_reduce(const Workspace& ws, const ViewsParam& views, int P, int R, float* g_w, int w_rows,
                              cudaStream_t st);
 int chain_blocks(int n);

@@ -60,7 +60,11 @@ class DigsState(C.Structure):
                 ("phi", C.c_void_p), ("w", C.c_void_p), ("n_w", C.c_int), ("m", C.c_void_p), ("v", C.c_void_p),
                 ("grad", C.c_void_p), ("iter", C.c_int), ("lat", DigsLattice), ("adam", DigsAdamConfig),
                 ("n_scans", C.c_int), ("scan_off", C.c_int * (DIGS_MAX_SCANS + 1)), ("iter_dev", C.c_void_p),
-                ("w_ctrl", C.c_void_p), ("n_ctrl", C.c_int), ("t_step", C.c_float)]
+                ("w_ctrl", C.c_void_p), ("n_ctrl", C.c_int), ("t_step", C.c_float), ("dens_grad", C.c_void_p)]
+
+
+class DigsDensifyOpts(C.Structure):
+    _fields_ = [("tau", C.c_float), ("n_projections", C.c_int), ("s_split", C.c_float), ("rho_min", C.c_float)]
 
 
 _lib = None
@@ -101,6 +105,10 @@ def lib() -> C.CDLL:
         "digs_cnn_train_step": (I, [P, P, P, P, I, C.c_float, I, P, P, P, I, P, I, P, S, P]),
         "digs_cnn_infer_bf16": (I, [P, I, P, P, I, P, P, S, P]),
         "digs_gemm_bf16": (I, [I, I, I, I, I, P, I, P, I, P, I, P, I, I, P, P, P]),
+        "digs_densify_workspace_size": (S, [I]),
+        "digs_densify_plan": (I, [I, P, P, P, P, P, P, P, S, P]),
+        "digs_densify_apply": (I, [P, P, P, P, I, P, P, P, P, P, P, P]),
+        "digs_gather_rows": (I, [P, P, I, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -115,7 +123,8 @@ def exported_symbols() -> List[str]:
             "digs_state_moments", "digs_state_workspace_size", "digs_state_size", "digs_step", "digs_sync_status", "digs_status_string", "digs_stage_times",
             "digs_kernel_launches", "digs_pair_stats", "digs_voxelize", "digs_dvf", "digs_cnn_params", "digs_cnn_workspace_size", "digs_cnn_init",
             "digs_cnn_prepare_input", "digs_cnn_forward", "digs_cnn_backward", "digs_cnn_train_step",
-            "digs_cnn_infer_bf16", "digs_gemm_bf16"]
+            "digs_cnn_infer_bf16", "digs_gemm_bf16", "digs_densify_workspace_size", "digs_densify_plan",
+            "digs_densify_apply", "digs_gather_rows"]
 
 
 DIGS_FLAG_TIME_STAGES = 2
@@ -411,6 +420,8 @@ class Reconstruction:
         self.ws = Workspace(dev)
         self.cap = {}
         self.loss = torch.zeros(1, device=dev)
+        self.dens_grad = None
+        self.dens_projections = 0
 
     def scan_params(self, s: int) -> Dict[str, torch.Tensor]:
         """Views of scan s's Gaussians and control points inside the state."""
@@ -458,7 +469,60 @@ class Reconstruction:
         o = opts_struct(self.cutoff, self.tile, DIGS_FLAG_TIME_STAGES if time_stages else 0, self.bwd_lanes)
         _check(lib().digs_step(C.byref(self.state), _ptr(_f32(meas, "meas")), ids, varr, B, C.byref(o),
                                _ptr(self.loss), self.ws.ptr, self.ws.nbytes, _stream()), "digs_step")
+        if self.dens_grad is not None:
+            self.dens_projections += B
         return self.loss
+
+    # ---- adaptive density control ----------------------------------------------------------------
+    def enable_density_stats(self) -> None:
+        """Let every step add the density-control statistic (sum over its projections of |dL/dmu'|) into
+        ``dens_grad`` (one scan only)."""
+        if self.S != 1:
+            raise ValueError("density control is for one-scan states")
+        self.dens_grad = torch.zeros(int(self.mu0.shape[0]), device=self.mu0.device)
+        self.dens_projections = 0
+        self.state.dens_grad = self.dens_grad.data_ptr()
+
+    def densify(self, tau: float = 5e-8, s_split: float = 4.0, rho_min: float = 1e-5,
+                generator: Optional[torch.Generator] = None) -> Dict[str, int]:
+        """Prune, clone and split Gaussians by the statistic gathered since the last call
+        (include/digs.h, "Adaptive density control"); the Adam moments of kept Gaussians carry over, new
+        ones start at zero, the statistic restarts.  Captured graphs of earlier steps no longer apply."""
+        if self.dens_grad is None or self.dens_projections < 1:
+            raise ValueError("enable_density_stats() and at least one step first")
+        n = int(self.mu0.shape[0])
+        action, dst = densify_plan(self.dens_grad, self.scale, self.rho, tau, self.dens_projections, s_split, rho_min)
+        n_out = int(dst[n].item())
+        z = torch.randn(n, 2, 3, device=self.mu0.device, generator=generator)
+        out = densify_apply(self.mu0, self.scale, self.quat, self.rho, action, dst, z, n_out)
+        src, new = out["src"], out["new"]
+        groups = []
+        off = 0
+        for d in (3, 3, 4, 1):  # mu0, log-scale, quat, density moments, per Gaussian
+            groups.append((off, d))
+            off += d * n
+        m_new, v_new = [], []
+        for o, d in groups:
+            m_new.append(gather_rows(src, new, self.m[o:o + d * n].view(n, d)).reshape(-1))
+            v_new.append(gather_rows(src, new, self.v[o:o + d * n].view(n, d)).reshape(-1))
+        self.m = torch.cat(m_new + [self.m[off:]])
+        self.v = torch.cat(v_new + [self.v[off:]])
+        self.grad = torch.zeros_like(self.m)
+        self.mu0, self.scale, self.quat, self.rho = out["mu0"], out["scale"], out["quat"], out["rho"]
+        st = self.state
+        st.n = n_out
+        st.mu0, st.scale, st.quat, st.rho = (self.mu0.data_ptr(), self.scale.data_ptr(), self.quat.data_ptr(),
+                                             self.rho.data_ptr())
+        st.m, st.v, st.grad = self.m.data_ptr(), self.v.data_ptr(), self.grad.data_ptr()
+        self.scan_off = [0, n_out]
+        st.scan_off[1] = n_out
+        self.dens_grad = torch.zeros(n_out, device=self.mu0.device)
+        st.dens_grad = self.dens_grad.data_ptr()
+        self.dens_projections = 0
+        self.cap = {}
+        a = action.cpu()
+        return dict(n_before=n, n_after=n_out, pruned=int((a == -1).sum()), cloned=int((a == 1).sum()),
+                    split=int((a == 2).sum()))
 
     def clone(self) -> "Reconstruction":
         """An independent copy of the state (parameters, Adam moments, step count)."""
@@ -528,6 +592,46 @@ def gemm_bf16(a: torch.Tensor, b: torch.Tensor, trans_a: bool = False, trans_b: 
                                 int(b.shape[1]), _ptr(bias), int(relu), _ptr(out), N, int(splits), _ptr(part),
                                 _ptr(status), _stream()), "digs_gemm_bf16")
     return out, status
+
+
+def densify_plan(grad_sum: torch.Tensor, scale: torch.Tensor, rho: torch.Tensor, tau: float, n_projections: int,
+                 s_split: float, rho_min: float) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Density-control plan (include/digs.h, digs_densify_plan): action [n] (-1 prune, 0 keep, 1 clone,
+    2 split) and dst [n + 1] (first output row of each Gaussian; dst[n] = output rows), int32 on the
+    device."""
+    n = int(scale.shape[0])
+    dev = scale.device
+    action = torch.empty(n, dtype=torch.int32, device=dev)
+    dst = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    ws = torch.empty(int(lib().digs_densify_workspace_size(n)), dtype=torch.uint8, device=dev)
+    o = DigsDensifyOpts(float(tau), int(n_projections), float(s_split), float(rho_min))
+    _check(lib().digs_densify_plan(n, _ptr(_f32(grad_sum, "grad_sum")), _ptr(_f32(scale, "scale")),
+                                   _ptr(_f32(rho, "rho")), C.byref(o), _ptr(action), _ptr(dst), _ptr(ws),
+                                   int(ws.numel()), _stream()), "digs_densify_plan")
+    return action, dst
+
+
+def densify_apply(mu0, scale, quat, rho, action, dst, z, n_out: int) -> Dict[str, torch.Tensor]:
+    """The densified cloud of a plan (digs_densify_apply); z: [n][2][3] standard normal draws."""
+    dev = mu0.device
+    out = dict(mu0=torch.empty(n_out, 3, device=dev), scale=torch.empty(n_out, 3, device=dev),
+               quat=torch.empty(n_out, 4, device=dev), rho=torch.empty(n_out, device=dev),
+               src=torch.empty(n_out, dtype=torch.int32, device=dev), new=torch.empty(n_out, dtype=torch.int32, device=dev))
+    g = gauss_struct(mu0, scale, quat, rho)
+    _check(lib().digs_densify_apply(C.byref(g), _ptr(action), _ptr(dst), _ptr(_f32(z.contiguous(), "z")), n_out,
+                                    _ptr(out["mu0"]), _ptr(out["scale"]), _ptr(out["quat"]), _ptr(out["rho"]),
+                                    _ptr(out["src"]), _ptr(out["new"]), _stream()), "digs_densify_apply")
+    return out
+
+
+def gather_rows(src: torch.Tensor, new: torch.Tensor, rows: torch.Tensor) -> torch.Tensor:
+    """rows [n][d] carried over to the densified cloud: the parent's row, zero for new rows."""
+    rows = _f32(rows, "rows").contiguous()
+    n_out, d = int(src.shape[0]), int(rows.shape[1]) if rows.dim() > 1 else 1
+    out = torch.empty(n_out, d, device=rows.device)
+    _check(lib().digs_gather_rows(_ptr(src), _ptr(new), n_out, d, _ptr(rows), _ptr(out), _stream()),
+           "digs_gather_rows")
+    return out
 
 
 DIGS_CNN_TENSOR_CORES = 1
