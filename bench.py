@@ -386,6 +386,39 @@ def warmstart_measurement(pkg, D, wl, meas, device, tile, lanes, B=16, warmup_it
     return out
 
 
+def density_measurement(rec, plan, mb, views, varrs, T0, steps=8, quantile=0.9):
+    """Adaptive density control on a copy of the bench state: the step with the statistic switched on
+    against the same step without it, then one densify (plan, new cloud, moments) with the threshold at the
+    statistic's 90th percentile; wall time around the densify, which reads the new size back to the host."""
+    import torch
+    r = rec.clone()
+    r.enable_density_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = {}
+    for mode in ("with_statistic", "without_statistic"):
+        if mode == "without_statistic":
+            r.state.dens_grad = None
+        torch.cuda.synchronize()
+        e0.record()
+        for s in range(steps):
+            r.step(mb[T0 + s], plan[T0 + s], views[T0 + s], varr=varrs[T0 + s])
+        e1.record()
+        torch.cuda.synchronize()
+        times[mode] = e0.elapsed_time(e1) / steps
+    r.state.dens_grad = r.dens_grad.data_ptr()
+    r.dens_projections = steps * len(plan[T0])  # the statistic summed over the first pass's projections
+    stat = r.dens_grad / r.dens_projections
+    tau = float(torch.quantile(stat, quantile).item())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = r.densify(tau=tau, s_split=4.0, rho_min=1e-5, generator=torch.Generator(device=r.mu0.device).manual_seed(0))
+    torch.cuda.synchronize()
+    t_dens = time.perf_counter() - t0
+    loss = float(r.step(mb[T0], plan[T0], views[T0], varr=varrs[T0]).item())
+    return {"step_ms_with_statistic": times["with_statistic"], "step_ms_without_statistic": times["without_statistic"],
+            "densify_ms": t_dens * 1e3, "tau": tau, **info, "loss_after": loss, "device_status": r.status()}
+
+
 def cnn_gemm_flops(B, R=3):
     """FLOPs of the weight-predictor CNN's GEMMs in one training step of batch B: the forward (four
     convolutions as im2col GEMMs, the 8194-wide and the R-wide layers), the weight gradients of all six
@@ -592,7 +625,9 @@ def run_ours(args):
     models = None
     if world == 1 and not args.no_batching:
         models = model_comparison(pkg, wl, device, tile, lanes, B=B)
-    warm = warm_cfg = cnn = None
+    warm = warm_cfg = cnn = dens = None
+    if world == 1 and not args.no_batching:
+        dens = density_measurement(rec, plan, mb, views, varrs, T0)
     if world == 1 and not args.no_warmstart:
         # the bench's protocol (10k pairs rendered at the network's 128 x 128), then the workload's stated one
         # (20k pairs rendered at 256 x 256 and 2 x 2-averaged), both from the same plain run
@@ -647,6 +682,8 @@ def run_ours(args):
         line["warm_start_stated_protocol"] = warm_cfg
     if cnn is not None:
         line["cnn"] = cnn
+    if dens is not None:
+        line["density_control"] = dens
     if models is not None:
         line["projection_models"] = models
     if world == 1 and not args.no_cpu_baseline:
