@@ -9,7 +9,8 @@
 // so that (2) one exclusive scan of the whole array gives every (projection, digit, block) its output
 // base; (3) each block ranks its keys stably -- each warp walks a contiguous run of 512 keys in order,
 // ranking equal digits inside a 32-key step with __match_any_sync and across steps with per-warp digit
-// counters -- and scatters them.  With one pass the ranges follow from the scanned histograms.
+// counters -- puts them in sorted order in shared memory and writes each digit's run out contiguously.
+// With one pass the ranges follow from the scanned histograms.
 #include "digs_internal.h"
 
 namespace digs {
@@ -109,7 +110,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
                                                                const uint32_t* __restrict__ seg, int P, int T, int shift,
                                                                const uint32_t* __restrict__ hist_scan) {
   __shared__ uint32_t wcnt[kSortWarps][256];
-  __shared__ uint32_t dbase[256];
+  __shared__ uint32_t dbase[256];   // output position of the block's first key of each digit
+  __shared__ uint32_t loff[256];    // position of that key inside the block's sorted run
+  __shared__ uint32_t wsum[kSortWarps];
+  __shared__ uint32_t sk[kSortTile], sv[kSortTile];
   const SortBlock s = sort_block(seg, P);
   if (s.idle) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -136,25 +140,47 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
     __syncwarp();
   }
   __syncthreads();
-  {  // exclusive scan of the per-warp counts of each digit, in warp order
-    uint32_t acc = 0;
+  uint32_t total = 0;  // keys of digit threadIdx.x in the block
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-      const uint32_t c = wcnt[w][threadIdx.x];
-      wcnt[w][threadIdx.x] = acc;
-      acc += c;
+  for (int w = 0; w < kSortWarps; ++w) {  // exclusive scan of the per-warp counts of each digit, in warp order
+    const uint32_t c = wcnt[w][threadIdx.x];
+    wcnt[w][threadIdx.x] = total;
+    total += c;
+  }
+  {  // exclusive scan of the digit totals over the digits: each digit's run inside the block
+    uint32_t x = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t before_w = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) before_w += w < warp ? wsum[w] : 0u;
+    loff[threadIdx.x] = before_w + x - total;
   }
   __syncthreads();
+  // the block's keys in sorted order in shared memory, then written out run by run (coalesced)
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
     const uint32_t idx = run + (uint32_t)(it * 32 + lane);
     if (idx < s.hi) {
       const uint32_t d = ((key[it] - kb) >> shift) & 255u;
-      const uint32_t pos = dbase[d] + wcnt[warp][d] + rank[it];
-      kout[pos] = key[it];
-      vout[pos] = val[it];
+      const uint32_t p = loff[d] + wcnt[warp][d] + rank[it];
+      sk[p] = key[it];
+      sv[p] = val[it];
     }
+  }
+  __syncthreads();
+  const uint32_t cnt = s.hi - s.lo;
+  for (uint32_t i = threadIdx.x; i < cnt; i += kSortThreads) {
+    const uint32_t k = sk[i];
+    const uint32_t d = ((k - kb) >> shift) & 255u;
+    const uint32_t pos = dbase[d] + (i - loff[d]);
+    kout[pos] = k;
+    vout[pos] = sv[i];
   }
 }
 
