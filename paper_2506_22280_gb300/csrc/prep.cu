@@ -149,34 +149,56 @@ cudaError_t launch_prep_fwd(const GaussPtrs& g, const ScanTable& sc, const Latti
   return cudaGetLastError();
 }
 
-// One thread per (projection, Gaussian) record i: write key = b * T + tile and value i for each tile of
-// its box, at the slots [offsets[i], offsets[i + 1]) reserved by the scan (so after the stable sort the
-// values are the record of each sorted position).  Pairs beyond the capacity are dropped and flagged.
+// Each warp emits the pairs of 32 consecutive (projection, Gaussian) records i: key = b * T + tile and
+// value i for each tile of i's box (rows of tiles, then tiles within a row), at the slots
+// [offsets[i], offsets[i + 1]) reserved by the scan, so that after the stable sort the values are the
+// record of each sorted position.  The warp's slots form one contiguous range; its lanes walk it 32 at a
+// time (coalesced stores), each finding the record that owns its slot by a binary search over the
+// warp's 32 offsets.  Pairs beyond the capacity are dropped and flagged.
 __global__ void __launch_bounds__(256) k_emit(const float4* __restrict__ rec, const uint32_t* __restrict__ offsets,
                                               int PN, int n, int tile, int tiles_x, int T, uint32_t* __restrict__ keys,
                                               uint32_t* __restrict__ vals, long long cap, uint32_t* n_pairs,
                                               int* status) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) {
-    uint32_t total = offsets[PN];
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gt == 0) {
+    const uint32_t total = offsets[PN];
     n_pairs[0] = total;
     n_pairs[1] = (long long)total > cap ? (uint32_t)cap : total;
     if ((long long)total > cap) set_status(status, DIGS_ERR_CAPACITY);
   }
-  if (i >= PN) return;
-  uint32_t off = offsets[i], end = offsets[i + 1];
-  if (off == end) return;
-  float4 c = rec[(size_t)i * DIGS_REC_F4 + 2];
-  int bx = __float_as_int(c.y), by = __float_as_int(c.z);
-  int tx0 = (bx & 0xffff) / tile, tx1 = (bx >> 16) / tile, ty0 = (by & 0xffff) / tile, ty1 = (by >> 16) / tile;
-  uint32_t base = (uint32_t)(i / n) * (uint32_t)T;
-  uint32_t k = off;
-  for (int ty = ty0; ty <= ty1; ++ty)
-    for (int tx = tx0; tx <= tx1; ++tx, ++k) {
-      if ((long long)k >= cap) return;
-      keys[k] = base + (uint32_t)(ty * tiles_x + tx);
-      vals[k] = (uint32_t)i;
+  const int lane = threadIdx.x & 31;
+  const int i0 = gt - lane;  // the warp's first record
+  if (i0 >= PN) return;      // whole warps only
+  const int i = i0 + lane;
+  const uint32_t off = i < PN ? offsets[i] : offsets[PN];
+  const uint32_t base = __shfl_sync(0xffffffffu, off, 0);
+  const uint32_t last = offsets[min(i0 + 32, PN)];
+  int tx0 = 0, w = 1, ty0 = 0;
+  if (i < PN && offsets[i + 1] != off) {
+    const float4 c = rec[(size_t)i * DIGS_REC_F4 + 2];
+    const int bx = __float_as_int(c.y), by = __float_as_int(c.z);
+    tx0 = (bx & 0xffff) / tile;
+    ty0 = (by & 0xffff) / tile;
+    w = (bx >> 16) / tile - tx0 + 1;
+  }
+  for (uint32_t k0 = base; k0 < last; k0 += 32) {  // the same trip count on every lane (shuffles below)
+    const uint32_t k = k0 + lane;
+    int r = 0;  // the last lane whose first slot is <= k (records with no slots share their successor's)
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const uint32_t o = __shfl_sync(0xffffffffu, off, r + step);
+      if (o <= k) r += step;
     }
+    const uint32_t t = k - __shfl_sync(0xffffffffu, off, r);
+    const int rw = __shfl_sync(0xffffffffu, w, r), rx0 = __shfl_sync(0xffffffffu, tx0, r);
+    const int ry0 = __shfl_sync(0xffffffffu, ty0, r);
+    const int ty = ry0 + (int)(t / (uint32_t)rw), tx = rx0 + (int)(t % (uint32_t)rw);
+    if (k < last && (long long)k < cap) {
+      const int ri = i0 + r;
+      keys[k] = (uint32_t)(ri / n) * (uint32_t)T + (uint32_t)(ty * tiles_x + tx);
+      vals[k] = (uint32_t)ri;
+    }
+  }
 }
 
 cudaError_t launch_emit(const Workspace& ws, cudaStream_t st) {
