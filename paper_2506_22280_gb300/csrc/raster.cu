@@ -270,6 +270,11 @@ __global__ void __launch_bounds__(FwdCfg<TS>::threads) k_raster_fwd(
     const int cnt = __popc(mask);
     int e = 0;
 #pragma unroll 1
+    for (; e + 3 < cnt; e += 4) {  // four entries per step: four independent dependency chains
+      const f2 va = fwd_pair<COUNT>(ent + e * 5, XX, YY, c2k, n_cut), vb = fwd_pair<COUNT>(ent + e * 5 + 5, XX, YY, c2k, n_cut);
+      const f2 vc = fwd_pair<COUNT>(ent + e * 5 + 10, XX, YY, c2k, n_cut), vd = fwd_pair<COUNT>(ent + e * 5 + 15, XX, YY, c2k, n_cut);
+      ACC = f2_add(f2_add(f2_add(f2_add(ACC, va), vb), vc), vd);  // list order
+    }
     for (; e + 1 < cnt; e += 2) {  // two entries per step: two independent dependency chains
       const f2 va = fwd_pair<COUNT>(ent + e * 5, XX, YY, c2k, n_cut), vb = fwd_pair<COUNT>(ent + e * 5 + 5, XX, YY, c2k, n_cut);
       ACC = f2_add(f2_add(ACC, va), vb);  // list order
