@@ -270,6 +270,13 @@ __global__ void __launch_bounds__(FwdCfg<TS>::threads) k_raster_fwd(
     const int cnt = __popc(mask);
     int e = 0;
 #pragma unroll 1
+    for (; e + 7 < cnt; e += 8) {  // eight entries per step
+      f2 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = fwd_pair<COUNT>(ent + (e + k) * 5, XX, YY, c2k, n_cut);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) ACC = f2_add(ACC, v[k]);  // list order
+    }
     for (; e + 3 < cnt; e += 4) {  // four entries per step: four independent dependency chains
       const f2 va = fwd_pair<COUNT>(ent + e * 5, XX, YY, c2k, n_cut), vb = fwd_pair<COUNT>(ent + e * 5 + 5, XX, YY, c2k, n_cut);
       const f2 vc = fwd_pair<COUNT>(ent + e * 5 + 10, XX, YY, c2k, n_cut), vd = fwd_pair<COUNT>(ent + e * 5 + 15, XX, YY, c2k, n_cut);
