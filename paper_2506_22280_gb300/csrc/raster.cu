@@ -346,7 +346,7 @@ __device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const HalfLanes& B
   const f2 N11 = f2_dup(kNegHalfLog2e * R0.n11), WN1 = f2_dup(R0.wn1);
   const f2 KAPK = f2_dup(R0.kappa * (1.f / kNegHalfLog2e)), MK1 = f2_dup(-1.f - R0.kappa);
   const f2 IK = f2_dup(1.f / kNegHalfLog2e), MONE = f2_dup(-1.f), STEP = f2_dup((float)B.ystep);
-  const float c2k = c2 * kNegHalfLog2e;
+  const f2 C2K = f2_dup(c2 * kNegHalfLog2e);
   const int pstep = B.ystep * nu, d2 = B.pdy * nu + B.pdx, hb = B.col2 ? h - B.pdy : 0;
   f2 DY = f2_pack(dy1, dy1 + (float)B.pdy);
   f2 S0 = f2_dup(0.f), S1 = S0, S2 = S0, S3 = S0, S4 = S0, S5 = S0, S6 = S0;
@@ -354,14 +354,18 @@ __device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const HalfLanes& B
     f2 NUM = f2_fma(DY, f2_fma(N11, DY, BQ), AQ);
     f2 T = f2_fma(WN1, DY, T0);
     f2 D = f2_fma(T, T, f2_mul(KAPK, NUM));
+    // E <= cutoff^2 taken as num <= c2 D (D > 0), i.e. k num >= k c2 D: known before the SFU work, so
+    // the two loads of dL/dI are in flight while it runs
+    f2 LIM = f2_mul(C2K, D);
+    float na, nb, la, lb;
+    f2_unpack(NUM, na, nb);
+    f2_unpack(LIM, la, lb);
+    const float ga = (na >= la) ? __ldg(gp) : 0.f;
+    const float gb = (r < hb && nb >= lb) ? __ldg(gp + d2) : 0.f;  // partner in the box
     f2 RS = f2_rsqrt(D);
     f2 INVD = f2_mul(RS, RS);
     f2 ARG = f2_mul(NUM, INVD);
     f2 BV = f2_mul(RS, f2_exp2(ARG));                      // V / amp
-    float aa, ab;
-    f2_unpack(ARG, aa, ab);
-    const float ga = (aa >= c2k) ? __ldg(gp) : 0.f;                      // E <= cutoff^2
-    const float gb = (r < hb && ab >= c2k) ? __ldg(gp + d2) : 0.f;      // partner in the box
     f2 G = f2_pack(ga, gb);
     S0 = f2_fma(G, BV, S0);
     f2 AL = f2_mul(G, f2_mul(BV, INVD));                     // (dL/dV * V / (2 D)) / (amp / 2)
