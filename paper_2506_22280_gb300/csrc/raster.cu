@@ -138,24 +138,18 @@ struct FwdCfg {
   static constexpr int threads = 32 * warps;
   static constexpr int batch = 32;                              // records a warp stages at a time
   static constexpr int raw_f4 = batch * DIGS_REC_F4;            // staged records
-  static constexpr int ent_f4 = batch * 5;                      // derived entries
+  static constexpr int ent_f4 = batch * 3;                      // derived entries
   static constexpr size_t smem = (size_t)warps * (raw_f4 + ent_f4) * sizeof(float4);
 };
 
-// A staged record -> the entry the pixel loop reads, each constant stored twice so that one 16-byte
-// shared load yields two packed operands:
-//   (k n00, k n00, k n01x2, k n01x2), (k n11, k n11, wn0, wn0), (wn1, wn1, kappa / k, kappa / k),
-//   (amp, amp, -xc, -xc), (-yc, -yc, 0, 0)
+// A staged record -> the entry the pixel loop reads:
+//   (k n00, k n01x2, k n11, wn0), (wn1, kappa / k, amp, -xc), (-yc, 0, 0, 0)
 // with k = -log2(e) / 2, so that the loop forms the exp2 argument k E = k num / D directly.
 __device__ __forceinline__ void derive_entry(const float4* raw, float4* ent) {
   const float4 a = raw[0], b = raw[1], c = raw[2];
-  const float n00 = kNegHalfLog2e * a.z, n01 = kNegHalfLog2e * a.w, n11 = kNegHalfLog2e * b.x;
-  const float kap = b.w * (1.f / kNegHalfLog2e);
-  ent[0] = make_float4(n00, n00, n01, n01);
-  ent[1] = make_float4(n11, n11, b.y, b.y);
-  ent[2] = make_float4(b.z, b.z, kap, kap);
-  ent[3] = make_float4(c.x, c.x, -a.x, -a.x);
-  ent[4] = make_float4(-a.y, -a.y, 0.f, 0.f);
+  ent[0] = make_float4(kNegHalfLog2e * a.z, kNegHalfLog2e * a.w, kNegHalfLog2e * b.x, b.y);
+  ent[1] = make_float4(b.z, b.w * (1.f / kNegHalfLog2e), c.x, -a.x);
+  ent[2] = make_float4(-a.y, 0.f, 0.f, 0.f);
 }
 
 // Whether the pixel rectangle [x0, x1] x [y0, y1] (a block's part of the record's box) can hold a pixel
@@ -197,15 +191,15 @@ __device__ __forceinline__ f2 f2_hi(const float4& v) { return f2_pack(v.z, v.w);
 // V / |X - s| of one entry at the lane's two pixels (XX, YY), zero outside the cutoff (k E < c2k).
 template <bool COUNT>
 __device__ __forceinline__ f2 fwd_pair(const float4* en, f2 XX, f2 YY, float c2k, unsigned& n_cut) {
-  const float4 q0 = en[0], q1 = en[1], q2 = en[2], q3 = en[3], q4 = en[4];
-  const f2 DX = f2_add(XX, f2_hi(q3)), DY = f2_add(YY, f2_lo(q4));
-  const f2 AQ = f2_mul(f2_mul(f2_lo(q0), DX), DX), BQ = f2_mul(f2_hi(q0), DX);
-  const f2 NUM = f2_fma(DY, f2_fma(f2_lo(q1), DY, BQ), AQ);  // k num
-  const f2 T = f2_fma(f2_lo(q2), DY, f2_fma(f2_hi(q1), DX, f2_dup(1.f)));
-  const f2 D = f2_fma(T, T, f2_mul(f2_hi(q2), NUM));
+  const float4 q0 = en[0], q1 = en[1], q2 = en[2];
+  const f2 DX = f2_add(XX, f2_dup(q1.w)), DY = f2_add(YY, f2_dup(q2.x));
+  const f2 AQ = f2_mul(f2_mul(f2_dup(q0.x), DX), DX), BQ = f2_mul(f2_dup(q0.y), DX);
+  const f2 NUM = f2_fma(DY, f2_fma(f2_dup(q0.z), DY, BQ), AQ);  // k num
+  const f2 T = f2_fma(f2_dup(q1.x), DY, f2_fma(f2_dup(q0.w), DX, f2_dup(1.f)));
+  const f2 D = f2_fma(T, T, f2_mul(f2_dup(q1.y), NUM));
   const f2 RS = f2_rsqrt(D);
   const f2 ARG = f2_mul(NUM, f2_mul(RS, RS));                  // k E
-  const f2 VAL = f2_mul(f2_mul(f2_lo(q3), RS), f2_exp2(ARG));
+  const f2 VAL = f2_mul(f2_mul(f2_dup(q1.z), RS), f2_exp2(ARG));
   float aa, ab, va, vb;
   f2_unpack(ARG, aa, ab);
   f2_unpack(VAL, va, vb);
@@ -264,7 +258,7 @@ __global__ void __launch_bounds__(FwdCfg<TS>::threads) k_raster_fwd(
     }
     // the meeting entries, compacted in list order: lane -> slot popc(mask below the lane)
     const unsigned mask = __ballot_sync(0xffffffffu, meets);
-    if (meets) derive_entry(raw + lane * DIGS_REC_F4, ent + __popc(mask & ((1u << lane) - 1u)) * 5);
+    if (meets) derive_entry(raw + lane * DIGS_REC_F4, ent + __popc(mask & ((1u << lane) - 1u)) * 3);
     __syncwarp();
     issue(k0 + C::batch);  // lands while this batch is swept
     const int cnt = __popc(mask);
@@ -273,20 +267,20 @@ __global__ void __launch_bounds__(FwdCfg<TS>::threads) k_raster_fwd(
     for (; e + 7 < cnt; e += 8) {  // eight entries per step
       f2 v[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = fwd_pair<COUNT>(ent + (e + k) * 5, XX, YY, c2k, n_cut);
+      for (int k = 0; k < 8; ++k) v[k] = fwd_pair<COUNT>(ent + (e + k) * 3, XX, YY, c2k, n_cut);
 #pragma unroll
       for (int k = 0; k < 8; ++k) ACC = f2_add(ACC, v[k]);  // list order
     }
     for (; e + 3 < cnt; e += 4) {  // four entries per step: four independent dependency chains
-      const f2 va = fwd_pair<COUNT>(ent + e * 5, XX, YY, c2k, n_cut), vb = fwd_pair<COUNT>(ent + e * 5 + 5, XX, YY, c2k, n_cut);
-      const f2 vc = fwd_pair<COUNT>(ent + e * 5 + 10, XX, YY, c2k, n_cut), vd = fwd_pair<COUNT>(ent + e * 5 + 15, XX, YY, c2k, n_cut);
+      const f2 va = fwd_pair<COUNT>(ent + e * 3, XX, YY, c2k, n_cut), vb = fwd_pair<COUNT>(ent + e * 3 + 3, XX, YY, c2k, n_cut);
+      const f2 vc = fwd_pair<COUNT>(ent + e * 3 + 6, XX, YY, c2k, n_cut), vd = fwd_pair<COUNT>(ent + e * 3 + 9, XX, YY, c2k, n_cut);
       ACC = f2_add(f2_add(f2_add(f2_add(ACC, va), vb), vc), vd);  // list order
     }
     for (; e + 1 < cnt; e += 2) {  // two entries per step: two independent dependency chains
-      const f2 va = fwd_pair<COUNT>(ent + e * 5, XX, YY, c2k, n_cut), vb = fwd_pair<COUNT>(ent + e * 5 + 5, XX, YY, c2k, n_cut);
+      const f2 va = fwd_pair<COUNT>(ent + e * 3, XX, YY, c2k, n_cut), vb = fwd_pair<COUNT>(ent + e * 3 + 3, XX, YY, c2k, n_cut);
       ACC = f2_add(f2_add(ACC, va), vb);  // list order
     }
-    if (e < cnt) ACC = f2_add(ACC, fwd_pair<COUNT>(ent + e * 5, XX, YY, c2k, n_cut));
+    if (e < cnt) ACC = f2_add(ACC, fwd_pair<COUNT>(ent + e * 3, XX, YY, c2k, n_cut));
     __syncwarp();
   }
   cp_async_wait_all();  // the last (empty) group
