@@ -318,19 +318,19 @@ __global__ void __launch_bounds__(kSlots * 32, 3) k_pair_sum(GaussPtrs g, const 
   }
 }
 
-// Second derivatives of u_r at each mean ([18 R][n], see ffd_hessian_point), for the mean's gradient.
-template <int R>
+// Second derivatives of u_r at each mean ([18 R][n], see ffd_hessian_rank), for the mean's gradient:
+// one thread per (Gaussian, rank), the rank from blockIdx.y.
 __global__ void __launch_bounds__(128) k_ffd_hessian(GaussPtrs g, const __grid_constant__ ScanTable sc, LatticeC L,
                                                     const float* __restrict__ phi, float* __restrict__ out) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.n) return;
+  const int r = blockIdx.y;
   const float x[3] = {g.mu0[3 * n], g.mu0[3 * n + 1], g.mu0[3 * n + 2]};
-  float H[R][18];
-  ffd_hessian_point<R>(phi + scan_of(sc, n) * sc.phi_stride, L, x, H);
+  float H[18];
+  const size_t rank_stride = (size_t)L.nx * L.ny * L.nz * 3;
+  ffd_hessian_rank(phi + scan_of(sc, n) * sc.phi_stride + r * rank_stride, L, x, H);
 #pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int c = 0; c < 18; ++c) out[(size_t)(r * 18 + c) * g.n + n] = H[r][c];
+  for (int c = 0; c < 18; ++c) out[(size_t)(r * 18 + c) * g.n + n] = H[c];
 }
 
 // (2) Per Gaussian: from the summed pair adjoints, the FFD backward and the reference-parameter gradients.
@@ -435,7 +435,7 @@ cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const Latt
       configured = true;                                                                                        \
     }                                                                                                           \
   }                                                                                                             \
-  k_ffd_hessian<RR><<<gb, 128, 0, st>>>(g, sc, L, phi, ws.ffd2);                                                \
+  k_ffd_hessian<<<dim3(gb.x, RR), 128, 0, st>>>(g, sc, L, phi, ws.ffd2);                                      \
   k_pair_sum<RR><<<gp, kSlots * 32, pair_sum_smem<RR>(), st>>>(g, sc, ws.ffd, w, views, P, ws.counts, ws.grec,   \
                                                               ws.gsum, ws.gw_part);                            \
   k_gauss_bwd<RR><<<gb, kChainThreads, 0, st>>>(g, sc, L, ws.ffd, ws.ffd2, ws.gsum, dens_grad, g_mu0, g_scale,  \

@@ -92,10 +92,10 @@ __device__ __forceinline__ void ffd_eval_point(const float* __restrict__ phi, co
   }
 }
 
-// Second derivatives d2 u_{r,c} / dx_m dx_j at x: H[r][6 c + s] for s = xx, yy, zz, xy, xz, yz.
-template <int R>
-__device__ __forceinline__ void ffd_hessian_point(const float* __restrict__ phi, const LatticeC& L, const float x[3],
-                                                  float H[R][18]) {
+// Second derivatives d2 u_{r,c} / dx_m dx_j of one rank's field at x (phi_r: that rank's control
+// points): H[6 c + s] for s = xx, yy, zz, xy, xz, yz.
+__device__ __forceinline__ void ffd_hessian_rank(const float* __restrict__ phi_r, const LatticeC& L, const float x[3],
+                                                 float H[18]) {
   int f[3];
   float u[3];
   lattice_cell(L, x, f, u);
@@ -112,10 +112,7 @@ __device__ __forceinline__ void ffd_hessian_point(const float* __restrict__ phi,
     }
   }
 #pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int c = 0; c < 18; ++c) H[r][c] = 0.f;
-  const size_t rank_stride = (size_t)L.nx * L.ny * L.nz * 3;
+  for (int c = 0; c < 18; ++c) H[c] = 0.f;
 #pragma unroll
   for (int n3 = 0; n3 < 4; ++n3) {
     int k = f[2] + n3;
@@ -132,15 +129,12 @@ __device__ __forceinline__ void ffd_hessian_point(const float* __restrict__ phi,
         const float dbx = dB[0][l], dby = dB[1][m], dbz = dB[2][n3];
         const float h[6] = {d2B[0][l] * by * bz, bx * d2B[1][m] * bz, bx * by * d2B[2][n3],
                             dbx * dby * bz,      dbx * by * dbz,      bx * dby * dbz};
-        const float* d = phi + (((size_t)k * L.ny + j) * L.nx + i) * 3;
+        const float* d = phi_r + (((size_t)k * L.ny + j) * L.nx + i) * 3;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
+        for (int c = 0; c < 3; ++c) {
+          const float v = __ldg(d + c);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float v = __ldg(d + r * rank_stride + c);
-#pragma unroll
-            for (int s = 0; s < 6; ++s) H[r][6 * c + s] = fmaf(h[s], v, H[r][6 * c + s]);
-          }
+          for (int s = 0; s < 6; ++s) H[6 * c + s] = fmaf(h[s], v, H[6 * c + s]);
         }
       }
     }
