@@ -50,6 +50,7 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.ranges = (uint2*)take((size_t)P * w.T * sizeof(uint2));
   w.order = (uint32_t*)take((size_t)P * w.T * 4);
   w.grec = (float4*)take(PN * DIGS_PARTIAL_F4 * sizeof(float4));
+  w.bcost = (uint8_t*)take(PN);
   w.bperm = (uint8_t*)take((size_t)P * ((n + 31) / 32) * 32);
   w.gw_part = (float*)take((size_t)pair_sum_blocks(n_total) * P * R * 4 + 4);
   w.loss_part = (float*)take((size_t)P * w.T * fwd_blocks(tile) * 4 + 4);

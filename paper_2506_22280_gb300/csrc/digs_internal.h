@@ -30,7 +30,8 @@ struct Workspace {
   uint2* ranges;          // [P * T] sorted-range of each (projection, tile)
   uint32_t* order;        // [P * T] forward launch order (longest lists first)
   float4* grec;           // [P * n * 3] backward: the ten pixel sums of each (projection, Gaussian) record
-  uint8_t* bperm;         // [P][32 ceil(n / 32)] backward: each group of 32 records in order of sweep passes
+  uint8_t* bcost;         // [P * n] backward sweep cost of each record: box pixels / 32, capped at 255
+  uint8_t* bperm;         // [P][32 ceil(n / 32)] backward: each group of 32 records in order of sweep cost
   float* gw_part;         // [pair-sum CTAs][P][R] dL/dw partial sums
   float* ffd;             // [12 R][n_total]: u_r (3R components) then grad u_r (9R) at each mean
   float* ffd2;            // [18 R][n_total]: second derivatives of u_r (6 per component)

@@ -440,28 +440,13 @@ __device__ __forceinline__ void group_reduce_store10(const float v[10], float* o
   if (store && (LPR == 16 || (threadIdx.x & 16) == 0) && local < (bit2 ? 5 : 3)) out[((hl & 8) ? 5 : 0) + local] = d;
 }
 
-// Sweep passes of a half-warp over a w x h box (the lane layouts of group_lanes<16>, slice by slice).
-__device__ __forceinline__ int bwd_passes16(int w, int h) {
-  int p = 0;
-  for (int cx = 0; cx < w; cx += 16) {
-    const int ws = min(16, w - cx);
-    if (ws <= 8) {
-      const int s2 = 2 * (16 / ws);
-      p += (h + s2 - 1) / s2;
-    } else {
-      const int s = 16 / ((ws + 1) / 2);
-      p += (h + s - 1) / s;
-    }
-  }
-  return p;
-}
-
 // The two records of a backward warp are swept in lockstep, so the warp takes as many passes as the
 // longer of the two.  Each warp here ranks a group of 32 consecutive records of one projection by their
-// pass counts (stable: ties in index order; bit-sliced ballots over a 9-bit key, records past n last)
-// and writes the record of each rank, so that the backward pairs records of adjacent ranks.
+// sweep cost (box pixels / 32, written by the set-up: the pass count up to the lane layout's rounding;
+// stable: ties in index order; bit-sliced ballots over a 9-bit key, records past n last) and writes
+// the record of each rank, so that the backward pairs records of adjacent ranks.
 // Grid: (ceil(G / 8), P) with G = ceil(n / 32) groups per projection; 256 threads.
-__global__ void __launch_bounds__(256) k_bwd_pairing(const float4* __restrict__ rec, const uint32_t* __restrict__ counts,
+__global__ void __launch_bounds__(256) k_bwd_pairing(const uint8_t* __restrict__ cost, const uint32_t* __restrict__ counts,
                                                      int N, int G, uint8_t* __restrict__ perm) {
   const int lane = threadIdx.x & 31;
   const int g = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -471,12 +456,7 @@ __global__ void __launch_bounds__(256) k_bwd_pairing(const float4* __restrict__ 
   unsigned key = 511u;
   if (n < N) {
     const size_t i = (size_t)b * N + n;
-    key = 0u;
-    if (counts[i] != 0u) {
-      const float4 c = rec[i * DIGS_REC_F4 + 2];
-      const int bx = __float_as_int(c.y), by = __float_as_int(c.z);
-      key = (unsigned)min(bwd_passes16((bx >> 16) - (bx & 0xffff) + 1, (by >> 16) - (by & 0xffff) + 1), 510);
-    }
+    key = counts[i] != 0u ? (unsigned)cost[i] : 0u;  // padding records of smaller scans have no tiles
   }
   unsigned lt = 0u, eq = 0xffffffffu;  // lanes with a smaller key; lanes whose key agrees so far
 #pragma unroll
@@ -596,7 +576,7 @@ cudaError_t launch_raster_bwd(const Workspace& ws, const ViewsParam& views, floa
                                                    (float*)ws.grec);
   } else {
     const int G = (ws.n + 31) / 32;
-    k_bwd_pairing<<<dim3((G + 7) / 8, ws.P), 256, 0, st>>>(ws.rec, ws.counts, ws.n, G, ws.bperm);
+    k_bwd_pairing<<<dim3((G + 7) / 8, ws.P), 256, 0, st>>>(ws.bcost, ws.counts, ws.n, G, ws.bperm);
     note_launches(1);
     dim3 grid((ws.n + kBwdThreads / 16 - 1) / (kBwdThreads / 16), ws.P);
     k_raster_bwd<16><<<grid, kBwdThreads, 0, st>>>(ws.rec, ws.counts, ws.n, ws.nu, ws.nv, ws.dldi, c2, ws.bperm,
