@@ -335,76 +335,68 @@ __global__ void __launch_bounds__(128) k_ffd_hessian(GaussPtrs g, const __grid_c
 
 // (2) Per Gaussian: from the summed pair adjoints, the FFD backward and the reference-parameter gradients.
 template <int R>
-__global__ void __launch_bounds__(kChainThreads) k_gauss_bwd(
+__global__ void __launch_bounds__(32 * R, 4) k_gauss_bwd(
     GaussPtrs g, const __grid_constant__ ScanTable sc, LatticeC L, const float* __restrict__ ffd,
     const float* __restrict__ ffd2,
     const float* __restrict__ gsum, float* __restrict__ dens_grad, float* __restrict__ g_mu0,
     float* __restrict__ g_scale, float* __restrict__ g_quat, float* __restrict__ g_rho, float* __restrict__ g_phi) {
-  __shared__ float Gs[12 * R * kChainThreads];  // dL/du_r (3R) then dL/d(grad u_r) (9R), thread-fastest
-  constexpr int ST = kChainThreads;
+  // warp r takes rank r of the CTA's 32 Gaussians: dL/du_r (3) then dL/d(grad u_r) (9), lane-fastest
+  __shared__ float Gs[R][12 * 32];
+  __shared__ float gpart[R][3][32];  // each rank's share of dL/dmu0
   const int N = g.n;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, r = (int)(threadIdx.x >> 5);
+  const int n = blockIdx.x * 32 + lane;
   const bool valid = n < N;
   const int scan = valid ? scan_of(sc, n) : 0;
-  float GU[R][3], GdU[R][9], gmu0[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gR[9], grho = 0.f;
+  float GU[3] = {0.f, 0.f, 0.f}, GdU[9], gm[3] = {0.f, 0.f, 0.f}, mu0[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) GU[r][c] = 0.f;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) GdU[r][c] = 0.f;
-  }
-#pragma unroll
-  for (int c = 0; c < 9; ++c) gR[c] = 0.f;
+  for (int c = 0; c < 9; ++c) GdU[c] = 0.f;
   if (valid) {
     const float* q = gsum + n;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      gmu0[c] = q[(size_t)c * N];
-      gs[c] = q[(size_t)(3 + c) * N];
-    }
+    for (int c = 0; c < 3; ++c) GU[c] = q[(size_t)(16 + 3 * r + c) * N];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) gR[c] = q[(size_t)(6 + c) * N];
-    grho = q[(size_t)15 * N];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) GU[r][c] = q[(size_t)(16 + 3 * r + c) * N];
-#pragma unroll
-      for (int c = 0; c < 9; ++c) GdU[r][c] = q[(size_t)(16 + 3 * R + 9 * r + c) * N];
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) Gs[(r * 3 + c) * ST + threadIdx.x] = GU[r][c];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) Gs[(3 * R + r * 9 + c) * ST + threadIdx.x] = GdU[r][c];
-  }
-  float mu0[3] = {0.f, 0.f, 0.f};
-  if (valid) {
+    for (int c = 0; c < 9; ++c) GdU[c] = q[(size_t)(16 + 3 * R + 9 * r + c) * N];
 #pragma unroll
     for (int c = 0; c < 3; ++c) mu0[c] = g.mu0[3 * n + c];
-    // u_r and grad u_r are evaluated at mu0: dL/dmu0 += sum_r (grad u_r)^T dL/du_r + H_r : dL/d(grad u_r)
+    // u_r and grad u_r are evaluated at mu0: dL/dmu0 += (grad u_r)^T dL/du_r + H_r : dL/d(grad u_r)
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float* du = ffd + (size_t)(3 * R + r * 9 + c * 3) * N + n;   // d u_rc / dx_m, m = 0..2
-        const float* h = ffd2 + (size_t)(r * 18 + c * 6) * N + n;          // xx, yy, zz, xy, xz, yz
-        const float hxx = h[0], hyy = h[(size_t)N], hzz = h[(size_t)2 * N];
-        const float hxy = h[(size_t)3 * N], hxz = h[(size_t)4 * N], hyz = h[(size_t)5 * N];
-        const float g0 = GdU[r][3 * c], g1 = GdU[r][3 * c + 1], g2 = GdU[r][3 * c + 2];
-        gmu0[0] += du[0] * GU[r][c] + hxx * g0 + hxy * g1 + hxz * g2;
-        gmu0[1] += du[(size_t)N] * GU[r][c] + hxy * g0 + hyy * g1 + hyz * g2;
-        gmu0[2] += du[(size_t)2 * N] * GU[r][c] + hxz * g0 + hyz * g1 + hzz * g2;
-      }
+    for (int c = 0; c < 3; ++c) {
+      const float* du = ffd + (size_t)(3 * R + r * 9 + c * 3) * N + n;   // d u_rc / dx_m, m = 0..2
+      const float* h = ffd2 + (size_t)(r * 18 + c * 6) * N + n;          // xx, yy, zz, xy, xz, yz
+      const float hxx = h[0], hyy = h[(size_t)N], hzz = h[(size_t)2 * N];
+      const float hxy = h[(size_t)3 * N], hxz = h[(size_t)4 * N], hyz = h[(size_t)5 * N];
+      const float g0 = GdU[3 * c], g1 = GdU[3 * c + 1], g2 = GdU[3 * c + 2];
+      gm[0] += du[0] * GU[c] + hxx * g0 + hxy * g1 + hxz * g2;
+      gm[1] += du[(size_t)N] * GU[c] + hxy * g0 + hyy * g1 + hyz * g2;
+      gm[2] += du[(size_t)2 * N] * GU[c] + hxz * g0 + hyz * g1 + hzz * g2;
     }
   }
-  // each thread reads back only its own column of Gs, so no barrier is needed
-  ffd_scatter_warp<R>(g_phi, sc.phi_stride, scan, L, mu0, valid, Gs + threadIdx.x, Gs + 3 * R * ST + threadIdx.x,
-                      ST);
-  if (!valid) return;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Gs[r][c * 32 + lane] = GU[c];
+    gpart[r][c][lane] = gm[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) Gs[r][(3 + c) * 32 + lane] = GdU[c];
+  // each lane reads back only its own column of Gs[r], so no barrier is needed before the scatter
+  const size_t rank_stride = (size_t)L.nx * L.ny * L.nz * 3;
+  ffd_scatter_warp<1>(g_phi + r * rank_stride, sc.phi_stride, scan, L, mu0, valid, &Gs[r][lane], &Gs[r][3 * 32 + lane],
+                      32);
+  __syncthreads();
+  if (r != 0 || !valid) return;
+  const float* q = gsum + n;
+  float gmu0[3], gs[3], gR[9];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    gmu0[c] = q[(size_t)c * N];
+#pragma unroll
+    for (int k = 0; k < R; ++k) gmu0[c] += gpart[k][c][lane];
+    gs[c] = q[(size_t)(3 + c) * N];
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) gR[c] = q[(size_t)(6 + c) * N];
+  const float grho = q[(size_t)15 * N];
   float qh[4], gq[4];
   const float q0 = g.quat[4 * n], q1 = g.quat[4 * n + 1], q2 = g.quat[4 * n + 2], q3 = g.quat[4 * n + 3];
   const float qn = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
@@ -438,7 +430,8 @@ cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const Latt
   k_ffd_hessian<<<dim3(gb.x, RR), 128, 0, st>>>(g, sc, L, phi, ws.ffd2);                                      \
   k_pair_sum<RR><<<gp, kSlots * 32, pair_sum_smem<RR>(), st>>>(g, sc, ws.ffd, w, views, P, ws.counts, ws.grec,   \
                                                               ws.gsum, ws.gw_part);                            \
-  k_gauss_bwd<RR><<<gb, kChainThreads, 0, st>>>(g, sc, L, ws.ffd, ws.ffd2, ws.gsum, dens_grad, g_mu0, g_scale,  \
+  k_gauss_bwd<RR><<<(g.n + 31) / 32, 32 * RR, 0, st>>>(g, sc, L, ws.ffd, ws.ffd2, ws.gsum, dens_grad, g_mu0,     \
+                                                       g_scale,                                              \
                                                g_quat, g_rho, g_phi)
   switch (L.R) {
     case 1: DIGS_CH(1); break;
