@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
   hist[s.hbase + threadIdx.x * s.nb + s.j] = h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint32_t* __restrict__ kin,
                                                                const uint32_t* __restrict__ vin,
                                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                                const uint32_t* __restrict__ seg, int P, int T, int shift,
