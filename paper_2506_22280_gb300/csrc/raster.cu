@@ -190,12 +190,14 @@ __device__ __forceinline__ f2 f2_hi(const float4& v) { return f2_pack(v.z, v.w);
 
 // V / |X - s| of one entry at the lane's two pixels (XX, YY), zero outside the cutoff (k E < c2k).
 template <bool COUNT>
-__device__ __forceinline__ f2 fwd_pair(const float4* en, f2 XX, f2 YY, float c2k, unsigned& n_cut) {
+__device__ __forceinline__ f2 fwd_pair(const float4* en, float xx, f2 YY, float c2k, unsigned& n_cut) {
   const float4 q0 = en[0], q1 = en[1], q2 = en[2];
-  const f2 DX = f2_add(XX, f2_dup(q1.w)), DY = f2_add(YY, f2_dup(q2.x));
-  const f2 AQ = f2_mul(f2_mul(f2_dup(q0.x), DX), DX), BQ = f2_mul(f2_dup(q0.y), DX);
-  const f2 NUM = f2_fma(DY, f2_fma(f2_dup(q0.z), DY, BQ), AQ);  // k num
-  const f2 T = f2_fma(f2_dup(q1.x), DY, f2_fma(f2_dup(q0.w), DX, f2_dup(1.f)));
+  // the lane's two pixels share their column: the dx terms are scalars
+  const float dx = xx + q1.w;
+  const float aq = q0.x * dx * dx, bq = q0.y * dx, t0 = fmaf(q0.w, dx, 1.f);
+  const f2 DY = f2_add(YY, f2_dup(q2.x));
+  const f2 NUM = f2_fma(DY, f2_fma(f2_dup(q0.z), DY, f2_dup(bq)), f2_dup(aq));  // k num
+  const f2 T = f2_fma(f2_dup(q1.x), DY, f2_dup(t0));
   const f2 D = f2_fma(T, T, f2_mul(f2_dup(q1.y), NUM));
   const f2 RS = f2_rsqrt(D);
   const f2 ARG = f2_mul(NUM, f2_mul(RS, RS));                  // k E
@@ -228,7 +230,8 @@ __global__ void __launch_bounds__(FwdCfg<TS>::threads) k_raster_fwd(
   const int b = (int)(bt / (uint32_t)T), tile = (int)(bt % (uint32_t)T);
   const int qx = (tile % tiles_x) * TS + (warp % C::blocks_x) * 8, qy = (tile / tiles_x) * TS + (warp / C::blocks_x) * 8;
   const int px = qx + (lane & 7), py = qy + (lane >> 3);  // the lane's pixels: (px, py) and (px, py + 4)
-  const f2 XX = f2_dup((float)px), YY = f2_pack((float)py, (float)(py + 4));
+  const float XX = (float)px;
+  const f2 YY = f2_pack((float)py, (float)(py + 4));
   const uint2 rg = ranges[(size_t)b * T + tile];
   const float c2k = c2 * kNegHalfLog2e;
   f2 ACC = f2_dup(0.f);
