@@ -10,7 +10,9 @@ Prints ONE JSON line (rank 0).  ``value`` = projections processed by all ranks /
 summed device time of the timed steps (CUDA events around each step; L2 is flushed between steps by a
 512 MB write outside the events).  ``e2e`` times the same steps end to end by the wall clock: every step's
 host-to-device copy of the batch's measured projections from pinned memory (on a copy stream, double
-buffered so that it overlaps the previous step), the step, and a device-to-host read of its loss.
+buffered so that it overlaps the previous step), the step (replayed from a graph captured on the device
+buffer its copy lands in, as in the device-timed loop; direct calls with --no-graph), and a
+device-to-host read of its loss.
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload instead.
 Multi-GPU (torchrun): every rank reconstructs its own independent scan (no data-path collective).
 """
@@ -580,6 +582,9 @@ def run_ours(args):
         # (step s's loss is read once step s + 1 has been launched)
         host = [m.cpu().pin_memory() for m in mb[T0:T0 + K]]
         bufs = [torch.empty_like(mb[0]) for _ in range(2)]
+        # as in the device-timed loop, each step is a replay of its captured graph (which reads the device
+        # input buffer its copy lands in)
+        graphs_e2e = rec.capture([(bufs[s % 2], plan[T0 + s], views[T0 + s]) for s in range(K)]) if use_graph else None
         loss_host = torch.empty(K, dtype=torch.float32).pin_memory()
         copy_stream = torch.cuda.Stream(device=device)
         main = torch.cuda.current_stream(device)
@@ -605,7 +610,11 @@ def run_ours(args):
             if s + 1 < K:
                 copy_in(s + 1)
             main.wait_event(copied[s % 2])
-            loss = rec.step(bufs[s % 2], plan[T0 + s], views[T0 + s], varr=varrs[T0 + s])
+            if graphs_e2e is not None:
+                graphs_e2e[s].replay()
+                loss = rec.loss
+            else:
+                loss = rec.step(bufs[s % 2], plan[T0 + s], views[T0 + s], varr=varrs[T0 + s])
             used[s % 2].record(main)
             loss_host[s:s + 1].copy_(loss.reshape(-1)[:1], non_blocking=True)
             read[s].record(main)
