@@ -95,10 +95,16 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
   h[threadIdx.x] = 0u;
   __syncthreads();
   const uint32_t kb = (uint32_t)s.b * (uint32_t)T;
-#pragma unroll 4
+  uint32_t k[kSortItems];  // every load issued before the first use
+#pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint32_t idx = s.lo + (uint32_t)(i * kSortThreads) + threadIdx.x;
-    if (idx < s.hi) atomicAdd(&h[((keys[idx] - kb) >> shift) & 255u], 1u);
+    k[i] = idx < s.hi ? keys[idx] : 0u;
+  }
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint32_t idx = s.lo + (uint32_t)(i * kSortThreads) + threadIdx.x;
+    if (idx < s.hi) atomicAdd(&h[((k[i] - kb) >> shift) & 255u], 1u);
   }
   __syncthreads();
   hist[s.hbase + threadIdx.x * s.nb + s.j] = h[threadIdx.x];
@@ -126,11 +132,16 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint32_t
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
 #pragma unroll
-  for (int it = 0; it < kSortItems; ++it) {
+  for (int it = 0; it < kSortItems; ++it) {  // every load issued before the ranking needs the first
     const uint32_t idx = run + (uint32_t)(it * 32 + lane);
     const bool valid = idx < s.hi;
     key[it] = valid ? kin[idx] : 0u;
     val[it] = valid ? vin[idx] : 0u;
+  }
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    const uint32_t idx = run + (uint32_t)(it * 32 + lane);
+    const bool valid = idx < s.hi;
     const uint32_t d = valid ? (((key[it] - kb) >> shift) & 255u) : 256u;  // 256: sentinel for the ragged tail
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t before = __popc(peers & lt_mask);
