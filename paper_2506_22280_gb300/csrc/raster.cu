@@ -9,18 +9,18 @@
 //
 // Forward: one CTA per (projection, tile) and one warp per 8 x 8 block of the tile; each lane owns two
 // pixels of the block and keeps their sums in registers.  Every warp walks the tile's sorted Gaussian
-// list in batches of 32 records staged by cp.async, keeps the Gaussians whose pixel box meets its block
-// and sweeps them in list order, two at a time: no canvas, no atomics, deterministic sums.  CTAs start
-// in order of decreasing list length.
+// list in batches of 32 records staged by cp.async, keeps the Gaussians whose cutoff ellipse meets its
+// block and sweeps them eight at a time, summed in list order: no canvas, no atomics, deterministic sums.
+// CTAs start in order of decreasing list length.
 //
-// Backward: needs no tile lists.  One half-warp (16 lanes) per (projection, Gaussian) record sweeps the
-// record's whole pixel box in 16-column slices, reading g = dL/dI * |X - s| straight from the
-// projection-sized image (L1/L2 resident).  Narrow slices (w <= 8): lane l owns column (l mod w),
-// starts at row (l div w) and takes the row pair (r, r + s), s = 16 div w, stepping 2s rows; wider
-// slices: the column pair (c, c + ceil(w/2)) of row (l div ceil(w/2)), stepping s = 16 div ceil(w/2)
-// rows.  Each lane accumulates seven sums per pixel of its pair and turns them into the ten sufficient
-// statistics of the record gradient; the half-warp reduces them with an 11-shuffle recursive halving
-// and ten lanes write them to the record's slot (no atomics).
+// Backward: needs no tile lists.  One half-warp per (projection, Gaussian) record (the two records of a
+// warp of similar box size, paired by k_bwd_pairing) sweeps the record's pixel box in 16-column slices,
+// reading g = dL/dI * |X - s| from the projection-sized image (L1/L2 resident).  Narrow slices (w <= 8):
+// lane l owns column (l mod w), starts at row (l div w) and takes the row pair (r, r + s), s = 16 div w,
+// stepping 2s rows; wider slices: the column pair (c, c + ceil(w/2)) of row (l div ceil(w/2)), stepping
+// s = 16 div ceil(w/2) rows.  Each lane accumulates seven sums per pixel of its pair and turns them into
+// the ten sufficient statistics of the record gradient; the half-warp reduces them with an 11-shuffle
+// recursive halving and ten lanes write them to the record's slot (no atomics).
 #include <algorithm>
 
 #include "digs_internal.h"
