@@ -62,7 +62,8 @@ size_t scan_tmp_words(int n);
 // sort.cu: stable sort of the pair keys (projection * T + tile) with their record values, the pairs being
 // grouped by projection as the emit step writes them (projection b's start is offsets[b * n]); count
 // read from the device; also writes ranges[P * T].  Returns via *out_keys / *out_vals which of the two
-// buffers holds the result.  seg: 2P + 2 words; hist: 256 * n_blocks + 1 words, n_blocks = sort_blocks.
+// buffers holds the result (*out_keys = nullptr after a single pass, T <= 256: the sorted keys are then
+// not written, only the ranges are needed).  seg: 2P + 2 words; hist: 256 * n_blocks + 1 words, n_blocks = sort_blocks.
 cudaError_t sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, const uint32_t* n_dev,
                        long long cap, const uint32_t* offsets, int n, int P, int T, int n_blocks, uint32_t* seg,
                        uint32_t* hist, uint32_t* scan_tmp, uint2* ranges, uint32_t** out_keys, uint32_t** out_vals,

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint32_t
     const uint32_t k = sk[i];
     const uint32_t d = ((k - kb) >> shift) & 255u;
     const uint32_t pos = dbase[d] + (i - loff[d]);
-    kout[pos] = k;
+    if (kout) kout[pos] = k;
     vout[pos] = sv[i];
   }
 }
@@ -232,12 +232,13 @@ cudaError_t sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint3
     k_sort_hist<<<n_blocks, kSortThreads, 0, st>>>(ki, seg, P, T, shift, hist);
     cudaError_t e = exclusive_scan(hist, hist, 256 * n_blocks, scan_tmp, st);
     if (e != cudaSuccess) return e;
-    k_sort_scatter<<<n_blocks, kSortThreads, 0, st>>>(ki, vi, ko, vo, seg, P, T, shift, hist);
+    // with one pass the sorted keys are not needed (the ranges come from the scanned histogram)
+    k_sort_scatter<<<n_blocks, kSortThreads, 0, st>>>(ki, vi, bits > 8 ? ko : nullptr, vo, seg, P, T, shift, hist);
     note_launches(2);
     uint32_t* t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
   }
-  *out_keys = ki;
+  *out_keys = bits > 8 ? ki : nullptr;
   *out_vals = vi;
   if (bits <= 8) {
     k_sort_ranges<<<(P * T + 255) / 256, 256, 0, st>>>(hist, seg, P, T, ranges);
