@@ -248,8 +248,10 @@ __global__ void __launch_bounds__(kSlots * 32, 3) k_pair_sum(GaussPtrs g, const 
   const bool valid = n < N;
   const int scan = valid ? scan_of(sc, n) : 0, nl = n - sc.off[scan];
   float* my = acc + slot * 32 + lane;
+  if (slot >= P) {  // a slot with no projection keeps a zero column
 #pragma unroll
-  for (int q = 0; q < Q; ++q) my[q * QS] = 0.f;
+    for (int q = 0; q < Q; ++q) my[q * QS] = 0.f;
+  }
   float mu0[3] = {0.f, 0.f, 0.f}, inv_s[3] = {1.f, 1.f, 1.f}, Rm[9], rho = 0.f;
   if (valid) {
 #pragma unroll
@@ -272,6 +274,11 @@ __global__ void __launch_bounds__(kSlots * 32, 3) k_pair_sum(GaussPtrs g, const 
 #pragma unroll
     for (int r = 0; r < R; ++r) gw[r] = 0.f;
     const size_t i = (size_t)b * NM + nl;
+    const bool first = b0 == 0;  // the slot's first projection writes its column, later ones add to it
+    auto put = [&](int q, float x) {
+      if (first) my[q * QS] = x;
+      else my[q * QS] += x;
+    };
     if (valid && v.scan == scan && counts[i] != 0u) {  // else the pair was culled by the projection set-up
       float S[10];
       {
@@ -287,20 +294,23 @@ __global__ void __launch_bounds__(kSlots * 32, 3) k_pair_sum(GaussPtrs g, const 
       pair_adjoint<R>(v, ffd, N, n, wr, mu0, inv_s, Rm, rho, S, gmu, gK, gs, gR, grho, gw);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        my[c * QS] += gmu[c];
-        my[(3 + c) * QS] += gs[c];
+        put(c, gmu[c]);
+        put(3 + c, gs[c]);
       }
 #pragma unroll
-      for (int c = 0; c < 9; ++c) my[(6 + c) * QS] += gR[c];
-      my[15 * QS] += grho;
+      for (int c = 0; c < 9; ++c) put(6 + c, gR[c]);
+      put(15, grho);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) my[(16 + 3 * r + c) * QS] += wr[r] * gmu[c];
+        for (int c = 0; c < 3; ++c) put(16 + 3 * r + c, wr[r] * gmu[c]);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) my[(16 + 3 * R + 9 * r + c) * QS] += wr[r] * gK[c];
+        for (int c = 0; c < 9; ++c) put(16 + 3 * R + 9 * r + c, wr[r] * gK[c]);
       }
-      my[(16 + 12 * R) * QS] += sqrtf(gmu[0] * gmu[0] + gmu[1] * gmu[1] + gmu[2] * gmu[2]);
+      put(16 + 12 * R, sqrtf(gmu[0] * gmu[0] + gmu[1] * gmu[1] + gmu[2] * gmu[2]));
+    } else if (first) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) my[q * QS] = 0.f;
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
