@@ -38,8 +38,13 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.counters = (unsigned long long*)(w.status ? (char*)w.status + 128 : nullptr);
   w.rec = (float4*)take(PN * DIGS_REC_F4 * sizeof(float4));
   w.counts = (uint32_t*)take((PN + 1) * 4);
+  w.n_chunks = bin_chunks(n, w.T);
+  const size_t chist_n = (size_t)P * w.T * std::max(w.n_chunks, 0);
+  w.tbox = (uint2*)take(PN * sizeof(uint2));
+  w.chist = (uint32_t*)take((chist_n + 1) * 4);
   w.offsets = (uint32_t*)take((PN + 1) * 4);
   size_t tmp = std::max(scan_tmp_words((int)PN), scan_tmp_words(256 * std::max(w.n_sort_blocks, 1)));
+  tmp = std::max(tmp, scan_tmp_words((int)chist_n));
   w.scan_tmp = (uint32_t*)take(tmp * 4);
   w.keys = (uint32_t*)take((size_t)cap * 4);
   w.vals = (uint32_t*)take((size_t)cap * 4);
@@ -267,13 +272,19 @@ digs_status bin(Call& c, const float* phi, const float* w) {
   Workspace& ws = c.ws;
   digs_status s = prep(c, phi, w);
   if (s != DIGS_OK) return s;
-  DIGS_TRY(exclusive_scan(ws.counts, ws.offsets, c.P * ws.n, ws.scan_tmp, c.st));
-  DIGS_TRY(launch_emit(ws, c.st));
-  mark(c, 2);
-  uint32_t *sk = nullptr, *sv = nullptr;
-  DIGS_TRY(sort_pairs(ws.keys, ws.vals, ws.keys_alt, ws.vals_alt, ws.n_pairs, ws.cap, ws.offsets, ws.n, c.P, ws.T,
-                      ws.n_sort_blocks, ws.seg, ws.hist, ws.scan_tmp, ws.ranges, &sk, &sv, c.st));
-  ws.srid = sv;
+  if (ws.n_chunks >= 0) {  // counting sort straight from the records (T <= kDirectMaxTiles)
+    DIGS_TRY(bin_direct(ws, c.st));
+    ws.srid = ws.vals;
+    mark(c, 2);
+  } else {  // emitted (key, record) pairs and a radix sort of the tile index
+    DIGS_TRY(exclusive_scan(ws.counts, ws.offsets, c.P * ws.n, ws.scan_tmp, c.st));
+    DIGS_TRY(launch_emit(ws, c.st));
+    mark(c, 2);
+    uint32_t *sk = nullptr, *sv = nullptr;
+    DIGS_TRY(sort_pairs(ws.keys, ws.vals, ws.keys_alt, ws.vals_alt, ws.n_pairs, ws.cap, ws.offsets, ws.n, c.P,
+                        ws.T, ws.n_sort_blocks, ws.seg, ws.hist, ws.scan_tmp, ws.ranges, &sk, &sv, c.st));
+    ws.srid = sv;
+  }
   DIGS_TRY(tile_order(ws.ranges, c.P * ws.T, ws.order, c.st));
   mark(c, 3);
   return DIGS_OK;

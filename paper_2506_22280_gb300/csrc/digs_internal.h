@@ -18,6 +18,8 @@ struct Workspace {
   unsigned long long* counters;  // [2] forward raster: box pairs evaluated, pairs within the cutoff
   float4* rec;            // [P * n * 3]
   uint32_t* counts;       // [P * n + 1] tiles touched per (projection, Gaussian)
+  uint2* tbox;            // [P * n] tile rectangle of each record: (tx0 | ty0 << 16, tx1 | ty1 << 16)
+  uint32_t* chist;        // [P * T * chunks + 1] direct binning: pairs per (projection, tile, record chunk), then their scan
   uint32_t* offsets;      // [P * n + 1] exclusive scan of counts (offsets[P*n] = total)
   uint32_t* scan_tmp;     // block sums of the scans
   uint32_t* keys;         // [cap] (projection, tile) key per pair
@@ -47,6 +49,7 @@ struct Workspace {
   int n_total;                                     // Gaussians of all scans
   int bwd_lanes;                                   // lanes per record in the backward raster (16 or 32)
   int n_sort_blocks;
+  int n_chunks;                                    // record chunks of the direct binning (-1: radix-sort path)
 };
 
 // Forward work items (8 x 8 pixel blocks) per tile.
@@ -72,6 +75,11 @@ cudaError_t sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint3
 cudaError_t tile_ranges(const uint32_t* sorted_keys, const uint32_t* n_dev, long long cap, uint2* ranges,
                         int n_ranges, cudaStream_t st);
 int sort_blocks(long long cap, int P);
+// Direct binning (T <= kDirectMaxTiles): counting sort of the (projection, tile) pairs straight from the
+// records' tile rectangles into ws.vals, plus ranges, pair counts and the capacity flag.
+constexpr int kDirectMaxTiles = 1024;
+int bin_chunks(int n, int T);
+cudaError_t bin_direct(const Workspace& ws, cudaStream_t st);
 // order[P * T]: (projection, tile) indices by descending range length (power-of-two classes).
 cudaError_t tile_order(const uint2* ranges, int n, uint32_t* order, cudaStream_t st);
 

@@ -67,7 +67,8 @@ template <int R>
 __global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, const __grid_constant__ ScanTable sc, LatticeC L, const float* __restrict__ phi,
                                                   const float* __restrict__ w, const __grid_constant__ ViewsParam views,
                                                   int P, float c2, int tile, int tiles_x, float4* __restrict__ rec,
-                                                  uint32_t* __restrict__ counts, uint8_t* __restrict__ bcost,
+                                                  uint32_t* __restrict__ counts, uint2* __restrict__ tbox,
+                                                  uint8_t* __restrict__ bcost,
                                                   float* __restrict__ ffd_out, int* status) {
   const int gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= g.n) return;
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, const __grid_cons
     float detK = inv3(K, Ki);
     Rec r;
     uint32_t cnt = 0, cost = 0;
+    uint2 tb = make_uint2(0u, 0u);
     bool alive = finite_in && detK > DIGS_FOLD_EPS;
     if (alive) {
       make_A(G.inv_s, G.R, Ki, A);
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, const __grid_cons
     if (alive) {
       int x0 = r.bx & 0xffff, x1 = r.bx >> 16, y0 = r.by & 0xffff, y1 = r.by >> 16;
       cnt = (uint32_t)((x1 / tile - x0 / tile + 1) * (y1 / tile - y0 / tile + 1));
+      tb = make_uint2((uint32_t)(x0 / tile) | ((uint32_t)(y0 / tile) << 16), (uint32_t)(x1 / tile) | ((uint32_t)(y1 / tile) << 16));
       cost = min(((uint32_t)(x1 - x0 + 1) * (uint32_t)(y1 - y0 + 1) + 31u) >> 5, 255u);  // backward passes
     } else {
       r = Rec{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0, 0};
@@ -123,6 +126,7 @@ __global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, const __grid_cons
     size_t idx = (size_t)b * sc.nmax + n;
     store_rec(rec + idx * DIGS_REC_F4, r);
     counts[idx] = cnt;
+    tbox[idx] = tb;
     bcost[idx] = (uint8_t)cost;
   }
 }
@@ -138,7 +142,7 @@ cudaError_t launch_prep_fwd(const GaussPtrs& g, const ScanTable& sc, const Latti
   dim3 grid((g.n + 127) / 128);
 #define DIGS_PREP(RR)                                                                                          \
   k_prep_fwd<RR><<<grid, 128, 0, st>>>(g, sc, L, phi, w, views, P, c2, ws.tile, ws.tiles_x, ws.rec, ws.counts, \
-                                       ws.bcost, ws.ffd, ws.status)
+                                       ws.tbox, ws.bcost, ws.ffd, ws.status)
   switch (L.R) {
     case 1: DIGS_PREP(1); break;
     case 2: DIGS_PREP(2); break;

@@ -269,6 +269,134 @@ cudaError_t tile_ranges(const uint32_t* sorted_keys, const uint32_t* n_dev, long
   return cudaGetLastError();
 }
 
+// ---- direct binning: a counting sort of the (projection, tile) pairs, for T <= kDirectMaxTiles ----
+// The records of a projection are cut into chunks of kBinChunk; k_bin_count counts each chunk's pairs per
+// tile, a scan over (projection, tile, chunk) turns the counts into positions, and k_bin_scatter writes
+// every pair's record id at its position: tile lists hold their records by chunk, then warp, then the
+// pair's place in its record's tile rectangle (row-major), then lane -- a fixed order, so the forward's
+// sums stay deterministic.  No keys are written and nothing is sorted.
+constexpr int kBinChunk = 256;
+constexpr int kBinWarps = kBinChunk / 32;
+
+int bin_chunks(int n, int T) { return T <= kDirectMaxTiles ? (n + kBinChunk - 1) / kBinChunk : -1; }
+
+__device__ __forceinline__ void unpack_tbox(uint2 v, int& tx0, int& ty0, int& tx1, int& ty1) {
+  tx0 = (int)(v.x & 0xffffu); ty0 = (int)(v.x >> 16); tx1 = (int)(v.y & 0xffffu); ty1 = (int)(v.y >> 16);
+}
+
+// Grid (chunks, P): chist[(b T + t) C + c] = pairs of tile t among chunk c's records of projection b.
+__global__ void __launch_bounds__(kBinChunk) k_bin_count(const uint2* __restrict__ tbox,
+                                                         const uint32_t* __restrict__ counts, int N, int T,
+                                                         int tiles_x, int C, uint32_t* __restrict__ chist) {
+  __shared__ uint32_t h[kDirectMaxTiles];
+  const int c = blockIdx.x, b = blockIdx.y;
+  for (int t = threadIdx.x; t < T; t += kBinChunk) h[t] = 0u;
+  __syncthreads();
+  const int n = c * kBinChunk + threadIdx.x;
+  if (n < N) {
+    const size_t i = (size_t)b * N + n;
+    if (counts[i] != 0u) {
+      int tx0, ty0, tx1, ty1;
+      unpack_tbox(tbox[i], tx0, ty0, tx1, ty1);
+      for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&h[ty * tiles_x + tx], 1u);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < T; t += kBinChunk) chist[((size_t)b * T + t) * C + c] = h[t];
+}
+
+// Grid (chunks, P): every pair's record id b N + n at its position (cscan: the scanned chist).  Pairs at
+// or past cap are dropped (k_bin_ranges flags them).
+__global__ void __launch_bounds__(kBinChunk) k_bin_scatter(const uint2* __restrict__ tbox,
+                                                           const uint32_t* __restrict__ counts, int N, int T,
+                                                           int tiles_x, int C, const uint32_t* __restrict__ cscan,
+                                                           long long cap, uint32_t* __restrict__ srid) {
+  __shared__ uint32_t wpos[kBinWarps * kDirectMaxTiles];  // per warp and tile: pairs, then next position
+  const int c = blockIdx.x, b = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = threadIdx.x; o < kBinWarps * T; o += kBinChunk) wpos[o] = 0u;
+  __syncthreads();
+  const int n = c * kBinChunk + threadIdx.x;
+  int cnt = 0, tx0 = 0, ty0 = 0, wt = 1;
+  if (n < N) {
+    const size_t i = (size_t)b * N + n;
+    if (counts[i] != 0u) {
+      int tx1, ty1;
+      unpack_tbox(tbox[i], tx0, ty0, tx1, ty1);
+      wt = tx1 - tx0 + 1;
+      cnt = wt * (ty1 - ty0 + 1);
+      for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&wpos[warp * T + ty * tiles_x + tx], 1u);
+    }
+  }
+  __syncthreads();
+  // each tile's first position for each warp: the chunk's base plus the pairs of the earlier warps
+  for (int t = threadIdx.x; t < T; t += kBinChunk) {
+    uint32_t run = cscan[((size_t)b * T + t) * C + c];
+#pragma unroll
+    for (int w = 0; w < kBinWarps; ++w) {
+      const uint32_t x = wpos[w * T + t];
+      wpos[w * T + t] = run;
+      run += x;
+    }
+  }
+  __syncthreads();
+  // the warp's pairs, slot k of every lane's rectangle at a time, lanes in order within a tile
+  const int kmax = __reduce_max_sync(0xffffffffu, cnt);
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t rid = (uint32_t)((size_t)b * N + n);
+  for (int k = 0; k < kmax; ++k) {
+    const bool has = k < cnt;
+    const int t = has ? (ty0 + k / wt) * tiles_x + tx0 + k % wt : T;  // T: no pair in this slot
+    const unsigned peers = __match_any_sync(0xffffffffu, t);
+    if (has) {
+      const uint32_t pos = wpos[warp * T + t] + (uint32_t)__popc(peers & lt);
+      if ((long long)pos < cap) srid[pos] = rid;
+    }
+    __syncwarp();
+    if (has && (peers & lt) == 0u) wpos[warp * T + t] += (uint32_t)__popc(peers);
+    __syncwarp();
+  }
+}
+
+// ranges[j] of the PT (projection, tile) lists from the scan (clamped to cap); the pair counts and the
+// capacity flag.
+__global__ void __launch_bounds__(256) k_bin_ranges(const uint32_t* __restrict__ cscan, int PT, int C,
+                                                    long long cap, uint2* __restrict__ ranges,
+                                                    uint32_t* __restrict__ n_pairs, int* status) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t total = cscan[(size_t)PT * C];
+  if (j == 0) {
+    n_pairs[0] = total;
+    n_pairs[1] = (long long)total > cap ? (uint32_t)cap : total;
+    if ((long long)total > cap) set_status(status, DIGS_ERR_CAPACITY);
+  }
+  if (j >= PT) return;
+  const long long x = cscan[(size_t)j * C], y = cscan[(size_t)(j + 1) * C];
+  ranges[j] = make_uint2((uint32_t)(x < cap ? x : cap), (uint32_t)(y < cap ? y : cap));
+}
+
+cudaError_t bin_direct(const Workspace& ws, cudaStream_t st) {
+  const int C = ws.n_chunks, PT = ws.P * ws.T;
+  if (C > 0) {
+    k_bin_count<<<dim3(C, ws.P), kBinChunk, 0, st>>>(ws.tbox, ws.counts, ws.n, ws.T, ws.tiles_x, C, ws.chist);
+    note_launches(1);
+  }
+  cudaError_t e = exclusive_scan(ws.chist, ws.chist, PT * C, ws.scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  if (C > 0) {
+    k_bin_scatter<<<dim3(C, ws.P), kBinChunk, 0, st>>>(ws.tbox, ws.counts, ws.n, ws.T, ws.tiles_x, C, ws.chist,
+                                                       ws.cap, ws.vals);
+    note_launches(1);
+  }
+  if (PT > 0) {
+    k_bin_ranges<<<(PT + 255) / 256, 256, 0, st>>>(ws.chist, PT, C, ws.cap, ws.ranges, ws.n_pairs, ws.status);
+    note_launches(1);
+  }
+  return cudaGetLastError();
+}
+
 // Launch order of the forward raster's CTAs: (projection, tile) indices by descending list length, in
 // 33 power-of-two classes (longest first), so that the heaviest tiles start in the first wave and the
 // tail of the launch is made of light ones.  Only the launch order depends on it, not any result.
