@@ -340,8 +340,9 @@ digs_status digs_gemm_bf16(int trans_a, int trans_b, int M, int N, int K, const 
 /* Stage timing: a call whose opts->flags has DIGS_FLAG_TIME_STAGES records CUDA events around each of
  * its stages on its stream.  digs_stage_times() waits for the last of them and writes the milliseconds
  * of each stage of the most recent timed call to ms[DIGS_NUM_STAGES] (0 for stages it did not run):
- * 0 FFD + deformation + projection set-up, 1 prefix sum + key emission, 2 radix sort + tile ranges,
- * 3 forward raster, 4 loss reduction, 5 backward raster, 6 per-Gaussian chain + FFD backward + dL/dw,
+ * 0 FFD + deformation + projection set-up, 1 binning (per-chunk tile counts, their prefix sum, the
+ * record-id scatter and the tile ranges; beyond 1024 tiles per projection: prefix sum + key emission),
+ * 2 forward launch order (beyond 1024 tiles: radix sort + tile ranges + launch order), 3 forward raster, 4 loss reduction, 5 backward raster, 6 per-Gaussian chain + FFD backward + dL/dw,
  * 7 fused Adam.  Process-wide state: time one call at a time. */
 #define DIGS_FLAG_TIME_STAGES 2
 #define DIGS_NUM_STAGES 8
