@@ -128,7 +128,7 @@ def exported_symbols() -> List[str]:
 
 
 DIGS_FLAG_TIME_STAGES = 2
-STAGES = ["setup", "bin", "sort", "raster_fwd", "loss", "raster_bwd", "chain_bwd", "adam"]
+STAGES = ["setup", "bin", "order", "raster_fwd", "loss", "raster_bwd", "chain_bwd", "adam"]
 
 
 def stage_times() -> Dict[str, float]:
