@@ -39,6 +39,7 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.rec = (float4*)take(PN * DIGS_REC_F4 * sizeof(float4));
   w.counts = (uint32_t*)take((PN + 1) * 4);
   w.n_chunks = bin_chunks(n, w.T);
+  if (w.n_chunks > 0 && (size_t)P * w.T * w.n_chunks >= ((size_t)1 << 30)) w.n_chunks = -1;  // scan length is an int
   const size_t chist_n = (size_t)P * w.T * std::max(w.n_chunks, 0);
   w.tbox = (uint2*)take(PN * sizeof(uint2));
   w.chist = (uint32_t*)take((chist_n + 1) * 4);
