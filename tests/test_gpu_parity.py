@@ -89,6 +89,17 @@ def test_project_fwd_ragged_detector_offsets_and_parallel(dev, P):
             assert relL2(out[b].cpu().numpy(), ref[b]) < 1e-5, (tile, b)
 
 
+def test_project_fwd_binning_paths(dev, P):
+    # 16-pixel tiles on 288 x 256: 288 tiles per projection, the counting-sort binning; 8-pixel tiles:
+    # 1152 tiles, beyond its limit, so the emitted pairs go through the radix sort
+    wl = synth.tiny(n=300, n_proj=2, nu=288, nv=256)
+    ref = O.render(gauss(wl), wl.lattice, wl.phi, wl.w, wl.views)
+    for tile in (16, 8):
+        out = P.Projector(wl.lattice, wl.views, tile=tile).forward(*gpu_inputs(wl, dev))
+        for b in range(2):
+            assert relL2(out[b].cpu().numpy(), ref[b]) < 1e-5, (tile, b)
+
+
 def test_project_fwd_degenerate_cases(dev, P):
     wl = synth.tiny(n=50, n_proj=2)
     # one Gaussian exactly at a tile corner, one far off the detector, one folded by the deformation
