@@ -1,5 +1,8 @@
-// Stable sort of the (projection, tile) pair keys with their record values, and the per-(projection,
-// tile) ranges of the sorted list.  The pairs come out of the emit step projection by projection, so
+// Binning of the (projection, tile) pairs into per-tile record lists.  Up to kDirectMaxTiles tiles per
+// projection, bin_direct (below) counts and places the pairs straight from the records' tile rectangles.
+// Beyond that, sort_pairs: a stable sort of the emitted (projection, tile) pair keys with their record
+// values, and the per-(projection, tile) ranges of the sorted list.  The pairs come out of the emit step
+// projection by projection, so
 // only the tile part of each key needs sorting, inside each projection's run: an LSD radix sort on the
 // tile index, 8 bits per pass (one pass when a projection has at most 256 tiles), whose blocks never
 // straddle two projections.  The pair count lives on the device (it comes out of the prefix sum), so
