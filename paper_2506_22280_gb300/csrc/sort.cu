@@ -321,11 +321,11 @@ __global__ void __launch_bounds__(kBinChunk) k_bin_scatter(const uint2* __restri
   for (int o = threadIdx.x; o < kBinWarps * T; o += kBinChunk) wpos[o] = 0u;
   __syncthreads();
   const int n = c * kBinChunk + threadIdx.x;
-  int cnt = 0, tx0 = 0, ty0 = 0, wt = 1;
+  int cnt = 0, tx0 = 0, ty0 = 0, tx1 = 0, wt = 1;
   if (n < N) {
     const size_t i = (size_t)b * N + n;
     if (counts[i] != 0u) {
-      int tx1, ty1;
+      int ty1;
       unpack_tbox(tbox[i], tx0, ty0, tx1, ty1);
       wt = tx1 - tx0 + 1;
       cnt = wt * (ty1 - ty0 + 1);
@@ -349,9 +349,16 @@ __global__ void __launch_bounds__(kBinChunk) k_bin_scatter(const uint2* __restri
   const int kmax = __reduce_max_sync(0xffffffffu, cnt);
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t rid = (uint32_t)((size_t)b * N + n);
+  int cx = tx0, ct = ty0 * tiles_x + tx0;  // slot k's tile column and index, stepped row-major
   for (int k = 0; k < kmax; ++k) {
     const bool has = k < cnt;
-    const int t = has ? (ty0 + k / wt) * tiles_x + tx0 + k % wt : T;  // T: no pair in this slot
+    const int t = has ? ct : T;  // T: no pair in this slot
+    if (++cx > tx1) {
+      cx = tx0;
+      ct += tiles_x - wt + 1;
+    } else {
+      ++ct;
+    }
     const unsigned peers = __match_any_sync(0xffffffffu, t);
     if (has) {
       const uint32_t pos = wpos[warp * T + t] + (uint32_t)__popc(peers & lt);
