@@ -132,7 +132,7 @@ digs_status digs_project_fwd(const DigsGaussians* g, const DigsLattice* lat, con
  *  - All calls share the array and each overwrites what the last one left: calls whose work overlaps
  *    on the GPU (other streams, other host threads) race and must not be issued.
  *  - Returns DIGS_ERR_ARG, before launching anything, if the problem's pair-independent scratch
- *    (records, counts, backward sums, ranges, per-pixel buffers: roughly 106 B per (projection,
+ *    (records, counts, backward sums, ranges, per-pixel buffers: roughly 118 B per (projection,
  *    Gaussian) plus 8 B per pixel) exceeds the array.  The call then waits for its stream and returns DIGS_ERR_CAPACITY if the
  *    (tile, Gaussian) pairs did not fit in the rest of the array (the output is then incomplete).
  *  - Calls no cudaMalloc, cudaFree or other allocating routine. */
