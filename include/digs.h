@@ -128,18 +128,31 @@ digs_status digs_project_fwd(const DigsGaussians* g, const DigsLattice* lat, con
  * set before it is loaded, and small C programs that should not have to size and manage a workspace.
  *  - Every GPU on which the library's device code is loaded holds the 32 MiB until the process exits.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- *    device current; make that first call before any stream capture.
+ *    device current.
+ *  - Synchronous: the call waits for its stream and returns the status the device recorded.  It cannot
+ *    be used inside stream capture (it reads that status back to the host) and returns DIGS_ERR_ARG,
+ *    launching nothing, when `stream` is capturing.
  *  - All calls share the array and each overwrites what the last one left: calls whose work overlaps
  *    on the GPU (other streams, other host threads) race and must not be issued.
- *  - Returns DIGS_ERR_ARG, before launching anything, if the problem's pair-independent scratch
- *    (records, counts, backward sums, ranges, per-pixel buffers: roughly 118 B per (projection,
- *    Gaussian) plus 8 B per pixel) exceeds the array.  The call then waits for its stream and returns DIGS_ERR_CAPACITY if the
- *    (tile, Gaussian) pairs did not fit in the rest of the array (the output is then incomplete).
+ *  - Returns DIGS_ERR_ARG, before launching anything, when the problem's pair-independent scratch,
+ *    digs_workspace_size(n, P, nu, nv, R, 0, opts) bytes (about 118 B per (projection, Gaussian) +
+ *    (168 R + 68) B per Gaussian + 8 B per pixel), exceeds the array.  Returns DIGS_ERR_CAPACITY if the
+ *    (tile, Gaussian) pairs (16 B each) did not fit in the rest of the array; the output is then
+ *    incomplete, and the next call starts with a clear status.
  *  - Calls no cudaMalloc, cudaFree or other allocating routine. */
 #define DIGS_STATIC_SCRATCH_BYTES (32u << 20)
 digs_status digs_project_fwd_static(const DigsGaussians* g, const DigsLattice* lat, const float* phi,
                                     const float* w, const DigsView* views, int P, const DigsOpts* opts,
                                     float* proj, void* stream);
+
+/* Forward projection and the L2 projection loss of Sec. 4.2 in one pass: writes
+ * loss_out[0] (device float) = mean over the P nv nu pixels of (I - meas)^2, with I the projections of
+ * digs_project_fwd; the residuals are squared and summed inside the raster kernel (per 8 x 8 block, then
+ * added in a fixed order), so no image needs to be read back.  meas: [P][nv][nu]; proj: optional
+ * [P][nv][nu] output of I (NULL: not written).  Same workspace as digs_project_fwd. */
+digs_status digs_project_loss(const DigsGaussians* g, const DigsLattice* lat, const float* phi, const float* w,
+                              const DigsView* views, int P, const DigsOpts* opts, const float* meas, float* proj,
+                              float* loss_out, void* ws, size_t ws_bytes, void* stream);
 
 /* Backward projection: given grad_proj = dL/dproj [P][nv][nu], write dL/d of every input:
  * g_mu0[n][3], g_scale[n][3], g_quat[n][4], g_rho[n], g_phi[R][nz][ny][nx][3], g_w[P][R].
@@ -335,6 +348,13 @@ digs_status digs_gemm_bf16(int trans_a, int trans_b, int M, int N, int K, const 
                            int ldb, const float* bias, int relu, float* C, int ldc, int splits, float* partial,
                            int* status, void* stream);
 
+/* Tests each K-loop wait of digs_gemm_bf16's kernel makes on its mbarrier before it gives up (the
+ * wait then sets *status to 1 and the output is undefined); tests < 0 restores the default (about
+ * 4 x 10^6 tests, well under a second).  The final wait for the block's own tensor-core operations,
+ * before it frees its tensor memory, always uses the default.  Process-wide; read when a GEMM is
+ * launched (a captured graph keeps the value of its capture).  For testing the give-up path. */
+digs_status digs_set_wait_limit(long long tests);
+
 /* ---- Diagnostics (not part of the method; used to measure it) ---------------------------------- */
 
 /* Stage timing: a call whose opts->flags has DIGS_FLAG_TIME_STAGES records CUDA events around each of
@@ -347,6 +367,15 @@ digs_status digs_gemm_bf16(int trans_a, int trans_b, int M, int N, int K, const 
 #define DIGS_FLAG_TIME_STAGES 2
 #define DIGS_NUM_STAGES 8
 digs_status digs_stage_times(float* ms);
+
+/* Microbenchmark of one arithmetic pipe, for the roofline of the splat kernels (their work per (pixel,
+ * Gaussian) pair is FP32 FMA-pipe arithmetic plus two SFU functions).  Enqueues on `stream` one launch
+ * of two 1024-thread CTAs per SM whose threads run eight independent chains of `iters` x 32 results of
+ * kind 0: scalar fma.rn.f32, 1: packed fma.rn.f32x2 (two results per instruction), 2: ex2.approx.ftz.f32,
+ * 3: rsqrt.approx.ftz.f32, and writes the number of FP32 results of the launch (an FMA counts once) to
+ * *lane_ops (host).  Time the launch with CUDA events on the stream; results / time is the pipe's rate.
+ * sink: device float the kernel may write (it never does in practice).  Asynchronous. */
+digs_status digs_pipe_bench(int kind, int iters, float* sink, long long* lane_ops, void* stream);
 
 /* Number of CUDA kernels this library has launched since it was loaded (memsets not counted). */
 long long digs_kernel_launches(void);

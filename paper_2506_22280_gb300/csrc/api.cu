@@ -374,6 +374,26 @@ digs_status digs_project_fwd(const DigsGaussians* g, const DigsLattice* lat, con
   return DIGS_OK;
 }
 
+digs_status digs_project_loss(const DigsGaussians* g, const DigsLattice* lat, const float* phi, const float* w,
+                              const DigsView* views, int P, const DigsOpts* opts, const float* meas, float* proj,
+                              float* loss_out, void* ws, size_t ws_bytes, void* stream) {
+  Call c;
+  digs_status s = prepare(g, lat, phi, w, views, P, opts, nullptr, ws, ws_bytes, stream, c);
+  if (s != DIGS_OK) return s;
+  if (!meas || !loss_out) return DIGS_ERR_ARG;
+  if (P == 0) {
+    DIGS_TRY(cudaMemsetAsync(loss_out, 0, sizeof(float), c.st));
+    return DIGS_OK;
+  }
+  s = bin(c, phi, w);
+  if (s != DIGS_OK) return s;
+  const float inv_count = 1.f / ((float)P * c.ws.nu * c.ws.nv);
+  DIGS_TRY(launch_raster_fwd(c.ws, c.views, c.c2, proj, meas, nullptr, inv_count, c.st));
+  mark(c, 4);
+  DIGS_TRY(launch_loss_reduce(c.ws.loss_part, P * c.ws.T * fwd_blocks(c.ws.tile), loss_out, inv_count, c.st));
+  return DIGS_OK;
+}
+
 digs_status digs_project_bwd(const DigsGaussians* g, const DigsLattice* lat, const float* phi, const float* w,
                              const DigsView* views, int P, const DigsOpts* opts, const float* grad_proj,
                              float* g_mu0, float* g_scale, float* g_quat, float* g_rho, float* g_phi, float* g_w,

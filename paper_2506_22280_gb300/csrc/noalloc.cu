@@ -4,6 +4,8 @@
 // The array is DIGS_STATIC_SCRATCH_BYTES (32 MiB).  Every GPU on which the library's code is loaded
 // holds it until the process exits.  All calls share it: a call overwrites what the previous one left,
 // and two calls whose work overlaps on the GPU (different streams, or different host threads) race on it.
+// Each call is synchronous (it waits for its stream to read the device status), so it is refused on a
+// stream that is being captured.
 #include <mutex>
 
 #include "digs_internal.h"
@@ -47,6 +49,10 @@ extern "C" digs_status digs_project_fwd_static(const DigsGaussians* g, const Dig
   size_t fixed = digs_workspace_size(g->n, P, nu, nv, lat->R, 0, opts);
   if (fixed == 0 || fixed > kStaticScratchBytes) return DIGS_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  // The call ends by reading the device status back to the host, which a capturing stream cannot do.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return DIGS_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return DIGS_ERR_ARG;
   // The status block (error word, pair counts) must start at zero; the array keeps the last call's bytes.
   if (cudaMemsetAsync(base, 0, 256, st) != cudaSuccess) return DIGS_ERR_CUDA;
   s = digs_project_fwd(g, lat, phi, w, views, P, opts, proj, base, kStaticScratchBytes, stream);

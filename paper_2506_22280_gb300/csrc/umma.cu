@@ -14,8 +14,9 @@
 //   * each warp reads its 32 accumulator lanes (rows) back with tcgen05.ld, adds the bias and applies
 //     ReLU when asked, and puts them in shared memory, from where whole rows go out with 16-byte stores.
 // gridDim.z > 1 splits K: block z sums k in [z kchunk, (z + 1) kchunk) into C + z zstride (no bias).
-// Every mbarrier wait is bounded; a wait that gives up sets *status to 1 and the block still waits
-// (bounded) for its own MMAs, frees its tensor memory and returns.
+// Every mbarrier wait is bounded; a wait of the K loop that gives up sets *status to 1, and the block
+// still waits for its own MMAs (with the default bound, whatever digs_set_wait_limit says), frees its
+// tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -33,6 +34,9 @@ constexpr int kTmemCols = 64;           // FP32 accumulator columns (= kBN)
 constexpr size_t kTcSmem = 1024 + 2 * kStageA + 2 * kStageB + 64;  // 1 KB alignment slack, buffers, barriers
 constexpr unsigned kWaitLimit = 1u << 22;                          // x ~100 ns
 
+// Tests a K-loop mbarrier wait makes before it gives up (digs_set_wait_limit; read at launch).
+unsigned g_loop_wait_limit = kWaitLimit;
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -40,10 +44,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 }
 
 // Waits for the completion of the mbarrier phase with the given parity: non-blocking tests with a short
-// sleep between them, false after kWaitLimit tests (well under a second).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// sleep between them, false after `limit` tests (kWaitLimit tests take well under a second).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned limit) {
   const uint32_t a = smem_u32(bar);
-  for (unsigned it = 0; it < kWaitLimit; ++it) {
+  for (unsigned it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -225,7 +229,8 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
                                                         const TB* __restrict__ B, int ldb, TC* __restrict__ C,
                                                         int ldc, int kchunk, long long zstride,
                                                         const float* __restrict__ bias, int relu, int vec,
-                                                        int* status, const ConvGeom ga, const ConvGeom gb) {
+                                                        int* status, const ConvGeom ga, const ConvGeom gb,
+                                                        unsigned wait_limit) {
   extern __shared__ unsigned char smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = sm;
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
   int issued = 0;  // slices whose MMAs were committed
   for (int s = 0; s < nk; ++s) {
     const int buf = s & 1;
-    if (s >= 2) ok = __syncthreads_and(ok && mbar_wait(bar + buf, (uint32_t)(((s >> 1) - 1) & 1)));
+    if (s >= 2) ok = __syncthreads_and(ok && mbar_wait(bar + buf, (uint32_t)(((s >> 1) - 1) & 1), wait_limit));
     if (!ok) break;
     stage<AT, BT, CA_, CB_>(A, lda, B, ldb, M, N, m0, n0, kb + s * kBK, ke, sA + buf * kStageA, sB + buf * kStageB,
                             vec, ga, gb);
@@ -275,8 +280,10 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
     }
     issued = s + 1;
   }
-  // the last commit tracks every MMA issued before it
-  if (issued > 0 && !mbar_wait(bar + ((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1))) ok = 0;
+  // the last commit tracks every MMA issued before it: always drained (default bound) before the tensor
+  // memory is read or freed, and the outcome made block-uniform
+  const bool drained = issued == 0 || mbar_wait(bar + ((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1), kWaitLimit);
+  ok = __syncthreads_and(ok && drained);
   tc_fence_after();
   // epilogue: accumulator lanes -> registers (+ bias, ReLU) -> the 128 x 64 tile in the (now idle)
   // staging buffers -> global rows, 4 consecutive columns per thread, 16 threads per row
@@ -350,7 +357,7 @@ cudaError_t launch_tc(int M, int N, int K, const TA* A, int lda, const TB* B, in
   const int vec = ((!AT && ((uintptr_t)A & 15) == 0 && lda % per16a == 0) ? 1 : 0) |
                   ((BT && ((uintptr_t)B & 15) == 0 && ldb % per16b == 0) ? 2 : 0);
   k_gemm_tc<AT, BT, CA_, CB_, TA, TB, TC><<<grid, kTcThreads, kTcSmem, st>>>(
-      M, N, K, A, lda, B, ldb, C, ldc, kchunk, zstride, bias, relu ? 1 : 0, vec, status, ga, gb);
+      M, N, K, A, lda, B, ldb, C, ldc, kchunk, zstride, bias, relu ? 1 : 0, vec, status, ga, gb, g_loop_wait_limit);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -423,6 +430,11 @@ cudaError_t gemm_tc_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, c
 }
 
 }  // namespace digs
+
+extern "C" digs_status digs_set_wait_limit(long long tests) {
+  digs::g_loop_wait_limit = tests < 0 ? digs::kWaitLimit : (unsigned)std::min<long long>(tests, 1LL << 30);
+  return DIGS_OK;
+}
 
 extern "C" digs_status digs_gemm_bf16(int trans_a, int trans_b, int M, int N, int K, const float* A, int lda,
                                       const float* B, int ldb, const float* bias, int relu, float* C, int ldc,

@@ -85,6 +85,7 @@ def lib() -> C.CDLL:
         "digs_count_pairs": (I, [P, P, P, P, P, I, P, P, S, C.POINTER(LL), P]),
         "digs_project_fwd": (I, [P, P, P, P, P, I, P, P, P, S, P]),
         "digs_project_bwd": (I, [P, P, P, P, P, I, P, P, P, P, P, P, P, P, P, S, P]),
+        "digs_project_loss": (I, [P, P, P, P, P, I, P, P, P, P, P, S, P]),
         "digs_state_moments": (S, [I, P, I, I]),
         "digs_state_workspace_size": (S, [P, I, I, I, LL, P]),
         "digs_state_size": (S, [P]),
@@ -109,6 +110,9 @@ def lib() -> C.CDLL:
         "digs_densify_plan": (I, [I, P, P, P, P, P, P, P, S, P]),
         "digs_densify_apply": (I, [P, P, P, P, I, P, P, P, P, P, P, P]),
         "digs_gather_rows": (I, [P, P, I, I, P, P, P]),
+        "digs_project_fwd_static": (I, [P, P, P, P, P, I, P, P, P]),
+        "digs_set_wait_limit": (I, [LL]),
+        "digs_pipe_bench": (I, [I, I, P, C.POINTER(LL), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -120,11 +124,13 @@ def lib() -> C.CDLL:
 
 def exported_symbols() -> List[str]:
     return ["digs_workspace_size", "digs_ffd_eval", "digs_count_pairs", "digs_project_fwd", "digs_project_bwd",
+            "digs_project_loss",
             "digs_state_moments", "digs_state_workspace_size", "digs_state_size", "digs_step", "digs_sync_status", "digs_status_string", "digs_stage_times",
             "digs_kernel_launches", "digs_pair_stats", "digs_voxelize", "digs_dvf", "digs_cnn_params", "digs_cnn_workspace_size", "digs_cnn_init",
             "digs_cnn_prepare_input", "digs_cnn_forward", "digs_cnn_backward", "digs_cnn_train_step",
             "digs_cnn_infer_bf16", "digs_gemm_bf16", "digs_densify_workspace_size", "digs_densify_plan",
-            "digs_densify_apply", "digs_gather_rows"]
+            "digs_densify_apply", "digs_gather_rows", "digs_project_fwd_static", "digs_set_wait_limit",
+            "digs_pipe_bench"]
 
 
 DIGS_FLAG_TIME_STAGES = 2
@@ -136,6 +142,32 @@ def stage_times() -> Dict[str, float]:
     arr = (C.c_float * len(STAGES))()
     _check(lib().digs_stage_times(arr), "digs_stage_times")
     return {k: float(arr[i]) for i, k in enumerate(STAGES)}
+
+
+PIPES = ("ffma", "ffma2", "ex2", "rsqrt")
+
+
+def pipe_rate(kind: str, iters: int = 4096, reps: int = 3) -> float:
+    """FP32 results per second of one arithmetic pipe (digs_pipe_bench): the best of `reps` launches,
+    each timed with CUDA events on the current stream after one untimed launch."""
+    k = PIPES.index(kind)
+    sink = torch.zeros(1, device="cuda")
+    ops = C.c_longlong(0)
+    best = 0.0
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _check(lib().digs_pipe_bench(k, int(iters), _ptr(sink), C.byref(ops), _stream()), "digs_pipe_bench")
+        e1.record()
+        e1.synchronize()
+        if r > 0:
+            best = max(best, ops.value / (e0.elapsed_time(e1) / 1e3))
+    return best
+
+
+def set_wait_limit(tests: int) -> None:
+    """Tests a tensor-core GEMM K-loop wait makes before it gives up (< 0: the default)."""
+    _check(lib().digs_set_wait_limit(int(tests)), "digs_set_wait_limit")
 
 
 def kernel_launches() -> int:
@@ -313,6 +345,20 @@ class Projector:
         _check(lib().digs_project_fwd(C.byref(g), C.byref(self.lat), _ptr(_f32(phi, "phi")), _ptr(_f32(w, "w")),
                                       self.varr, self.P, C.byref(self.opts), _ptr(out), self.ws.ptr, self.ws.nbytes,
                                       _stream()), "digs_project_fwd")
+        return out
+
+    def loss(self, mu0, scale, quat, rho, phi, w, meas: torch.Tensor, out: Optional[torch.Tensor] = None,
+             proj: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Mean over the views' pixels of (I - meas)^2 (device tensor [1]), the residuals squared and
+        summed in the raster kernel (digs_project_loss); proj, if given, receives I."""
+        self.reserve(mu0, scale, quat, rho, phi, w)
+        if out is None:
+            out = torch.empty(1, device=mu0.device, dtype=torch.float32)
+        g = gauss_struct(mu0, scale, quat, rho)
+        _check(lib().digs_project_loss(C.byref(g), C.byref(self.lat), _ptr(_f32(phi, "phi")), _ptr(_f32(w, "w")),
+                                       self.varr, self.P, C.byref(self.opts), _ptr(_f32(meas.contiguous(), "meas")),
+                                       _ptr(proj), _ptr(out), self.ws.ptr, self.ws.nbytes, _stream()),
+               "digs_project_loss")
         return out
 
     def backward(self, mu0, scale, quat, rho, phi, w, grad_proj, reuse: bool = False):

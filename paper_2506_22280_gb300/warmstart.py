@@ -68,15 +68,20 @@ def train(predictor: D.WeightPredictor, imgs: torch.Tensor, cs: torch.Tensor, W:
 
 def scan_loss(rec: D.Reconstruction, meas: torch.Tensor, views: Sequence[Dict], w: torch.Tensor,
               chunk: int = 128, scan: int = 0) -> float:
-    """Mean squared projection error of the reconstruction over a whole scan with weights w [P][R]."""
+    """Mean squared projection error of the reconstruction over a whole scan with weights w [P][R]: the
+    library's fused forward + loss (digs_project_loss) per chunk of views, the chunk means weighted by
+    their pixel counts."""
     p = rec.scan_params(scan)
-    tot = 0.0
-    for s in range(0, len(views), chunk):
+    dev = rec.mu0.device
+    losses = torch.zeros(math.ceil(len(views) / chunk), device=dev)
+    counts = []
+    for k, s in enumerate(range(0, len(views), chunk)):
         v = list(views[s:s + chunk])
-        pj = D.Projector(rec.lattice, v, tile=rec.tile, device=rec.mu0.device)
-        I = pj.forward(p["mu0"], p["scale"], p["quat"], p["rho"], p["phi"], w[s:s + len(v)].contiguous())
-        tot += float(((I - meas[s:s + len(v)]) ** 2).sum().item())
-    return tot / float(meas.numel())
+        pj = D.Projector(rec.lattice, v, tile=rec.tile, device=dev)
+        pj.loss(p["mu0"], p["scale"], p["quat"], p["rho"], p["phi"], w[s:s + len(v)].contiguous(),
+                meas[s:s + len(v)], out=losses[k:k + 1])
+        counts.append(len(v))
+    return sum(l * c for l, c in zip(losses.tolist(), counts)) / float(len(views))
 
 
 def propose_weights(predictor: D.WeightPredictor, meas: torch.Tensor, angles: np.ndarray) -> torch.Tensor:

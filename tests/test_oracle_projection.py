@@ -244,3 +244,41 @@ def test_render_pixels_matches_full_render():
     ij = np.array([[0, 0], [31, 32], [40, 10], [63, 63], [12, 50]])
     vals = O.render_pixels(g, wl.lattice, wl.phi, wl.w, wl.views[0], wl.w[0], ij)
     assert np.allclose(vals, full[ij[:, 1], ij[:, 0]], rtol=1e-9, atol=1e-15)
+
+
+def test_mse_loss_is_the_mean_over_every_pixel_of_every_projection():
+    # two 1 x 2 projections, residuals 1, 0, -2, 0: the mean of the squares over the four pixels is 5 / 4
+    # (the sum would give 5, per-projection means summed 2.5, the root of the mean 1.118)
+    I = np.array([[[1.0, 2.0]], [[3.0, 4.0]]])
+    M = np.array([[[0.0, 2.0]], [[5.0, 4.0]]])
+    assert O.mse_loss(I, M) == 1.25
+    assert O.mse_loss(M, M) == 0.0
+
+
+def test_gaussians_behind_the_source_or_around_it_are_dropped():
+    views = synth.circular_views([0.4], 1000.0, 1500.0, 17, 17, 4.0, 4.0)
+    v = O.view_tensors(views[0])
+    src = np.asarray(views[0]["src"], dtype=float)
+    phi, w = _zero_motion()
+    lat = _static_lattice()
+    # behind the source: the whole line through the source and a pixel would meet it, but it lies on the
+    # far side of the source from the detector
+    behind = _one(1.2 * src, [5.0] * 3, [1, 0, 0, 0], 0.02)
+    front = _one(0.2 * src, [5.0] * 3, [1, 0, 0, 0], 0.02)
+    for cut in (3.5, None):
+        assert np.abs(O.render(behind, lat, phi, w, views, cutoff=cut, mode="brute")).max() == 0.0
+        assert O.render(front, lat, phi, w, views, cutoff=cut, mode="brute").max() > 0.0
+    # a Gaussian whose cutoff ellipsoid holds the source (Mahalanobis distance of the source
+    # 1000 / 400 = 2.5 < 3.5) is dropped with the cutoff on; at 1000 / 250 = 4 > 3.5 it is kept
+    wide = _one([0.0, 0.0, 0.0], [400.0] * 3, [1, 0, 0, 0], 1e-4)
+    kept = _one([0.0, 0.0, 0.0], [250.0] * 3, [1, 0, 0, 0], 1e-4)
+    assert np.abs(O.render(wide, lat, phi, w, views, cutoff=3.5, mode="brute")).max() == 0.0
+    assert O.render(wide, lat, phi, w, views, cutoff=None, mode="brute").max() > 0.0
+    assert O.render(kept, lat, phi, w, views, cutoff=3.5, mode="brute").max() > 0.0
+    # the mask itself on the three cases
+    mu = torch.tensor(np.stack([1.2 * src, 0.2 * src, np.zeros(3)]), dtype=DT)
+    sig = torch.tensor([5.0, 5.0, 400.0], dtype=DT)
+    P = torch.diag_embed((1.0 / sig ** 2)[:, None].expand(3, 3))
+    K = torch.eye(3, dtype=DT).expand(3, 3, 3)
+    assert O.alive_mask(v, mu, P, K, 3.5).tolist() == [False, True, False]
+    assert O.alive_mask(v, mu, P, K, None).tolist() == [False, True, True]

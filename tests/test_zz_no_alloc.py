@@ -3,8 +3,10 @@
 Its scratch is a fixed 32 MiB array inside the library, so a caller that has no way to call cudaMalloc
 (a plug-in whose host owns the device memory, a fixed memory budget) can still project.  This test calls
 it through the C-ABI, twice in a row and on two different problems, and checks each result against the
-workspace-based digs_project_fwd within the projection tolerance used everywhere else (rel-L2 1e-5);
-then checks that a problem too large for the array is refused before anything runs.
+workspace-based digs_project_fwd and against the FP64 oracle within the projection tolerance used
+everywhere else (rel-L2 1e-5); then checks that a problem too large for the array is refused before
+anything runs, and that a problem whose pairs overflow the array reports DIGS_ERR_CAPACITY while the next
+call starts clean.
 """
 import ctypes as C
 
@@ -13,13 +15,14 @@ import pytest
 import torch
 
 import synth
+from oracle import digs_oracle as O
 
 pytestmark = pytest.mark.gpu
 
 
 def _relL2(a, b):
-    a = a.double().cpu().numpy()
-    b = b.double().cpu().numpy()
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
@@ -48,10 +51,15 @@ def _call_static(D, f, wl, ins, out):
              len(wl.views), C.byref(opts), C.c_void_p(out.data_ptr()), stream)
 
 
+def _oracle(wl):
+    return O.render(dict(mu0=wl.mu0, scale=wl.scale, quat=wl.quat, rho=wl.rho), wl.lattice, wl.phi, wl.w, wl.views)
+
+
 def test_static_scratch_forward_matches_workspace_forward():
     D, f = _setup()
     first = synth.tiny()                                   # 2,000 Gaussians, 16 views of 64 x 64
     second = synth.tiny(seed=3, n=700, n_proj=3, nu=61, nv=47)
+    refs = {id(first): _oracle(first), id(second): _oracle(second)}
     for wl in (first, second, first):                      # consecutive calls reuse the same array
         ins = _tensors(wl)
         ref = D.Projector(wl.lattice, wl.views).forward(*ins)
@@ -59,7 +67,9 @@ def test_static_scratch_forward_matches_workspace_forward():
         assert _call_static(D, f, wl, ins, out) == 0
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
-        assert _relL2(out, ref) <= 1e-5
+        got = out.cpu().numpy()
+        assert _relL2(got, ref.cpu().numpy()) <= 1e-5
+        assert _relL2(got, refs[id(wl)]) <= 1e-5
 
 
 def test_static_scratch_refuses_oversized_problem():
@@ -71,3 +81,27 @@ def test_static_scratch_refuses_oversized_problem():
     assert _call_static(D, f, wl, ins, out) == 1
     torch.cuda.synchronize()
     assert float(out.abs().max()) == 0.0
+
+
+def test_static_scratch_pair_overflow_then_clean_call():
+    D, f = _setup()
+    # 1,000 wide Gaussians (scales x 8) seen from 128 views of 64 x 64: every record covers most of the
+    # 16 tiles of its view, about 2 M (tile, Gaussian) pairs, more than the array holds after the
+    # pair-independent part (about 20 MB of the 32 MiB)
+    big = synth.tiny(seed=4, n=1000, n_proj=128)
+    big.scale = big.scale * 8.0
+    fixed = D.workspace_size(big.n, 128, 64, 64, big.R, 0)
+    assert fixed < (32 << 20)
+    ins = _tensors(big)
+    out = torch.zeros(128, 64, 64, device="cuda")
+    assert _call_static(D, f, big, ins, out) == 3           # DIGS_ERR_CAPACITY
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
+    small = synth.tiny(seed=6, n=500, n_proj=4)
+    ins = _tensors(small)
+    out = torch.full((4, 64, 64), float("nan"), device="cuda")
+    assert _call_static(D, f, small, ins, out) == 0
+    torch.cuda.synchronize()
+    ref = D.Projector(small.lattice, small.views).forward(*ins)
+    assert _relL2(out.cpu().numpy(), ref.cpu().numpy()) <= 1e-5
+    assert _relL2(out.cpu().numpy(), _oracle(small)) <= 1e-5
