@@ -370,8 +370,8 @@ digs_status digs_stage_times(float* ms);
 
 /* Microbenchmark of one arithmetic pipe, for the roofline of the splat kernels (their work per (pixel,
  * Gaussian) pair is FP32 FMA-pipe arithmetic plus two SFU functions).  Enqueues on `stream` one launch
- * of two 1024-thread CTAs per SM whose threads run eight independent chains of `iters` x 32 results of
- * kind 0: scalar fma.rn.f32, 1: packed fma.rn.f32x2 (two results per instruction), 2: ex2.approx.ftz.f32,
+ * of two 1024-thread CTAs per SM whose threads run eight independent chains of `iters` x 4 results (x 8
+ * for kind 1) of kind 0: scalar fma.rn.f32, 1: packed fma.rn.f32x2 (two results per instruction), 2: ex2.approx.ftz.f32,
  * 3: rsqrt.approx.ftz.f32, and writes the number of FP32 results of the launch (an FMA counts once) to
  * *lane_ops (host).  Time the launch with CUDA events on the stream; results / time is the pipe's rate.
  * sink: device float the kernel may write (it never does in practice).  Asynchronous. */

@@ -364,6 +364,40 @@ def render_view_bbox(v, mu, sigma, P, rho, alive, cutoff) -> torch.Tensor:
     return img.index_add(0, pix, V * mask.to(DT))
 
 
+def cutoff_margin(gauss: Dict, lattice: Dict, phi, w, views: Sequence[Dict], cutoff: float = 3.5) -> np.ndarray:
+    """Per Gaussian, the smallest |E - cutoff^2| / cutoff^2 over its (pixel, view) pairs, E the squared
+    Mahalanobis distance from the pixel ray to the deformed mean (Eq. 4 with the deformation of Eq. 7-11),
+    in float64 (inf for a Gaussian without pairs).  A pair whose margin is at the level of FP32 rounding
+    (~1e-7) is decided by rounding: a float32 evaluation of the same E may include it or not, so parity
+    tests that compare gradients element by element leave such Gaussians out.  Pairs are taken from the
+    box of the 1.05 x cutoff ellipsoid, so that near misses just outside the cutoff count too."""
+    T = _inputs(gauss, phi, w)
+    with torch.no_grad():
+        sigma0 = covariance(T["scale"], T["quat"])
+        U, dU = ffd_eval(T["phi"], lattice, T["mu0"])
+        n = T["mu0"].shape[0]
+        out = torch.full((n,), float("inf"), dtype=DT)
+        c2 = cutoff * cutoff
+        for b, view in enumerate(views):
+            v = view_tensors(view)
+            mu, sigma, K = deform(T["mu0"], sigma0, U, dU, T["w"][b])
+            P = torch.linalg.inv(sigma)
+            alive = alive_mask(v, mu, P, K, cutoff)
+            pix, g = bbox_pairs(v, mu, sigma, alive, 1.05 * cutoff)  # also the near misses just outside
+            if g.numel() == 0:
+                continue
+            X = pixel_centres(v)[pix]
+            d = ray_directions(v, X)
+            m = (X if v["parallel"] else v["src"][None]) - mu[g]
+            Pd = torch.einsum("nij,nj->ni", P[g], d)
+            a = (d * Pd).sum(-1)
+            bb = (m * Pd).sum(-1)
+            c = torch.einsum("ni,nij,nj->n", m, P[g], m)
+            _, _, E = pair_values(a, bb, c, T["rho"][g], cutoff)
+            out = out.scatter_reduce(0, g, (E - c2).abs() / c2, reduce="amin")
+    return out.numpy()
+
+
 def _inputs(gauss: Dict, phi, w):
     return dict(mu0=_t(gauss["mu0"]), scale=_t(gauss["scale"]), quat=_t(gauss["quat"]), rho=_t(gauss["rho"]),
                 phi=_t(phi), w=_t(w))

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdigs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "prep.cu", "scan.cu", "sort.cu", "raster.cu", "chain.cu", "adam.cu", "noalloc.cu", "cnn.cu", "temporal.cu", "volume.cu", "umma.cu", "density.cu", "peaks.cu"]
+SOURCES = ["api.cu", "prep.cu", "scan.cu", "sort.cu", "raster.cu", "chain.cu", "adam.cu", "noalloc.cu", "cnn.cu", "temporal.cu", "volume.cu", "umma.cu", "density.cu", "peaks.cu", "cnn_tc.cu"]
 
 
 def nvcc() -> str:

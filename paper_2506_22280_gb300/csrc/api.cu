@@ -62,7 +62,7 @@ size_t layout(Workspace* ws, void* base, int n, int P, int nu, int nv, int R, lo
   w.loss_part = (float*)take((size_t)P * w.T * fwd_blocks(tile) * 4 + 4);
   w.ffd = (float*)take((size_t)12 * R * n_total * 4 + 4);
   w.ffd2 = (float*)take((size_t)18 * R * n_total * 4 + 4);
-  w.gsum = (float*)take((size_t)(17 + 12 * R) * n_total * 4 + 4);
+  w.gsum = (float*)take((size_t)(11 + 12 * R) * n_total * 4 + 4);
   w.proj = (float*)take((size_t)P * nu * nv * 4);
   w.dldi = (float*)take((size_t)P * nu * nv * 4);
   w.gw_rows = (float*)take((size_t)w_rows * R * 4 + 4);

@@ -150,12 +150,20 @@ __device__ __forceinline__ void ffd_scatter_warp(float* __restrict__ g_phi_all, 
 }
 
 // Adjoint of one (projection b, Gaussian n) pair from its ten pixel sums S: dL/dmu' (gmu), dL/dK (gK),
-// dL/ds (gs), dL/dR (gR), dL/drho (grho) and dL/dw_r (gw).  mu0, inv_s = 1 / s, Rm, rho: the Gaussian.
+// dL/ds (gs), dL/dtheta (gth: the gradient for a rotation R -> R (I + [theta]x) of the Gaussian's own
+// axes), dL/drho (grho) and dL/dw_r (gw).  mu0, sc = s, inv_s = 1 / s, Rm, rho: the Gaussian.
+//
+// The record depends on A = S^-1 R^T K^-1 only through A^T A (the deformed precision), so dL/dA = 2 A G
+// with G symmetric and C = A dL/dA^T is symmetric.  The rotation moves A by -S^-1 [theta]x S A, hence
+// dL/dtheta_i = -C_jk (s_j / s_k - s_k / s_j) for (i, j, k) cyclic: the symmetric part of C times the
+// scale anisotropy, both formed without cancellation, where a general dL/dR projected onto rotations
+// afterwards would subtract two nearly equal FP32 numbers for nearly isotropic Gaussians.
 template <int R>
 __device__ __forceinline__ void pair_adjoint(const ViewC& v, const float* __restrict__ ffd, int N, int n,
-                                             const float* wr, const float mu0[3], const float inv_s[3],
-                                             const float Rm[9], float rho, const float S[10], float gmu[3],
-                                             float gK[9], float gs[3], float gR[9], float& grho, float gw[R]) {
+                                             const float* wr, const float mu0[3], const float sc[3],
+                                             const float inv_s[3], const float Rm[9], float rho, const float S[10],
+                                             float gmu[3], float gK[9], float gs[3], float gth[3], float& grho,
+                                             float gw[R]) {
   float mu[3], K[9];
 #pragma unroll
   for (int c = 0; c < 3; ++c) mu[c] = mu0[c];
@@ -190,12 +198,16 @@ __device__ __forceinline__ void pair_adjoint(const ViewC& v, const float* __rest
 #pragma unroll
   for (int ii = 0; ii < 3; ++ii)
     gs[ii] = -inv_s[ii] * (gA[3 * ii] * A[3 * ii] + gA[3 * ii + 1] * A[3 * ii + 1] + gA[3 * ii + 2] * A[3 * ii + 2]);
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int bb = 0; bb < 3; ++bb)
-      gR[3 * a + bb] =
-          inv_s[bb] * (gA[3 * bb] * Ki[3 * a] + gA[3 * bb + 1] * Ki[3 * a + 1] + gA[3 * bb + 2] * Ki[3 * a + 2]);
+  {
+    auto csym = [&](int i, int j) {  // (C_ij + C_ji) / 2, C_ij = A_i . (dL/dA)_j (rows)
+      return 0.5f * (A[3 * i] * gA[3 * j] + A[3 * i + 1] * gA[3 * j + 1] + A[3 * i + 2] * gA[3 * j + 2] +
+                     A[3 * j] * gA[3 * i] + A[3 * j + 1] * gA[3 * i + 1] + A[3 * j + 2] * gA[3 * i + 2]);
+    };
+    auto aniso = [&](int j, int k) { return (sc[j] - sc[k]) * (sc[j] + sc[k]) * inv_s[j] * inv_s[k]; };
+    gth[0] = -csym(1, 2) * aniso(1, 2);
+    gth[1] = -csym(2, 0) * aniso(2, 0);
+    gth[2] = -csym(0, 1) * aniso(0, 1);
+  }
   {
     float Tm[9];
 #pragma unroll
@@ -223,12 +235,12 @@ __device__ __forceinline__ void pair_adjoint(const ViewC& v, const float* __rest
 // (1) Per Gaussian, the pair adjoints summed over its projections.  A CTA takes 32 Gaussians (its lanes)
 // and kSlots projection slots (its warps): warp k handles projections k, k + kSlots, ..., each thread
 // adding its pair's adjoint into its own shared-memory column; the slots are then summed in order.
-// gsum [17 + 12 R][N]: dL/dmu' (3), dL/ds (3), dL/dR (9), dL/drho (1), sum_b w_br dL/dmu'_b (3R),
+// gsum [11 + 12 R][N]: dL/dmu' (3), dL/ds (3), dL/dtheta (3), dL/drho (1), sum_b w_br dL/dmu'_b (3R),
 // sum_b w_br dL/dK_b (9R) and sum_b |dL/dmu'_b| (the density-control statistic).  gw_part [CTA][P][R]: dL/dw_r of each projection summed over the CTA's
 // Gaussians (a warp sum; each (CTA, projection) is written by one warp).
 constexpr int kSlots = 8;
 template <int R>
-__host__ __device__ constexpr int gauss_sum_count() { return 17 + 12 * R; }
+__host__ __device__ constexpr int gauss_sum_count() { return 11 + 12 * R; }
 template <int R>
 constexpr size_t pair_sum_smem() { return (size_t)gauss_sum_count<R>() * kSlots * 32 * sizeof(float); }
 int pair_sum_blocks(int n) { return (n + 31) / 32; }
@@ -252,12 +264,13 @@ __global__ void __launch_bounds__(kSlots * 32, 3) k_pair_sum(GaussPtrs g, const 
 #pragma unroll
     for (int q = 0; q < Q; ++q) my[q * QS] = 0.f;
   }
-  float mu0[3] = {0.f, 0.f, 0.f}, inv_s[3] = {1.f, 1.f, 1.f}, Rm[9], rho = 0.f;
+  float mu0[3] = {0.f, 0.f, 0.f}, scl[3] = {1.f, 1.f, 1.f}, inv_s[3] = {1.f, 1.f, 1.f}, Rm[9], rho = 0.f;
   if (valid) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       mu0[c] = g.mu0[3 * n + c];
-      inv_s[c] = 1.f / g.scale[3 * n + c];
+      scl[c] = g.scale[3 * n + c];
+      inv_s[c] = 1.f / scl[c];
     }
     const float q0 = g.quat[4 * n], q1 = g.quat[4 * n + 1], q2 = g.quat[4 * n + 2], q3 = g.quat[4 * n + 3];
     const float iq = 1.f / sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
@@ -288,26 +301,25 @@ __global__ void __launch_bounds__(kSlots * 32, 3) k_pair_sum(GaussPtrs g, const 
         S[4] = c.x; S[5] = c.y; S[6] = c.z; S[7] = c.w;
         S[8] = d.x; S[9] = d.y;
       }
-      float wr[R], gmu[3], gK[9], gs[3], gR[9], grho;
+      float wr[R], gmu[3], gK[9], gs[3], gth[3], grho;
 #pragma unroll
       for (int r = 0; r < R; ++r) wr[r] = __ldg(wb + r);
-      pair_adjoint<R>(v, ffd, N, n, wr, mu0, inv_s, Rm, rho, S, gmu, gK, gs, gR, grho, gw);
+      pair_adjoint<R>(v, ffd, N, n, wr, mu0, scl, inv_s, Rm, rho, S, gmu, gK, gs, gth, grho, gw);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         put(c, gmu[c]);
         put(3 + c, gs[c]);
+        put(6 + c, gth[c]);
       }
-#pragma unroll
-      for (int c = 0; c < 9; ++c) put(6 + c, gR[c]);
-      put(15, grho);
+      put(9, grho);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) put(16 + 3 * r + c, wr[r] * gmu[c]);
+        for (int c = 0; c < 3; ++c) put(10 + 3 * r + c, wr[r] * gmu[c]);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) put(16 + 3 * R + 9 * r + c, wr[r] * gK[c]);
+        for (int c = 0; c < 9; ++c) put(10 + 3 * R + 9 * r + c, wr[r] * gK[c]);
       }
-      put(16 + 12 * R, sqrtf(gmu[0] * gmu[0] + gmu[1] * gmu[1] + gmu[2] * gmu[2]));
+      put(10 + 12 * R, sqrtf(gmu[0] * gmu[0] + gmu[1] * gmu[1] + gmu[2] * gmu[2]));
     } else if (first) {
 #pragma unroll
       for (int q = 0; q < Q; ++q) my[q * QS] = 0.f;
@@ -364,9 +376,9 @@ __global__ void __launch_bounds__(32 * R, 4) k_gauss_bwd(
   if (valid) {
     const float* q = gsum + n;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) GU[c] = q[(size_t)(16 + 3 * r + c) * N];
+    for (int c = 0; c < 3; ++c) GU[c] = q[(size_t)(10 + 3 * r + c) * N];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) GdU[c] = q[(size_t)(16 + 3 * R + 9 * r + c) * N];
+    for (int c = 0; c < 9; ++c) GdU[c] = q[(size_t)(10 + 3 * R + 9 * r + c) * N];
 #pragma unroll
     for (int c = 0; c < 3; ++c) mu0[c] = g.mu0[3 * n + c];
     // u_r and grad u_r are evaluated at mu0: dL/dmu0 += (grad u_r)^T dL/du_r + H_r : dL/d(grad u_r)
@@ -396,22 +408,21 @@ __global__ void __launch_bounds__(32 * R, 4) k_gauss_bwd(
   __syncthreads();
   if (r != 0 || !valid) return;
   const float* q = gsum + n;
-  float gmu0[3], gs[3], gR[9];
+  float gmu0[3], gs[3], gth[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     gmu0[c] = q[(size_t)c * N];
 #pragma unroll
     for (int k = 0; k < R; ++k) gmu0[c] += gpart[k][c][lane];
     gs[c] = q[(size_t)(3 + c) * N];
+    gth[c] = q[(size_t)(6 + c) * N];
   }
-#pragma unroll
-  for (int c = 0; c < 9; ++c) gR[c] = q[(size_t)(6 + c) * N];
-  const float grho = q[(size_t)15 * N];
+  const float grho = q[(size_t)9 * N];
   float qh[4], gq[4];
   const float q0 = g.quat[4 * n], q1 = g.quat[4 * n + 1], q2 = g.quat[4 * n + 2], q3 = g.quat[4 * n + 3];
   const float qn = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
   qh[0] = q0 / qn; qh[1] = q1 / qn; qh[2] = q2 / qn; qh[3] = q3 / qn;
-  quat_bwd(qh, qn, gR, gq);
+  quat_bwd_rot(qh, qn, gth, gq);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     g_mu0[3 * n + c] = gmu0[c];
@@ -420,7 +431,7 @@ __global__ void __launch_bounds__(32 * R, 4) k_gauss_bwd(
 #pragma unroll
   for (int c = 0; c < 4; ++c) g_quat[4 * n + c] = gq[c];
   g_rho[n] = grho;
-  if (dens_grad) dens_grad[n] += gsum[(size_t)(16 + 12 * R) * N + n];  // density-control statistic
+  if (dens_grad) dens_grad[n] += gsum[(size_t)(10 + 12 * R) * N + n];  // density-control statistic
 }
 
 cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const LatticeC& L, const float* phi,

@@ -23,12 +23,6 @@
 
 namespace digs {
 
-// umma.cu: the tensor-core GEMM with BF16 operands and output, B K-major (B(k, n) = B[n ldb + k]).
-cudaError_t gemm_tc_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
-                         __nv_bfloat16* C, int ldc, const float* bias, bool relu, int* status, cudaStream_t st);
-cudaError_t gemm_tc_conv_fwd_bf16(int M, int N, int K, const __nv_bfloat16* act, ConvGeom g, const __nv_bfloat16* W,
-                                  int ldw, __nv_bfloat16* C, int ldc, const float* bias, bool relu, cudaStream_t st);
-
 namespace {
 
 constexpr int kConvs = 4;
@@ -66,18 +60,11 @@ ParamOffsets param_offsets(int R) {
 
 size_t rows(int l, int B) { return (size_t)B * kEdge[l + 1] * kEdge[l + 1]; }  // output pixels of conv l
 size_t kdim(int l) { return (size_t)9 * kCh[l]; }
-int ilog2(int v) {
-  int k = 0;
-  while ((1 << k) < v) ++k;
-  return k;
-}
-// Input geometry of conv l for the tensor-core GEMM's implicit im2col.
-ConvGeom conv_geom(int l) { return ConvGeom{kEdge[l], kEdge[l], ilog2(kEdge[l + 1]), ilog2(kCh[l])}; }
 
 // Workspace of one batch: activations for the backward, gradients, split-K partials, BF16 copies.
 struct CnnWs {
   float *col[kConvs], *act[kConvs], *feat, *h, *out, *dout, *dh, *dfeat, *dact0, *dact1, *dcol, *part, *loss;
-  __nv_bfloat16 *pb, *xb, *colb, *actb0, *actb1, *featb, *hb;
+  CnnTc tc;  // the tensor-core path's BF16 activations, gradients and weight copies (cnn_tc.cu)
   size_t bytes;
 };
 
@@ -117,14 +104,7 @@ CnnWs cnn_layout(void* base, int B, int R) {
   w.dcol = (float*)take(max_col * 4);
   w.part = (float*)take((size_t)part_floats(B) * 4);  // split-K and bias partials
   w.loss = (float*)take(256);
-  const ParamOffsets po = param_offsets(R);
-  w.pb = (__nv_bfloat16*)take(po.total * 2);
-  w.xb = (__nv_bfloat16*)take((size_t)B * 128 * 128 * 2);
-  w.colb = (__nv_bfloat16*)take(max_col * 2);
-  w.actb0 = (__nv_bfloat16*)take(max_act * 2);
-  w.actb1 = (__nv_bfloat16*)take(max_act * 2);
-  w.featb = (__nv_bfloat16*)take((size_t)B * kFeatIn * 2);
-  w.hb = (__nv_bfloat16*)take((size_t)B * kHid * 2);
+  off += cnn_tc_layout(p ? p + off : nullptr, B, &w.tc);
   w.bytes = off;
   return w;
 }
@@ -218,14 +198,6 @@ cudaError_t gemm(int M, int N, int K, const TA* A, int lda, const TB* B, int ldb
                                                    relu ? 1 : 0);
   note_launches(1);
   return cudaGetLastError();
-}
-
-// An FP32-in / FP32-out GEMM of the training path: on the tensor cores (BF16 operands) if tc, else SIMT.
-template <bool AT, bool BT>
-cudaError_t gemm_f32(bool tc, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-                     const float* bias, bool relu, cudaStream_t st, int splits = 1, long long zstride = 0) {
-  if (tc) return gemm_tc(AT, BT, M, N, K, A, lda, B, ldb, C, ldc, bias, relu, splits, zstride, nullptr, st);
-  return gemm<AT, BT>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, st, splits, zstride);
 }
 
 // out[i] (+)= sum_z part[z][i], z in a fixed order.
@@ -420,31 +392,39 @@ NetPtrs<T> net_ptrs(const T* wp, const float* bp, const ParamOffsets& o) {
     if (e__ != cudaSuccess) return e__;      \
   } while (0)
 
-// FP32 forward keeping every activation in the workspace for the backward.
+CnnNet cnn_net(const NetPtrs<float>& N) {
+  CnnNet n;
+  for (int l = 0; l < kConvs; ++l) {
+    n.w[l] = N.w[l];
+    n.b[l] = N.b[l];
+  }
+  n.w1 = N.w1;
+  n.b1 = N.b1;
+  return n;
+}
+
+// Forward keeping every activation in the workspace for the backward.  tc: the tensor-core path of
+// cnn_tc.cu up to the dense layer's output (BF16 activations), else FP32 SIMT GEMMs over im2col
+// matrices; the R-wide output layer is FP32 either way.
 cudaError_t forward_f32(const NetPtrs<float>& N, int R, const float* img, const float* cs, int B, const CnnWs& w,
                         bool tc, cudaStream_t st) {
-  const float* in = img;
-  for (int l = 0; l < kConvs; ++l) {
-    const int H = kEdge[l], C = kCh[l];
-    if (tc && l > 0) {  // the tensor-core GEMM gathers the im2col matrix of act[l - 1] itself
-      CNN_TRY(gemm_tc_conv_fwd((int)rows(l, B), kCh[l + 1], (int)kdim(l), in, conv_geom(l), N.w[l], (int)kdim(l),
-                               w.act[l], kCh[l + 1], N.b[l], true, st));
-    } else {
+  if (tc) {
+    CNN_TRY(cnn_tc_forward(cnn_net(N), img, cs, B, w.tc, w.h, st));
+  } else {
+    const float* in = img;
+    for (int l = 0; l < kConvs; ++l) {
+      const int H = kEdge[l], C = kCh[l];
       const long long ncol = (long long)rows(l, B) * kdim(l);
       k_im2col<float, float><<<grid_for(ncol), 256, 0, st>>>(in, B, H, H, C, w.col[l]);
       note_launches(1);
-      CNN_TRY(gemm_f32<false, true>(tc, (int)rows(l, B), kCh[l + 1], (int)kdim(l), w.col[l], (int)kdim(l), N.w[l],
-                                    (int)kdim(l), w.act[l], kCh[l + 1], N.b[l], true, st));
+      CNN_TRY(gemm<false, true>((int)rows(l, B), kCh[l + 1], (int)kdim(l), w.col[l], (int)kdim(l), N.w[l],
+                                (int)kdim(l), w.act[l], kCh[l + 1], N.b[l], true, st));
+      in = w.act[l];
     }
-    in = w.act[l];
-  }
-  k_features<float, float><<<grid_for((long long)B * kFeatIn), 256, 0, st>>>(w.act[kConvs - 1], cs, B, w.feat);
-  note_launches(1);
-  if (tc)  // 8194-deep and only B x 128 wide: split K over 16 blocks per tile
-    CNN_TRY(gemm_tc_sum(false, true, B, kHid, kFeatIn, w.feat, kFeatIn, N.w1, kFeatIn, w.h, kHid, N.b1, true, 16,
-                        w.part, nullptr, st));
-  else
+    k_features<float, float><<<grid_for((long long)B * kFeatIn), 256, 0, st>>>(w.act[kConvs - 1], cs, B, w.feat);
+    note_launches(1);
     CNN_TRY(gemm<false, true>(B, kHid, kFeatIn, w.feat, kFeatIn, N.w1, kFeatIn, w.h, kHid, N.b1, true, st));
+  }
   CNN_TRY(gemm<false, true>(B, R, kHid, w.h, kHid, N.w2, kHid, w.out, R, N.b2, false, st));
   return cudaGetLastError();
 }
@@ -458,12 +438,19 @@ cudaError_t backward_f32(const NetPtrs<float>& N, const ParamOffsets& o, int R, 
   CNN_TRY(gemm<false, false>(B, kHid, R, w.dout, R, N.w2, kHid, w.dh, kHid, nullptr, false, st));
   k_relu_bwd<<<grid_for((long long)B * kHid), 256, 0, st>>>(w.h, (long long)B * kHid, w.dh);
   note_launches(1);
-  // hidden layer
-  CNN_TRY(gemm_f32<true, false>(tc, kHid, kFeatIn, B, w.dh, kHid, w.feat, kFeatIn, grad + o.w1, kFeatIn, nullptr,
-                                false, st));
   CNN_TRY(colsum(w.dh, B, kHid, w.part, grad + o.b1, st));
-  CNN_TRY(gemm_f32<false, false>(tc, B, kFeatIn, kHid, w.dh, kHid, N.w1, kFeatIn, w.dfeat, kFeatIn, nullptr, false,
-                                 st));
+  if (tc) {
+    CnnGrad g;
+    for (int l = 0; l < kConvs; ++l) {
+      g.w[l] = grad + o.w[l];
+      g.b[l] = grad + o.b[l];
+    }
+    g.w1 = grad + o.w1;
+    return cnn_tc_backward(B, w.tc, w.dh, g, st);
+  }
+  // hidden layer
+  CNN_TRY(gemm<true, false>(kHid, kFeatIn, B, w.dh, kHid, w.feat, kFeatIn, grad + o.w1, kFeatIn, nullptr, false, st));
+  CNN_TRY(gemm<false, false>(B, kFeatIn, kHid, w.dh, kHid, N.w1, kFeatIn, w.dfeat, kFeatIn, nullptr, false, st));
   k_feat_grad<<<grid_for((long long)B * kFeat), 256, 0, st>>>(w.dfeat, B, w.dact0);
   note_launches(1);
   // convolutions, last to first; dact0 holds dL/d(output of conv l)
@@ -474,23 +461,13 @@ cudaError_t backward_f32(const NetPtrs<float>& N, const ParamOffsets& o, int R, 
     k_relu_bwd<<<grid_for((long long)M * Nn), 256, 0, st>>>(w.act[l], (long long)M * Nn, dY);
     note_launches(1);
     const long long ndw = (long long)Nn * K;
-    // split K (the B x H x W rows): dW has few 128 x 64 tiles (Nn <= 128 rows, K <= 1152 columns), so the
-    // tensor-core path splits until about 4 CTAs per SM are busy, keeping >= 256 rows per split and the
-    // partials within the buffer
-    const long long tiles = (long long)((K + 63) / 64) * ((Nn + 127) / 128);
-    const int splits = tc ? (int)std::max<long long>(1, std::min<long long>({(4LL * 152 + tiles - 1) / tiles,
-                                                                             (M + 255) / 256, part_floats(B) / ndw,
-                                                                             1024}))
-                          : kSplits;
-    if (tc && l > 0)  // the im2col matrix of act[l - 1], gathered by the GEMM (the forward stored none)
-      CNN_TRY(gemm_tc_conv_dw(Nn, K, M, dY, Nn, w.act[l - 1], conv_geom(l), w.part, K, splits, ndw, st));
-    else
-      CNN_TRY(gemm_f32<true, false>(tc, Nn, K, M, dY, Nn, w.col[l], K, w.part, K, nullptr, false, st, splits, ndw));
+    const int splits = kSplits;  // split the B x H x W rows: dW is at most 128 x 1152
+    CNN_TRY(gemm<true, false>(Nn, K, M, dY, Nn, w.col[l], K, w.part, K, nullptr, false, st, splits, ndw));
     k_sum_splits<<<(unsigned)((ndw + 255) / 256), 256, 0, st>>>(w.part, splits, ndw, grad + o.w[l], 0);
     note_launches(1);
     CNN_TRY(colsum(dY, M, Nn, w.part, grad + o.b[l], st));
     if (l > 0) {
-      CNN_TRY(gemm_f32<false, false>(tc, M, K, Nn, dY, Nn, N.w[l], K, w.dcol, K, nullptr, false, st));
+      CNN_TRY(gemm<false, false>(M, K, Nn, dY, Nn, N.w[l], K, w.dcol, K, nullptr, false, st));
       const int H = kEdge[l], C = kCh[l];
       k_col2im<<<grid_for((long long)B * H * H * C), 256, 0, st>>>(w.dcol, B, H, H, C, dX);
       note_launches(1);
@@ -597,35 +574,9 @@ digs_status digs_cnn_infer_bf16(const float* params, int R, const float* img, co
   if (w.bytes > ws_bytes) return DIGS_ERR_ARG;
   const ParamOffsets o = param_offsets(R);
   cudaStream_t st = (cudaStream_t)stream;
-  k_to_bf16<<<grid_for((long long)o.total), 256, 0, st>>>(params, (long long)o.total, w.pb);
-  k_to_bf16<<<grid_for((long long)B * 128 * 128), 256, 0, st>>>(img, (long long)B * 128 * 128, w.xb);
-  note_launches(2);
-  const NetPtrs<__nv_bfloat16> N = net_ptrs<__nv_bfloat16>(w.pb, params, o);  // biases stay FP32
-  const __nv_bfloat16* in = w.xb;
-  __nv_bfloat16* out_act = w.actb0;
-  for (int l = 0; l < kConvs; ++l) {
-    const int H = kEdge[l], C = kCh[l];
-    if (l > 0) {
-      if (gemm_tc_conv_fwd_bf16((int)rows(l, B), kCh[l + 1], (int)kdim(l), in, conv_geom(l), N.w[l], (int)kdim(l),
-                                out_act, kCh[l + 1], N.b[l], true, st) != cudaSuccess)
-        return DIGS_ERR_CUDA;
-    } else {
-      const long long ncol = (long long)rows(l, B) * kdim(l);
-      k_im2col<__nv_bfloat16, __nv_bfloat16><<<grid_for(ncol), 256, 0, st>>>(in, B, H, H, C, w.colb);
-      note_launches(1);
-      if (gemm_tc_bf16((int)rows(l, B), kCh[l + 1], (int)kdim(l), w.colb, (int)kdim(l), N.w[l], (int)kdim(l), out_act,
-                       kCh[l + 1], N.b[l], true, nullptr, st) != cudaSuccess)
-        return DIGS_ERR_CUDA;
-    }
-    in = out_act;
-    out_act = (out_act == w.actb0) ? w.actb1 : w.actb0;
-  }
-  k_features<__nv_bfloat16, __nv_bfloat16><<<grid_for((long long)B * kFeatIn), 256, 0, st>>>(in, cs, B, w.featb);
-  note_launches(1);
-  if (gemm_tc_bf16(B, kHid, kFeatIn, w.featb, kFeatIn, N.w1, kFeatIn, w.hb, kHid, N.b1, true, nullptr, st) !=
-      cudaSuccess)
-    return DIGS_ERR_CUDA;
-  if (gemm<false, true>(B, R, kHid, w.hb, kHid, N.w2, kHid, w_out, R, N.b2, false, st) != cudaSuccess)
+  const NetPtrs<float> N = net_ptrs<float>(params, params, o);
+  if (cnn_tc_forward(cnn_net(N), img, cs, B, w.tc, w.h, st) != cudaSuccess) return DIGS_ERR_CUDA;
+  if (gemm<false, true>(B, R, kHid, w.h, kHid, N.w2, kHid, w_out, R, N.b2, false, st) != cudaSuccess)
     return DIGS_ERR_CUDA;
   return DIGS_OK;
 }

@@ -1,0 +1,771 @@
+// The weight-predictor CNN on the tensor cores: forward (training and inference) and parameter gradient
+// with BF16 operands and FP32 accumulation in tensor memory (tcgen05, sm_103a).
+//
+// Activations live in BF16, NHWC, exactly as the GEMMs consume them: the post-ReLU output of every
+// convolution is rounded once by the epilogue that produces it (the rounding the tensor cores would
+// apply anyway), its sign is the ReLU mask of the backward.  Every GEMM is one launch of one kernel
+// template: 128 threads per 128-row tile of C; the four warps fill a 4-stage ring of 64-deep K slices of
+// A and B with 16-byte cp.async copies (zero-filled where an operand is padding), one thread issues the
+// four 128 x BN x 16 MMAs of a slice and commits them to the slice's mbarrier, and the accumulator goes
+// through a per-role epilogue.  Operands are read in place, K-major or MN-major:
+//   forward conv        C[pixel][co] = im2col(act)[pixel][(tap, ci)] W[co][(tap, ci)]^T   (A gathered)
+//   data gradient       one GEMM per output-pixel parity class (py, px) of the stride-2 convolution:
+//                       the input pixel (2Y + py, 2X + px) receives only the taps with ky = 1 (py = 0) or
+//                       ky in {0, 2} (py = 1), and likewise in x, so
+//                       dX_class[(b, Y, X)][ci] = sum over the class's taps and co of
+//                       dY[(b, y(Y, ky), x(X, kx))][co] W[co][ky][kx][ci] -- no col2im
+//   weight gradient     dW[(tap, ci)][co] = sum over pixels of im2col(act)[pixel][(tap, ci)] dY[pixel][co],
+//                       both operands MN-major (channel-contiguous), split over pixels
+//   dense layer         feat W1^T (split K), its weight and data gradients with MN-major operands.
+// Epilogues fuse what surrounds each GEMM: bias and ReLU with the BF16 rounding (forward), the ReLU mask
+// of the layer below with the BF16 rounding of its gradient and per-CTA column sums for its bias
+// gradient (data gradient), transposed partial stores (weight gradients).  The first convolution has a
+// single input channel (K = 9) and runs on the SIMT pipes with the same rounded operands.
+// Every mbarrier wait is bounded; a K-loop wait that gives up sets *status and the CTA drains its own
+// MMAs (default bound) before it frees its tensor memory.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "digs_internal.h"
+#include "tcgen05.cuh"
+
+namespace digs {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kThr = 128;
+constexpr int kBM = 128, kBK = 64;
+constexpr int kStages = 4;
+
+// ---- geometry of the network (cnn.cu holds the parameter layout) --------------------------------
+constexpr int kCh[5] = {1, 32, 64, 128, 128};
+constexpr int kEdge[5] = {128, 64, 32, 16, 8};
+constexpr int kFeat = 8192, kFeatPitch = 8200, kHid = 128;
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ void unpack8(const uint4& u, float f[8]) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    f[2 * i] = __uint_as_float(w[i] << 16);
+    f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+  }
+}
+
+// 16-byte asynchronous copy global -> shared; src == nullptr fills the 16 bytes with zeros (no bytes read).
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, const void* valid_any) {
+  const int n = src ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src ? src : valid_any), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// ---- operand loaders -------------------------------------------------------------------------------
+// K-major loaders return the address of the 8 reduction elements [k, k + 8) of operand row `row`;
+// MN-major loaders the address of the 8 row elements [mn, mn + 8) at reduction index k; nullptr where
+// the operand is zero.  kdim(K) is the reduction length of the CTA's GEMM.
+
+struct PlainK {  // X[row][k] = p[row * ld + k]
+  const bf16* p;
+  int ld, rows;
+  __device__ const bf16* kchunk(int row, int k) const { return row < rows ? p + (size_t)row * ld + k : nullptr; }
+  __device__ int kdim(int K) const { return K; }
+  __device__ int zsplit() const { return blockIdx.z; }
+};
+
+struct PlainMN {  // X[mn][k] = p[k * ld + mn]
+  const bf16* p;
+  int ld, cols;
+  __device__ const bf16* mnchunk(int mn, int k) const { return mn < cols ? p + (size_t)k * ld + mn : nullptr; }
+  __device__ int kdim(int K) const { return K; }
+  __device__ int zsplit() const { return blockIdx.z; }
+};
+
+// Implicit im2col of a 3 x 3, stride-2, padding-1 convolution over an NHWC input H x W x C (powers of
+// two, C >= 8): row p = output pixel (b, y, x), column (tap, c) = in[b][2y + ky - 1][2x + kx - 1][c].
+struct ConvGeomB {
+  const bf16* act;
+  int H, lwo, lc, rows, cols;  // input height (= width); log2 output width; log2 C; pixels; 9 C
+  __device__ const bf16* at(int p, int kk) const {
+    if (p >= rows || kk >= cols) return nullptr;
+    const int tap = kk >> lc, c = kk & ((1 << lc) - 1), ky = tap / 3, kx = tap - 3 * ky;
+    const int x = p & ((1 << lwo) - 1), y = (p >> lwo) & ((1 << lwo) - 1), b = p >> (2 * lwo);
+    const int iy = 2 * y + ky - 1, ix = 2 * x + kx - 1;
+    if (iy < 0 || iy >= H || ix < 0 || ix >= H) return nullptr;
+    return act + ((((size_t)b * H + iy) * H + ix) << lc) + c;
+  }
+};
+struct ConvK {  // A = im2col, rows = output pixels, reduction = (tap, c)
+  ConvGeomB g;
+  __device__ const bf16* kchunk(int row, int k) const { return g.at(row, k); }
+  __device__ int kdim(int K) const { return K; }
+  __device__ int zsplit() const { return blockIdx.z; }
+};
+struct ConvMN {  // A = im2col^T, rows = (tap, c), reduction = output pixels
+  ConvGeomB g;
+  __device__ const bf16* mnchunk(int mn, int k) const { return g.at(k, mn); }
+  __device__ int kdim(int K) const { return K; }
+  __device__ int zsplit() const { return blockIdx.z; }
+};
+
+// Taps (ky, kx) that reach input pixels of parity class z = 2 py + px, and the offset of the class's
+// weight block (in units of N C) in the class-ordered transposed weights.
+__device__ __forceinline__ int class_taps(int z) { return (z == 0) ? 1 : (z == 3 ? 4 : 2); }
+__device__ __forceinline__ int class_off(int z) { return z == 0 ? 0 : (z == 1 ? 1 : (z == 2 ? 3 : 5)); }
+__host__ __device__ __forceinline__ void class_tap(int z, int t, int& ky, int& kx) {
+  const int py = z >> 1, px = z & 1;
+  const int nx = px ? 2 : 1;
+  const int ty = t / nx, tx = t - ty * nx;
+  ky = py ? 2 * ty : 1;
+  kx = px ? 2 * tx : 1;
+}
+
+// A of the data-gradient GEMM of class z = blockIdx.z: row (b, Y, X) of the class grid (Ho x Ho, the
+// output size of the convolution), reduction (t, co) over the class's taps and the N output channels:
+// dY[b][y][x][co] with 2y + ky - 1 = 2Y + py, 2x + kx - 1 = 2X + px.
+struct ParityK {
+  const bf16* dy;
+  int lho, ln, rows;  // log2 Ho; log2 N; rows = B Ho Ho
+  __device__ const bf16* kchunk(int row, int k) const {
+    if (row >= rows) return nullptr;
+    const int z = blockIdx.z, t = k >> ln, co = k & ((1 << ln) - 1);
+    int ky, kx;
+    class_tap(z, t, ky, kx);
+    const int Ho = 1 << lho;
+    const int X = row & (Ho - 1), Y = (row >> lho) & (Ho - 1), b = row >> (2 * lho);
+    const int y = (2 * Y + (z >> 1) + 1 - ky) >> 1, x = (2 * X + (z & 1) + 1 - kx) >> 1;
+    if (y >= Ho || x >= Ho) return nullptr;
+    return dy + ((((((size_t)b << lho) + y) << lho) + x) << ln) + co;
+  }
+  __device__ int kdim(int) const { return class_taps(blockIdx.z) << ln; }
+  __device__ int zsplit() const { return 0; }  // blockIdx.z is the class, not a split
+};
+
+// B of the data-gradient GEMM: the class's weights transposed, wt[class block][ci][(t, co)].
+struct ClassWt {
+  const bf16* wt;
+  int ln, C;  // log2 N (output channels of the convolution), C input channels (rows)
+  __device__ const bf16* kchunk(int row, int k) const {
+    if (row >= C) return nullptr;
+    const int z = blockIdx.z, kc = class_taps(z) << ln;
+    return wt + ((size_t)class_off(z) << ln) * C + (size_t)row * kc + k;
+  }
+  __device__ int kdim(int K) const { return K; }
+};
+
+// ---- epilogues ---------------------------------------------------------------------------------------
+// apply(row, col0, v[16], acc): the accumulator's row `row`, columns [col0, col0 + 16) of the CTA's tile
+// (global indices); acc is a per-thread running value; finish(...) runs once per thread after all
+// columns, with the CTA's shared scratch (all threads call it).
+
+// BF16 rows (+ bias, ReLU): out[(row / group) * gpitch + (row % group) * rpitch + col].
+struct EpiBf16 {
+  bf16* out;
+  const float* bias;
+  int relu, rows, group, gpitch, rpitch;
+  __device__ void apply(int row, int col0, float v[16], float&, float*) const {
+    if (row >= rows) return;
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float a = v[2 * j] + bias[col0 + 2 * j], b = v[2 * j + 1] + bias[col0 + 2 * j + 1];
+      if (relu) {
+        a = fmaxf(a, 0.f);
+        b = fmaxf(b, 0.f);
+      }
+      w[j] = pack2(a, b);
+    }
+    uint4* d = reinterpret_cast<uint4*>(out + (size_t)(row / group) * gpitch + (size_t)(row % group) * rpitch + col0);
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  }
+  __device__ void finish(int, float, float*, int) const {}
+};
+
+// FP32 rows of split z: part[z * zstride + row * ld + col].
+struct EpiF32 {
+  float* part;
+  long long zstride;
+  int rows, ld;
+  __device__ void apply(int row, int col0, float v[16], float&, float*) const {
+    if (row >= rows) return;
+    float4* d = reinterpret_cast<float4*>(part + blockIdx.z * zstride + (size_t)row * ld + col0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  }
+  __device__ void finish(int, float, float*, int) const {}
+};
+
+// Transposed FP32 store of split z: out[z * zstride + col * ld + row] for row < rows (coalesced: the
+// lanes of a warp hold consecutive rows).
+struct EpiF32T {
+  float* out;
+  long long zstride;
+  int rows, ld;
+  __device__ void apply(int row, int col0, float v[16], float&, float*) const {
+    if (row >= rows) return;
+    float* d = out + blockIdx.z * zstride + (size_t)col0 * ld + row;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) d[(size_t)j * ld] = v[j];
+  }
+  __device__ void finish(int, float, float*, int) const {}
+};
+
+// Sum 16 per-lane values over the warp's 32 lanes by recursive halving (16 shuffles); lane l ends with
+// the total of value 8 b4 + 4 b3 + 2 b2 + b1 (b_i = bit i of l).
+__device__ __forceinline__ float warp_sum16(float v[16], int lane) {
+#pragma unroll
+  for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
+    const bool hi = (lane & bit) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = hi ? v[i] : v[i + half], keep = hi ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+__device__ __forceinline__ int sum16_col(int lane) {
+  return 8 * ((lane >> 4) & 1) + 4 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
+}
+
+// Data gradient of class z: row (b, Y, X) is input pixel (b, 2Y + py, 2X + px) of a layer with C = BN
+// channels and H x H pixels; dY_in = dX * [act > 0] (act: that layer's post-ReLU output), stored in BF16
+// at the NHWC index; the masked FP32 values are summed per column over the CTA's rows into
+// colpart[z * gridDim.x + blockIdx.x][col] (bias gradient of that layer).
+template <int BN>
+struct EpiDx {
+  bf16* dy_out;
+  const bf16* act;
+  float* colpart;
+  int lho, H, rows;
+  __device__ void apply(int row, int col0, float v[16], float&, float* scratch) const {
+    const int z = blockIdx.z;
+    if (row < rows) {
+      const int Ho = 1 << lho;
+      const int X = row & (Ho - 1), Y = (row >> lho) & (Ho - 1), b = row >> (2 * lho);
+      const size_t idx = (((size_t)b * H + 2 * Y + (z >> 1)) * H + 2 * X + (z & 1)) * BN + col0;
+      const uint4* a = reinterpret_cast<const uint4*>(act + idx);
+      float m[16];
+      unpack8(a[0], m);
+      unpack8(a[1], m + 8);
+      uint32_t w[8];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = m[j] > 0.f ? v[j] : 0.f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[j] = pack2(v[2 * j], v[2 * j + 1]);
+      uint4* d = reinterpret_cast<uint4*>(dy_out + idx);
+      d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = 0.f;
+    }
+    // column sums over the warp's 32 rows, into the shared scratch [warp][BN] (written in finish order)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float s = warp_sum16(v, lane);
+    if ((lane & 1) == 0) scratch[warp * BN + col0 - blockIdx.y * BN + sum16_col(lane)] = s;
+  }
+  __device__ void finish(int, float, float* scratch, int tid) const {
+    __syncthreads();
+    if (tid < BN) {
+      const float s = scratch[tid] + scratch[BN + tid] + scratch[2 * BN + tid] + scratch[3 * BN + tid];
+      colpart[((size_t)blockIdx.z * gridDim.x + blockIdx.x) * BN + tid] = s;
+    }
+  }
+};
+
+// Gradient of the dense layer's input, rows f (feature) and columns b (batch entry):
+// dY3[b][f] = dfeat[b][f] [act3[b][f] > 0] in BF16 for f < 8192 (the convolution features; the two angle
+// inputs get no gradient), and each row's sum over the CTA's columns into rowpart[blockIdx.y][f] (the
+// last convolution's bias gradient sums them over y-tiles and pixels).
+struct EpiDfeat {
+  bf16* dy3;
+  const bf16* feat;  // [B][kFeatPitch], act3 in its first 8192 columns
+  float* rowpart;
+  int nb;
+  __device__ void apply(int row, int col0, float v[16], float& acc, float*) const {
+    if (row >= kFeat) return;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int b = col0 + j;
+      if (b < nb) {
+        const float a = __bfloat162float(feat[(size_t)b * kFeatPitch + row]);
+        const float y = a > 0.f ? v[j] : 0.f;
+        dy3[(size_t)b * kFeat + row] = __float2bfloat16_rn(y);
+        acc += y;
+      }
+    }
+  }
+  __device__ void finish(int row, float acc, float*, int) const {
+    if (row < kFeat) rowpart[(size_t)blockIdx.y * kFeat + row] = acc;
+  }
+};
+
+// ---- the GEMM kernel -------------------------------------------------------------------------------
+template <int BN, bool AMN, bool BMN>
+struct Cfg {
+  static constexpr int kA = kBM * kBK * 2;  // bytes of one A slice (16 KB)
+  static constexpr int kB = BN * kBK * 2;
+  static constexpr int kStage = kA + kB;
+  // Room past the stage ring for an MN-major operand: reads that follow either reading of a
+  // descriptor's two strides stay inside the CTA's shared memory.
+  static constexpr int kPad = (AMN || BMN) ? 48 * 1024 : 0;
+  static constexpr size_t kSmem = 1024 + (size_t)kStages * kStage + kPad + 128;
+};
+
+// Shared-memory byte offset of a 16-byte chunk: K-major (row, kc) of a ROWS x 64 slice; MN-major
+// (mn chunk mc, k) of an MN x 64 slice.
+__device__ __forceinline__ uint32_t off_k(int row, int kc) { return (uint32_t)(((row >> 3) * 8 + kc) * 128 + (row & 7) * 16); }
+template <int MN>
+__device__ __forceinline__ uint32_t off_mn(int mc, int k) {
+  return (uint32_t)(((k >> 3) * (MN / 8) + mc) * 128 + (k & 7) * 16);
+}
+
+// Fills one operand slice: ROWS (MN extent) x 64 reduction elements starting at (r0, k0); the thread's
+// chunks are q = tid + 128 i, laid out so that a warp's copies fill whole 128-byte core-matrix rows.
+template <int ROWS, bool MN, class L>
+__device__ __forceinline__ void fill(const L& ld, uint32_t sdst, int r0, int k0, int kend, const void* any) {
+#pragma unroll
+  for (int i = 0; i < ROWS / 16; ++i) {
+    const int q = threadIdx.x + kThr * i;
+    if constexpr (!MN) {
+      const int row = (q & 7) | ((q >> 6) << 3), kc = (q >> 3) & 7;
+      const int k = k0 + kc * 8;
+      cp16(sdst + off_k(row, kc), k < kend ? ld.kchunk(r0 + row, k) : nullptr, any);
+    } else {
+      constexpr int G = ROWS / 8;
+      const int rest = q >> 3, mc = rest & (G - 1), k = ((rest / G) << 3) | (q & 7);
+      cp16(sdst + off_mn<ROWS>(mc, k), k0 + k < kend ? ld.mnchunk(r0 + mc * 8, k0 + k) : nullptr, any);
+    }
+  }
+}
+
+template <int ROWS, bool MN>
+__device__ __forceinline__ uint64_t slice_desc(uint32_t a, int j) {
+  if constexpr (!MN) return tc::smem_desc(a + j * 256, 128, 1024);
+  return tc::smem_desc(a + j * 2 * (ROWS / 8) * 128, (ROWS / 8) * 128, 128);
+}
+
+// C tile (128 x BN) of CTA (blockIdx.x, blockIdx.y); blockIdx.z = split of the reduction (kchunk each)
+// or, for the data gradient, the parity class (its loaders read blockIdx.z).
+template <int BN, bool AMN, bool BMN, class LA, class LB, class EP>
+__global__ void __launch_bounds__(kThr, 1) k_cnn_gemm(const LA la, const LB lb, const EP ep, int K, int kchunk, int* status,
+                                                      unsigned wait_limit, const void* any) {
+  using C = Cfg<BN, AMN, BMN>;
+  extern __shared__ unsigned char smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bar = (uint64_t*)(sm + kStages * C::kStage + C::kPad);
+  uint32_t* tslot = (uint32_t*)(bar + kStages);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int Kz = la.kdim(K);
+  const long long kb0 = (long long)la.zsplit() * kchunk;
+  const int kb = kb0 >= Kz ? Kz : (int)kb0;
+  const int ke = (int)min((long long)Kz, (long long)kb + kchunk);
+  const int nk = ke > kb ? (ke - kb + kBK - 1) / kBK : 0;
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < kStages; ++s) tc::mbar_init(bar + s, 1);
+    tc::mbar_init_fence();
+  }
+  if (warp == 0) tc::tmem_alloc(tslot, BN);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t sbase = tc::smem_u32(sm);
+  constexpr uint32_t idesc = tc::idesc_bf16(kBM, BN, AMN, BMN);
+  auto load = [&](int s) {
+    const uint32_t sa = sbase + (s % kStages) * C::kStage;
+    const int k0 = kb + s * kBK;
+    fill<kBM, AMN>(la, sa, m0, k0, ke, any);
+    fill<BN, BMN>(lb, sa + C::kA, n0, k0, ke, any);
+  };
+#pragma unroll
+  for (int s = 0; s < kStages - 1; ++s) {
+    if (s < nk) load(s);
+    cp_commit();
+  }
+  int ok = 1, issued = 0;
+  for (int c = 0; c < nk; ++c) {
+    cp_wait<kStages - 2>();     // this thread's copies of slice c have landed
+    tc::fence_async_smem();     // ... and are visible to the tensor core
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t sa = sbase + (c % kStages) * C::kStage, sb = sa + C::kA;
+#pragma unroll
+      for (int j = 0; j < kBK / 16; ++j)
+        tc::mma_bf16(tmem, slice_desc<kBM, AMN>(sa, j), slice_desc<BN, BMN>(sb, j), idesc, (c > 0 || j > 0) ? 1u : 0u);
+      tc::mma_commit(bar + c % kStages);
+    }
+    issued = c + 1;
+    const int nxt = c + kStages - 1;  // refills the buffer of slice c - 1 once its MMAs are done
+    if (nxt < nk) {
+      if (c >= 1) ok = ok && tc::mbar_wait(bar + (c - 1) % kStages, (uint32_t)(((c - 1) / kStages) & 1), wait_limit);
+      if (ok) load(nxt);
+    }
+    cp_commit();
+  }
+  cp_wait<0>();
+  const bool drained = issued == 0 ||
+                       tc::mbar_wait(bar + (issued - 1) % kStages, (uint32_t)(((issued - 1) / kStages) & 1), tc::kWaitLimit);
+  ok = __syncthreads_and(ok && drained);
+  tc::fence_after();
+  float* scratch = reinterpret_cast<float*>(sm);  // the stage ring is idle now
+  float acc = 0.f;
+  const int row = m0 + warp * 32 + lane;
+  if (ok) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (issued == 0) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+      }
+      ep.apply(row, n0 + c0, v, acc, scratch);
+    }
+  }
+  if (ok) ep.finish(row, acc, scratch, tid);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_dealloc(tmem, BN);
+  }
+  if (!ok && tid == 0 && status) atomicExch(status, 1);
+}
+
+// ---- SIMT kernels and small steps --------------------------------------------------------------------
+
+// First convolution (1 -> 32 channels, 128^2 -> 64^2): act0[p][co] = relu(b[co] + sum over taps of
+// r(w[co][tap]) img(tap)), r = BF16 rounding, img the BF16-rounded input; one thread per output pixel,
+// 32 channels stored as four 16-byte BF16 chunks.
+__global__ void __launch_bounds__(256) k_conv0_fwd(const bf16* __restrict__ img, const float* __restrict__ w,
+                                                   const float* __restrict__ bias, int npix, bf16* __restrict__ out) {
+  __shared__ float sw[32 * 9], sb[32];
+  for (int i = threadIdx.x; i < 32 * 9; i += blockDim.x) sw[i] = bf16r(w[i]);
+  if (threadIdx.x < 32) sb[threadIdx.x] = bias[threadIdx.x];
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npix) return;
+  const int x = p & 63, y = (p >> 6) & 63, b = p >> 12;
+  float xin[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    const int iy = 2 * y + t / 3 - 1, ix = 2 * x + t % 3 - 1;
+    xin[t] = (iy >= 0 && iy < 128 && ix >= 0 && ix < 128) ? __bfloat162float(img[((size_t)b * 128 + iy) * 128 + ix])
+                                                           : 0.f;
+  }
+  uint4* d = reinterpret_cast<uint4*>(out + (size_t)p * 32);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int co = 8 * q + j;
+      float a = sb[co];
+#pragma unroll
+      for (int t = 0; t < 9; ++t) a = fmaf(sw[co * 9 + t], xin[t], a);
+      o[j] = fmaxf(a, 0.f);
+    }
+    d[q] = make_uint4(pack2(o[0], o[1]), pack2(o[2], o[3]), pack2(o[4], o[5]), pack2(o[6], o[7]));
+  }
+}
+
+// Weight gradient of the first convolution: part[block][co * 9 + tap] = sum over the block's pixels of
+// dY0[p][co] img(tap) (both BF16), tiles of 64 pixels staged in shared memory, grid-stride over tiles.
+__global__ void __launch_bounds__(256) k_conv0_dw(const bf16* __restrict__ dy, const bf16* __restrict__ img, int npix,
+                                                  float* __restrict__ part) {
+  __shared__ float sdy[64][33];
+  __shared__ float sx[64][9];
+  const int tid = threadIdx.x;
+  const int o0 = tid, o1 = 256 + tid;  // outputs co * 9 + tap; o1 valid for tid < 32
+  float a0 = 0.f, a1 = 0.f;
+  for (long long p0 = (long long)blockIdx.x * 64; p0 < npix; p0 += (long long)gridDim.x * 64) {
+    {
+      const int pix = tid >> 2, cq = tid & 3;
+      const long long p = p0 + pix;
+      float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (p < npix) unpack8(*reinterpret_cast<const uint4*>(dy + p * 32 + cq * 8), f);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) sdy[pix][cq * 8 + j] = f[j];
+    }
+    for (int i = tid; i < 64 * 9; i += 256) {
+      const int pix = i / 9, t = i - 9 * pix;
+      const long long p = p0 + pix;
+      float v = 0.f;
+      if (p < npix) {
+        const int x = (int)(p & 63), y = (int)((p >> 6) & 63), b = (int)(p >> 12);
+        const int iy = 2 * y + t / 3 - 1, ix = 2 * x + t % 3 - 1;
+        if (iy >= 0 && iy < 128 && ix >= 0 && ix < 128) v = __bfloat162float(img[((size_t)b * 128 + iy) * 128 + ix]);
+      }
+      sx[pix][t] = v;
+    }
+    __syncthreads();
+    {
+      const int co = o0 / 9, t = o0 - 9 * co;
+#pragma unroll 8
+      for (int q = 0; q < 64; ++q) a0 = fmaf(sdy[q][co], sx[q][t], a0);
+    }
+    if (tid < 32) {
+      const int co = o1 / 9, t = o1 - 9 * co;
+#pragma unroll 8
+      for (int q = 0; q < 64; ++q) a1 = fmaf(sdy[q][co], sx[q][t], a1);
+    }
+    __syncthreads();
+  }
+  part[(size_t)blockIdx.x * 288 + o0] = a0;
+  if (tid < 32) part[(size_t)blockIdx.x * 288 + o1] = a1;
+}
+
+// out[c] = sum over r < R of in[r * ld + c], rows in a fixed order (strided over the block's 8 warps,
+// then the 8 warp sums in order); 32 columns per block.
+__global__ void __launch_bounds__(256) k_colreduce(const float* __restrict__ in, int R, int cols, int ld,
+                                                   float* __restrict__ out) {
+  __shared__ float red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (c < cols)
+    for (int r = warp; r < R; r += 8) s += in[(size_t)r * ld + c];
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && c < cols) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += red[k][lane];
+    out[c] = t;
+  }
+}
+
+// out[i] = sum over z of part[z * n + i], z in order (+ bias[i % nb] and ReLU when bias != nullptr).
+__global__ void k_sum_z(const float* __restrict__ part, int Z, long long n, const float* __restrict__ bias, int nb,
+                        float* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < Z; ++z) s += part[(size_t)z * n + i];
+    if (bias) s = fmaxf(s + bias[i % nb], 0.f);
+    out[i] = s;
+  }
+}
+
+// out[r][c] = BF16 of in[r][c] for c < cols, 0 for cols <= c < ld (row pitch ld).
+__global__ void k_to_bf16_rows(const float* __restrict__ in, int rows, int cols, int ld, bf16* __restrict__ out) {
+  const long long n = (long long)rows * ld;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / ld), c = (int)(i - (long long)r * ld);
+    out[i] = __float2bfloat16_rn(c < cols ? in[(size_t)r * cols + c] : 0.f);
+  }
+}
+
+// Class-ordered transposed weights of a convolution with N output and C input channels:
+// wt[class block z][ci][(t, co)] = BF16 of w[co][ky_t][kx_t][ci] for the class's taps t.
+__global__ void k_wt_class(const float* __restrict__ w, int N, int C, bf16* __restrict__ wt) {
+  const long long total = 9LL * N * C, NC = (long long)N * C;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int z = e < NC ? 0 : (e < 3 * NC ? 1 : (e < 5 * NC ? 2 : 3));
+    const long long local = e - (long long)class_off(z) * NC;
+    const int kc = class_taps(z) * N;
+    const int ci = (int)(local / kc), rem = (int)(local - (long long)ci * kc), t = rem / N, co = rem - t * N;
+    int ky, kx;
+    class_tap(z, t, ky, kx);
+    wt[e] = __float2bfloat16_rn(w[((size_t)co * 9 + ky * 3 + kx) * C + ci]);
+  }
+}
+
+// The dense layer's two angle inputs and zero padding: feat[b][8192 + j] = BF16 of (cos, sin, 0, ...).
+__global__ void k_feat_tail(bf16* __restrict__ feat, const float* __restrict__ cs, int B) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * (kFeatPitch - kFeat)) return;
+  const int b = i / (kFeatPitch - kFeat), j = i - b * (kFeatPitch - kFeat);
+  feat[(size_t)b * kFeatPitch + kFeat + j] = __float2bfloat16_rn(j < 2 ? cs[2 * b + j] : 0.f);
+}
+
+__global__ void k_f32_to_bf16(const float* __restrict__ x, long long n, bf16* __restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
+unsigned grid_of(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16)); }
+
+// One GEMM launch: M rows of C in 128-row tiles, gy column tiles of BN, gz splits (or classes).
+template <int BN, bool AMN, bool BMN, class LA, class LB, class EP>
+cudaError_t gemm(const LA& la, const LB& lb, const EP& ep, int M, int K, int gy, int gz, int kchunk, const void* any,
+                 cudaStream_t st) {
+  using C = Cfg<BN, AMN, BMN>;
+  auto kern = k_cnn_gemm<BN, AMN, BMN, LA, LB, EP>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (M <= 0) return cudaSuccess;
+  kern<<<dim3((M + kBM - 1) / kBM, gy, gz), kThr, C::kSmem, st>>>(la, lb, ep, K, kchunk, nullptr, tc::kWaitLimit, any);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+#define TC_TRY(...)                       \
+  do {                                    \
+    cudaError_t e__ = (__VA_ARGS__);      \
+    if (e__ != cudaSuccess) return e__;   \
+  } while (0)
+
+// Splits of a pixel-reduction weight gradient: about two CTAs per SM over the row tiles, at least four
+// 64-pixel slices per split, partials within the buffer.
+int dw_splits(int tiles, long long pixels, long long part_floats, long long tile_floats) {
+  long long z = (2LL * 152 + tiles - 1) / tiles;
+  z = std::min(z, std::max(1LL, pixels / 256));
+  z = std::min(z, std::max(1LL, part_floats / tile_floats));
+  return (int)std::max(1LL, z);
+}
+int chunk_of(long long n, int z) { return (int)(((n + z - 1) / z + kBK - 1) / kBK * kBK); }
+
+}  // namespace
+
+// ---- host side -------------------------------------------------------------------------------------
+
+size_t cnn_tc_layout(void* base, int B, CnnTc* t) {
+  size_t off = 0;
+  char* p = (char*)base;
+  auto take = [&](size_t bytes) -> void* {
+    void* q = p ? p + off : nullptr;
+    off += (bytes + 255) & ~(size_t)255;
+    return q;
+  };
+  CnnTc w{};
+  w.imgb = (uint16_t*)take((size_t)B * 128 * 128 * 2);
+  for (int l = 0; l < 3; ++l) w.act[l] = (uint16_t*)take((size_t)B * kEdge[l + 1] * kEdge[l + 1] * kCh[l + 1] * 2);
+  w.feat = (uint16_t*)take((size_t)B * kFeatPitch * 2);
+  w.dy[0] = (uint16_t*)take((size_t)B * 4096 * 32 * 2);  // dY of conv 2, then of conv 0
+  w.dy[1] = (uint16_t*)take((size_t)B * 1024 * 64 * 2);  // dY of conv 1
+  w.dy3 = (uint16_t*)take((size_t)B * kFeat * 2);
+  w.dhb = (uint16_t*)take((size_t)B * kHid * 2);
+  for (int l = 1; l < 4; ++l) {
+    w.wb[l] = (uint16_t*)take((size_t)kCh[l + 1] * 9 * kCh[l] * 2);
+    w.wt[l] = (uint16_t*)take((size_t)kCh[l + 1] * 9 * kCh[l] * 2);
+  }
+  w.wb[0] = w.wt[0] = nullptr;
+  w.w1b = (uint16_t*)take((size_t)kHid * kFeatPitch * 2);
+  w.part_floats = std::max<long long>(16LL * B * kHid, 5LL << 20);
+  w.part = (float*)take((size_t)w.part_floats * 4);
+  w.colpart_floats = std::max<long long>({1024LL * B, 8192LL * ((B + 127) / 128), 2LL * 152 * 288});
+  w.colpart = (float*)take((size_t)w.colpart_floats * 4);
+  if (t) *t = w;
+  return off;
+}
+
+cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs, int B, const CnnTc& t, float* h,
+                           cudaStream_t st) {
+  // BF16 copies of the weights: row-major (forward), class-ordered transposed (data gradient)
+  for (int l = 1; l < 4; ++l) {
+    const int N = kCh[l + 1], Kl = 9 * kCh[l];
+    k_to_bf16_rows<<<grid_of((long long)N * Kl), 256, 0, st>>>(net.w[l], N, Kl, Kl, (bf16*)t.wb[l]);
+    k_wt_class<<<grid_of((long long)N * Kl), 256, 0, st>>>(net.w[l], N, kCh[l], (bf16*)t.wt[l]);
+  }
+  k_to_bf16_rows<<<grid_of((long long)kHid * kFeatPitch), 256, 0, st>>>(net.w1, kHid, kFeat + 2, kFeatPitch,
+                                                                      (bf16*)t.w1b);
+  note_launches(7);
+  const int npix0 = B * 4096;
+  k_f32_to_bf16<<<grid_of((long long)B * 16384), 256, 0, st>>>(img, (long long)B * 16384, (bf16*)t.imgb);
+  k_conv0_fwd<<<(npix0 + 255) / 256, 256, 0, st>>>((const bf16*)t.imgb, net.w[0], net.b[0], npix0, (bf16*)t.act[0]);
+  note_launches(2);
+  const void* any = t.wb[1];
+  for (int l = 1; l < 4; ++l) {
+    const int H = kEdge[l], lwo = l == 1 ? 5 : (l == 2 ? 4 : 3), lc = l == 1 ? 5 : (l == 2 ? 6 : 7);
+    const int rows = B * kEdge[l + 1] * kEdge[l + 1], N = kCh[l + 1], Kl = 9 * kCh[l];
+    const ConvK A{ConvGeomB{(const bf16*)t.act[l - 1], H, lwo, lc, rows, Kl}};
+    const PlainK Bw{(const bf16*)t.wb[l], Kl, N};
+    if (l == 1) {
+      const EpiBf16 ep{(bf16*)t.act[1], net.b[1], 1, rows, 1 << 30, 0, N};
+      TC_TRY((gemm<64, false, false>(A, Bw, ep, rows, Kl, 1, 1, Kl, any, st)));
+    } else if (l == 2) {
+      const EpiBf16 ep{(bf16*)t.act[2], net.b[2], 1, rows, 1 << 30, 0, N};
+      TC_TRY((gemm<128, false, false>(A, Bw, ep, rows, Kl, 1, 1, Kl, any, st)));
+    } else {  // the last convolution writes the dense layer's feature rows ((y, x, c) order, pitch 8200)
+      const EpiBf16 ep{(bf16*)t.feat, net.b[3], 1, rows, 64, kFeatPitch, N};
+      TC_TRY((gemm<128, false, false>(A, Bw, ep, rows, Kl, 1, 1, Kl, any, st)));
+    }
+  }
+  k_feat_tail<<<(B * (kFeatPitch - kFeat) + 255) / 256, 256, 0, st>>>((bf16*)t.feat, cs, B);
+  note_launches(1);
+  // dense layer: K = 8200 split 16 ways into FP32 partials, then summed with bias and ReLU
+  const int Z = 16, kc = chunk_of(kFeatPitch, Z);
+  const EpiF32 ep{t.part, (long long)B * kHid, B, kHid};
+  TC_TRY((gemm<128, false, false>(PlainK{(const bf16*)t.feat, kFeatPitch, B}, PlainK{(const bf16*)t.w1b, kFeatPitch, kHid},
+                                  ep, B, kFeatPitch, 1, Z, kc, any, st)));
+  k_sum_z<<<grid_of((long long)B * kHid), 256, 0, st>>>(t.part, Z, (long long)B * kHid, net.b1, kHid, h);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGrad& g, cudaStream_t st) {
+  const void* any = t.wb[1];
+  k_f32_to_bf16<<<grid_of((long long)B * kHid), 256, 0, st>>>(dh, (long long)B * kHid, (bf16*)t.dhb);
+  note_launches(1);
+  // dense layer: dW1[n][f] = sum_b dh[b][n] feat[b][f] (rows f, both operands MN-major)
+  TC_TRY((gemm<128, true, true>(PlainMN{(const bf16*)t.feat, kFeatPitch, kFeatPitch}, PlainMN{(const bf16*)t.dhb, kHid, kHid},
+                                EpiF32T{g.w1, 0, kFeat + 2, kFeat + 2}, kFeatPitch, B, 1, 1, B, any, st)));
+  // ... and dfeat[b][f] = sum_n dh[b][n] W1[n][f] -> dY of the last convolution (masked, BF16) + row sums
+  const int gy = (B + 127) / 128;
+  TC_TRY((gemm<128, true, false>(PlainMN{(const bf16*)t.w1b, kFeatPitch, kFeat}, PlainK{(const bf16*)t.dhb, kHid, B},
+                                 EpiDfeat{(bf16*)t.dy3, (const bf16*)t.feat, t.colpart, B}, kFeat, kHid, gy, 1, kHid, any,
+                                 st)));
+  k_colreduce<<<(128 + 31) / 32, 256, 0, st>>>(t.colpart, gy * 64, 128, 128, g.b[3]);
+  note_launches(1);
+  // convolutions 3, 2, 1: weight gradient (split over pixels), then the data gradient of the layer below
+  const bf16* dyl = (const bf16*)t.dy3;
+  for (int l = 3; l >= 1; --l) {
+    const int H = kEdge[l], lwo = l == 1 ? 5 : (l == 2 ? 4 : 3), lc = l == 1 ? 5 : (l == 2 ? 6 : 7);
+    const int ln = l == 1 ? 6 : 7;  // log2 N_l
+    const int rows = B * kEdge[l + 1] * kEdge[l + 1], N = kCh[l + 1], Kl = 9 * kCh[l], C = kCh[l];
+    const ConvGeomB geo{(const bf16*)t.act[l - 1], H, lwo, lc, rows, Kl};
+    const int tiles = (Kl + kBM - 1) / kBM;
+    const int Z = dw_splits(tiles, rows, t.part_floats, (long long)N * Kl);
+    const int kc = chunk_of(rows, Z);
+    const EpiF32T epw{t.part, (long long)N * Kl, Kl, Kl};
+    if (N == 64)
+      TC_TRY((gemm<64, true, true>(ConvMN{geo}, PlainMN{dyl, N, N}, epw, Kl, rows, 1, Z, kc, any, st)));
+    else
+      TC_TRY((gemm<128, true, true>(ConvMN{geo}, PlainMN{dyl, N, N}, epw, Kl, rows, 1, Z, kc, any, st)));
+    k_sum_z<<<grid_of((long long)N * Kl), 256, 0, st>>>(t.part, Z, (long long)N * Kl, nullptr, 1, g.w[l]);
+    note_launches(1);
+    // data gradient, four parity classes in one launch; output dY of conv l - 1 and its bias partials
+    bf16* dyo = (bf16*)(l == 2 ? t.dy[1] : t.dy[0]);
+    const ParityK A{dyl, lwo, ln, rows};
+    const ClassWt Bw{(const bf16*)t.wt[l], ln, C};
+    if (C == 128)
+      TC_TRY((gemm<128, false, false>(A, Bw, EpiDx<128>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
+                                      9 * N, 1, 4, 1 << 30, any, st)));
+    else if (C == 64)
+      TC_TRY((gemm<64, false, false>(A, Bw, EpiDx<64>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
+                                     9 * N, 1, 4, 1 << 30, any, st)));
+    else
+      TC_TRY((gemm<32, false, false>(A, Bw, EpiDx<32>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
+                                     9 * N, 1, 4, 1 << 30, any, st)));
+    k_colreduce<<<(C + 31) / 32, 256, 0, st>>>(t.colpart, 4 * ((rows + kBM - 1) / kBM), C, C, g.b[l - 1]);
+    note_launches(1);
+    dyl = dyo;
+  }
+  // the first convolution's weight gradient on the SIMT pipes
+  const int G = 2 * 152;
+  k_conv0_dw<<<G, 256, 0, st>>>(dyl, (const bf16*)t.imgb, B * 4096, t.colpart);
+  k_colreduce<<<(288 + 31) / 32, 256, 0, st>>>(t.colpart, G, 288, 288, g.w[0]);
+  note_launches(2);
+  return cudaGetLastError();
+}
+
+}  // namespace digs

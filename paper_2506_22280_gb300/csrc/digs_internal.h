@@ -37,7 +37,7 @@ struct Workspace {
   float* gw_part;         // [pair-sum CTAs][P][R] dL/dw partial sums
   float* ffd;             // [12 R][n_total]: u_r (3R components) then grad u_r (9R) at each mean
   float* ffd2;            // [18 R][n_total]: second derivatives of u_r (6 per component)
-  float* gsum;            // [17 + 12 R][n_total]: each Gaussian's pair adjoints summed over its projections
+  float* gsum;            // [11 + 12 R][n_total]: each Gaussian's pair adjoints summed over its projections
   float* loss_part;       // [P * T * fwd_blocks(tile)] forward: squared residuals per 8 x 8 block (warp)
   float* proj;            // [P * nv * nu] (digs_step)
   float* dldi;            // [P * nv * nu] (digs_step)
@@ -109,18 +109,6 @@ cudaError_t launch_gw_reduce(const Workspace& ws, const ViewsParam& views, int P
 int chain_blocks(int n);
 int pair_sum_blocks(int n);
 
-// Geometry of a 3 x 3, stride-2, padding-1 convolution input (NHWC, H x W x C) whose im2col matrix a
-// tensor-core GEMM reads implicitly: lwo = log2 of the output width W / 2 (= output height), lc = log2 C.
-struct ConvGeom {
-  int H, W, lwo, lc;
-};
-// umma.cu: implicit-im2col GEMMs: forward C[m][n] = act(sum_k im2col(act)[m][k] W[n][k] + bias[n]);
-// weight gradient C[m][n] (+ z zstride) = sum over the split's rows k of dY[k][m] im2col(act)[k][n].
-cudaError_t gemm_tc_conv_fwd(int M, int N, int K, const float* act, ConvGeom g, const float* W, int ldw, float* C,
-                             int ldc, const float* bias, bool relu, cudaStream_t st);
-cudaError_t gemm_tc_conv_dw(int M, int N, int K, const float* dY, int ldy, const float* act, ConvGeom g, float* C,
-                            int ldc, int splits, long long zstride, cudaStream_t st);
-
 // umma.cu: tensor-core GEMM (BF16 operands rounded from FP32, FP32 accumulation); C(m, n) = sum_k
 // A(m, k) B(k, n) with A(m, k) = at ? A[k lda + m] : A[m lda + k], B(k, n) = bt ? B[n ldb + k] :
 // B[k ldb + n]; splits > 1: partial sums over K ranges into C + z zstride (bias and ReLU not applied).
@@ -144,6 +132,30 @@ cudaError_t launch_temporal_bwd(const float* g_w, int n_ctrl, int R, float t_ste
                                 float* g_ctrl, cudaStream_t st);
 
 // adam.cu
+// cnn_tc.cu: the weight-predictor CNN on the tensor cores.  Parameter and gradient pointers per layer
+// (FP32, in cnn.cu's layout: conv weights [Co][3][3][Ci], dense weights W1 [128][8194]).
+struct CnnNet {
+  const float *w[4], *b[4], *w1, *b1;
+};
+struct CnnGrad {
+  float *w[4], *b[4], *w1;
+};
+// BF16 (16-bit words) and FP32 buffers of one batch size, carved out of the caller's workspace.
+struct CnnTc {
+  uint16_t *imgb, *act[3], *feat, *dy[2], *dy3, *dhb, *wb[4], *w1b, *wt[4];
+  float *part, *colpart;
+  long long part_floats, colpart_floats;
+};
+// Bytes of the buffers for batch B (base == nullptr: size only), 256-byte aligned.
+size_t cnn_tc_layout(void* base, int B, CnnTc* t);
+// Forward to the dense layer's ReLU output h [B][128] (FP32); keeps the activations for the backward.
+cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs, int B, const CnnTc& t, float* h,
+                           cudaStream_t st);
+// Parameter gradients of every layer but the output one (and but the dense layer's bias), from
+// dh = dL/d(dense pre-activation) [B][128] (FP32, already masked by the dense layer's ReLU), through the
+// activations and weights that the last cnn_tc_forward on the same buffers kept.
+cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGrad& g, cudaStream_t st);
+
 struct AdamGroup {
   float* p;
   const float* g;

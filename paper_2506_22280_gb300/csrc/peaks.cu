@@ -94,7 +94,7 @@ extern "C" digs_status digs_pipe_bench(int kind, int iters, float* sink, long lo
     default: k_pipe<3><<<grid, kPeakThreads, 0, st>>>(iters, 0.5f, sink); break;
   }
   note_launches(1);
-  // per thread and iteration: 4 x 8 scalar results (kinds 0, 2, 3) or 8 x 4 packed pairs (kind 1)
-  *lane_ops = (long long)grid.x * kPeakThreads * (long long)iters * 32LL;
+  // per thread and iteration: 4 x 8 scalar results (kinds 0, 2, 3) or 8 x 4 packed pairs, 64 results (kind 1)
+  *lane_ops = (long long)grid.x * kPeakThreads * (long long)iters * (kind == 1 ? 64LL : 32LL);
   return cudaGetLastError() == cudaSuccess ? DIGS_OK : DIGS_ERR_CUDA;
 }

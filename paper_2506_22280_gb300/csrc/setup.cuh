@@ -23,19 +23,16 @@ __device__ __forceinline__ void quat_to_R(const float q[4], float R[9]) {
   R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
 }
 
-// dL/dq for dL/dR = gR, through R(q_hat) and q_hat = q / |q|.
-__device__ __forceinline__ void quat_bwd(const float qh[4], float qnorm, const float g[9], float gq[4]) {
-  float w = qh[0], x = qh[1], y = qh[2], z = qh[3];
-  float gw = 2.f * (-z * g[1] + y * g[2] + z * g[3] - x * g[5] - y * g[6] + x * g[7]);
-  float gx = 2.f * (y * g[1] + z * g[2] + y * g[3] - 2.f * x * g[4] - w * g[5] + z * g[6] + w * g[7] - 2.f * x * g[8]);
-  float gy = 2.f * (-2.f * y * g[0] + x * g[1] + w * g[2] + x * g[3] + z * g[5] - w * g[6] + z * g[7] - 2.f * y * g[8]);
-  float gz = 2.f * (-2.f * z * g[0] - w * g[1] + x * g[2] + w * g[3] - 2.f * z * g[4] + y * g[5] + x * g[6] + y * g[7]);
-  float dot = w * gw + x * gx + y * gy + z * gz;
-  float inv = 1.f / qnorm;
-  gq[0] = (gw - w * dot) * inv;
-  gq[1] = (gx - x * dot) * inv;
-  gq[2] = (gy - y * dot) * inv;
-  gq[3] = (gz - z * dot) * inv;
+// dL/dq for the gradient gth of a rotation R -> R (I + [theta]x) of the Gaussian's axes: the unit
+// quaternion moves by q_hat (x) (0, theta / 2) (Hamilton product, R(q1 (x) q2) = R(q1) R(q2)), so
+// dL/dq_hat = 2 q_hat (x) (0, gth), tangent to the unit sphere, and q_hat = q / |q| divides it by |q|.
+__device__ __forceinline__ void quat_bwd_rot(const float qh[4], float qnorm, const float gth[3], float gq[4]) {
+  const float w = qh[0], x = qh[1], y = qh[2], z = qh[3];
+  const float f = 2.f / qnorm;
+  gq[0] = -f * (x * gth[0] + y * gth[1] + z * gth[2]);
+  gq[1] = f * (w * gth[0] + y * gth[2] - z * gth[1]);
+  gq[2] = f * (w * gth[1] + z * gth[0] - x * gth[2]);
+  gq[3] = f * (w * gth[2] + x * gth[1] - y * gth[0]);
 }
 
 // Inverse (row-major) by the adjugate; returns det K.

@@ -1,8 +1,9 @@
 // Dense GEMM on the fifth-generation tensor cores (tcgen05, sm_103a): C = op(A) op(B) with BF16 operands
-// and FP32 accumulation in tensor memory, for the weight-predictor CNN's layers.
+// and FP32 accumulation in tensor memory, behind digs_gemm_bf16 (FP32 operands rounded while staged).
+// The CNN's own layers run on the kernels of cnn_tc.cu, which read BF16 activations in place.
 //
 // C(m, n) = sum_k A(m, k) B(k, n); A(m, k) = AT ? A[k lda + m] : A[m lda + k] and
-// B(k, n) = BT ? B[n ldb + k] : B[k ldb + n], FP32 or BF16 in global memory.  One CTA of 128 threads per
+// B(k, n) = BT ? B[n ldb + k] : B[k ldb + n], FP32 in global memory.  One CTA of 128 threads per
 // 128 x 64 tile of C:
 //   * all four warps stage 64-deep K slices of A (128 x 64) and B (64 x 64) into shared memory,
 //     rounding to BF16 (round to nearest even) and writing the K-major, non-swizzled layout the tensor
@@ -22,6 +23,7 @@
 #include <algorithm>
 
 #include "digs_internal.h"
+#include "tcgen05.cuh"
 
 namespace digs {
 namespace {
@@ -32,101 +34,41 @@ constexpr int kStageA = kBM * kBK * 2;  // bytes of one A slice (16 KB)
 constexpr int kStageB = kBN * kBK * 2;  // bytes of one B slice (8 KB)
 constexpr int kTmemCols = 64;           // FP32 accumulator columns (= kBN)
 constexpr size_t kTcSmem = 1024 + 2 * kStageA + 2 * kStageB + 64;  // 1 KB alignment slack, buffers, barriers
-constexpr unsigned kWaitLimit = 1u << 22;                          // x ~100 ns
+constexpr unsigned kWaitLimit = tc::kWaitLimit;
 
 // Tests a K-loop mbarrier wait makes before it gives up (digs_set_wait_limit; read at launch).
 unsigned g_loop_wait_limit = kWaitLimit;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using tc::fence_after;
+using tc::fence_async_smem;
+using tc::fence_before;
+using tc::mbar_init;
+using tc::mbar_wait;
+using tc::mma_commit;
+using tc::smem_desc;
+using tc::smem_u32;
+using tc::tmem_ld16;
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-// Waits for the completion of the mbarrier phase with the given parity: non-blocking tests with a short
-// sleep between them, false after `limit` tests (kWaitLimit tests take well under a second).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned limit) {
-  const uint32_t a = smem_u32(bar);
-  for (unsigned it = 0; it < limit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (it >= 64) __nanosleep(64);
-  }
-  return false;
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor, K-major without swizzle: start address, leading-dimension byte
-// offset (between core matrices adjacent in K), stride-dimension byte offset (between 8-row groups),
-// all in 16-byte units; descriptor version 1 (bits 46-47); layout type 0 (no swizzle, bits 61-63).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits 7-9 and
-// 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 in bits 17-22, M / 16 in bits 24-28.
-constexpr uint32_t kIdesc =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+constexpr uint32_t kIdesc = tc::idesc_bf16(kBM, kBN, false, false);
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// 16 consecutive FP32 columns of this thread's accumulator lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+  tc::mma_bf16(tmem_d, da, db, kIdesc, accumulate);
 }
 
 __device__ __forceinline__ float ld_f(const float* p) { return __ldg(p); }
-__device__ __forceinline__ float ld_f(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 __device__ __forceinline__ void st_c(float* p, float v) { *p = v; }
-__device__ __forceinline__ void st_c(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 __device__ __forceinline__ void st_c4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-__device__ __forceinline__ void st_c4(__nv_bfloat16* p, float4 v) {
-  *reinterpret_cast<uint2*>(p) = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
-}
 
 // A whole 8-element chunk with 16-byte loads (vec: the operand's base and pitch allow them).
 __device__ __forceinline__ uint4 load_vec8(const float* p) {
   const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
   return make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(b.x, b.y), pack_bf16(b.z, b.w));
 }
-__device__ __forceinline__ uint4 load_vec8(const __nv_bfloat16* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
 
 // One 8-element K chunk of row `row` of an operand, K-range [k, k + 8) clipped to [.., kend), rows
 // beyond `rows` zero; T (transposed) reads element (row, kk) at P[kk ld + row], else P[row ld + kk].
@@ -143,72 +85,25 @@ __device__ __forceinline__ uint4 load_chunk(const TP* __restrict__ P, int ld, in
   return make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
 }
 
-// Implicit im2col of a 3 x 3, stride-2, padding-1 convolution over an NHWC input of H x W x C (C and
-// the output width W / 2 powers of two): element (p, k) with p the output pixel (b, y, x) and
-// k = (ky 3 + kx) C + c is in[b][2y + ky - 1][2x + kx - 1][c], zero outside the input.
-__device__ __forceinline__ int conv_offset(const ConvGeom& g, int p, int k) {
-  const int lw = g.lwo, x = p & ((1 << lw) - 1), y = (p >> lw) & ((1 << lw) - 1), b = p >> (2 * lw);
-  const int tap = k >> g.lc, c = k & ((1 << g.lc) - 1), ky = tap / 3, kx = tap - 3 * ky;
-  const int iy = 2 * y + ky - 1, ix = 2 * x + kx - 1;
-  if (iy < 0 || iy >= g.H || ix < 0 || ix >= g.W) return -1;
-  return ((b * g.H + iy) * g.W + ix) << g.lc | c;
-}
-
-// Row p's K chunk [k, k + 8) of the implicit im2col matrix (rows < rows, k < kend), as BF16: with C a
-// multiple of 8 the chunk is 8 channels of one tap, contiguous in the input.
-template <typename TP>
-__device__ __forceinline__ uint4 conv_chunk_row(const ConvGeom& g, const TP* __restrict__ P, int p, int rows, int k,
-                                                int kend) {
-  if ((g.lc >= 3) && p < rows && k + 8 <= kend) {
-    const int o = conv_offset(g, p, k);
-    return o < 0 ? make_uint4(0u, 0u, 0u, 0u) : load_vec8(P + o);
-  }
-  float x[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    const int o = (p < rows && k + e < kend) ? conv_offset(g, p, k + e) : -1;
-    x[e] = o >= 0 ? ld_f(P + o) : 0.f;
-  }
-  return make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
-}
-
-// Column n's chunk of 8 consecutive rows [p, p + 8) of the implicit im2col matrix, as BF16.
-template <typename TP>
-__device__ __forceinline__ uint4 conv_chunk_col(const ConvGeom& g, const TP* __restrict__ P, int n, int cols, int p,
-                                                int pend) {
-  float x[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    const int o = (n < cols && p + e < pend) ? conv_offset(g, p + e, n) : -1;
-    x[e] = o >= 0 ? ld_f(P + o) : 0.f;
-  }
-  return make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
-}
-
 // Stage the K slice [k0, k0 + 64) of the block's A rows and B columns.  Consecutive threads take
 // consecutive K chunks when K is the contiguous global index, else consecutive rows.  Every chunk is
 // loaded (and rounded) before any is stored, so that all of the thread's loads are in flight together.
-// CA_ (CB_): A (B) is the implicit im2col matrix of the input at A (B) with geometry ga (gb): A(m, k) =
-// im2col[m][k] (AT false), B(k, n) = im2col[k][n] (BT false).
-template <bool AT, bool BT, bool CA_, bool CB_, typename TA, typename TB>
+template <bool AT, bool BT, typename TA, typename TB>
 __device__ __forceinline__ void stage(const TA* __restrict__ A, int lda, const TB* __restrict__ B, int ldb, int M,
-                                      int N, int m0, int n0, int k0, int kend, uint8_t* sA, uint8_t* sB, int vec,
-                                      const ConvGeom& ga, const ConvGeom& gb) {
+                                      int N, int m0, int n0, int k0, int kend, uint8_t* sA, uint8_t* sB, int vec) {
   constexpr int CA = (kBM * 8) / kTcThreads, CB = (kBN * 8) / kTcThreads;
   uint4 va[CA], vb[CB];
 #pragma unroll
   for (int i = 0; i < CA; ++i) {
     const int c = threadIdx.x + i * kTcThreads;
     const int kc = AT ? c / kBM : c & 7, mm = AT ? c % kBM : c >> 3;
-    va[i] = CA_ ? conv_chunk_row(ga, A, m0 + mm, M, k0 + kc * 8, kend)
-                : load_chunk<AT>(A, lda, m0 + mm, M, k0 + kc * 8, kend, (vec & 1) != 0);
+    va[i] = load_chunk<AT>(A, lda, m0 + mm, M, k0 + kc * 8, kend, (vec & 1) != 0);
   }
 #pragma unroll
   for (int i = 0; i < CB; ++i) {
     const int c = threadIdx.x + i * kTcThreads;
     const int kc = BT ? c & 7 : c / kBN, nn = BT ? c >> 3 : c % kBN;
-    vb[i] = CB_ ? conv_chunk_col(gb, B, n0 + nn, N, k0 + kc * 8, kend)
-                : load_chunk<!BT>(B, ldb, n0 + nn, N, k0 + kc * 8, kend, (vec & 2) != 0);
+    vb[i] = load_chunk<!BT>(B, ldb, n0 + nn, N, k0 + kc * 8, kend, (vec & 2) != 0);
   }
 #pragma unroll
   for (int i = 0; i < CA; ++i) {
@@ -224,13 +119,12 @@ __device__ __forceinline__ void stage(const TA* __restrict__ A, int lda, const T
   }
 }
 
-template <bool AT, bool BT, bool CA_, bool CB_, typename TA, typename TB, typename TC>
+template <bool AT, bool BT, typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, const TA* __restrict__ A, int lda,
                                                         const TB* __restrict__ B, int ldb, TC* __restrict__ C,
                                                         int ldc, int kchunk, long long zstride,
                                                         const float* __restrict__ bias, int relu, int vec,
-                                                        int* status, const ConvGeom ga, const ConvGeom gb,
-                                                        unsigned wait_limit) {
+                                                        int* status, unsigned wait_limit) {
   extern __shared__ unsigned char smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = sm;
@@ -244,17 +138,14 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     mbar_init(bar + 1, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tc::mbar_init_fence();
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc::tmem_alloc(tslot, kTmemCols);
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
-  tc_fence_after();
+  fence_after();
   const uint32_t tmem = *tslot;
   int ok = 1;
   int issued = 0;  // slices whose MMAs were committed
@@ -262,12 +153,11 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
     const int buf = s & 1;
     if (s >= 2) ok = __syncthreads_and(ok && mbar_wait(bar + buf, (uint32_t)(((s >> 1) - 1) & 1), wait_limit));
     if (!ok) break;
-    stage<AT, BT, CA_, CB_>(A, lda, B, ldb, M, N, m0, n0, kb + s * kBK, ke, sA + buf * kStageA, sB + buf * kStageB,
-                            vec, ga, gb);
+    stage<AT, BT>(A, lda, B, ldb, M, N, m0, n0, kb + s * kBK, ke, sA + buf * kStageA, sB + buf * kStageB, vec);
     fence_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
-      tc_fence_after();
+      fence_after();
       const uint32_t a0 = smem_u32(sA + buf * kStageA), b0 = smem_u32(sB + buf * kStageB);
 #pragma unroll
       for (int j = 0; j < kBK / 16; ++j) {
@@ -284,7 +174,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
   // memory is read or freed, and the outcome made block-uniform
   const bool drained = issued == 0 || mbar_wait(bar + ((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1), kWaitLimit);
   ok = __syncthreads_and(ok && drained);
-  tc_fence_after();
+  fence_after();
   // epilogue: accumulator lanes -> registers (+ bias, ReLU) -> the 128 x 64 tile in the (now idle)
   // staging buffers -> global rows, 4 consecutive columns per thread, 16 threads per row
   constexpr int TP = kBN + 4;  // tile row pitch in floats (16-byte aligned rows)
@@ -329,22 +219,21 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
       }
     }
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
   if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    fence_after();
+    tc::tmem_dealloc(tmem, kTmemCols);
   }
   if (!ok && threadIdx.x == 0 && status) atomicExch(status, 1);
 }
 
-template <bool AT, bool BT, typename TA, typename TB, typename TC, bool CA_ = false, bool CB_ = false>
+template <bool AT, bool BT, typename TA, typename TB, typename TC>
 cudaError_t launch_tc(int M, int N, int K, const TA* A, int lda, const TB* B, int ldb, TC* C, int ldc,
-                      const float* bias, bool relu, int splits, long long zstride, int* status, cudaStream_t st,
-                      ConvGeom ga = ConvGeom{}, ConvGeom gb = ConvGeom{}) {
+                      const float* bias, bool relu, int splits, long long zstride, int* status, cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<AT, BT, CA_, CB_, TA, TB, TC>,
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<AT, BT, TA, TB, TC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     if (e != cudaSuccess) return e;
     configured = true;
@@ -356,8 +245,8 @@ cudaError_t launch_tc(int M, int N, int K, const TA* A, int lda, const TB* B, in
   constexpr int per16a = 16 / (int)sizeof(TA), per16b = 16 / (int)sizeof(TB);
   const int vec = ((!AT && ((uintptr_t)A & 15) == 0 && lda % per16a == 0) ? 1 : 0) |
                   ((BT && ((uintptr_t)B & 15) == 0 && ldb % per16b == 0) ? 2 : 0);
-  k_gemm_tc<AT, BT, CA_, CB_, TA, TB, TC><<<grid, kTcThreads, kTcSmem, st>>>(
-      M, N, K, A, lda, B, ldb, C, ldc, kchunk, zstride, bias, relu ? 1 : 0, vec, status, ga, gb, g_loop_wait_limit);
+  k_gemm_tc<AT, BT, TA, TB, TC><<<grid, kTcThreads, kTcSmem, st>>>(
+      M, N, K, A, lda, B, ldb, C, ldc, kchunk, zstride, bias, relu ? 1 : 0, vec, status, g_loop_wait_limit);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -400,33 +289,6 @@ cudaError_t gemm_tc_sum(bool at, bool bt, int M, int N, int K, const float* A, i
                                                                                      bias, relu ? 1 : 0);
   note_launches(1);
   return cudaGetLastError();
-}
-
-cudaError_t gemm_tc_conv_fwd(int M, int N, int K, const float* act, ConvGeom g, const float* W, int ldw, float* C,
-                             int ldc, const float* bias, bool relu, cudaStream_t st) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  return launch_tc<false, true, float, float, float, true, false>(M, N, K, act, 0, W, ldw, C, ldc, bias, relu, 1, 0,
-                                                                  nullptr, st, g, ConvGeom{});
-}
-
-cudaError_t gemm_tc_conv_dw(int M, int N, int K, const float* dY, int ldy, const float* act, ConvGeom g, float* C,
-                            int ldc, int splits, long long zstride, cudaStream_t st) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  return launch_tc<true, false, float, float, float, false, true>(M, N, K, dY, ldy, act, 0, C, ldc, nullptr, false,
-                                                                  splits, zstride, nullptr, st, ConvGeom{}, g);
-}
-
-cudaError_t gemm_tc_conv_fwd_bf16(int M, int N, int K, const __nv_bfloat16* act, ConvGeom g, const __nv_bfloat16* W,
-                                  int ldw, __nv_bfloat16* C, int ldc, const float* bias, bool relu, cudaStream_t st) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  return launch_tc<false, true, __nv_bfloat16, __nv_bfloat16, __nv_bfloat16, true, false>(
-      M, N, K, act, 0, W, ldw, C, ldc, bias, relu, 1, 0, nullptr, st, g, ConvGeom{});
-}
-
-cudaError_t gemm_tc_bf16(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
-                         __nv_bfloat16* C, int ldc, const float* bias, bool relu, int* status, cudaStream_t st) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  return launch_tc<false, true>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, 1, 0, status, st);
 }
 
 }  // namespace digs

@@ -14,13 +14,16 @@ shared-memory column (the chain rule through Eq. 7-11 of Sec. 3.2-3.3, summed ov
   sum_b w_br dL/dw_br = sum_k phi_rk . dL/dphi_rk (the projections do not change under
   (w_r, phi_r) -> (a w_r, phi_r / a)).
 
-Tolerances: rel-L2 over the whole tensor, projections and losses <= 1e-5, gradients <= 1e-4.
+Tolerances: rel-L2 over the whole tensor, projections and losses <= 1e-5, gradients <= 1e-4.  Gaussians
+with a (pixel, view) pair within FP32 rounding of the cutoff (conftest.unambiguous) are left out of the
+clouds, since the float32 kernels and the float64 oracle may decide such a pair differently.
 """
 import numpy as np
 import pytest
 import torch
 
 import synth
+from conftest import unambiguous
 from oracle import digs_oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -55,6 +58,7 @@ def pkg():
 @pytest.mark.parametrize("n_views", [16, 17])
 def test_project_bwd_more_views_than_slots(pkg, n_views):
     wl = synth.tiny(n_proj=n_views)
+    wl = wl.subset(unambiguous(wl, wl.w, wl.views))
     gp = synth.random_grad_proj(n_views, 64, 64, seed=11)
     pj = pkg.Projector(wl.lattice, wl.views, tile=16, bwd_lanes=16)
     ins = [T(wl.mu0), T(wl.scale), T(wl.quat), T(wl.rho), T(wl.phi), T(wl.w)]
@@ -83,10 +87,11 @@ def test_step_batch_beyond_slots(pkg, B):
     ref_state = synth.tiny(n_proj=24, motion_seed=77)
     g_meas = dict(mu0=ref_state.mu0 + 0.3, scale=ref_state.scale, quat=ref_state.quat, rho=ref_state.rho * 1.1)
     meas = O.render(g_meas, ref_state.lattice, ref_state.phi, ref_state.w, ref_state.views)
-    rec = pkg.Reconstruction(wl.mu0, wl.scale, wl.quat, wl.rho, wl.phi, wl.w, wl.lattice,
-                             D.adam_config(LR0, LR1, 100))
     ids = sorted(np.random.default_rng(B).choice(24, B, replace=False).tolist())
     views = [wl.views[i] for i in ids]
+    wl = wl.subset(unambiguous(wl, wl.w[ids], views))
+    rec = pkg.Reconstruction(wl.mu0, wl.scale, wl.quat, wl.rho, wl.phi, wl.w, wl.lattice,
+                             D.adam_config(LR0, LR1, 100))
     loss = float(rec.step(T(meas[ids]), ids, views).item())
     assert rec.status() == 0
     g = gauss(wl)
@@ -124,11 +129,13 @@ def test_multiscan_step_26_items(pkg):
         ref = synth.tiny(seed=20 + s, n=n, motion_seed=400 + s)
         g_meas = dict(mu0=ref.mu0 + 0.3, scale=ref.scale, quat=ref.quat, rho=ref.rho * 1.1)
         scans.append((wl, O.render(g_meas, ref.lattice, ref.phi, ref.w, ref.views)))
+    per_scan = {0: [0, 1, 3, 4, 6, 7, 9, 10, 12, 13, 15], 1: [0, 2, 5, 6, 8, 9, 11, 14, 15], 2: [1, 4, 7, 8, 11, 14]}
+    scans = [(wl.subset(unambiguous(wl, wl.w[per_scan[s]], [wl.views[i] for i in per_scan[s]])), meas)
+             for s, (wl, meas) in enumerate(scans)]
     cat = lambda k: np.concatenate([getattr(wl, k) for wl, _ in scans], 0)
     rec = pkg.Reconstruction(cat("mu0"), cat("scale"), cat("quat"), cat("rho"), np.stack([wl.phi for wl, _ in scans]),
                              np.concatenate([wl.w for wl, _ in scans]), scans[0][0].lattice,
                              D.adam_config(LR0, LR1, 100), scan_sizes=[wl.n for wl, _ in scans])
-    per_scan = {0: [0, 1, 3, 4, 6, 7, 9, 10, 12, 13, 15], 1: [0, 2, 5, 6, 8, 9, 11, 14, 15], 2: [1, 4, 7, 8, 11, 14]}
     batch = []
     for k in range(11):  # interleaved: scan 0, 1, 2, 0, 1, 2, ...
         for s in range(3):
@@ -178,6 +185,7 @@ def test_thorax_100k_16_views_subset_gradients_and_identities(pkg):
     got = {k: g[k].cpu().numpy().astype(np.float64) for k in GROUPS}
     # a seeded 1,000-Gaussian subset against the oracle with the same dL/dI
     idx = np.sort(np.random.default_rng(7).choice(wl.n, 1000, replace=False))
+    idx = idx[unambiguous(one.subset(idx), one.w, one.views)]
     sub = one.subset(idx)
     ref = O.project_vjp(gauss(sub), sub.lattice, sub.phi, sub.w, sub.views, gp)
     for k in ("mu0", "scale", "quat", "rho"):

@@ -282,3 +282,23 @@ def test_gaussians_behind_the_source_or_around_it_are_dropped():
     K = torch.eye(3, dtype=DT).expand(3, 3, 3)
     assert O.alive_mask(v, mu, P, K, 3.5).tolist() == [False, True, False]
     assert O.alive_mask(v, mu, P, K, None).tolist() == [False, True, True]
+
+
+def test_cutoff_margin_of_an_isotropic_gaussian():
+    # isotropic sigma at the isocentre: E of a pixel ray is (distance from the ray to the centre / sigma)^2
+    sig = 2.0
+    views = synth.circular_views([0.7, 2.1], 1000.0, 1500.0, 31, 29, 0.5, 0.5)
+    phi, w = _zero_motion(P=2)
+    g = _one([0.0, 0.0, 0.0], [sig] * 3, [1, 0, 0, 0], 0.02)
+    got = O.cutoff_margin(g, _static_lattice(), phi, w, views)[0]
+    best = np.inf
+    for view in views:
+        v = O.view_tensors(view)
+        X = O.pixel_centres(v).numpy()
+        s = np.asarray(view["src"], dtype=float)
+        d = (X - s) / np.linalg.norm(X - s, axis=1, keepdims=True)
+        dist = np.linalg.norm(np.cross(-s[None], d), axis=1)
+        E = (dist / sig) ** 2
+        near = E <= (1.05 * 3.5) ** 2
+        best = min(best, float(np.min(np.abs(E[near] - 12.25) / 12.25)))
+    assert abs(got - best) <= 1e-9 * max(best, 1e-12) + 1e-12, (got, best)
