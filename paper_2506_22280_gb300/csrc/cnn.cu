@@ -200,6 +200,57 @@ cudaError_t gemm(int M, int N, int K, const TA* A, int lda, const TB* B, int ldb
   return cudaGetLastError();
 }
 
+// The R-wide output layer, FP32: out[b][r] = b2[r] + sum_n h[b][n] W2[r][n], one warp per batch entry.
+__global__ void __launch_bounds__(256) k_fc2_fwd(const float* __restrict__ h, const float* __restrict__ w2,
+                                                 const float* __restrict__ b2, int B, int R, float* __restrict__ out) {
+  const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (b >= B) return;  // whole warps
+  float x[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) x[q] = h[(size_t)b * kHid + lane + 32 * q];
+  for (int r = 0; r < R; ++r) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s = fmaf(x[q], w2[r * kHid + lane + 32 * q], s);
+    s = warp_sum(s);
+    if (lane == 0) out[(size_t)b * R + r] = s + b2[r];
+  }
+}
+
+// Its parameter gradient, per block of batch entries (blockIdx.x selects entries b = blockIdx.x,
+// blockIdx.x + gridDim.x, ...): part[block][r kHid + n] = sum_b dout[b][r] h[b][n] (threads n < kHid) and
+// part[block][R kHid + r] = sum_b dout[b][r] (threads kHid + r); the blocks are added in order after.
+__global__ void __launch_bounds__(kHid + 32) k_fc2_wgrad(const float* __restrict__ dout, const float* __restrict__ h,
+                                                         int B, int R, float* __restrict__ part) {
+  const int n = threadIdx.x;
+  float acc[DIGS_MAX_R] = {0.f, 0.f, 0.f, 0.f};
+  if (n < kHid) {
+    for (int b = blockIdx.x; b < B; b += gridDim.x) {
+      const float x = h[(size_t)b * kHid + n];
+#pragma unroll
+      for (int r = 0; r < DIGS_MAX_R; ++r)
+        if (r < R) acc[r] = fmaf(dout[(size_t)b * R + r], x, acc[r]);
+    }
+    for (int r = 0; r < R; ++r) part[(size_t)blockIdx.x * (R * kHid + R) + r * kHid + n] = acc[r];
+  } else if (n - kHid < R) {
+    const int r = n - kHid;
+    float t = 0.f;
+    for (int b = blockIdx.x; b < B; b += gridDim.x) t += dout[(size_t)b * R + r];
+    part[(size_t)blockIdx.x * (R * kHid + R) + R * kHid + r] = t;
+  }
+}
+
+// dh[b][n] = [h[b][n] > 0] sum_r dout[b][r] W2[r][n]: the gradient of the dense layer's pre-activation.
+__global__ void k_fc2_dh(const float* __restrict__ dout, const float* __restrict__ w2, const float* __restrict__ h,
+                         int B, int R, float* __restrict__ dh) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * kHid) return;
+  const int b = i / kHid, n = i - b * kHid;
+  float s = 0.f;
+  for (int r = 0; r < R; ++r) s = fmaf(dout[(size_t)b * R + r], w2[r * kHid + n], s);
+  dh[i] = h[i] > 0.f ? s : 0.f;
+}
+
 // out[i] (+)= sum_z part[z][i], z in a fixed order.
 __global__ void k_sum_splits(const float* __restrict__ part, int splits, long long n, float* __restrict__ out,
                              int accumulate) {
@@ -425,7 +476,8 @@ cudaError_t forward_f32(const NetPtrs<float>& N, int R, const float* img, const 
     note_launches(1);
     CNN_TRY(gemm<false, true>(B, kHid, kFeatIn, w.feat, kFeatIn, N.w1, kFeatIn, w.h, kHid, N.b1, true, st));
   }
-  CNN_TRY(gemm<false, true>(B, R, kHid, w.h, kHid, N.w2, kHid, w.out, R, N.b2, false, st));
+  k_fc2_fwd<<<(B + 7) / 8, 256, 0, st>>>(w.h, N.w2, N.b2, B, R, w.out);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -433,11 +485,11 @@ cudaError_t forward_f32(const NetPtrs<float>& N, int R, const float* img, const 
 cudaError_t backward_f32(const NetPtrs<float>& N, const ParamOffsets& o, int R, int B, const CnnWs& w, float* grad,
                          bool tc, cudaStream_t st) {
   // output layer
-  CNN_TRY(gemm<true, false>(R, kHid, B, w.dout, R, w.h, kHid, grad + o.w2, kHid, nullptr, false, st));
-  CNN_TRY(colsum(w.dout, B, R, w.part, grad + o.b2, st));
-  CNN_TRY(gemm<false, false>(B, kHid, R, w.dout, R, N.w2, kHid, w.dh, kHid, nullptr, false, st));
-  k_relu_bwd<<<grid_for((long long)B * kHid), 256, 0, st>>>(w.h, (long long)B * kHid, w.dh);
-  note_launches(1);
+  constexpr int kFc2Blocks = 16;
+  k_fc2_wgrad<<<kFc2Blocks, kHid + 32, 0, st>>>(w.dout, w.h, B, R, w.part);
+  k_sum_splits<<<(R * kHid + R + 255) / 256, 256, 0, st>>>(w.part, kFc2Blocks, R * kHid + R, grad + o.w2, 0);
+  k_fc2_dh<<<(B * kHid + 255) / 256, 256, 0, st>>>(w.dout, N.w2, w.h, B, R, w.dh);
+  note_launches(3);
   CNN_TRY(colsum(w.dh, B, kHid, w.part, grad + o.b1, st));
   if (tc) {
     CnnGrad g;
@@ -576,8 +628,9 @@ digs_status digs_cnn_infer_bf16(const float* params, int R, const float* img, co
   cudaStream_t st = (cudaStream_t)stream;
   const NetPtrs<float> N = net_ptrs<float>(params, params, o);
   if (cnn_tc_forward(cnn_net(N), img, cs, B, w.tc, w.h, st) != cudaSuccess) return DIGS_ERR_CUDA;
-  if (gemm<false, true>(B, R, kHid, w.h, kHid, N.w2, kHid, w_out, R, N.b2, false, st) != cudaSuccess)
-    return DIGS_ERR_CUDA;
+  k_fc2_fwd<<<(B + 7) / 8, 256, 0, st>>>(w.h, N.w2, N.b2, B, R, w_out);
+  note_launches(1);
+  if (cudaGetLastError() != cudaSuccess) return DIGS_ERR_CUDA;
   return DIGS_OK;
 }
 

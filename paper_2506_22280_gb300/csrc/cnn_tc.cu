@@ -4,7 +4,7 @@
 // Activations live in BF16, NHWC, exactly as the GEMMs consume them: the post-ReLU output of every
 // convolution is rounded once by the epilogue that produces it (the rounding the tensor cores would
 // apply anyway), its sign is the ReLU mask of the backward.  Every GEMM is one launch of one kernel
-// template: 128 threads per 128-row tile of C; the four warps fill a 4-stage ring of 64-deep K slices of
+// template: 128 threads per CTA, looping over 128-row tiles of C; the four warps fill a ring of 2-4 stages of 64-deep K slices of
 // A and B with 16-byte cp.async copies (zero-filled where an operand is padding), one thread issues the
 // four 128 x BN x 16 MMAs of a slice and commits them to the slice's mbarrier, and the accumulator goes
 // through a per-role epilogue.  Operands are read in place, K-major or MN-major:
@@ -37,7 +37,6 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int kThr = 128;
 constexpr int kBM = 128, kBK = 64;
-constexpr int kStages = 4;
 
 // ---- geometry of the network (cnn.cu holds the parameter layout) --------------------------------
 constexpr int kCh[5] = {1, 32, 64, 128, 128};
@@ -187,7 +186,7 @@ struct EpiBf16 {
     d[0] = make_uint4(w[0], w[1], w[2], w[3]);
     d[1] = make_uint4(w[4], w[5], w[6], w[7]);
   }
-  __device__ void finish(int, float, float*, int) const {}
+  __device__ void finish(int, float, float*, int, int, int) const {}
 };
 
 // FP32 rows of split z: part[z * zstride + row * ld + col].
@@ -201,7 +200,7 @@ struct EpiF32 {
 #pragma unroll
     for (int q = 0; q < 4; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   }
-  __device__ void finish(int, float, float*, int) const {}
+  __device__ void finish(int, float, float*, int, int, int) const {}
 };
 
 // Transposed FP32 store of split z: out[z * zstride + col * ld + row] for row < rows (coalesced: the
@@ -216,7 +215,7 @@ struct EpiF32T {
 #pragma unroll
     for (int j = 0; j < 16; ++j) d[(size_t)j * ld] = v[j];
   }
-  __device__ void finish(int, float, float*, int) const {}
+  __device__ void finish(int, float, float*, int, int, int) const {}
 };
 
 // Sum 16 per-lane values over the warp's 32 lanes by recursive halving (16 shuffles); lane l ends with
@@ -240,7 +239,7 @@ __device__ __forceinline__ int sum16_col(int lane) {
 // Data gradient of class z: row (b, Y, X) is input pixel (b, 2Y + py, 2X + px) of a layer with C = BN
 // channels and H x H pixels; dY_in = dX * [act > 0] (act: that layer's post-ReLU output), stored in BF16
 // at the NHWC index; the masked FP32 values are summed per column over the CTA's rows into
-// colpart[z * gridDim.x + blockIdx.x][col] (bias gradient of that layer).
+// colpart[z * n_mt + mt][col] (bias gradient of that layer; mt the row tile).
 template <int BN>
 struct EpiDx {
   bf16* dy_out;
@@ -274,52 +273,66 @@ struct EpiDx {
     const float s = warp_sum16(v, lane);
     if ((lane & 1) == 0) scratch[warp * BN + col0 - blockIdx.y * BN + sum16_col(lane)] = s;
   }
-  __device__ void finish(int, float, float* scratch, int tid) const {
+  __device__ void finish(int, float, float* scratch, int tid, int mt, int n_mt) const {
     __syncthreads();
     if (tid < BN) {
       const float s = scratch[tid] + scratch[BN + tid] + scratch[2 * BN + tid] + scratch[3 * BN + tid];
-      colpart[((size_t)blockIdx.z * gridDim.x + blockIdx.x) * BN + tid] = s;
+      colpart[((size_t)blockIdx.z * n_mt + mt) * BN + tid] = s;
     }
   }
 };
 
-// Gradient of the dense layer's input, rows f (feature) and columns b (batch entry):
-// dY3[b][f] = dfeat[b][f] [act3[b][f] > 0] in BF16 for f < 8192 (the convolution features; the two angle
-// inputs get no gradient), and each row's sum over the CTA's columns into rowpart[blockIdx.y][f] (the
-// last convolution's bias gradient sums them over y-tiles and pixels).
+// Gradient of the dense layer's input, rows b (batch entry) and columns f (feature, blockIdx.y selects
+// 128 of them, i.e. one pixel's 128 channels of the last convolution):
+// dY3[b][f] = dfeat[b][f] [act3[b][f] > 0] in BF16 (feat holds act3 in its first 8192 columns; the two
+// angle inputs get no gradient), and the masked FP32 values summed per column over the CTA's rows into
+// colpart[blockIdx.y * n_mt + mt][c] (the last convolution's bias gradient sums those rows).
 struct EpiDfeat {
   bf16* dy3;
-  const bf16* feat;  // [B][kFeatPitch], act3 in its first 8192 columns
-  float* rowpart;
+  const bf16* feat;  // [B][kFeatPitch]
+  float* colpart;
   int nb;
-  __device__ void apply(int row, int col0, float v[16], float& acc, float*) const {
-    if (row >= kFeat) return;
+  __device__ void apply(int row, int col0, float v[16], float&, float* scratch) const {
+    if (row < nb) {
+      const uint4* a = reinterpret_cast<const uint4*>(feat + (size_t)row * kFeatPitch + col0);
+      float m[16];
+      unpack8(a[0], m);
+      unpack8(a[1], m + 8);
+      uint32_t w[8];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int b = col0 + j;
-      if (b < nb) {
-        const float a = __bfloat162float(feat[(size_t)b * kFeatPitch + row]);
-        const float y = a > 0.f ? v[j] : 0.f;
-        dy3[(size_t)b * kFeat + row] = __float2bfloat16_rn(y);
-        acc += y;
-      }
+      for (int j = 0; j < 16; ++j) v[j] = m[j] > 0.f ? v[j] : 0.f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[j] = pack2(v[2 * j], v[2 * j + 1]);
+      uint4* d = reinterpret_cast<uint4*>(dy3 + (size_t)row * kFeat + col0);
+      d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = 0.f;
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float s = warp_sum16(v, lane);
+    if ((lane & 1) == 0) scratch[warp * 128 + col0 - blockIdx.y * 128 + sum16_col(lane)] = s;
   }
-  __device__ void finish(int row, float acc, float*, int) const {
-    if (row < kFeat) rowpart[(size_t)blockIdx.y * kFeat + row] = acc;
+  __device__ void finish(int, float, float* scratch, int tid, int mt, int n_mt) const {
+    __syncthreads();
+    if (tid < 128) {
+      const float s = scratch[tid] + scratch[128 + tid] + scratch[256 + tid] + scratch[384 + tid];
+      colpart[((size_t)blockIdx.y * n_mt + mt) * 128 + tid] = s;
+    }
   }
 };
 
 // ---- the GEMM kernel -------------------------------------------------------------------------------
-template <int BN, bool AMN, bool BMN>
+// S stages of (A, B) slices: 4 for long reductions, fewer where a CTA has only a few slices, so that
+// more CTAs share an SM (at most five: 5 x 32 ... 2 x 128 tensor-memory columns stay within the 512).
+template <int BN, int S>
 struct Cfg {
   static constexpr int kA = kBM * kBK * 2;  // bytes of one A slice (16 KB)
   static constexpr int kB = BN * kBK * 2;
   static constexpr int kStage = kA + kB;
-  // Room past the stage ring for an MN-major operand: reads that follow either reading of a
-  // descriptor's two strides stay inside the CTA's shared memory.
-  static constexpr int kPad = (AMN || BMN) ? 48 * 1024 : 0;
-  static constexpr size_t kSmem = 1024 + (size_t)kStages * kStage + kPad + 128;
+  static constexpr int kScratch = 4 * BN * 4;  // epilogue column sums [warp][BN]
+  static constexpr size_t kSmem = 1024 + (size_t)S * kStage + 128 + kScratch;
 };
 
 // Shared-memory byte offset of a 16-byte chunk: K-major (row, kc) of a ROWS x 64 slice; MN-major
@@ -355,18 +368,21 @@ __device__ __forceinline__ uint64_t slice_desc(uint32_t a, int j) {
   return tc::smem_desc(a + j * 2 * (ROWS / 8) * 128, (ROWS / 8) * 128, 128);
 }
 
-// C tile (128 x BN) of CTA (blockIdx.x, blockIdx.y); blockIdx.z = split of the reduction (kchunk each)
-// or, for the data gradient, the parity class (its loaders read blockIdx.z).
-template <int BN, bool AMN, bool BMN, class LA, class LB, class EP>
-__global__ void __launch_bounds__(kThr, 1) k_cnn_gemm(const LA la, const LB lb, const EP ep, int K, int kchunk, int* status,
-                                                      unsigned wait_limit, const void* any) {
-  using C = Cfg<BN, AMN, BMN>;
+// C tiles (128 x BN) of rows [mt 128, mt 128 + 128) for mt = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (n_mt row tiles in all), columns from blockIdx.y BN; blockIdx.z = split of the reduction (kchunk
+// each) or, for the data gradient, the parity class (its loaders read blockIdx.z).  The tensor memory
+// and the mbarrier ring stay with the CTA across its tiles; g counts the slices issued so far, which
+// selects the stage buffer (g mod S) and the mbarrier phase (g div S).
+template <int BN, int kStages, bool AMN, bool BMN, class LA, class LB, class EP>
+__global__ void __launch_bounds__(kThr, 1) k_cnn_gemm(const LA la, const LB lb, const EP ep, int n_mt, int K, int kchunk,
+                                                      int* status, unsigned wait_limit, const void* any) {
+  using C = Cfg<BN, kStages>;
   extern __shared__ unsigned char smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bar = (uint64_t*)(sm + kStages * C::kStage + C::kPad);
+  uint64_t* bar = (uint64_t*)(sm + kStages * C::kStage);
   uint32_t* tslot = (uint32_t*)(bar + kStages);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int n0 = blockIdx.y * BN;
   const int Kz = la.kdim(K);
   const long long kb0 = (long long)la.zsplit() * kchunk;
   const int kb = kb0 >= Kz ? Kz : (int)kb0;
@@ -384,48 +400,64 @@ __global__ void __launch_bounds__(kThr, 1) k_cnn_gemm(const LA la, const LB lb, 
   const uint32_t tmem = *tslot;
   const uint32_t sbase = tc::smem_u32(sm);
   constexpr uint32_t idesc = tc::idesc_bf16(kBM, BN, AMN, BMN);
-  auto load = [&](int s) {
-    const uint32_t sa = sbase + (s % kStages) * C::kStage;
-    const int k0 = kb + s * kBK;
-    fill<kBM, AMN>(la, sa, m0, k0, ke, any);
-    fill<BN, BMN>(lb, sa + C::kA, n0, k0, ke, any);
+  float* scratch = reinterpret_cast<float*>((uint8_t*)bar + 128);  // the epilogue's column sums
+  int ok = 1;
+  unsigned g = 0;
+  // the first S - 1 slices of a tile, into the stage buffers g, g + 1, ... (all free: no MMA in flight)
+  auto prologue = [&](int m0) {
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) {
+      if (s < nk) {
+        const uint32_t sa = sbase + ((g + s) % kStages) * C::kStage;
+        fill<kBM, AMN>(la, sa, m0, kb + s * kBK, ke, any);
+        fill<BN, BMN>(lb, sa + C::kA, n0, kb + s * kBK, ke, any);
+      }
+      cp_commit();
+    }
   };
+  int mt = blockIdx.x;
+  if (mt < n_mt) prologue(mt * kBM);
+  while (mt < n_mt) {
+    const int m0 = mt * kBM;
+    int issued = 0;
+    for (int c = 0; c < nk; ++c) {
+      cp_wait<kStages - 2>();     // this thread's copies of slice c have landed
+      tc::fence_async_smem();     // ... and are visible to the tensor core
+      ok = __syncthreads_and(ok);
+      if (!ok) break;
+      const unsigned gc = g + c;
+      if (tid == 0) {
+        tc::fence_after();
+        const uint32_t sa = sbase + (gc % kStages) * C::kStage, sb = sa + C::kA;
 #pragma unroll
-  for (int s = 0; s < kStages - 1; ++s) {
-    if (s < nk) load(s);
-    cp_commit();
-  }
-  int ok = 1, issued = 0;
-  for (int c = 0; c < nk; ++c) {
-    cp_wait<kStages - 2>();     // this thread's copies of slice c have landed
-    tc::fence_async_smem();     // ... and are visible to the tensor core
-    ok = __syncthreads_and(ok);
+        for (int j = 0; j < kBK / 16; ++j)
+          tc::mma_bf16(tmem, slice_desc<kBM, AMN>(sa, j), slice_desc<BN, BMN>(sb, j), idesc, (c > 0 || j > 0) ? 1u : 0u);
+        tc::mma_commit(bar + gc % kStages);
+      }
+      issued = c + 1;
+      const int nxt = c + kStages - 1;  // refills the buffer of slice c - 1 once its MMAs are done
+      if (nxt < nk) {
+        if (c >= 1) ok = ok && tc::mbar_wait(bar + (gc - 1) % kStages, ((gc - 1) / kStages) & 1u, wait_limit);
+        if (ok) {
+          const uint32_t sa = sbase + ((g + nxt) % kStages) * C::kStage;
+          fill<kBM, AMN>(la, sa, m0, kb + nxt * kBK, ke, any);
+          fill<BN, BMN>(lb, sa + C::kA, n0, kb + nxt * kBK, ke, any);
+        }
+      }
+      cp_commit();
+    }
+    cp_wait<0>();
+    const unsigned gl = g + issued - 1;  // the last slice: its commit tracks all the tile's MMAs
+    const bool drained = issued == 0 || tc::mbar_wait(bar + gl % kStages, (gl / kStages) & 1u, tc::kWaitLimit);
+    ok = __syncthreads_and(ok && drained);
+    tc::fence_after();
+    g += issued;
     if (!ok) break;
-    if (tid == 0) {
-      tc::fence_after();
-      const uint32_t sa = sbase + (c % kStages) * C::kStage, sb = sa + C::kA;
-#pragma unroll
-      for (int j = 0; j < kBK / 16; ++j)
-        tc::mma_bf16(tmem, slice_desc<kBM, AMN>(sa, j), slice_desc<BN, BMN>(sb, j), idesc, (c > 0 || j > 0) ? 1u : 0u);
-      tc::mma_commit(bar + c % kStages);
-    }
-    issued = c + 1;
-    const int nxt = c + kStages - 1;  // refills the buffer of slice c - 1 once its MMAs are done
-    if (nxt < nk) {
-      if (c >= 1) ok = ok && tc::mbar_wait(bar + (c - 1) % kStages, (uint32_t)(((c - 1) / kStages) & 1), wait_limit);
-      if (ok) load(nxt);
-    }
-    cp_commit();
-  }
-  cp_wait<0>();
-  const bool drained = issued == 0 ||
-                       tc::mbar_wait(bar + (issued - 1) % kStages, (uint32_t)(((issued - 1) / kStages) & 1), tc::kWaitLimit);
-  ok = __syncthreads_and(ok && drained);
-  tc::fence_after();
-  float* scratch = reinterpret_cast<float*>(sm);  // the stage ring is idle now
-  float acc = 0.f;
-  const int row = m0 + warp * 32 + lane;
-  if (ok) {
+    // the next tile's first copies go out now, so that they land while this tile's epilogue runs
+    const int next = mt + gridDim.x;
+    if (next < n_mt) prologue(next * kBM);
+    float acc = 0.f;
+    const int row = m0 + warp * 32 + lane;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
       float v[16];
@@ -436,8 +468,14 @@ __global__ void __launch_bounds__(kThr, 1) k_cnn_gemm(const LA la, const LB lb, 
       }
       ep.apply(row, n0 + c0, v, acc, scratch);
     }
+    ep.finish(row, acc, scratch, tid, mt, n_mt);
+    // the accumulator and the scratch are free again before the next tile's MMAs
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    mt = next;
   }
-  if (ok) ep.finish(row, acc, scratch, tid);
+  cp_wait<0>();
   tc::fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -485,68 +523,78 @@ __global__ void __launch_bounds__(256) k_conv0_fwd(const bf16* __restrict__ img,
 }
 
 // Weight gradient of the first convolution: part[block][co * 9 + tap] = sum over the block's pixels of
-// dY0[p][co] img(tap) (both BF16), tiles of 64 pixels staged in shared memory, grid-stride over tiles.
+// dY0[p][co] img(tap) (both BF16).  Thread t owns the channels 4 (t & 7) ... + 3 and the pixel stream
+// t >> 3 (32 streams per block, grid-stride over the pixels, four pixels per step with all their loads
+// issued first); its 36 products per pixel accumulate in registers, and the block's 32 streams are
+// added in a fixed order through shared memory.
 __global__ void __launch_bounds__(256) k_conv0_dw(const bf16* __restrict__ dy, const bf16* __restrict__ img, int npix,
                                                   float* __restrict__ part) {
-  __shared__ float sdy[64][33];
-  __shared__ float sx[64][9];
-  const int tid = threadIdx.x;
-  const int o0 = tid, o1 = 256 + tid;  // outputs co * 9 + tap; o1 valid for tid < 32
-  float a0 = 0.f, a1 = 0.f;
-  for (long long p0 = (long long)blockIdx.x * 64; p0 < npix; p0 += (long long)gridDim.x * 64) {
-    {
-      const int pix = tid >> 2, cq = tid & 3;
-      const long long p = p0 + pix;
-      float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (p < npix) unpack8(*reinterpret_cast<const uint4*>(dy + p * 32 + cq * 8), f);
+  __shared__ float red[32][289];
+  const int cg = threadIdx.x & 7, sid = threadIdx.x >> 3;
+  float acc[4][9];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) sdy[pix][cq * 8 + j] = f[j];
-    }
-    for (int i = tid; i < 64 * 9; i += 256) {
-      const int pix = i / 9, t = i - 9 * pix;
-      const long long p = p0 + pix;
-      float v = 0.f;
-      if (p < npix) {
-        const int x = (int)(p & 63), y = (int)((p >> 6) & 63), b = (int)(p >> 12);
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[j][t] = 0.f;
+  const long long stride = (long long)gridDim.x * 32;
+  for (long long p0 = (long long)blockIdx.x * 32 + sid; p0 < npix; p0 += 4 * stride) {
+    uint2 u[4];
+    float xv[4][9];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long p = p0 + q * stride;
+      const bool in = p < npix;
+      u[q] = in ? *reinterpret_cast<const uint2*>(dy + p * 32 + cg * 4) : make_uint2(0u, 0u);
+      const int x = (int)(p & 63), y = (int)((p >> 6) & 63), b = (int)(p >> 12);
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
         const int iy = 2 * y + t / 3 - 1, ix = 2 * x + t % 3 - 1;
-        if (iy >= 0 && iy < 128 && ix >= 0 && ix < 128) v = __bfloat162float(img[((size_t)b * 128 + iy) * 128 + ix]);
+        xv[q][t] = (in && iy >= 0 && iy < 128 && ix >= 0 && ix < 128)
+                       ? __bfloat162float(img[((size_t)b * 128 + iy) * 128 + ix])
+                       : 0.f;
       }
-      sx[pix][t] = v;
     }
-    __syncthreads();
-    {
-      const int co = o0 / 9, t = o0 - 9 * co;
-#pragma unroll 8
-      for (int q = 0; q < 64; ++q) a0 = fmaf(sdy[q][co], sx[q][t], a0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float d[4] = {__uint_as_float(u[q].x << 16), __uint_as_float(u[q].x & 0xFFFF0000u),
+                          __uint_as_float(u[q].y << 16), __uint_as_float(u[q].y & 0xFFFF0000u)};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int t = 0; t < 9; ++t) acc[j][t] = fmaf(d[j], xv[q][t], acc[j][t]);
     }
-    if (tid < 32) {
-      const int co = o1 / 9, t = o1 - 9 * co;
-#pragma unroll 8
-      for (int q = 0; q < 64; ++q) a1 = fmaf(sdy[q][co], sx[q][t], a1);
-    }
-    __syncthreads();
   }
-  part[(size_t)blockIdx.x * 288 + o0] = a0;
-  if (tid < 32) part[(size_t)blockIdx.x * 288 + o1] = a1;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int t = 0; t < 9; ++t) red[sid][(cg * 4 + j) * 9 + t] = acc[j][t];
+  __syncthreads();
+  for (int o = threadIdx.x; o < 288; o += blockDim.x) {
+    float sum = 0.f;
+    for (int k = 0; k < 32; ++k) sum += red[k][o];
+    part[(size_t)blockIdx.x * 288 + o] = sum;
+  }
 }
 
-// out[c] = sum over r < R of in[r * ld + c], rows in a fixed order (strided over the block's 8 warps,
-// then the 8 warp sums in order); 32 columns per block.
-__global__ void __launch_bounds__(256) k_colreduce(const float* __restrict__ in, int R, int cols, int ld,
+// out[y * cols + c] = sum over the rows [y chunk, (y + 1) chunk) of in[r * ld + c], rows in a fixed order
+// (strided over the block's 8 warps, then the 8 warp sums in order); 32 columns per block, blockIdx.y
+// the row chunk.
+__global__ void __launch_bounds__(256) k_colreduce(const float* __restrict__ in, int R, int cols, int ld, int chunk,
                                                    float* __restrict__ out) {
   __shared__ float red[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + lane;
+  const int r0 = blockIdx.y * chunk, r1 = min(R, r0 + chunk);
   float s = 0.f;
   if (c < cols)
-    for (int r = warp; r < R; r += 8) s += in[(size_t)r * ld + c];
+    for (int r = r0 + warp; r < r1; r += 8) s += in[(size_t)r * ld + c];
   red[warp][lane] = s;
   __syncthreads();
   if (warp == 0 && c < cols) {
     float t = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) t += red[k][lane];
-    out[c] = t;
+    out[(size_t)blockIdx.y * cols + c] = t;
   }
 }
 
@@ -601,11 +649,11 @@ __global__ void k_f32_to_bf16(const float* __restrict__ x, long long n, bf16* __
 unsigned grid_of(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16)); }
 
 // One GEMM launch: M rows of C in 128-row tiles, gy column tiles of BN, gz splits (or classes).
-template <int BN, bool AMN, bool BMN, class LA, class LB, class EP>
+template <int BN, int S, bool AMN, bool BMN, class LA, class LB, class EP>
 cudaError_t gemm(const LA& la, const LB& lb, const EP& ep, int M, int K, int gy, int gz, int kchunk, const void* any,
                  cudaStream_t st) {
-  using C = Cfg<BN, AMN, BMN>;
-  auto kern = k_cnn_gemm<BN, AMN, BMN, LA, LB, EP>;
+  using C = Cfg<BN, S>;
+  auto kern = k_cnn_gemm<BN, S, AMN, BMN, LA, LB, EP>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem);
@@ -613,7 +661,14 @@ cudaError_t gemm(const LA& la, const LB& lb, const EP& ep, int M, int K, int gy,
     configured = true;
   }
   if (M <= 0) return cudaSuccess;
-  kern<<<dim3((M + kBM - 1) / kBM, gy, gz), kThr, C::kSmem, st>>>(la, lb, ep, K, kchunk, nullptr, tc::kWaitLimit, any);
+  // row tiles per CTA: enough CTAs for every SM to hold as many as its shared memory allows, several
+  // tiles each when there are more
+  const int n_mt = (M + kBM - 1) / kBM;
+  const long long per_sm = std::max(1, std::min(5, (int)(227 * 1024 / C::kSmem)));
+  const long long total = (long long)n_mt * gy * gz, target = 4LL * 152 * per_sm;
+  const int per_cta = (int)std::max(1LL, (total + target - 1) / target);
+  const int gx = (n_mt + per_cta - 1) / per_cta;
+  kern<<<dim3(gx, gy, gz), kThr, C::kSmem, st>>>(la, lb, ep, n_mt, K, kchunk, nullptr, tc::kWaitLimit, any);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -633,6 +688,22 @@ int dw_splits(int tiles, long long pixels, long long part_floats, long long tile
   return (int)std::max(1LL, z);
 }
 int chunk_of(long long n, int z) { return (int)(((n + z - 1) / z + kBK - 1) / kBK * kBK); }
+
+// out[c] = sum over r < R of in[r * ld + c] in a fixed order: row chunks of 64 summed into scratch by
+// many blocks, then the chunk sums by one block per 32 columns (one pass when R <= 512).
+cudaError_t colreduce(const float* in, int R, int cols, int ld, float* out, float* scratch, cudaStream_t st) {
+  const unsigned gx = (unsigned)((cols + 31) / 32);
+  if (R <= 512) {
+    k_colreduce<<<dim3(gx, 1), 256, 0, st>>>(in, R, cols, ld, R, out);
+    note_launches(1);
+    return cudaGetLastError();
+  }
+  const int chunk = 64, nch = (R + chunk - 1) / chunk;
+  k_colreduce<<<dim3(gx, nch), 256, 0, st>>>(in, R, cols, ld, chunk, scratch);
+  k_colreduce<<<dim3(gx, 1), 256, 0, st>>>(scratch, nch, cols, cols, nch, out);
+  note_launches(2);
+  return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -691,13 +762,13 @@ cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs,
     const PlainK Bw{(const bf16*)t.wb[l], Kl, N};
     if (l == 1) {
       const EpiBf16 ep{(bf16*)t.act[1], net.b[1], 1, rows, 1 << 30, 0, N};
-      TC_TRY((gemm<64, false, false>(A, Bw, ep, rows, Kl, 1, 1, Kl, any, st)));
+      TC_TRY((gemm<64, 3, false, false>(A, Bw, ep, rows, Kl, 1, 1, Kl, any, st)));
     } else if (l == 2) {
       const EpiBf16 ep{(bf16*)t.act[2], net.b[2], 1, rows, 1 << 30, 0, N};
-      TC_TRY((gemm<128, false, false>(A, Bw, ep, rows, Kl, 1, 1, Kl, any, st)));
+      TC_TRY((gemm<128, 3, false, false>(A, Bw, ep, rows, Kl, 1, 1, Kl, any, st)));
     } else {  // the last convolution writes the dense layer's feature rows ((y, x, c) order, pitch 8200)
       const EpiBf16 ep{(bf16*)t.feat, net.b[3], 1, rows, 64, kFeatPitch, N};
-      TC_TRY((gemm<128, false, false>(A, Bw, ep, rows, Kl, 1, 1, Kl, any, st)));
+      TC_TRY((gemm<128, 4, false, false>(A, Bw, ep, rows, Kl, 1, 1, Kl, any, st)));
     }
   }
   k_feat_tail<<<(B * (kFeatPitch - kFeat) + 255) / 256, 256, 0, st>>>((bf16*)t.feat, cs, B);
@@ -705,7 +776,7 @@ cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs,
   // dense layer: K = 8200 split 16 ways into FP32 partials, then summed with bias and ReLU
   const int Z = 16, kc = chunk_of(kFeatPitch, Z);
   const EpiF32 ep{t.part, (long long)B * kHid, B, kHid};
-  TC_TRY((gemm<128, false, false>(PlainK{(const bf16*)t.feat, kFeatPitch, B}, PlainK{(const bf16*)t.w1b, kFeatPitch, kHid},
+  TC_TRY((gemm<128, 4, false, false>(PlainK{(const bf16*)t.feat, kFeatPitch, B}, PlainK{(const bf16*)t.w1b, kFeatPitch, kHid},
                                   ep, B, kFeatPitch, 1, Z, kc, any, st)));
   k_sum_z<<<grid_of((long long)B * kHid), 256, 0, st>>>(t.part, Z, (long long)B * kHid, net.b1, kHid, h);
   note_launches(1);
@@ -717,15 +788,15 @@ cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGra
   k_f32_to_bf16<<<grid_of((long long)B * kHid), 256, 0, st>>>(dh, (long long)B * kHid, (bf16*)t.dhb);
   note_launches(1);
   // dense layer: dW1[n][f] = sum_b dh[b][n] feat[b][f] (rows f, both operands MN-major)
-  TC_TRY((gemm<128, true, true>(PlainMN{(const bf16*)t.feat, kFeatPitch, kFeatPitch}, PlainMN{(const bf16*)t.dhb, kHid, kHid},
+  TC_TRY((gemm<128, 3, true, true>(PlainMN{(const bf16*)t.feat, kFeatPitch, kFeatPitch}, PlainMN{(const bf16*)t.dhb, kHid, kHid},
                                 EpiF32T{g.w1, 0, kFeat + 2, kFeat + 2}, kFeatPitch, B, 1, 1, B, any, st)));
-  // ... and dfeat[b][f] = sum_n dh[b][n] W1[n][f] -> dY of the last convolution (masked, BF16) + row sums
-  const int gy = (B + 127) / 128;
-  TC_TRY((gemm<128, true, false>(PlainMN{(const bf16*)t.w1b, kFeatPitch, kFeat}, PlainK{(const bf16*)t.dhb, kHid, B},
-                                 EpiDfeat{(bf16*)t.dy3, (const bf16*)t.feat, t.colpart, B}, kFeat, kHid, gy, 1, kHid, any,
-                                 st)));
-  k_colreduce<<<(128 + 31) / 32, 256, 0, st>>>(t.colpart, gy * 64, 128, 128, g.b[3]);
-  note_launches(1);
+  // ... and dfeat[b][f] = sum_n dh[b][n] W1[n][f] (rows b, B MN-major) -> dY of the last convolution
+  // (masked, BF16) and its per-channel column sums
+  const int nmt = (B + kBM - 1) / kBM;
+  TC_TRY((gemm<128, 2, false, true>(PlainK{(const bf16*)t.dhb, kHid, B}, PlainMN{(const bf16*)t.w1b, kFeatPitch, kFeat},
+                                    EpiDfeat{(bf16*)t.dy3, (const bf16*)t.feat, t.colpart, B}, B, kHid, kFeat / 128, 1,
+                                    kHid, any, st)));
+  TC_TRY(colreduce(t.colpart, (kFeat / 128) * nmt, 128, 128, g.b[3], t.part, st));
   // convolutions 3, 2, 1: weight gradient (split over pixels), then the data gradient of the layer below
   const bf16* dyl = (const bf16*)t.dy3;
   for (int l = 3; l >= 1; --l) {
@@ -738,9 +809,9 @@ cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGra
     const int kc = chunk_of(rows, Z);
     const EpiF32T epw{t.part, (long long)N * Kl, Kl, Kl};
     if (N == 64)
-      TC_TRY((gemm<64, true, true>(ConvMN{geo}, PlainMN{dyl, N, N}, epw, Kl, rows, 1, Z, kc, any, st)));
+      TC_TRY((gemm<64, 4, true, true>(ConvMN{geo}, PlainMN{dyl, N, N}, epw, Kl, rows, 1, Z, kc, any, st)));
     else
-      TC_TRY((gemm<128, true, true>(ConvMN{geo}, PlainMN{dyl, N, N}, epw, Kl, rows, 1, Z, kc, any, st)));
+      TC_TRY((gemm<128, 4, true, true>(ConvMN{geo}, PlainMN{dyl, N, N}, epw, Kl, rows, 1, Z, kc, any, st)));
     k_sum_z<<<grid_of((long long)N * Kl), 256, 0, st>>>(t.part, Z, (long long)N * Kl, nullptr, 1, g.w[l]);
     note_launches(1);
     // data gradient, four parity classes in one launch; output dY of conv l - 1 and its bias partials
@@ -748,23 +819,22 @@ cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGra
     const ParityK A{dyl, lwo, ln, rows};
     const ClassWt Bw{(const bf16*)t.wt[l], ln, C};
     if (C == 128)
-      TC_TRY((gemm<128, false, false>(A, Bw, EpiDx<128>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
+      TC_TRY((gemm<128, 3, false, false>(A, Bw, EpiDx<128>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
                                       9 * N, 1, 4, 1 << 30, any, st)));
     else if (C == 64)
-      TC_TRY((gemm<64, false, false>(A, Bw, EpiDx<64>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
+      TC_TRY((gemm<64, 3, false, false>(A, Bw, EpiDx<64>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
                                      9 * N, 1, 4, 1 << 30, any, st)));
     else
-      TC_TRY((gemm<32, false, false>(A, Bw, EpiDx<32>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
+      TC_TRY((gemm<32, 2, false, false>(A, Bw, EpiDx<32>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
                                      9 * N, 1, 4, 1 << 30, any, st)));
-    k_colreduce<<<(C + 31) / 32, 256, 0, st>>>(t.colpart, 4 * ((rows + kBM - 1) / kBM), C, C, g.b[l - 1]);
-    note_launches(1);
+    TC_TRY(colreduce(t.colpart, 4 * ((rows + kBM - 1) / kBM), C, C, g.b[l - 1], t.part, st));
     dyl = dyo;
   }
   // the first convolution's weight gradient on the SIMT pipes
   const int G = 2 * 152;
   k_conv0_dw<<<G, 256, 0, st>>>(dyl, (const bf16*)t.imgb, B * 4096, t.colpart);
-  k_colreduce<<<(288 + 31) / 32, 256, 0, st>>>(t.colpart, G, 288, 288, g.w[0]);
-  note_launches(2);
+  note_launches(1);
+  TC_TRY(colreduce(t.colpart, G, 288, 288, g.w[0], t.part, st));
   return cudaGetLastError();
 }
 
