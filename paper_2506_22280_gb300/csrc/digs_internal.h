@@ -109,7 +109,7 @@ cudaError_t launch_gw_reduce(const Workspace& ws, const ViewsParam& views, int P
 int chain_blocks(int n);
 int pair_sum_blocks(int n);
 
-// umma.cu: tensor-core GEMM (BF16 operands rounded from FP32, FP32 accumulation); C(m, n) = sum_k
+// umma.cu: tensor-core GEMM behind digs_gemm_bf16 (BF16 operands rounded from FP32, FP32 accumulation); C(m, n) = sum_k
 // A(m, k) B(k, n) with A(m, k) = at ? A[k lda + m] : A[m lda + k], B(k, n) = bt ? B[n ldb + k] :
 // B[k ldb + n]; splits > 1: partial sums over K ranges into C + z zstride (bias and ReLU not applied).
 // *status (optional) is set to 1 if a bounded wait gave up.
@@ -131,7 +131,6 @@ cudaError_t launch_temporal_eval(const float* ctrl, int n_ctrl, int R, float t_s
 cudaError_t launch_temporal_bwd(const float* g_w, int n_ctrl, int R, float t_step, const RowsParam& rows, int B,
                                 float* g_ctrl, cudaStream_t st);
 
-// adam.cu
 // cnn_tc.cu: the weight-predictor CNN on the tensor cores.  Parameter and gradient pointers per layer
 // (FP32, in cnn.cu's layout: conv weights [Co][3][3][Ci], dense weights W1 [128][8194]).
 struct CnnNet {
@@ -156,6 +155,7 @@ cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs,
 // activations and weights that the last cnn_tc_forward on the same buffers kept.
 cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGrad& g, cudaStream_t st);
 
+// adam.cu
 struct AdamGroup {
   float* p;
   const float* g;

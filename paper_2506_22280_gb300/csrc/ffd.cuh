@@ -141,69 +141,3 @@ __device__ __forceinline__ void ffd_hessian_rank(const float* __restrict__ phi_r
   }
 }
 
-// Backward of ffd_eval_point for upstream gradients GU = dL/dU and GdU = dL/d(dU):
-//   dL/dphi_r[node]_c += beta GU_c + sum_j GdU_cj d_j beta          (atomically, into g_phi)
-//   dL/dx_m           += sum_{r,node,c} phi_c (GU_c d_m beta + sum_j GdU_cj d_m d_j beta)
-template <int R>
-__device__ __forceinline__ void ffd_bwd_point(const float* __restrict__ phi, float* __restrict__ g_phi,
-                                              const LatticeC& L, const float x[3], const float GU[R][3],
-                                              const float GdU[R][9], float gx_out[3]) {
-  int f[3];
-  float u[3];
-  lattice_cell(L, x, f, u);
-  float B[3][4], dB[3][4], d2B[3][4];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    bspline4(u[a], B[a]);
-    bspline4_d1(u[a], dB[a]);
-    bspline4_d2(u[a], d2B[a]);
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      dB[a][l] *= L.inv_h[a];
-      d2B[a][l] *= L.inv_h[a] * L.inv_h[a];
-    }
-  }
-  float gxm[3] = {0.f, 0.f, 0.f};
-  const size_t rank_stride = (size_t)L.nx * L.ny * L.nz * 3;
-  for (int n3 = 0; n3 < 4; ++n3) {
-    int k = f[2] + n3;
-    if (k < 0 || k >= L.nz) continue;
-    for (int m = 0; m < 4; ++m) {
-      int j = f[1] + m;
-      if (j < 0 || j >= L.ny) continue;
-      for (int l = 0; l < 4; ++l) {
-        int i = f[0] + l;
-        if (i < 0 || i >= L.nx) continue;
-        float bx = B[0][l], by = B[1][m], bz = B[2][n3];
-        float dbx = dB[0][l], dby = dB[1][m], dbz = dB[2][n3];
-        float beta = bx * by * bz;
-        float gb[3] = {dbx * by * bz, bx * dby * bz, bx * by * dbz};
-        // Hessian of beta, symmetric
-        float hxx = d2B[0][l] * by * bz, hyy = bx * d2B[1][m] * bz, hzz = bx * by * d2B[2][n3];
-        float hxy = dbx * dby * bz, hxz = dbx * by * dbz, hyz = bx * dby * dbz;
-        size_t node = (((size_t)k * L.ny + j) * L.nx + i) * 3;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const float* d = phi + r * rank_stride + node;
-          float v0 = __ldg(d), v1 = __ldg(d + 1), v2 = __ldg(d + 2);
-          float* gp = g_phi + r * rank_stride + node;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            float gval = beta * GU[r][c] + GdU[r][3 * c] * gb[0] + GdU[r][3 * c + 1] * gb[1] + GdU[r][3 * c + 2] * gb[2];
-            atomicAdd(gp + c, gval);
-          }
-          float q = v0 * GU[r][0] + v1 * GU[r][1] + v2 * GU[r][2];
-          float Q0 = v0 * GdU[r][0] + v1 * GdU[r][3] + v2 * GdU[r][6];
-          float Q1 = v0 * GdU[r][1] + v1 * GdU[r][4] + v2 * GdU[r][7];
-          float Q2 = v0 * GdU[r][2] + v1 * GdU[r][5] + v2 * GdU[r][8];
-          gxm[0] += q * gb[0] + hxx * Q0 + hxy * Q1 + hxz * Q2;
-          gxm[1] += q * gb[1] + hxy * Q0 + hyy * Q1 + hyz * Q2;
-          gxm[2] += q * gb[2] + hxz * Q0 + hyz * Q1 + hzz * Q2;
-        }
-      }
-    }
-  }
-  gx_out[0] += gxm[0];
-  gx_out[1] += gxm[1];
-  gx_out[2] += gxm[2];
-}

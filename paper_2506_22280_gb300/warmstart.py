@@ -91,13 +91,42 @@ def propose_weights(predictor: D.WeightPredictor, meas: torch.Tensor, angles: np
     return predictor.predict(img, cs)
 
 
+def train_and_propose(predictor: D.WeightPredictor, imgs: torch.Tensor, cs: torch.Tensor, W: torch.Tensor,
+                      epochs: int, rec: D.Reconstruction, meas: torch.Tensor, views: Sequence[Dict],
+                      angles: np.ndarray, batch: int = 256, lr: float = 1e-3, seed: int = 0) -> Dict:
+    """Train for up to `epochs` epochs; after each, propose every projection's weights and score the
+    proposal by the full-scan loss of the current model (the judge of the warm start, computed from the
+    measured projections only).  Returns the best proposal, its epoch and loss, and the per-epoch record."""
+    n = int(imgs.shape[0])
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    img_m = predictor.prepare(meas)
+    cs_m = torch.as_tensor(np.stack([np.cos(angles), np.sin(angles)], 1), dtype=torch.float32, device=meas.device)
+    best, history = None, []
+    for e in range(epochs):
+        perm = torch.randperm(n, generator=g).to(imgs.device)
+        tot = torch.zeros((), device=imgs.device)
+        steps = 0
+        for s in range(0, n - batch + 1, batch):
+            idx = perm[s:s + batch]
+            tot += predictor.train_step(imgs[idx].contiguous(), cs[idx].contiguous(), W[idx].contiguous(), lr)[0]
+            steps += 1
+        proposal = predictor.predict(img_m, cs_m)
+        loss = scan_loss(rec, meas, views, proposal)
+        history.append(dict(epoch=e + 1, train_loss=float(tot.item()) / max(steps, 1), scan_loss=loss))
+        if best is None or loss < best["loss"]:
+            best = dict(proposal=proposal, loss=loss, epoch=e + 1)
+    return dict(proposal=best["proposal"], loss=best["loss"], epoch=best["epoch"], history=history)
+
+
 def warm_start(rec: D.Reconstruction, predictor: D.WeightPredictor, meas: torch.Tensor, views: Sequence[Dict],
-               angles: np.ndarray, rows: Sequence[int]) -> Dict:
+               angles: np.ndarray, rows: Sequence[int], proposal: torch.Tensor = None) -> Dict:
     """Replace the weight rows `rows` of the reconstruction (the scan's projections, in the order of meas /
-    views / angles) by the CNN's proposal if that lowers the full-scan loss; report both losses."""
+    views / angles) by the CNN's proposal (or the given one) if that lowers the full-scan loss; report both
+    losses."""
     rows_t = torch.as_tensor(list(rows), device=rec.w.device)
     current = rec.w[rows_t].contiguous()
-    proposal = propose_weights(predictor, meas, angles)
+    if proposal is None:
+        proposal = propose_weights(predictor, meas, angles)
     l_cur = scan_loss(rec, meas, views, current)
     l_new = scan_loss(rec, meas, views, proposal)
     accepted = l_new < l_cur
