@@ -202,9 +202,11 @@ def render_measured(pkg, wl, device):
     return out
 
 
-def traffic_for(kernel):
+def traffic_for(kernel, projections, tile, lanes):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the current
-    source of that kernel (else None)."""
+    source of that kernel with the same tile and backward lanes (else None).  The capture holds fewer
+    projections than a bench launch: its records, tile counts and images all grow in proportion to the
+    projections of the launch, so its bytes are scaled by projections / captured projections."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
@@ -214,7 +216,9 @@ def traffic_for(kernel):
         src = open(os.path.join(ROOT, "paper_2506_22280_gb300", "csrc", rec["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest() != rec["sha256"]:
             return None
-        return float(rec["bytes_per_launch"])
+        if int(rec["tile"]) != tile or int(rec["bwd_lanes"]) != lanes:
+            return None
+        return float(rec["bytes_per_launch"]) * projections / float(rec["projections"])
     except Exception:
         return None
 
@@ -775,7 +779,7 @@ def run_ours(args):
     mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = float(mp.get("hbm_gbs", 6800.0)) * 1e9
-    kernels = {k: kernel_roofline(k, pairs["cutoff_pairs"], stages[k], peaks, traffic_for("k_" + k))
+    kernels = {k: kernel_roofline(k, pairs["cutoff_pairs"], stages[k], peaks, traffic_for("k_" + k, B, tile, lanes))
                for k in ("raster_fwd", "raster_bwd")}
     dom = max(kernels, key=lambda k: stages[k])
     roofline = dict(kernels[dom], box_pairs_per_launch=pairs["box_pairs"], tile_pairs_per_launch=pairs["tile_pairs"])

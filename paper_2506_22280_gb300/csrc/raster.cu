@@ -20,7 +20,9 @@
 // stepping 2s rows; wider slices: the column pair (c, c + ceil(w/2)) of row (l div ceil(w/2)), stepping
 // s = 16 div ceil(w/2) rows.  Each lane accumulates seven sums per pixel of its pair and turns them into
 // the ten sufficient statistics of the record gradient; the half-warp reduces them with an 11-shuffle
-// recursive halving and ten lanes write them to the record's slot (no atomics).
+// recursive halving and ten lanes write them to the record's slot (no atomics).  A CTA sweeps four units
+// of 16 records in turn, each unit's records and tile counts copied to shared memory by cp.async while
+// the unit before it is swept.
 #include <algorithm>
 
 #include "digs_internal.h"
@@ -33,8 +35,13 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // ---- packed FP32x2: the two pixels of a lane's pair in one register pair ------------------------
 typedef unsigned long long f2;
@@ -327,11 +334,17 @@ __global__ void __launch_bounds__(FwdCfg<TS>::threads) k_raster_fwd(
 // ---- backward: one half-warp per (projection, Gaussian) record, over the record's whole pixel box ----
 
 constexpr int kBwdThreads = 256;
+constexpr int kBwdRounds = 4;  // record units per backward CTA
 
 // Adds the lane's share of the ten record-gradient sums, all but the first divided by amp / 2:
 // sum g V/amp; sum dL/dnum (dx^2, dx dy, dy^2); sum dL/dnum (dx, dy); sum dL/dt (1, dx, dy);
 // sum dL/dkappa.  gp points at g = dL/dI * |X - s| of the lane's first pixel in the projection image
 // (row pitch nu); (dx1, dy1) is that pixel's offset from the projected mean.
+//
+// Per pixel, with A = (g V / amp) / D and B = A (E - 1): dL/dnum = kappa B - A, dL/dt / 2 = B t and
+// dL/dkappa = B num.  A lane's pixel keeps its column, so t = t0 + wn1 dy and num = a + b dy + n11 dy^2
+// with column constants t0, a, b: every sum above is a combination of the six dy-moments
+// sum A dy^j and sum B dy^j (j = 0, 1, 2), which are all the loop accumulates besides sum g V / amp.
 __device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const HalfLanes& B, int h, float dx1, float dy1,
                                                const float* __restrict__ gp, int nu, float c2, float Sv[10]) {
   // k = -log2(e) / 2 is folded into the quadratic form: NUM = k num, ARG = k E (the exp2 argument)
@@ -341,12 +354,12 @@ __device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const HalfLanes& B
   const f2 BQ = f2_mul(f2_dup(kNegHalfLog2e * R0.n01x2), DX);
   const f2 T0 = f2_fma(f2_dup(R0.wn0), DX, f2_dup(1.f));
   const f2 N11 = f2_dup(kNegHalfLog2e * R0.n11), WN1 = f2_dup(R0.wn1);
-  const f2 KAPK = f2_dup(R0.kappa * (1.f / kNegHalfLog2e)), MK1 = f2_dup(-1.f - R0.kappa);
+  const f2 KAPK = f2_dup(R0.kappa * (1.f / kNegHalfLog2e));
   const f2 IK = f2_dup(1.f / kNegHalfLog2e), MONE = f2_dup(-1.f), STEP = f2_dup((float)B.ystep);
   const f2 C2K = f2_dup(c2 * kNegHalfLog2e);
   const int pstep = B.ystep * nu, d2 = B.pdy * nu + B.pdx, hb = B.col2 ? h - B.pdy : 0;
   f2 DY = f2_pack(dy1, dy1 + (float)B.pdy);
-  f2 S0 = f2_dup(0.f), S1 = S0, S2 = S0, S3 = S0, S4 = S0, S5 = S0, S6 = S0;
+  f2 S0 = f2_dup(0.f), A0 = S0, A1 = S0, A2 = S0, B0 = S0, B1 = S0, B2 = S0;
   for (int r = B.r0; r < h; r += B.ystep, DY = f2_add(DY, STEP), gp += pstep) {
     f2 NUM = f2_fma(DY, f2_fma(N11, DY, BQ), AQ);
     f2 T = f2_fma(WN1, DY, T0);
@@ -363,40 +376,49 @@ __device__ __forceinline__ void bwd_box_pixels(const Rec& R0, const HalfLanes& B
     f2 INVD = f2_mul(RS, RS);
     f2 ARG = f2_mul(NUM, INVD);
     f2 BV = f2_mul(RS, f2_exp2(ARG));                      // V / amp
-    f2 G = f2_pack(ga, gb);
-    S0 = f2_fma(G, BV, S0);
-    f2 AL = f2_mul(G, f2_mul(BV, INVD));                     // (dL/dV * V / (2 D)) / (amp / 2)
-    f2 EM1 = f2_fma(ARG, IK, MONE);                         // E - 1
-    f2 GNUM = f2_mul(AL, f2_fma(KAPK, ARG, MK1));          // dL/dnum = AL (kappa (E - 1) - 1)
-    f2 AEM = f2_mul(AL, EM1);
-    f2 GTH = f2_mul(AEM, T);                                 // (dL/dt) / 2
-    f2 GND = f2_mul(GNUM, DY);
-    S1 = f2_add(S1, GNUM);
-    S2 = f2_add(S2, GND);
-    S3 = f2_fma(GND, DY, S3);
-    S4 = f2_add(S4, GTH);
-    S5 = f2_fma(GTH, DY, S5);
-    S6 = f2_fma(AEM, NUM, S6);                               // k dL/dkappa
+    f2 GA = f2_mul(f2_pack(ga, gb), BV);                  // g V / amp
+    S0 = f2_add(S0, GA);
+    f2 AL = f2_mul(GA, INVD);                               // A = (dL/dV V / (2 D)) / (amp / 2)
+    f2 AE = f2_mul(AL, f2_fma(ARG, IK, MONE));              // B = A (E - 1)
+    f2 ALD = f2_mul(AL, DY), AED = f2_mul(AE, DY);
+    A0 = f2_add(A0, AL);
+    A1 = f2_add(A1, ALD);
+    A2 = f2_fma(ALD, DY, A2);
+    B0 = f2_add(B0, AE);
+    B1 = f2_add(B1, AED);
+    B2 = f2_fma(AED, DY, B2);
   }
-  // each pixel of the pair keeps its column, so its dx-moments follow from its dy-moments
-  float a[7][2];
-  const f2 Sp[7] = {S0, S1, S2, S3, S4, S5, S6};
-#pragma unroll
-  for (int i = 0; i < 7; ++i) f2_unpack(Sp[i], a[i][0], a[i][1]);
+  // per pixel of the pair: the dy-moments of dL/dnum, dL/dt and dL/dkappa from those of A and B, then
+  // the dx-moments from the pixel's column
+  float s0[2], a0[2], a1[2], a2[2], b0[2], b1[2], b2[2], aq[2], bq[2], t0[2];
+  f2_unpack(S0, s0[0], s0[1]);
+  f2_unpack(A0, a0[0], a0[1]);
+  f2_unpack(A1, a1[0], a1[1]);
+  f2_unpack(A2, a2[0], a2[1]);
+  f2_unpack(B0, b0[0], b0[1]);
+  f2_unpack(B1, b1[0], b1[1]);
+  f2_unpack(B2, b2[0], b2[1]);
+  f2_unpack(AQ, aq[0], aq[1]);
+  f2_unpack(BQ, bq[0], bq[1]);
+  f2_unpack(T0, t0[0], t0[1]);
+  const float kap = R0.kappa, wn1 = R0.wn1, n11k = kNegHalfLog2e * R0.n11;
   const float dxs[2] = {dx1, dx2};
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const float dx = dxs[j];
-    Sv[0] += a[0][j];
-    Sv[1] += dx * dx * a[1][j];
-    Sv[2] += dx * a[2][j];
-    Sv[3] += a[3][j];
-    Sv[4] += dx * a[1][j];
-    Sv[5] += a[2][j];
-    Sv[6] += 2.f * a[4][j];
-    Sv[7] += 2.f * dx * a[4][j];
-    Sv[8] += 2.f * a[5][j];
-    Sv[9] += a[6][j] * (1.f / kNegHalfLog2e);
+    const float g0 = fmaf(kap, b0[j], -a0[j]), g1 = fmaf(kap, b1[j], -a1[j]), g2 = fmaf(kap, b2[j], -a2[j]);
+    const float th0 = fmaf(t0[j], b0[j], wn1 * b1[j]), th1 = fmaf(t0[j], b1[j], wn1 * b2[j]);
+    const float gk = fmaf(aq[j], b0[j], fmaf(bq[j], b1[j], n11k * b2[j]));
+    Sv[0] += s0[j];
+    Sv[1] += dx * dx * g0;
+    Sv[2] += dx * g1;
+    Sv[3] += g2;
+    Sv[4] += dx * g0;
+    Sv[5] += g1;
+    Sv[6] += 2.f * th0;
+    Sv[7] += 2.f * dx * th0;
+    Sv[8] += 2.f * th1;
+    Sv[9] += gk * (1.f / kNegHalfLog2e);
   }
 }
 
@@ -480,43 +502,79 @@ __global__ void __launch_bounds__(256) k_bwd_pairing(const uint8_t* __restrict__
 // One group of LPR lanes (16: two records per warp, 32: one) per (projection, Gaussian) record: the ten
 // sums over every pixel of the record's box, reduced over the group and written to grec[record] (12
 // floats, the last two unused).  Records whose Gaussian was culled get zeros.
-// Grid: (ceil(N / (256 / LPR)), P).
+// Each CTA takes `rounds` consecutive units of 256 / LPR records (unit u of projection b: for LPR = 16
+// ranks 16 (u mod 2) .. + 15 of record group u / 2 in k_bwd_pairing's order, else records 8u .. 8u + 7).
+// A group's record and its tile count go to shared memory by cp.async two units ahead (double buffer;
+// the unit after that has its record index loaded while the current one is swept), so that only a CTA's
+// first unit waits for them.
+// Grid: (ceil(units / rounds), P), units = ceil(N / (256 / LPR)).
 template <int LPR>
 __global__ void __launch_bounds__(kBwdThreads, 4) k_raster_bwd(const float4* __restrict__ rec,
                                                                 const uint32_t* __restrict__ counts, int N, int nu,
                                                                 int nv, const float* __restrict__ gpix, float c2,
                                                                 const uint8_t* __restrict__ perm,
-                                                                float* __restrict__ grec) {
-  constexpr int kRecords = kBwdThreads / LPR;  // records per CTA
+                                                                float* __restrict__ grec, int rounds) {
+  constexpr int kRecords = kBwdThreads / LPR;  // records per unit
+  __shared__ __align__(16) float4 sbuf[2][kRecords][DIGS_REC_F4 + 1];  // record, then its tile count
   const int hl = threadIdx.x & (LPR - 1);
   const int b = blockIdx.y;
   const int slot = (int)(threadIdx.x / LPR);
-  int n = blockIdx.x * kRecords + slot;
-  if (LPR == 16) {  // CTA pairs share a group of 32 records, taken in the order of k_bwd_pairing
-    const int g = blockIdx.x >> 1;
-    n = g * 32 + perm[((size_t)b * ((N + 31) >> 5) + g) * 32 + (blockIdx.x & 1) * 16 + slot];
-  }
-  const bool valid = n < N;
-  const size_t i = (size_t)b * N + (valid ? n : 0);
-  float Sv[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (valid && counts[i] != 0u) {
-    const Rec R0 = load_rec(rec + i * DIGS_REC_F4);
-    const int x0 = R0.bx & 0xffff, x1 = R0.bx >> 16, y0 = R0.by & 0xffff, y1 = R0.by >> 16;
-    const int w = x1 - x0 + 1, h = y1 - y0 + 1;
-    const float* gimg = gpix + (size_t)b * nv * nu;
-    for (int cx = 0; cx < w; cx += LPR) {  // boxes wider than LPR pixels: LPR-column slices
-      const HalfLanes B = group_lanes<LPR>(min(LPR, w - cx), h, hl);
-      if (B.active) {
-        const int px = x0 + cx + B.c, py = y0 + B.r0;
-        const float* gp = gimg + (size_t)py * nu + px;
-        bwd_box_pixels(R0, B, h, (float)px - R0.xc, (float)py - R0.yc, gp, nu, c2, Sv);
-      }
+  const int units = (N + kRecords - 1) / kRecords;
+  const int G = (N + 31) >> 5;
+  const int u0 = blockIdx.x * rounds;
+  auto record_of = [&](int u) -> int {  // this group's record in unit u (N: none)
+    if (u >= units || u - u0 >= rounds) return N;
+    if (LPR == 16) {  // unit pairs share a group of 32 records, taken in the order of k_bwd_pairing
+      const int g = u >> 1;
+      return g * 32 + perm[((size_t)b * G + g) * 32 + (u & 1) * 16 + slot];
     }
-    const float amph = 0.5f * R0.amp;
+    return u * kRecords + slot;
+  };
+  auto fetch = [&](int n, int buf) {  // one commit group per call and thread, empty or not
+    if (n < N && hl <= DIGS_REC_F4) {
+      const size_t i = (size_t)b * N + n;
+      if (hl < DIGS_REC_F4)
+        cp_async16(&sbuf[buf][slot][hl], rec + i * DIGS_REC_F4 + hl);
+      else
+        cp_async4(&sbuf[buf][slot][DIGS_REC_F4], counts + i);
+    }
+    cp_async_commit();
+  };
+  int n_cur = record_of(u0), n_next = record_of(u0 + 1);
+  fetch(n_cur, 0);
+  fetch(n_next, 1);
+  const float* gimg = gpix + (size_t)b * nv * nu;
+  for (int r = 0; r < rounds; ++r) {
+    const int n_after = record_of(u0 + r + 2);  // in flight while this unit is swept
+    const int buf = r & 1;
+    cp_async_wait_but_one();  // this unit's copies have landed (the next unit's may still be in flight)
+    __syncwarp();
+    const bool valid = n_cur < N;
+    float Sv[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid && __float_as_uint(sbuf[buf][slot][DIGS_REC_F4].x) != 0u) {
+      const Rec R0 = load_rec(&sbuf[buf][slot][0]);
+      const int x0 = R0.bx & 0xffff, x1 = R0.bx >> 16, y0 = R0.by & 0xffff, y1 = R0.by >> 16;
+      const int w = x1 - x0 + 1, h = y1 - y0 + 1;
+      for (int cx = 0; cx < w; cx += LPR) {  // boxes wider than LPR pixels: LPR-column slices
+        const HalfLanes B = group_lanes<LPR>(min(LPR, w - cx), h, hl);
+        if (B.active) {
+          const int px = x0 + cx + B.c, py = y0 + B.r0;
+          const float* gp = gimg + (size_t)py * nu + px;
+          bwd_box_pixels(R0, B, h, (float)px - R0.xc, (float)py - R0.yc, gp, nu, c2, Sv);
+        }
+      }
+      const float amph = 0.5f * R0.amp;
 #pragma unroll
-    for (int q = 1; q < 10; ++q) Sv[q] *= amph;
+      for (int q = 1; q < 10; ++q) Sv[q] *= amph;
+    }
+    group_reduce_store10<LPR>(Sv, grec + ((size_t)b * N + (valid ? n_cur : 0)) * (DIGS_PARTIAL_F4 * 4),
+                              threadIdx.x & 15, valid);
+    __syncwarp();  // every lane has read this buffer before it is refilled
+    fetch(n_after, buf);
+    n_cur = n_next;
+    n_next = n_after;
   }
-  group_reduce_store10<LPR>(Sv, grec + i * (DIGS_PARTIAL_F4 * 4), threadIdx.x & 15, valid);
+  cp_async_wait_all();
 }
 
 // g = dL/dI * |X - s| for every pixel (the per-pixel factor of the line integral, applied once).
@@ -574,16 +632,18 @@ cudaError_t launch_raster_bwd(const Workspace& ws, const ViewsParam& views, floa
     note_launches(1);
   }
   if (ws.bwd_lanes == 32) {
-    dim3 grid((ws.n + kBwdThreads / 32 - 1) / (kBwdThreads / 32), ws.P);
+    const int units = (ws.n + kBwdThreads / 32 - 1) / (kBwdThreads / 32);
+    dim3 grid((units + kBwdRounds - 1) / kBwdRounds, ws.P);
     k_raster_bwd<32><<<grid, kBwdThreads, 0, st>>>(ws.rec, ws.counts, ws.n, ws.nu, ws.nv, ws.dldi, c2, nullptr,
-                                                   (float*)ws.grec);
+                                                   (float*)ws.grec, kBwdRounds);
   } else {
     const int G = (ws.n + 31) / 32;
     k_bwd_pairing<<<dim3((G + 7) / 8, ws.P), 256, 0, st>>>(ws.bcost, ws.counts, ws.n, G, ws.bperm);
     note_launches(1);
-    dim3 grid((ws.n + kBwdThreads / 16 - 1) / (kBwdThreads / 16), ws.P);
+    const int units = (ws.n + kBwdThreads / 16 - 1) / (kBwdThreads / 16);
+    dim3 grid((units + kBwdRounds - 1) / kBwdRounds, ws.P);
     k_raster_bwd<16><<<grid, kBwdThreads, 0, st>>>(ws.rec, ws.counts, ws.n, ws.nu, ws.nv, ws.dldi, c2, ws.bperm,
-                                                   (float*)ws.grec);
+                                                   (float*)ws.grec, kBwdRounds);
   }
   note_launches(1);
   return cudaGetLastError();
