@@ -97,7 +97,8 @@ cudaError_t launch_raster_fwd(const Workspace& ws, const ViewsParam& views, floa
 // grad_proj = dL/dI, or nullptr when ws.dldi already holds dL/dI * |X - s| (from the step's forward).
 cudaError_t launch_raster_bwd(const Workspace& ws, const ViewsParam& views, float c2, const float* grad_proj,
                               cudaStream_t st);
-cudaError_t launch_loss_reduce(const float* part, int n, float* out, float scale, cudaStream_t st);
+// Sums part[0 .. n) in a fixed order (overwriting part) and writes scale * sum to out[0].
+cudaError_t launch_loss_reduce(float* part, int n, float* out, float scale, cudaStream_t st);
 
 // chain.cu
 cudaError_t launch_chain_bwd(const GaussPtrs& g, const ScanTable& sc, const LatticeC& L, const float* phi,

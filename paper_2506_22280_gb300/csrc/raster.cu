@@ -150,13 +150,20 @@ struct FwdCfg {
 };
 
 // A staged record -> the entry the pixel loop reads:
-//   (k n00, k n01x2, k n11, wn0), (wn1, kappa / k, amp, -xc), (-yc, 0, 0, 0)
-// with k = -log2(e) / 2, so that the loop forms the exp2 argument k E = k num / D directly.
+//   (k n00 / sg^2, k n01x2 / sg^2, k n11 / sg^2, wn0 / sg), (wn1 / sg, kappa / k, amp / sg, -xc), (-yc, 1 / sg, 0, 0)
+// with k = -log2(e) / 2, so that the loop forms the exp2 argument k E = k num / D directly, and
+// sg = |amp| (1 when |amp| lies outside [2^-40, 2^40]): num and t scaled by 1 / sg^2 and 1 / sg scale D
+// by 1 / sg^2 and leave E unchanged, so the SFU's rsqrt of the scaled D is sg D^-1/2 and the amplitude
+// costs no multiply in the loop (amp / sg, i.e. the sign of amp, is applied by the accumulating FMA).
 __device__ __forceinline__ void derive_entry(const float4* raw, float4* ent) {
   const float4 a = raw[0], b = raw[1], c = raw[2];
-  ent[0] = make_float4(kNegHalfLog2e * a.z, kNegHalfLog2e * a.w, kNegHalfLog2e * b.x, b.y);
-  ent[1] = make_float4(b.z, b.w * (1.f / kNegHalfLog2e), c.x, -a.x);
-  ent[2] = make_float4(-a.y, 0.f, 0.f, 0.f);
+  const float mag = fabsf(c.x);
+  const bool fold = mag >= 0x1p-40f && mag <= 0x1p40f;
+  const float s1 = fold ? __frcp_rn(mag) : 1.f, s2 = s1 * s1;
+  const float sgn = fold ? copysignf(1.f, c.x) : c.x;
+  ent[0] = make_float4(kNegHalfLog2e * a.z * s2, kNegHalfLog2e * a.w * s2, kNegHalfLog2e * b.x * s2, b.y * s1);
+  ent[1] = make_float4(b.z * s1, b.w * (1.f / kNegHalfLog2e), sgn, -a.x);
+  ent[2] = make_float4(-a.y, s1, 0.f, 0.f);
 }
 
 // Whether the pixel rectangle [x0, x1] x [y0, y1] (a block's part of the record's box) can hold a pixel
@@ -195,25 +202,27 @@ __device__ __forceinline__ bool ellipse_meets(const float4* r3, int x0, int x1, 
 __device__ __forceinline__ f2 f2_lo(const float4& v) { return f2_pack(v.x, v.y); }
 __device__ __forceinline__ f2 f2_hi(const float4& v) { return f2_pack(v.z, v.w); }
 
-// V / |X - s| of one entry at the lane's two pixels (XX, YY), zero outside the cutoff (k E < c2k).
+// V / (|X - s| amp / sg) of one entry at the lane's two pixels (XX, YY), zero outside the cutoff
+// (k E < c2k); *sgn = amp / sg, the factor the caller accumulates it with.
 template <bool COUNT>
-__device__ __forceinline__ f2 fwd_pair(const float4* en, float xx, f2 YY, float c2k, unsigned& n_cut) {
+__device__ __forceinline__ f2 fwd_pair(const float4* en, float xx, f2 YY, float c2k, unsigned& n_cut, float& sgn) {
   const float4 q0 = en[0], q1 = en[1], q2 = en[2];
   // the lane's two pixels share their column: the dx terms are scalars
   const float dx = xx + q1.w;
-  const float aq = q0.x * dx * dx, bq = q0.y * dx, t0 = fmaf(q0.w, dx, 1.f);
+  const float aq = q0.x * dx * dx, bq = q0.y * dx, t0 = fmaf(q0.w, dx, q2.y);
   const f2 DY = f2_add(YY, f2_dup(q2.x));
-  const f2 NUM = f2_fma(DY, f2_fma(f2_dup(q0.z), DY, f2_dup(bq)), f2_dup(aq));  // k num
-  const f2 T = f2_fma(f2_dup(q1.x), DY, f2_dup(t0));
-  const f2 D = f2_fma(T, T, f2_mul(f2_dup(q1.y), NUM));
-  const f2 RS = f2_rsqrt(D);
-  const f2 ARG = f2_mul(NUM, f2_mul(RS, RS));                  // k E
-  const f2 VAL = f2_mul(f2_mul(f2_dup(q1.z), RS), f2_exp2(ARG));
+  const f2 NUM = f2_fma(DY, f2_fma(f2_dup(q0.z), DY, f2_dup(bq)), f2_dup(aq));  // k num / sg^2
+  const f2 T = f2_fma(f2_dup(q1.x), DY, f2_dup(t0));                             // t / sg
+  const f2 D = f2_fma(T, T, f2_mul(f2_dup(q1.y), NUM));                          // D / sg^2
+  const f2 RS = f2_rsqrt(D);                                                      // sg D^-1/2
+  const f2 ARG = f2_mul(NUM, f2_mul(RS, RS));                                     // k E
+  const f2 VAL = f2_mul(RS, f2_exp2(ARG));
   float aa, ab, va, vb;
   f2_unpack(ARG, aa, ab);
   f2_unpack(VAL, va, vb);
   const bool ia = aa >= c2k, ib = ab >= c2k;
   if (COUNT) n_cut += (unsigned)ia + (unsigned)ib;
+  sgn = q1.z;
   return f2_pack(ia ? va : 0.f, ib ? vb : 0.f);
 }
 
@@ -273,24 +282,22 @@ __global__ void __launch_bounds__(FwdCfg<TS>::threads) k_raster_fwd(
     issue(k0 + C::batch);  // lands while this batch is swept
     const int cnt = __popc(mask);
     int e = 0;
-#pragma unroll 1
-    for (; e + 7 < cnt; e += 8) {  // eight entries per step
+    // n entries from e: all evaluated (independent dependency chains), then accumulated in list order
+    auto sweep = [&](int n) {
       f2 v[8];
+      float sg[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = fwd_pair<COUNT>(ent + (e + k) * 3, XX, YY, c2k, n_cut);
+      for (int k = 0; k < 8; ++k)
+        if (k < n) v[k] = fwd_pair<COUNT>(ent + (e + k) * 3, XX, YY, c2k, n_cut, sg[k]);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) ACC = f2_add(ACC, v[k]);  // list order
-    }
-    for (; e + 3 < cnt; e += 4) {  // four entries per step: four independent dependency chains
-      const f2 va = fwd_pair<COUNT>(ent + e * 3, XX, YY, c2k, n_cut), vb = fwd_pair<COUNT>(ent + e * 3 + 3, XX, YY, c2k, n_cut);
-      const f2 vc = fwd_pair<COUNT>(ent + e * 3 + 6, XX, YY, c2k, n_cut), vd = fwd_pair<COUNT>(ent + e * 3 + 9, XX, YY, c2k, n_cut);
-      ACC = f2_add(f2_add(f2_add(f2_add(ACC, va), vb), vc), vd);  // list order
-    }
-    for (; e + 1 < cnt; e += 2) {  // two entries per step: two independent dependency chains
-      const f2 va = fwd_pair<COUNT>(ent + e * 3, XX, YY, c2k, n_cut), vb = fwd_pair<COUNT>(ent + e * 3 + 3, XX, YY, c2k, n_cut);
-      ACC = f2_add(f2_add(ACC, va), vb);  // list order
-    }
-    if (e < cnt) ACC = f2_add(ACC, fwd_pair<COUNT>(ent + e * 3, XX, YY, c2k, n_cut));
+      for (int k = 0; k < 8; ++k)
+        if (k < n) ACC = f2_fma(f2_dup(sg[k]), v[k], ACC);
+    };
+#pragma unroll 1
+    for (; e + 7 < cnt; e += 8) sweep(8);  // eight entries per step
+    if (e + 3 < cnt) { sweep(4); e += 4; }
+    if (e + 1 < cnt) { sweep(2); e += 2; }
+    if (e < cnt) sweep(1);
     __syncwarp();
   }
   cp_async_wait_all();  // the last (empty) group
@@ -649,25 +656,50 @@ cudaError_t launch_raster_bwd(const Workspace& ws, const ViewsParam& views, floa
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(1024) k_loss_reduce(const float* __restrict__ part, int n, float* out,
-                                                      float scale) {
+// Sum of n partials in a fixed order: a block sums `chunk` consecutive values in one pass of its threads
+// (strided), reduced by shuffles and through shared memory.  With more than one block, each block's sum
+// replaces the first value of its own chunk (read only by that block) and one block then sums those.
+__device__ __forceinline__ float block_sum_strided(const float* __restrict__ part, long long i0, long long i1,
+                                                   long long stride) {
   __shared__ float red[32];
   float s = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  for (long long i = i0 + (long long)threadIdx.x * stride; i < i1; i += (long long)blockDim.x * stride) s += part[i];
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
+  float t = 0.f;
   if (threadIdx.x < 32) {
-    float t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
     t = warp_sum(t);
-    if (threadIdx.x == 0) out[0] = t * scale;
   }
+  return t;  // valid in thread 0
 }
 
-cudaError_t launch_loss_reduce(const float* part, int n, float* out, float scale, cudaStream_t st) {
-  // part holds per-tile sums of squared residuals; out[0] = scale * their sum
-  k_loss_reduce<<<1, 1024, 0, st>>>(part, n, out, scale);
-  note_launches(1);
+__global__ void __launch_bounds__(256) k_loss_partial(float* __restrict__ part, long long n, long long chunk) {
+  const long long i0 = (long long)blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  const float t = block_sum_strided(part, i0, i1, 1);
+  __syncthreads();  // every thread has read its values before the chunk's first one is replaced
+  if (threadIdx.x == 0) part[i0] = t;
+}
+
+__global__ void __launch_bounds__(1024) k_loss_reduce(const float* __restrict__ part, long long n, long long stride,
+                                                      float* out, float scale) {
+  const float t = block_sum_strided(part, 0, n, stride);
+  if (threadIdx.x == 0) out[0] = t * scale;
+}
+
+cudaError_t launch_loss_reduce(float* part, int n, float* out, float scale, cudaStream_t st) {
+  // part holds per-warp sums of squared residuals; out[0] = scale * their sum (part is overwritten)
+  constexpr long long kChunk = 2048;
+  if (n <= 4 * kChunk) {
+    k_loss_reduce<<<1, 1024, 0, st>>>(part, n, 1, out, scale);
+    note_launches(1);
+  } else {
+    const long long blocks = (n + kChunk - 1) / kChunk;
+    k_loss_partial<<<(unsigned)blocks, 256, 0, st>>>(part, n, kChunk);
+    k_loss_reduce<<<1, 1024, 0, st>>>(part, n, kChunk, out, scale);
+    note_launches(2);
+  }
   return cudaGetLastError();
 }
 
