@@ -12,6 +12,22 @@
 #define DIGS_SQRT_2PI 2.5066282746310002f
 #define DIGS_LOG2E 1.4426950408889634f
 
+namespace digs {
+// Asynchronous global -> shared copies (16 bytes: both addresses 16-byte aligned; 4 bytes: 4-byte
+// aligned), their commit groups and the waits for them (per thread).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+}  // namespace digs
+
 // Per-projection geometry, derived on the host in double precision and passed by value.
 // The detector frame is (e_u, e_v, n_d) with n_d the unit normal pointing from the source side to the
 // detector; every point is handled through its coordinates in that frame so that FP32 never subtracts
