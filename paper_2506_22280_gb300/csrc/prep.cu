@@ -61,23 +61,17 @@ __device__ __forceinline__ void load_gauss(const GaussPtrs& g, int n, GaussLocal
   o.rho = g.rho[n];
 }
 
-// One thread per Gaussian; loops over the call's projections of its scan so the FFD is evaluated once.
-// Record (b, n) of scan-local Gaussian n sits at b * nmax + n.
+// (1) One thread per Gaussian: u_r and grad u_r at its reference mean (the FFD, Eq. 10-11), kept for the
+// set-up and the backward in component-major order ([12 R][n]: coalesced for every pass that reads them).
 template <int R>
-__global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, const __grid_constant__ ScanTable sc, LatticeC L, const float* __restrict__ phi,
-                                                  const float* __restrict__ w, const __grid_constant__ ViewsParam views,
-                                                  int P, float c2, int tile, int tiles_x, float4* __restrict__ rec,
-                                                  uint32_t* __restrict__ counts, uint2* __restrict__ tbox,
-                                                  uint8_t* __restrict__ bcost,
-                                                  float* __restrict__ ffd_out, int* status) {
+__global__ void __launch_bounds__(128) k_prep_ffd(GaussPtrs g, const __grid_constant__ ScanTable sc, LatticeC L,
+                                                  const float* __restrict__ phi, float* __restrict__ ffd_out) {
   const int gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= g.n) return;
-  const int s = scan_of(sc, gi), n = gi - sc.off[s];
-  GaussLocal G;
-  load_gauss(g, gi, G);
+  const int s = scan_of(sc, gi);
+  const float x[3] = {g.mu0[3 * gi], g.mu0[3 * gi + 1], g.mu0[3 * gi + 2]};
   float U[R][3], dU[R][9];
-  ffd_eval_point<R>(phi + s * sc.phi_stride, L, G.mu0, U, dU);
-  // keep u_r and grad u_r for the backward, component-major ([12 R][n]: coalesced for both passes)
+  ffd_eval_point<R>(phi + s * sc.phi_stride, L, x, U, dU);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
 #pragma unroll
@@ -85,10 +79,36 @@ __global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, const __grid_cons
 #pragma unroll
     for (int c = 0; c < 9; ++c) ffd_out[(size_t)(3 * R + r * 9 + c) * g.n + gi] = dU[r][c];
   }
+}
 
-  bool finite_in = isfinite(G.mu0[0] + G.mu0[1] + G.mu0[2] + G.s[0] + G.s[1] + G.s[2] + G.qnorm + G.rho);
-  if (!finite_in) set_status(status, DIGS_ERR_NONFINITE);
-  for (int b = 0; b < P; ++b) {
+// (2) One thread per (Gaussian, group of kPrepGroup projections): the deformation-informed warp (Eq. 7-8)
+// and the projection record of each projection of the group that renders the Gaussian's scan.
+// Record (b, n) of scan-local Gaussian n sits at b * nmax + n.  Grid: (ceil(n / 128), ceil(P / kPrepGroup)).
+constexpr int kPrepGroup = 16;
+template <int R>
+__global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, const __grid_constant__ ScanTable sc,
+                                                  const float* __restrict__ w, const __grid_constant__ ViewsParam views,
+                                                  int P, float c2, int tile, float4* __restrict__ rec,
+                                                  uint32_t* __restrict__ counts, uint2* __restrict__ tbox,
+                                                  uint8_t* __restrict__ bcost, const float* __restrict__ ffd,
+                                                  int* status) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= g.n) return;
+  const int s = scan_of(sc, gi), n = gi - sc.off[s];
+  GaussLocal G;
+  load_gauss(g, gi, G);
+  float U[R][3], dU[R][9];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) U[r][c] = ffd[(size_t)(r * 3 + c) * g.n + gi];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) dU[r][c] = ffd[(size_t)(3 * R + r * 9 + c) * g.n + gi];
+  }
+  const bool finite_in = isfinite(G.mu0[0] + G.mu0[1] + G.mu0[2] + G.s[0] + G.s[1] + G.s[2] + G.qnorm + G.rho);
+  if (!finite_in && blockIdx.y == 0) set_status(status, DIGS_ERR_NONFINITE);
+  const int b1 = min(P, ((int)blockIdx.y + 1) * kPrepGroup);
+  for (int b = (int)blockIdx.y * kPrepGroup; b < b1; ++b) {
     const ViewC& v = views.v[b];
     if (v.scan != s) continue;
     const float* wb = w + (size_t)v.w_row * R;
@@ -140,9 +160,11 @@ cudaError_t launch_prep_fwd(const GaussPtrs& g, const ScanTable& sc, const Latti
     if (e != cudaSuccess) return e;
   }
   dim3 grid((g.n + 127) / 128);
-#define DIGS_PREP(RR)                                                                                          \
-  k_prep_fwd<RR><<<grid, 128, 0, st>>>(g, sc, L, phi, w, views, P, c2, ws.tile, ws.tiles_x, ws.rec, ws.counts, \
-                                       ws.tbox, ws.bcost, ws.ffd, ws.status)
+  dim3 grid2(grid.x, (P + kPrepGroup - 1) / kPrepGroup);
+#define DIGS_PREP(RR)                                                                                        \
+  k_prep_ffd<RR><<<grid, 128, 0, st>>>(g, sc, L, phi, ws.ffd);                                                \
+  k_prep_fwd<RR><<<grid2, 128, 0, st>>>(g, sc, w, views, P, c2, ws.tile, ws.rec, ws.counts, ws.tbox, ws.bcost, \
+                                        ws.ffd, ws.status)
   switch (L.R) {
     case 1: DIGS_PREP(1); break;
     case 2: DIGS_PREP(2); break;
@@ -151,7 +173,7 @@ cudaError_t launch_prep_fwd(const GaussPtrs& g, const ScanTable& sc, const Latti
     default: return cudaErrorInvalidValue;
   }
 #undef DIGS_PREP
-  note_launches(1);
+  note_launches(2);
   return cudaGetLastError();
 }
 
