@@ -527,8 +527,8 @@ __global__ void __launch_bounds__(256) k_conv0_fwd(const bf16* __restrict__ img,
 // t >> 3 (32 streams per block, grid-stride over the pixels, four pixels per step with all their loads
 // issued first); its 36 products per pixel accumulate in registers, and the block's 32 streams are
 // added in a fixed order through shared memory.
-__global__ void __launch_bounds__(256) k_conv0_dw(const bf16* __restrict__ dy, const bf16* __restrict__ img, int npix,
-                                                  float* __restrict__ part) {
+__global__ void __launch_bounds__(256, 4) k_conv0_dw(const bf16* __restrict__ dy, const bf16* __restrict__ img,
+                                                     int npix, float* __restrict__ part) {
   __shared__ float red[32][289];
   const int cg = threadIdx.x & 7, sid = threadIdx.x >> 3;
   float acc[4][9];
@@ -537,32 +537,23 @@ __global__ void __launch_bounds__(256) k_conv0_dw(const bf16* __restrict__ dy, c
 #pragma unroll
     for (int t = 0; t < 9; ++t) acc[j][t] = 0.f;
   const long long stride = (long long)gridDim.x * 32;
-  for (long long p0 = (long long)blockIdx.x * 32 + sid; p0 < npix; p0 += 4 * stride) {
-    uint2 u[4];
-    float xv[4][9];
+#pragma unroll 2
+  for (long long p = (long long)blockIdx.x * 32 + sid; p < npix; p += stride) {
+    const uint2 u = *reinterpret_cast<const uint2*>(dy + p * 32 + cg * 4);
+    const int x = (int)(p & 63), y = (int)((p >> 6) & 63), b = (int)(p >> 12);
+    float xv[9];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const long long p = p0 + q * stride;
-      const bool in = p < npix;
-      u[q] = in ? *reinterpret_cast<const uint2*>(dy + p * 32 + cg * 4) : make_uint2(0u, 0u);
-      const int x = (int)(p & 63), y = (int)((p >> 6) & 63), b = (int)(p >> 12);
-#pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int iy = 2 * y + t / 3 - 1, ix = 2 * x + t % 3 - 1;
-        xv[q][t] = (in && iy >= 0 && iy < 128 && ix >= 0 && ix < 128)
-                       ? __bfloat162float(img[((size_t)b * 128 + iy) * 128 + ix])
-                       : 0.f;
-      }
+    for (int t = 0; t < 9; ++t) {
+      const int iy = 2 * y + t / 3 - 1, ix = 2 * x + t % 3 - 1;
+      xv[t] = (iy >= 0 && iy < 128 && ix >= 0 && ix < 128) ? __bfloat162float(img[((size_t)b * 128 + iy) * 128 + ix])
+                                                          : 0.f;
     }
+    const float d[4] = {__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                        __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u)};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float d[4] = {__uint_as_float(u[q].x << 16), __uint_as_float(u[q].x & 0xFFFF0000u),
-                          __uint_as_float(u[q].y << 16), __uint_as_float(u[q].y & 0xFFFF0000u)};
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int t = 0; t < 9; ++t) acc[j][t] = fmaf(d[j], xv[q][t], acc[j][t]);
-    }
+      for (int t = 0; t < 9; ++t) acc[j][t] = fmaf(d[j], xv[t], acc[j][t]);
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j)
@@ -598,14 +589,25 @@ __global__ void __launch_bounds__(256) k_colreduce(const float* __restrict__ in,
   }
 }
 
-// out[i] = sum over z of part[z * n + i], z in order (+ bias[i % nb] and ReLU when bias != nullptr).
-__global__ void k_sum_z(const float* __restrict__ part, int Z, long long n, const float* __restrict__ bias, int nb,
-                        float* __restrict__ out) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int z = 0; z < Z; ++z) s += part[(size_t)z * n + i];
-    if (bias) s = fmaxf(s + bias[i % nb], 0.f);
-    out[i] = s;
+// out[i] = sum over z of part[z * n + i] (+ bias[i % nb] and ReLU when bias != nullptr), in a fixed order:
+// 32 outputs per block, warp w adding the splits z = w, w + 8, ... in order (coalesced over the outputs),
+// then the eight warp sums added in warp order.
+__global__ void __launch_bounds__(256) k_sum_z(const float* __restrict__ part, int Z, long long n,
+                                               const float* __restrict__ bias, int nb, float* __restrict__ out) {
+  __shared__ float red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long i = (long long)blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (i < n)
+    for (int z = warp; z < Z; z += 8) s += part[(size_t)z * n + i];
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && i < n) {
+    float t = red[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) t += red[w][lane];
+    if (bias) t = fmaxf(t + bias[i % nb], 0.f);
+    out[i] = t;
   }
 }
 
@@ -681,6 +683,8 @@ cudaError_t gemm(const LA& la, const LB& lb, const EP& ep, int M, int K, int gy,
 
 // Splits of a pixel-reduction weight gradient: about two CTAs per SM over the row tiles, at least four
 // 64-pixel slices per split, partials within the buffer.
+constexpr int kConv0Ctas = 4 * 152;  // k_conv0_dw: four CTAs per SM (its register limit)
+
 int dw_splits(int tiles, long long pixels, long long part_floats, long long tile_floats) {
   long long z = (2LL * 152 + tiles - 1) / tiles;
   z = std::min(z, std::max(1LL, pixels / 256));
@@ -733,7 +737,7 @@ size_t cnn_tc_layout(void* base, int B, CnnTc* t) {
   w.w1b = (uint16_t*)take((size_t)kHid * kFeatPitch * 2);
   w.part_floats = std::max<long long>(16LL * B * kHid, 5LL << 20);
   w.part = (float*)take((size_t)w.part_floats * 4);
-  w.colpart_floats = std::max<long long>({1024LL * B, 8192LL * ((B + 127) / 128), 2LL * 152 * 288});
+  w.colpart_floats = std::max<long long>({1024LL * B, 8192LL * ((B + 127) / 128), (long long)kConv0Ctas * 288});
   w.colpart = (float*)take((size_t)w.colpart_floats * 4);
   if (t) *t = w;
   return off;
@@ -778,7 +782,7 @@ cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs,
   const EpiF32 ep{t.part, (long long)B * kHid, B, kHid};
   TC_TRY((gemm<128, 4, false, false>(PlainK{(const bf16*)t.feat, kFeatPitch, B}, PlainK{(const bf16*)t.w1b, kFeatPitch, kHid},
                                   ep, B, kFeatPitch, 1, Z, kc, any, st)));
-  k_sum_z<<<grid_of((long long)B * kHid), 256, 0, st>>>(t.part, Z, (long long)B * kHid, net.b1, kHid, h);
+  k_sum_z<<<(unsigned)(((long long)B * kHid + 31) / 32), 256, 0, st>>>(t.part, Z, (long long)B * kHid, net.b1, kHid, h);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -812,7 +816,7 @@ cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGra
       TC_TRY((gemm<64, 4, true, true>(ConvMN{geo}, PlainMN{dyl, N, N}, epw, Kl, rows, 1, Z, kc, any, st)));
     else
       TC_TRY((gemm<128, 4, true, true>(ConvMN{geo}, PlainMN{dyl, N, N}, epw, Kl, rows, 1, Z, kc, any, st)));
-    k_sum_z<<<grid_of((long long)N * Kl), 256, 0, st>>>(t.part, Z, (long long)N * Kl, nullptr, 1, g.w[l]);
+    k_sum_z<<<(unsigned)(((long long)N * Kl + 31) / 32), 256, 0, st>>>(t.part, Z, (long long)N * Kl, nullptr, 1, g.w[l]);
     note_launches(1);
     // data gradient, four parity classes in one launch; output dY of conv l - 1 and its bias partials
     bf16* dyo = (bf16*)(l == 2 ? t.dy[1] : t.dy[0]);
@@ -831,7 +835,7 @@ cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGra
     dyl = dyo;
   }
   // the first convolution's weight gradient on the SIMT pipes
-  const int G = 2 * 152;
+  const int G = kConv0Ctas;
   k_conv0_dw<<<G, 256, 0, st>>>(dyl, (const bf16*)t.imgb, B * 4096, t.colpart);
   note_launches(1);
   TC_TRY(colreduce(t.colpart, G, 288, 288, g.w[0], t.part, st));
