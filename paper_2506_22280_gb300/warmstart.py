@@ -95,8 +95,9 @@ def train_and_propose(predictor: D.WeightPredictor, imgs: torch.Tensor, cs: torc
                       epochs: int, rec: D.Reconstruction, meas: torch.Tensor, views: Sequence[Dict],
                       angles: np.ndarray, batch: int = 256, lr: float = 1e-3, seed: int = 0) -> Dict:
     """Train for up to `epochs` epochs; after each, propose every projection's weights and score the
-    proposal by the full-scan loss of the current model (the judge of the warm start, computed from the
-    measured projections only).  Returns the best proposal, its epoch and loss, and the per-epoch record."""
+    proposal by the full-scan loss of the current model (the warm start's acceptance criterion, computed
+    from the measured projections only).  Returns the best proposal, its epoch and loss, and the per-epoch
+    record."""
     n = int(imgs.shape[0])
     g = torch.Generator(device="cpu").manual_seed(seed)
     img_m = predictor.prepare(meas)
