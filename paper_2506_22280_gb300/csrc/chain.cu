@@ -246,7 +246,7 @@ constexpr size_t pair_sum_smem() { return (size_t)gauss_sum_count<R>() * kSlots 
 int pair_sum_blocks(int n) { return (n + 31) / 32; }
 
 template <int R>
-__global__ void __launch_bounds__(kSlots * 32, 3) k_pair_sum(GaussPtrs g, const __grid_constant__ ScanTable sc,
+__global__ void __launch_bounds__(kSlots * 32, 2) k_pair_sum(GaussPtrs g, const __grid_constant__ ScanTable sc,
                                                              const float* __restrict__ ffd, const float* __restrict__ w,
                                                              const __grid_constant__ ViewsParam views, int P,
                                                              const uint32_t* __restrict__ counts,
