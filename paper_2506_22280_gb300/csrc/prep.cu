@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(128) k_prep_ffd(GaussPtrs g, const __grid_cons
 // Record (b, n) of scan-local Gaussian n sits at b * nmax + n.  Grid: (ceil(n / 128), ceil(P / kPrepGroup)).
 constexpr int kPrepGroup = 16;
 template <int R>
-__global__ void __launch_bounds__(128) k_prep_fwd(GaussPtrs g, const __grid_constant__ ScanTable sc,
+__global__ void __launch_bounds__(128, 5) k_prep_fwd(GaussPtrs g, const __grid_constant__ ScanTable sc,
                                                   const float* __restrict__ w, const __grid_constant__ ViewsParam views,
                                                   int P, float c2, int tile, float4* __restrict__ rec,
                                                   uint32_t* __restrict__ counts, uint2* __restrict__ tbox,
