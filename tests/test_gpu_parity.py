@@ -127,6 +127,24 @@ def test_project_fwd_degenerate_cases(dev, P):
     assert relL2(o1.cpu().numpy(), r1) < 1e-5
 
 
+def test_project_fwd_amplitude_range(dev, P):
+    # the forward folds |amp| into each entry's quadratic form when 2^-40 <= |amp| <= 2^40 and applies
+    # the sign in the accumulation; outside that range (and for amp = 0) it multiplies by amp instead.
+    # Densities of mixed sign with zeros, and whole clouds scaled far below and far above that range.
+    wl = synth.tiny(n=800, n_proj=4)
+    rng = np.random.default_rng(31)
+    base = wl.rho.copy()
+    cases = {"mixed": base * rng.choice([1.0, -1.0, 0.0], size=base.shape),
+             "tiny": base * 1e-30, "huge": base * 1e25}
+    for name, rho in cases.items():
+        wl.rho = rho.astype(np.float32)
+        ref = O.render(gauss(wl), wl.lattice, wl.phi, wl.w, wl.views)
+        out = P.Projector(wl.lattice, wl.views).forward(*gpu_inputs(wl, dev))
+        assert np.isfinite(out.cpu().numpy()).all(), name
+        e = relL2(out.cpu().numpy(), ref)
+        assert e < 1e-5, (name, e)
+
+
 def test_project_fwd_empty_cloud(dev, P):
     wl = synth.tiny(n=5, n_proj=2).subset([])
     pj = P.Projector(wl.lattice, wl.views)
