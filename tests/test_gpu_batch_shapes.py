@@ -4,9 +4,10 @@ shared-memory column (the chain rule through Eq. 7-11 of Sec. 3.2-3.3, summed ov
 
 * ``digs_project_bwd`` on the tiny cloud with P = 16 (two full slot groups) and P = 17 (a ragged third
   group holding one projection), all six gradients against the FP64 oracle.
-* ``digs_step`` with B = 16 and B = 17: loss, the six in-step gradients and the first Adam update.
+* ``digs_step`` with B = 16, B = 17 and B = 128 (the benchmark's projections per step: 16 per slot):
+  loss, the six in-step gradients and the first Adam update.
 * One step over three scans of uneven Gaussian counts with B = 26 items (11 / 9 / 6 per scan).
-* The 100k-Gaussian thorax with the benchmark's 16 projections, tile 16 and 16 lanes per record: the
+* The 100k-Gaussian thorax with 16 and with the benchmark's 128 projections, tile 16 and 16 lanes per record: the
   gradients of a seeded 1,000-Gaussian subset against the oracle run on that subset with the same
   dL/dI (a Gaussian's own gradient depends only on its parameters, the motion model and dL/dI), plus
   three identities that hold at any size: q . dL/dq = 0 per Gaussian (the quaternion is normalised
@@ -80,14 +81,15 @@ def _split_grad(grad, n, nphi):
             "rho": grad[10 * n:11 * n], "phi": grad[11 * n:11 * n + nphi], "w": grad[11 * n + nphi:]}
 
 
-@pytest.mark.parametrize("B", [16, 17])
+@pytest.mark.parametrize("B", [16, 17, 128])
 def test_step_batch_beyond_slots(pkg, B):
     from paper_2506_22280_gb300 import digs as D
-    wl = synth.tiny(n_proj=24)
-    ref_state = synth.tiny(n_proj=24, motion_seed=77)
+    n_proj, n = (24, 2000) if B <= 17 else (136, 1000)
+    wl = synth.tiny(n=n, n_proj=n_proj)
+    ref_state = synth.tiny(n=n, n_proj=n_proj, motion_seed=77)
     g_meas = dict(mu0=ref_state.mu0 + 0.3, scale=ref_state.scale, quat=ref_state.quat, rho=ref_state.rho * 1.1)
     meas = O.render(g_meas, ref_state.lattice, ref_state.phi, ref_state.w, ref_state.views)
-    ids = sorted(np.random.default_rng(B).choice(24, B, replace=False).tolist())
+    ids = sorted(np.random.default_rng(B).choice(n_proj, B, replace=False).tolist())
     views = [wl.views[i] for i in ids]
     wl = wl.subset(unambiguous(wl, wl.w[ids], views))
     rec = pkg.Reconstruction(wl.mu0, wl.scale, wl.quat, wl.rho, wl.phi, wl.w, wl.lattice,
@@ -172,11 +174,12 @@ def test_multiscan_step_26_items(pkg):
     assert relL2(grad[11 * N + 3 * nphi:].reshape(-1, 2), g_w_ref) < 1e-4
 
 
-def test_thorax_100k_16_views_subset_gradients_and_identities(pkg):
+@pytest.mark.parametrize("n_views", [16, 128])
+def test_thorax_100k_subset_gradients_and_identities(pkg, n_views):
     wl = synth.thorax(seed=1, n=100_000)
-    ids = [int((j * 42) % 680) for j in range(16)]
+    ids = [int((j * (680 // n_views)) % 680) for j in range(n_views)]
     one = wl.select_views(ids)
-    gp = synth.random_grad_proj(16, 256, 256, seed=9)
+    gp = synth.random_grad_proj(n_views, 256, 256, seed=9)
     pj = pkg.Projector(wl.lattice, one.views, tile=16, bwd_lanes=16)
     ins = [T(wl.mu0), T(wl.scale), T(wl.quat), T(wl.rho), T(wl.phi), T(one.w)]
     I = pj.forward(*ins)
@@ -184,7 +187,7 @@ def test_thorax_100k_16_views_subset_gradients_and_identities(pkg):
     assert pj.status() == 0
     got = {k: g[k].cpu().numpy().astype(np.float64) for k in GROUPS}
     # a seeded 1,000-Gaussian subset against the oracle with the same dL/dI
-    idx = np.sort(np.random.default_rng(7).choice(wl.n, 1000, replace=False))
+    idx = np.sort(np.random.default_rng(7).choice(wl.n, 1000 if n_views <= 16 else 300, replace=False))
     idx = idx[unambiguous(one.subset(idx), one.w, one.views)]
     sub = one.subset(idx)
     ref = O.project_vjp(gauss(sub), sub.lattice, sub.phi, sub.w, sub.views, gp)
@@ -202,7 +205,7 @@ def test_thorax_100k_16_views_subset_gradients_and_identities(pkg):
     assert abs(lhs - rhs) <= 1e-4 * float(np.abs(Ih * gp).sum()), (lhs, rhs)
     # per rank: sum_b w_br dL/dw_br = sum_k phi_rk . dL/dphi_rk
     R = wl.R
-    gw, gphi = got["w"].reshape(16, R), got["phi"].reshape(R, -1)
+    gw, gphi = got["w"].reshape(n_views, R), got["phi"].reshape(R, -1)
     phi = wl.phi.reshape(R, -1)
     for r in range(R):
         a = float((one.w[:, r] * gw[:, r]).sum())
