@@ -11,7 +11,9 @@
 // pixels of the block and keeps their sums in registers.  Every warp walks the tile's sorted Gaussian
 // list in batches of 32 records staged by cp.async, keeps the Gaussians whose cutoff ellipse meets its
 // block and sweeps them eight at a time, summed in list order: no canvas, no atomics, deterministic sums.
-// CTAs start in order of decreasing list length.
+// An entry carries its quadratic form scaled by 1/|amp|^2 (and t by 1/|amp|), so that the reciprocal
+// square root of the scaled D is |amp| D^-1/2; the accumulating FMA applies the sign of amp.  CTAs start
+// in order of decreasing list length.
 //
 // Backward: needs no tile lists.  One half-warp per (projection, Gaussian) record (the two records of a
 // warp of similar box size, paired by k_bwd_pairing) sweeps the record's pixel box in 16-column slices,
@@ -23,6 +25,8 @@
 // recursive halving and ten lanes write them to the record's slot (no atomics).  A CTA sweeps four units
 // of 16 records in turn, each unit's records and tile counts copied to shared memory by cp.async while
 // the unit before it is swept.
+//
+// Loss: per-warp partials of the squared residuals from the forward, summed in two fixed-order levels.
 #include <algorithm>
 
 #include "digs_internal.h"
