@@ -374,7 +374,7 @@ __device__ __forceinline__ uint64_t slice_desc(uint32_t a, int j) {
 // and the mbarrier ring stay with the CTA across its tiles; g counts the slices issued so far, which
 // selects the stage buffer (g mod S) and the mbarrier phase (g div S).
 template <int BN, int kStages, bool AMN, bool BMN, class LA, class LB, class EP>
-__global__ void __launch_bounds__(kThr, 1) k_cnn_gemm(const LA la, const LB lb, const EP ep, int n_mt, int K, int kchunk,
+__global__ void __launch_bounds__(kThr, BN == 32 ? 5 : 1) k_cnn_gemm(const LA la, const LB lb, const EP ep, int n_mt, int K, int kchunk,
                                                       int* status, unsigned wait_limit, const void* any) {
   using C = Cfg<BN, kStages>;
   extern __shared__ unsigned char smem_raw[];
