@@ -460,7 +460,7 @@ def warmstart_measurement(pkg, D, wl, meas, device, tile, lanes, B=16, warmup_it
         torch.cuda.synchronize()
         t_render = time.perf_counter() - t0
         sel = WS.train_and_propose(pred, imgs, cs, W, epochs, warm, meas, wl.views, np.asarray(wl.angles),
-                                   batch=256, lr=1e-3)
+                                   batch=256, lr=3e-4)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0 - t_render
         losses = sel["history"]
@@ -487,8 +487,8 @@ def warmstart_measurement(pkg, D, wl, meas, device, tile, lanes, B=16, warmup_it
         out.append({"protocol": (f"{warmup_iters} shared plain steps, then plain until the scan loss changes by < "
                                  f"{100 * plateau_rel:g} % over {chunk * every} steps vs CNN warm start ({n_pairs} pairs "
                                  f"rendered at {render_res}x{render_res}" + (", 2x2-averaged" if render_res == 256 else "")
-                                 + f", up to {epochs} epochs, the epoch whose proposal has the lowest scan loss, BF16 "
-                                 "inference, accept if the scan loss falls) + the same steps "
+                                 + f", up to {epochs} epochs at learning rate 3e-4, the epoch whose proposal has the "
+                                 "lowest scan loss, BF16 inference, accept if the scan loss falls) + the same steps "
                                  f"until the scan loss is within 1% of the plain plateau; B = {B}, wall time; scan-loss "
                                  "evaluations excluded (reported as eval_s)"),
                     "plain_s": t_plain, "plain_steps": iters, "plain_final_scan_loss": final,

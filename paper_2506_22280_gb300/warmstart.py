@@ -93,7 +93,7 @@ def propose_weights(predictor: D.WeightPredictor, meas: torch.Tensor, angles: np
 
 def train_and_propose(predictor: D.WeightPredictor, imgs: torch.Tensor, cs: torch.Tensor, W: torch.Tensor,
                       epochs: int, rec: D.Reconstruction, meas: torch.Tensor, views: Sequence[Dict],
-                      angles: np.ndarray, batch: int = 256, lr: float = 1e-3, seed: int = 0) -> Dict:
+                      angles: np.ndarray, batch: int = 256, lr: float = 3e-4, seed: int = 0) -> Dict:
     """Train for up to `epochs` epochs; after each, propose every projection's weights and score the
     proposal by the full-scan loss of the current model (the warm start's acceptance criterion, computed
     from the measured projections only).  Returns the best proposal, its epoch and loss, and the per-epoch
