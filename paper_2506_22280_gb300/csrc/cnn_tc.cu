@@ -374,7 +374,7 @@ __device__ __forceinline__ uint64_t slice_desc(uint32_t a, int j) {
 // and the mbarrier ring stay with the CTA across its tiles; g counts the slices issued so far, which
 // selects the stage buffer (g mod S) and the mbarrier phase (g div S).
 template <int BN, int kStages, bool AMN, bool BMN, class LA, class LB, class EP>
-__global__ void __launch_bounds__(kThr, BN == 32 ? 5 : 1) k_cnn_gemm(const LA la, const LB lb, const EP ep, int n_mt, int K, int kchunk,
+__global__ void __launch_bounds__(kThr, BN == 32 ? 5 : (BN == 64 ? (kStages == 2 ? 4 : (kStages == 3 ? 3 : 2)) : 1)) k_cnn_gemm(const LA la, const LB lb, const EP ep, int n_mt, int K, int kchunk,
                                                       int* status, unsigned wait_limit, const void* any) {
   using C = Cfg<BN, kStages>;
   extern __shared__ unsigned char smem_raw[];
@@ -766,7 +766,7 @@ cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs,
     const PlainK Bw{(const bf16*)t.wb[l], Kl, N};
     if (l == 1) {
       const EpiBf16 ep{(bf16*)t.act[1], net.b[1], 1, rows, 1 << 30, 0, N};
-      TC_TRY((gemm<64, 3, false, false>(A, Bw, ep, rows, Kl, 1, 1, Kl, any, st)));
+      TC_TRY((gemm<64, 2, false, false>(A, Bw, ep, rows, Kl, 1, 1, Kl, any, st)));
     } else if (l == 2) {
       const EpiBf16 ep{(bf16*)t.act[2], net.b[2], 1, rows, 1 << 30, 0, N};
       TC_TRY((gemm<128, 3, false, false>(A, Bw, ep, rows, Kl, 1, 1, Kl, any, st)));
@@ -813,7 +813,7 @@ cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGra
     const int kc = chunk_of(rows, Z);
     const EpiF32T epw{t.part, (long long)N * Kl, Kl, Kl};
     if (N == 64)
-      TC_TRY((gemm<64, 4, true, true>(ConvMN{geo}, PlainMN{dyl, N, N}, epw, Kl, rows, 1, Z, kc, any, st)));
+      TC_TRY((gemm<64, 3, true, true>(ConvMN{geo}, PlainMN{dyl, N, N}, epw, Kl, rows, 1, Z, kc, any, st)));
     else
       TC_TRY((gemm<128, 4, true, true>(ConvMN{geo}, PlainMN{dyl, N, N}, epw, Kl, rows, 1, Z, kc, any, st)));
     k_sum_z<<<(unsigned)(((long long)N * Kl + 31) / 32), 256, 0, st>>>(t.part, Z, (long long)N * Kl, nullptr, 1, g.w[l]);
@@ -826,7 +826,7 @@ cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGra
       TC_TRY((gemm<128, 3, false, false>(A, Bw, EpiDx<128>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
                                       9 * N, 1, 4, 1 << 30, any, st)));
     else if (C == 64)
-      TC_TRY((gemm<64, 3, false, false>(A, Bw, EpiDx<64>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
+      TC_TRY((gemm<64, 2, false, false>(A, Bw, EpiDx<64>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
                                      9 * N, 1, 4, 1 << 30, any, st)));
     else
       TC_TRY((gemm<32, 2, false, false>(A, Bw, EpiDx<32>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
