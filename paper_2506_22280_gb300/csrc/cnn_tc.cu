@@ -611,27 +611,45 @@ __global__ void __launch_bounds__(256) k_sum_z(const float* __restrict__ part, i
   }
 }
 
-// out[r][c] = BF16 of in[r][c] for c < cols, 0 for cols <= c < ld (row pitch ld).
-__global__ void k_to_bf16_rows(const float* __restrict__ in, int rows, int cols, int ld, bf16* __restrict__ out) {
-  const long long n = (long long)rows * ld;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(i / ld), c = (int)(i - (long long)r * ld);
-    out[i] = __float2bfloat16_rn(c < cols ? in[(size_t)r * cols + c] : 0.f);
-  }
-}
-
-// Class-ordered transposed weights of a convolution with N output and C input channels:
-// wt[class block z][ci][(t, co)] = BF16 of w[co][ky_t][kx_t][ci] for the class's taps t.
-__global__ void k_wt_class(const float* __restrict__ w, int N, int C, bf16* __restrict__ wt) {
-  const long long total = 9LL * N * C, NC = (long long)N * C;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int z = e < NC ? 0 : (e < 3 * NC ? 1 : (e < 5 * NC ? 2 : 3));
-    const long long local = e - (long long)class_off(z) * NC;
-    const int kc = class_taps(z) * N;
-    const int ci = (int)(local / kc), rem = (int)(local - (long long)ci * kc), t = rem / N, co = rem - t * N;
-    int ky, kx;
-    class_tap(z, t, ky, kx);
-    wt[e] = __float2bfloat16_rn(w[((size_t)co * 9 + ky * 3 + kx) * C + ci]);
+// All of a forward's BF16 conversions in one launch: job k covers the elements [start[k], start[k + 1])
+// of a grid-stride loop.  Kind 0, rows: out[r][c] = BF16 of in[r][c] for c < b, 0 for b <= c < c_pitch
+// (a rows, row pitch c).  Kind 1, the class-ordered transposed weights of a convolution with N = a output
+// and C = b input channels: out[class block z][ci][(t, co)] = BF16 of w[co][ky_t][kx_t][ci] for the
+// class's taps t.  Kind 2: out[e] = BF16 of in[e].
+struct BfJob {
+  const float* in;
+  bf16* out;
+  int kind, a, b, c;
+};
+struct BfJobs {
+  BfJob job[8];
+  long long start[9];
+  int count;
+};
+__global__ void __launch_bounds__(256) k_to_bf16_jobs(const __grid_constant__ BfJobs J) {
+  const long long total = J.start[J.count];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < J.count && i >= J.start[k + 1]) ++k;
+    const BfJob& jb = J.job[k];
+    const long long e = i - J.start[k];
+    float x;
+    if (jb.kind == 0) {
+      const int r = (int)(e / jb.c), c = (int)(e - (long long)r * jb.c);
+      x = c < jb.b ? jb.in[(size_t)r * jb.b + c] : 0.f;
+    } else if (jb.kind == 1) {
+      const long long NC = (long long)jb.a * jb.b;
+      const int z = e < NC ? 0 : (e < 3 * NC ? 1 : (e < 5 * NC ? 2 : 3));
+      const long long local = e - (long long)class_off(z) * NC;
+      const int kc = class_taps(z) * jb.a;
+      const int ci = (int)(local / kc), rem = (int)(local - (long long)ci * kc), t = rem / jb.a, co = rem - t * jb.a;
+      int ky, kx;
+      class_tap(z, t, ky, kx);
+      x = jb.in[((size_t)co * 9 + ky * 3 + kx) * jb.b + ci];
+    } else {
+      x = jb.in[e];
+    }
+    jb.out[e] = __float2bfloat16_rn(x);
   }
 }
 
@@ -745,17 +763,25 @@ size_t cnn_tc_layout(void* base, int B, CnnTc* t) {
 
 cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs, int B, const CnnTc& t, float* h,
                            cudaStream_t st) {
-  // BF16 copies of the weights: row-major (forward), class-ordered transposed (data gradient)
+  // BF16 copies of the weights, row-major (forward) and class-ordered transposed (data gradient), and of
+  // the input images: one launch
+  BfJobs J{};
+  long long at = 0;
+  auto add = [&](const float* in, bf16* out, int kind, int a, int b, int c, long long n) {
+    J.job[J.count] = BfJob{in, out, kind, a, b, c};
+    J.start[J.count++] = at;
+    at += n;
+  };
   for (int l = 1; l < 4; ++l) {
     const int N = kCh[l + 1], Kl = 9 * kCh[l];
-    k_to_bf16_rows<<<grid_of((long long)N * Kl), 256, 0, st>>>(net.w[l], N, Kl, Kl, (bf16*)t.wb[l]);
-    k_wt_class<<<grid_of((long long)N * Kl), 256, 0, st>>>(net.w[l], N, kCh[l], (bf16*)t.wt[l]);
+    add(net.w[l], (bf16*)t.wb[l], 0, N, Kl, Kl, (long long)N * Kl);
+    add(net.w[l], (bf16*)t.wt[l], 1, N, kCh[l], 0, (long long)N * Kl);
   }
-  k_to_bf16_rows<<<grid_of((long long)kHid * kFeatPitch), 256, 0, st>>>(net.w1, kHid, kFeat + 2, kFeatPitch,
-                                                                      (bf16*)t.w1b);
-  note_launches(7);
+  add(net.w1, (bf16*)t.w1b, 0, kHid, kFeat + 2, kFeatPitch, (long long)kHid * kFeatPitch);
+  add(img, (bf16*)t.imgb, 2, 0, 0, 0, (long long)B * 16384);
+  J.start[J.count] = at;
+  k_to_bf16_jobs<<<grid_of(at), 256, 0, st>>>(J);
   const int npix0 = B * 4096;
-  k_f32_to_bf16<<<grid_of((long long)B * 16384), 256, 0, st>>>(img, (long long)B * 16384, (bf16*)t.imgb);
   k_conv0_fwd<<<(npix0 + 255) / 256, 256, 0, st>>>((const bf16*)t.imgb, net.w[0], net.b[0], npix0, (bf16*)t.act[0]);
   note_launches(2);
   const void* any = t.wb[1];
