@@ -241,14 +241,18 @@ __global__ void __launch_bounds__(kHid + 32) k_fc2_wgrad(const float* __restrict
 }
 
 // dh[b][n] = [h[b][n] > 0] sum_r dout[b][r] W2[r][n]: the gradient of the dense layer's pre-activation.
+// dh = dL/d(dense pre-activation), masked by the dense layer's ReLU; with dhb, also its BF16 copy (the
+// tensor-core backward's operand).
 __global__ void k_fc2_dh(const float* __restrict__ dout, const float* __restrict__ w2, const float* __restrict__ h,
-                         int B, int R, float* __restrict__ dh) {
+                         int B, int R, float* __restrict__ dh, uint16_t* __restrict__ dhb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B * kHid) return;
   const int b = i / kHid, n = i - b * kHid;
   float s = 0.f;
   for (int r = 0; r < R; ++r) s = fmaf(dout[(size_t)b * R + r], w2[r * kHid + n], s);
-  dh[i] = h[i] > 0.f ? s : 0.f;
+  const float v = h[i] > 0.f ? s : 0.f;
+  dh[i] = v;
+  if (dhb) dhb[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
 // out[i] (+)= sum_z part[z][i], z in a fixed order.
@@ -488,7 +492,7 @@ cudaError_t backward_f32(const NetPtrs<float>& N, const ParamOffsets& o, int R, 
   constexpr int kFc2Blocks = 16;
   k_fc2_wgrad<<<kFc2Blocks, kHid + 32, 0, st>>>(w.dout, w.h, B, R, w.part);
   k_sum_splits<<<(R * kHid + R + 255) / 256, 256, 0, st>>>(w.part, kFc2Blocks, R * kHid + R, grad + o.w2, 0);
-  k_fc2_dh<<<(B * kHid + 255) / 256, 256, 0, st>>>(w.dout, N.w2, w.h, B, R, w.dh);
+  k_fc2_dh<<<(B * kHid + 255) / 256, 256, 0, st>>>(w.dout, N.w2, w.h, B, R, w.dh, tc ? w.tc.dhb : nullptr);
   note_launches(3);
   CNN_TRY(colsum(w.dh, B, kHid, w.part, grad + o.b1, st));
   if (tc) {

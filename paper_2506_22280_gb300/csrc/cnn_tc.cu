@@ -661,11 +661,6 @@ __global__ void k_feat_tail(bf16* __restrict__ feat, const float* __restrict__ c
   feat[(size_t)b * kFeatPitch + kFeat + j] = __float2bfloat16_rn(j < 2 ? cs[2 * b + j] : 0.f);
 }
 
-__global__ void k_f32_to_bf16(const float* __restrict__ x, long long n, bf16* __restrict__ y) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = __float2bfloat16_rn(x[i]);
-}
-
 unsigned grid_of(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16)); }
 
 // One GEMM launch: M rows of C in 128-row tiles, gy column tiles of BN, gz splits (or classes).
@@ -815,8 +810,7 @@ cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs,
 
 cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGrad& g, cudaStream_t st) {
   const void* any = t.wb[1];
-  k_f32_to_bf16<<<grid_of((long long)B * kHid), 256, 0, st>>>(dh, (long long)B * kHid, (bf16*)t.dhb);
-  note_launches(1);
+  (void)dh;  // its BF16 copy t.dhb, written with it, is what the GEMMs read
   // dense layer: dW1[n][f] = sum_b dh[b][n] feat[b][f] (rows f, both operands MN-major)
   TC_TRY((gemm<128, 3, true, true>(PlainMN{(const bf16*)t.feat, kFeatPitch, kFeatPitch}, PlainMN{(const bf16*)t.dhb, kHid, kHid},
                                 EpiF32T{g.w1, 0, kFeat + 2, kFeat + 2}, kFeatPitch, B, 1, 1, B, any, st)));

@@ -152,8 +152,9 @@ size_t cnn_tc_layout(void* base, int B, CnnTc* t);
 cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs, int B, const CnnTc& t, float* h,
                            cudaStream_t st);
 // Parameter gradients of every layer but the output one (and but the dense layer's bias), from
-// dh = dL/d(dense pre-activation) [B][128] (FP32, already masked by the dense layer's ReLU), through the
-// activations and weights that the last cnn_tc_forward on the same buffers kept.
+// dh = dL/d(dense pre-activation) [B][128] (already masked by the dense layer's ReLU; its BF16 copy in
+// t.dhb, written by the caller with it), through the activations and weights that the last
+// cnn_tc_forward on the same buffers kept.
 cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGrad& g, cudaStream_t st);
 
 // adam.cu
