@@ -567,12 +567,16 @@ __global__ void __launch_bounds__(256, 4) k_conv0_dw(const bf16* __restrict__ dy
   }
 }
 
-// out[y * cols + c] = sum over the rows [y chunk, (y + 1) chunk) of in[r * ld + c], rows in a fixed order
-// (strided over the block's 8 warps, then the 8 warp sums in order); 32 columns per block, blockIdx.y
-// the row chunk.
-__global__ void __launch_bounds__(256) k_colreduce(const float* __restrict__ in, int R, int cols, int ld, int chunk,
-                                                   float* __restrict__ out) {
+// out[c] = sum over the rows r < R of in[r * ld + c], in one launch: block (x, y) sums rows
+// [y chunk, (y + 1) chunk) of the columns 32 x .. 32 x + 31 (strided over its 8 warps, then the warp sums
+// in order) into part[y * cols + c]; the last block of column group x to finish (a ticket counter per
+// group, reset by that block) then adds the gridDim.y partials in chunk order.  The result does not depend
+// on which block finishes last, and no block waits for another.
+__global__ void __launch_bounds__(256) k_colreduce_once(const float* __restrict__ in, int R, int cols, int ld,
+                                                        int chunk, float* part, float* __restrict__ out,
+                                                        unsigned* tickets) {
   __shared__ float red[8][32];
+  __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + lane;
   const int r0 = blockIdx.y * chunk, r1 = min(R, r0 + chunk);
@@ -585,8 +589,26 @@ __global__ void __launch_bounds__(256) k_colreduce(const float* __restrict__ in,
     float t = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) t += red[k][lane];
-    out[(size_t)blockIdx.y * cols + c] = t;
+    part[(size_t)blockIdx.y * cols + c] = t;
   }
+  __threadfence();  // this block's partials are visible before its ticket is taken
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&tickets[blockIdx.x], 1u) == gridDim.y - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  s = 0.f;
+  if (c < cols)
+    for (int y = warp; y < (int)gridDim.y; y += 8) s += __ldcg(&part[(size_t)y * cols + c]);
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && c < cols) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += red[k][lane];
+    out[c] = t;
+  }
+  if (threadIdx.x == 0) tickets[blockIdx.x] = 0u;
 }
 
 // out[i] = sum over z of part[z * n + i] (+ bias[i % nb] and ReLU when bias != nullptr), in a fixed order:
@@ -697,6 +719,7 @@ cudaError_t gemm(const LA& la, const LB& lb, const EP& ep, int M, int K, int gy,
 // Splits of a pixel-reduction weight gradient: about two CTAs per SM over the row tiles, at least four
 // 64-pixel slices per split, partials within the buffer.
 constexpr int kConv0Ctas = 4 * 152;  // k_conv0_dw: four CTAs per SM (its register limit)
+constexpr int kColTickets = 64;      // colreduce ticket counters (column groups of 32)
 
 int dw_splits(int tiles, long long pixels, long long part_floats, long long tile_floats) {
   long long z = (2LL * 152 + tiles - 1) / tiles;
@@ -708,17 +731,13 @@ int chunk_of(long long n, int z) { return (int)(((n + z - 1) / z + kBK - 1) / kB
 
 // out[c] = sum over r < R of in[r * ld + c] in a fixed order: row chunks of 64 summed into scratch by
 // many blocks, then the chunk sums by one block per 32 columns (one pass when R <= 512).
-cudaError_t colreduce(const float* in, int R, int cols, int ld, float* out, float* scratch, cudaStream_t st) {
+// tickets: (cols + 31) / 32 counters, zero on entry (and left zero).
+cudaError_t colreduce(const float* in, int R, int cols, int ld, float* out, float* scratch, unsigned* tickets,
+                      cudaStream_t st) {
   const unsigned gx = (unsigned)((cols + 31) / 32);
-  if (R <= 512) {
-    k_colreduce<<<dim3(gx, 1), 256, 0, st>>>(in, R, cols, ld, R, out);
-    note_launches(1);
-    return cudaGetLastError();
-  }
-  const int chunk = 64, nch = (R + chunk - 1) / chunk;
-  k_colreduce<<<dim3(gx, nch), 256, 0, st>>>(in, R, cols, ld, chunk, scratch);
-  k_colreduce<<<dim3(gx, 1), 256, 0, st>>>(scratch, nch, cols, cols, nch, out);
-  note_launches(2);
+  const int chunk = R <= 2048 ? 64 : 128, nch = (R + chunk - 1) / chunk;
+  k_colreduce_once<<<dim3(gx, nch), 256, 0, st>>>(in, R, cols, ld, chunk, scratch, out, tickets);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -752,6 +771,7 @@ size_t cnn_tc_layout(void* base, int B, CnnTc* t) {
   w.part = (float*)take((size_t)w.part_floats * 4);
   w.colpart_floats = std::max<long long>({1024LL * B, 8192LL * ((B + 127) / 128), (long long)kConv0Ctas * 288});
   w.colpart = (float*)take((size_t)w.colpart_floats * 4);
+  w.tickets = (unsigned*)take(kColTickets * sizeof(unsigned));
   if (t) *t = w;
   return off;
 }
@@ -811,6 +831,8 @@ cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs,
 cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGrad& g, cudaStream_t st) {
   const void* any = t.wb[1];
   (void)dh;  // its BF16 copy t.dhb, written with it, is what the GEMMs read
+  const cudaError_t ez = cudaMemsetAsync(t.tickets, 0, kColTickets * sizeof(unsigned), st);
+  if (ez != cudaSuccess) return ez;
   // dense layer: dW1[n][f] = sum_b dh[b][n] feat[b][f] (rows f, both operands MN-major)
   TC_TRY((gemm<128, 3, true, true>(PlainMN{(const bf16*)t.feat, kFeatPitch, kFeatPitch}, PlainMN{(const bf16*)t.dhb, kHid, kHid},
                                 EpiF32T{g.w1, 0, kFeat + 2, kFeat + 2}, kFeatPitch, B, 1, 1, B, any, st)));
@@ -820,7 +842,7 @@ cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGra
   TC_TRY((gemm<128, 2, false, true>(PlainK{(const bf16*)t.dhb, kHid, B}, PlainMN{(const bf16*)t.w1b, kFeatPitch, kFeat},
                                     EpiDfeat{(bf16*)t.dy3, (const bf16*)t.feat, t.colpart, B}, B, kHid, kFeat / 128, 1,
                                     kHid, any, st)));
-  TC_TRY(colreduce(t.colpart, (kFeat / 128) * nmt, 128, 128, g.b[3], t.part, st));
+  TC_TRY(colreduce(t.colpart, (kFeat / 128) * nmt, 128, 128, g.b[3], t.part, t.tickets, st));
   // convolutions 3, 2, 1: weight gradient (split over pixels), then the data gradient of the layer below
   const bf16* dyl = (const bf16*)t.dy3;
   for (int l = 3; l >= 1; --l) {
@@ -851,14 +873,14 @@ cudaError_t cnn_tc_backward(int B, const CnnTc& t, const float* dh, const CnnGra
     else
       TC_TRY((gemm<32, 2, false, false>(A, Bw, EpiDx<32>{dyo, (const bf16*)t.act[l - 1], t.colpart, lwo, H, rows}, rows,
                                      9 * N, 1, 4, 1 << 30, any, st)));
-    TC_TRY(colreduce(t.colpart, 4 * ((rows + kBM - 1) / kBM), C, C, g.b[l - 1], t.part, st));
+    TC_TRY(colreduce(t.colpart, 4 * ((rows + kBM - 1) / kBM), C, C, g.b[l - 1], t.part, t.tickets, st));
     dyl = dyo;
   }
   // the first convolution's weight gradient on the SIMT pipes
   const int G = kConv0Ctas;
   k_conv0_dw<<<G, 256, 0, st>>>(dyl, (const bf16*)t.imgb, B * 4096, t.colpart);
   note_launches(1);
-  TC_TRY(colreduce(t.colpart, G, 288, 288, g.w[0], t.part, st));
+  TC_TRY(colreduce(t.colpart, G, 288, 288, g.w[0], t.part, t.tickets, st));
   return cudaGetLastError();
 }
 

@@ -145,6 +145,7 @@ struct CnnTc {
   uint16_t *imgb, *act[3], *feat, *dy[2], *dy3, *dhb, *wb[4], *w1b, *wt[4];
   float *part, *colpart;
   long long part_floats, colpart_floats;
+  unsigned* tickets;  // counters of the single-launch column reductions (zeroed by cnn_tc_backward)
 };
 // Bytes of the buffers for batch B (base == nullptr: size only), 256-byte aligned.
 size_t cnn_tc_layout(void* base, int B, CnnTc* t);
