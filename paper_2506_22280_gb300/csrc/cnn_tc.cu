@@ -488,10 +488,11 @@ __global__ void __launch_bounds__(kThr, BN == 32 ? 5 : (BN == 64 ? (kStages == 2
 // ---- SIMT kernels and small steps --------------------------------------------------------------------
 
 // First convolution (1 -> 32 channels, 128^2 -> 64^2): act0[p][co] = relu(b[co] + sum over taps of
-// r(w[co][tap]) img(tap)), r = BF16 rounding, img the BF16-rounded input; one thread per output pixel,
-// 32 channels stored as four 16-byte BF16 chunks.
-__global__ void __launch_bounds__(256) k_conv0_fwd(const bf16* __restrict__ img, const float* __restrict__ w,
-                                                   const float* __restrict__ bias, int npix, bf16* __restrict__ out) {
+// r(w[co][tap]) r(img(tap))), r = BF16 rounding, img the FP32 input; one thread per output pixel, 32
+// channels stored as four 16-byte BF16 chunks; the rounded input is also stored (imgb) for the backward.
+__global__ void __launch_bounds__(256) k_conv0_fwd(const float* __restrict__ img, const float* __restrict__ w,
+                                                   const float* __restrict__ bias, int npix, bf16* __restrict__ out,
+                                                   bf16* __restrict__ imgb) {
   __shared__ float sw[32 * 9], sb[32];
   for (int i = threadIdx.x; i < 32 * 9; i += blockDim.x) sw[i] = bf16r(w[i]);
   if (threadIdx.x < 32) sb[threadIdx.x] = bias[threadIdx.x];
@@ -503,8 +504,14 @@ __global__ void __launch_bounds__(256) k_conv0_fwd(const bf16* __restrict__ img,
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
     const int iy = 2 * y + t / 3 - 1, ix = 2 * x + t % 3 - 1;
-    xin[t] = (iy >= 0 && iy < 128 && ix >= 0 && ix < 128) ? __bfloat162float(img[((size_t)b * 128 + iy) * 128 + ix])
-                                                           : 0.f;
+    xin[t] = (iy >= 0 && iy < 128 && ix >= 0 && ix < 128) ? bf16r(img[((size_t)b * 128 + iy) * 128 + ix]) : 0.f;
+  }
+  // the BF16 input the weight gradient reads: this pixel writes input pixels (2y + dy, 2x + dx), dy, dx in
+  // {0, 1} (its taps 4, 5, 7, 8), so every input pixel is written exactly once
+  {
+    uint32_t* row0 = reinterpret_cast<uint32_t*>(imgb + ((size_t)b * 128 + 2 * y) * 128 + 2 * x);
+    row0[0] = pack2(xin[4], xin[5]);
+    row0[64] = pack2(xin[7], xin[8]);  // the next row: 128 BF16 = 64 words further
   }
   uint4* d = reinterpret_cast<uint4*>(out + (size_t)p * 32);
 #pragma unroll
@@ -633,7 +640,7 @@ __global__ void __launch_bounds__(256) k_sum_z(const float* __restrict__ part, i
   }
 }
 
-// All of a forward's BF16 conversions in one launch: job k covers the elements [start[k], start[k + 1])
+// All of a forward's weight conversions to BF16 in one launch: job k covers the elements [start[k], start[k + 1])
 // of a grid-stride loop.  Kind 0, rows: out[r][c] = BF16 of in[r][c] for c < b, 0 for b <= c < c_pitch
 // (a rows, row pitch c).  Kind 1, the class-ordered transposed weights of a convolution with N = a output
 // and C = b input channels: out[class block z][ci][(t, co)] = BF16 of w[co][ky_t][kx_t][ci] for the
@@ -778,8 +785,8 @@ size_t cnn_tc_layout(void* base, int B, CnnTc* t) {
 
 cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs, int B, const CnnTc& t, float* h,
                            cudaStream_t st) {
-  // BF16 copies of the weights, row-major (forward) and class-ordered transposed (data gradient), and of
-  // the input images: one launch
+  // BF16 copies of the weights, row-major (forward) and class-ordered transposed (data gradient): one
+  // launch (the first convolution rounds the input images itself and stores their BF16 copy)
   BfJobs J{};
   long long at = 0;
   auto add = [&](const float* in, bf16* out, int kind, int a, int b, int c, long long n) {
@@ -793,11 +800,10 @@ cudaError_t cnn_tc_forward(const CnnNet& net, const float* img, const float* cs,
     add(net.w[l], (bf16*)t.wt[l], 1, N, kCh[l], 0, (long long)N * Kl);
   }
   add(net.w1, (bf16*)t.w1b, 0, kHid, kFeat + 2, kFeatPitch, (long long)kHid * kFeatPitch);
-  add(img, (bf16*)t.imgb, 2, 0, 0, 0, (long long)B * 16384);
   J.start[J.count] = at;
   k_to_bf16_jobs<<<grid_of(at), 256, 0, st>>>(J);
   const int npix0 = B * 4096;
-  k_conv0_fwd<<<(npix0 + 255) / 256, 256, 0, st>>>((const bf16*)t.imgb, net.w[0], net.b[0], npix0, (bf16*)t.act[0]);
+  k_conv0_fwd<<<(npix0 + 255) / 256, 256, 0, st>>>(img, net.w[0], net.b[0], npix0, (bf16*)t.act[0], (bf16*)t.imgb);
   note_launches(2);
   const void* any = t.wb[1];
   for (int l = 1; l < 4; ++l) {
